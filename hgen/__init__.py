@@ -1,0 +1,182 @@
+"""Seeded synthetic hypergraph generator (shared input of the oracle and the CUDA path).
+
+This package holds no part of the counting method: it draws hyperedges and
+returns a hyperedge->vertex CSR (``e_ptr`` int64 [|E|+1], ``e_idx`` int32 [nnz],
+rows sorted ascending, no repeated vertex inside a hyperedge, no two equal
+hyperedges).  The native part is ``gen.c``; ``build()`` compiles it with plain
+gcc and ``-ffp-contract=off`` so that x86-64 and AArch64 produce byte-identical
+output.
+
+The workloads below are shaped after the paper's data (Table 3: co-authorship,
+tags, email ...).  Their recipe, one per named workload, is:
+
+* ``tiny_plain``  |V|=1,000  |E|=2,000  sizes U{2..6}           Zipf(1.1) seed 0
+* ``coauthor``    |V|=1e5    |E|=5e5    sizes power law 2.5 [2,25] Zipf(1.0) seed 1, vertex degree cap 100
+* ``tag_heavy``   |V|=2e4    |E|=2e6    sizes log-normal(1.5,1.0) [2,200] Zipf(1.2) seed 2, degree cap 1000
+* ``batched(s)``  |E| log-uniform [100, 2e5], |V|=|E|/4, power law 2.2 [2,50], Zipf(1.0), seed s, cap 100
+* ``served(m)``   |E| log-uniform [1e3, 1e6], |V|=|E|/5, otherwise as ``coauthor``, seed 5000+m
+
+The degree cap withdraws a vertex from later draws once it is in that many
+hyperedges; without it the Zipf head puts a single vertex in ~8% of all
+hyperedges and the exact count needs >1e14 classified triples.
+"""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+import os
+import subprocess
+from dataclasses import dataclass, replace
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gen.c")
+_LIB = os.path.join(_HERE, "libhgen.so")
+
+SIZE_UNIFORM, SIZE_POWERLAW, SIZE_LOGNORMAL = 0, 1, 2
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [
+        ("num_vertices", ctypes.c_int64),
+        ("num_edges", ctypes.c_int64),
+        ("seed", ctypes.c_uint64),
+        ("size_dist", ctypes.c_int32),
+        ("size_lo", ctypes.c_int32),
+        ("size_hi", ctypes.c_int32),
+        ("degree_cap", ctypes.c_int32),
+        ("size_p1", ctypes.c_double),
+        ("size_p2", ctypes.c_double),
+        ("zipf_s", ctypes.c_double),
+        ("dedup", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+@dataclass(frozen=True)
+class HypergraphSpec:
+    """Parameters of one synthetic hypergraph."""
+
+    num_vertices: int
+    num_edges: int
+    seed: int
+    size_dist: int = SIZE_UNIFORM
+    size_lo: int = 2
+    size_hi: int = 6
+    size_p1: float = 0.0
+    size_p2: float = 0.0
+    zipf_s: float = 1.0
+    degree_cap: int = 0
+    dedup: bool = True
+    name: str = "custom"
+
+    def _c(self) -> _Params:
+        return _Params(
+            int(self.num_vertices), int(self.num_edges), int(self.seed) & (2**64 - 1),
+            int(self.size_dist), int(self.size_lo), int(min(self.size_hi, self.num_vertices)),
+            int(self.degree_cap), float(self.size_p1), float(self.size_p2), float(self.zipf_s),
+            1 if self.dedup else 0, 0,
+        )
+
+
+def build(force: bool = False) -> str:
+    """Compile gen.c into libhgen.so next to it (plain gcc, no FMA contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        lib.hgen_sizes.argtypes = [ctypes.POINTER(_Params), ctypes.c_void_p]
+        lib.hgen_sizes.restype = ctypes.c_int
+        lib.hgen_fill.argtypes = [ctypes.POINTER(_Params), ctypes.c_void_p, ctypes.c_void_p,
+                                  ctypes.c_void_p]
+        lib.hgen_fill.restype = ctypes.c_int
+        lib.hgen_loguniform_int.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                            ctypes.c_int64]
+        lib.hgen_loguniform_int.restype = ctypes.c_int64
+        lib.hgen_det_log.argtypes = [ctypes.c_double]
+        lib.hgen_det_log.restype = ctypes.c_double
+        lib.hgen_det_exp.argtypes = [ctypes.c_double]
+        lib.hgen_det_exp.restype = ctypes.c_double
+        _lib = lib
+    return _lib
+
+
+_ERRORS = {-1: "bad argument", -2: "out of memory", -3: "not enough available vertices",
+           -4: "could not draw a fresh hyperedge"}
+
+
+def generate(spec: HypergraphSpec) -> tuple[np.ndarray, np.ndarray]:
+    """Return (e_ptr int64[|E|+1], e_idx int32[nnz]) for the spec."""
+    lib = _load()
+    p = spec._c()
+    sizes = np.empty(spec.num_edges, dtype=np.int32)
+    rc = lib.hgen_sizes(ctypes.byref(p), sizes.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"hgen_sizes: {_ERRORS.get(rc, rc)}")
+    e_ptr = np.zeros(spec.num_edges + 1, dtype=np.int64)
+    np.cumsum(sizes, out=e_ptr[1:])
+    e_idx = np.empty(int(e_ptr[-1]), dtype=np.int32)
+    rc = lib.hgen_fill(ctypes.byref(p), sizes.ctypes.data, e_ptr.ctypes.data, e_idx.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"hgen_fill: {_ERRORS.get(rc, rc)}")
+    return e_ptr, e_idx
+
+
+def loguniform_int(seed: int, tag: int, lo: int, hi: int) -> int:
+    return int(_load().hgen_loguniform_int(seed & (2**64 - 1), tag, lo, hi))
+
+
+def csr_hash(e_ptr: np.ndarray, e_idx: np.ndarray) -> str:
+    """Content hash of a CSR (little-endian int64 offsets then int32 ids)."""
+    h = hashlib.blake2b(digest_size=16)
+    h.update(np.ascontiguousarray(e_ptr, dtype="<i8").tobytes())
+    h.update(np.ascontiguousarray(e_idx, dtype="<i4").tobytes())
+    return h.hexdigest()
+
+
+def prefix(e_ptr: np.ndarray, e_idx: np.ndarray, num_edges: int) -> tuple[np.ndarray, np.ndarray]:
+    """The sub-hypergraph made of the first `num_edges` hyperedges of a CSR."""
+    p = np.ascontiguousarray(e_ptr[: num_edges + 1])
+    return p, np.ascontiguousarray(e_idx[: int(p[-1])])
+
+
+# ---------------------------------------------------------------- named workloads
+
+TINY_PLAIN = HypergraphSpec(1000, 2000, 0, SIZE_UNIFORM, 2, 6, zipf_s=1.1, name="tiny_plain")
+COAUTHOR = HypergraphSpec(100_000, 500_000, 1, SIZE_POWERLAW, 2, 25, size_p1=2.5, zipf_s=1.0,
+                          degree_cap=100, name="coauthor")
+TAG_HEAVY = HypergraphSpec(20_000, 2_000_000, 2, SIZE_LOGNORMAL, 2, 200, size_p1=1.5,
+                           size_p2=1.0, zipf_s=1.2, degree_cap=1000, name="tag_heavy")
+
+
+def batched(seed: int) -> HypergraphSpec:
+    """One member of the 4,096-hypergraph batch (seeds 100..4195)."""
+    ne = loguniform_int(seed, 0, 100, 200_000)
+    nv = max(ne // 4, 2)
+    return HypergraphSpec(nv, ne, seed, SIZE_POWERLAW, 2, 50, size_p1=2.2, zipf_s=1.0,
+                          degree_cap=100, name=f"batched_{seed}")
+
+
+def served(member: int) -> HypergraphSpec:
+    """One of the 64 resident hypergraphs of the serving workload."""
+    seed = 5000 + member
+    ne = loguniform_int(seed, 0, 1000, 1_000_000)
+    return replace(COAUTHOR, num_vertices=max(ne // 5, 2), num_edges=ne, seed=seed,
+                   name=f"served_{member}")
+
+
+WORKLOADS = {"tiny_plain": TINY_PLAIN, "coauthor": COAUTHOR, "tag_heavy": TAG_HEAVY}

@@ -1,0 +1,358 @@
+// Oracle: a plain, slow, obviously correct CPU restatement of exact
+// hyper-triangle counting (Yin et al., "Efficient Computation of
+// Hyper-triangles on Hypergraphs", PVLDB 18(3)).
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or call
+// this file: only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg
+// use it.  It shares no code, table or header with the CUDA library.
+//
+// What it computes (all exact integers):
+//   * per-pattern hyper-triangle counts H[1..20] and the total T (Def. 2.4);
+//   * hyperwedge statistics: W = |wedges|, W_t (intersection type), W_c
+//     (inclusion type) (Def. 2.2, Def. 2.3);
+//   * connected triples sum_i C(|N(e_i)|, 2) and open hyper-triangles (Def. 5.1).
+//
+// Two enumerations:
+//   * mode 0 follows Exact-bs (Algorithm 1): build the projection graph
+//     N(e_i) = { e_j : e_i and e_j share a vertex } (Sec. 2), then for every
+//     e_i and every pair {e_j, e_k} of its neighbours with i < min(j, k), test
+//     e_j and e_k for a common vertex and classify the triple.  Only the pairs
+//     with j, k > i are visited, which is the same set Algorithm 1 keeps after
+//     its i < min{j,k} test.
+//   * mode 1 is brute force over all C(|E|, 3) triples (tiny inputs only).
+//
+// Classification (Def. 2.4): a triple {e_i, e_j, e_k} has seven Venn regions
+//   (a) e_i only  (b) e_j only  (c) e_k only  (d) e_i and e_j, not e_k
+//   (e) e_j and e_k, not e_i  (f) e_k and e_i, not e_j  (g) all three.
+// The pattern is decided by which regions are non-empty, up to relabelling
+// the three hyperedges.  The paper's pattern figure is not available, so the
+// numbering below is a reading of the text: pattern 1 is the CCC class, 2-5
+// TCC, 6-8 TTC, 9-20 TTT (Sec. 2), 9-16 have region (g) non-empty and 17-20
+// have it empty (Sec. 3.2).  Inside each class the numbers are fixed by the
+// O(1) rules of Algorithm 5 (patterns 1-8) and by the case study of Sec. 6.2
+// (co-authorship triangles of patterns 10 and 12, e-mail triangles of
+// pattern 5); the order of 9, 11 and 13-20 is parity unpinned (the paper
+// shows them only in a figure): ascending number of non-empty pairwise
+// regions (d, e, f), then ascending number of non-empty single regions.
+#include <algorithm>
+#include <chrono>
+#include <cstdint>
+#include <cstring>
+#include <set>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// Region letters of each pattern in one labelling of (e_i, e_j, e_k).
+const char* const kPatternRegions[20] = {
+    "adg",      // 1  CCC: chain e_k inside e_j inside e_i
+    "abg",      // 2  TCC: e_k equal to e_i cap e_j
+    "abdg",     // 3  TCC: e_k strictly inside e_i cap e_j
+    "deg",      // 4  TCC: e_j equal to e_i cup e_k
+    "bdeg",     // 5  TCC: e_j strictly contains e_i cup e_k
+    "acdg",     // 6  TTC
+    "adeg",     // 7  TTC
+    "abdeg",    // 8  TTC
+    "abcg",     // 9  DenseTTT
+    "abcdg",    // 10 DenseTTT
+    "acdeg",    // 11 DenseTTT
+    "abcdeg",   // 12 DenseTTT
+    "defg",     // 13 DenseTTT
+    "adefg",    // 14 DenseTTT
+    "abdefg",   // 15 DenseTTT
+    "abcdefg",  // 16 DenseTTT
+    "def",      // 17 SparseTTT
+    "adef",     // 18 SparseTTT
+    "abdef",    // 19 SparseTTT
+    "abcdef",   // 20 SparseTTT
+};
+
+// Which of the three sets (i, j, k) contain each region a..g.
+const int kRegionIn[7][3] = {
+    {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {0, 1, 1}, {1, 0, 1}, {1, 1, 1}};
+
+int region_of(int in_i, int in_j, int in_k) {
+  for (int r = 0; r < 7; ++r)
+    if (kRegionIn[r][0] == in_i && kRegionIn[r][1] == in_j && kRegionIn[r][2] == in_k) return r;
+  return -1;
+}
+
+// Relabel a region bit mask: set number s of the new labelling is set perm[s] of the old.
+int relabel(int mask, const int perm[3]) {
+  int out = 0;
+  for (int r = 0; r < 7; ++r) {
+    if (!(mask >> r & 1)) continue;
+    int in_new[3];
+    for (int s = 0; s < 3; ++s) in_new[s] = kRegionIn[r][perm[s]];
+    out |= 1 << region_of(in_new[0], in_new[1], in_new[2]);
+  }
+  return out;
+}
+
+// mask -> pattern number (0 = not a pattern), built once from kPatternRegions
+struct PatternMap {
+  int of_mask[128];
+  int conflict;
+  PatternMap() : conflict(0) {
+    std::memset(of_mask, 0, sizeof(of_mask));
+    const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    for (int p = 0; p < 20; ++p) {
+      int m = 0;
+      for (const char* c = kPatternRegions[p]; *c; ++c) m |= 1 << (*c - 'a');
+      for (const auto& pr : perms) {
+        int lm = relabel(m, pr);
+        if (of_mask[lm] != 0 && of_mask[lm] != p + 1) conflict = 1;
+        of_mask[lm] = p + 1;
+      }
+    }
+  }
+};
+const PatternMap& pattern_map() {
+  static PatternMap pm;
+  return pm;
+}
+
+using VSet = std::set<int32_t>;
+
+// Seven-region non-emptiness mask of (A, B, C), written from the definitions.
+int region_mask(const VSet& A, const VSet& B, const VSet& C) {
+  int mask = 0;
+  for (int32_t x : A) mask |= 1 << region_of(1, B.count(x) ? 1 : 0, C.count(x) ? 1 : 0);
+  for (int32_t x : B)
+    if (!A.count(x)) mask |= 1 << region_of(0, 1, C.count(x) ? 1 : 0);
+  for (int32_t x : C)
+    if (!A.count(x) && !B.count(x)) mask |= 1 << region_of(0, 0, 1);
+  return mask;
+}
+
+bool intersects(const VSet& A, const VSet& B) {
+  for (int32_t x : A)
+    if (B.count(x)) return true;
+  return false;
+}
+
+size_t common(const VSet& A, const VSet& B) {
+  size_t n = 0;
+  for (int32_t x : A) n += B.count(x);
+  return n;
+}
+
+struct Graph {
+  int32_t nv = 0, ne = 0;
+  std::vector<VSet> e;                      // hyperedge vertex sets
+  std::vector<std::vector<int32_t>> Ev;     // E_v: hyperedges containing v, ascending
+};
+
+int load(Graph& g, int32_t nv, int32_t ne, const int64_t* e_ptr, const int32_t* e_idx) {
+  g.nv = nv;
+  g.ne = ne;
+  g.e.assign(ne, VSet());
+  g.Ev.assign(nv, {});
+  for (int32_t i = 0; i < ne; ++i) {
+    if (e_ptr[i + 1] <= e_ptr[i]) return -2;                  // empty hyperedge
+    for (int64_t p = e_ptr[i]; p < e_ptr[i + 1]; ++p) {
+      int32_t v = e_idx[p];
+      if (v < 0 || v >= nv) return -3;
+      if (!g.e[i].insert(v).second) return -4;                 // repeated vertex
+      g.Ev[v].push_back(i);
+    }
+  }
+  return 0;
+}
+
+// N(e_i) as an ascending vector, from the union of E_v over v in e_i.
+std::vector<int32_t> neighbours(const Graph& g, int32_t i) {
+  std::set<int32_t> n;
+  for (int32_t v : g.e[i])
+    for (int32_t j : g.Ev[v])
+      if (j != i) n.insert(j);
+  return std::vector<int32_t>(n.begin(), n.end());
+}
+
+bool adjacent(const std::vector<std::vector<int32_t>>& N, int32_t j, int32_t k) {
+  return std::binary_search(N[j].begin(), N[j].end(), k);
+}
+
+}  // namespace
+
+extern "C" {
+
+// stats layout
+enum { ST_W = 0, ST_WT, ST_WC, ST_CONNECTED, ST_OPEN, ST_MAXDEG, ST_T, ST_DUP, ST_N };
+
+int oracle_pattern_table_ok() { return pattern_map().conflict ? 0 : 1; }
+
+// Pattern number (1..20) of one labelled region mask; 0 if none.
+int oracle_pattern_of_mask(int mask) {
+  if (mask < 0 || mask > 127) return 0;
+  return pattern_map().of_mask[mask];
+}
+
+// Region mask of three explicit vertex lists.
+int oracle_region_mask(const int32_t* a, int na, const int32_t* b, int nb, const int32_t* c,
+                       int nc) {
+  VSet A(a, a + na), B(b, b + nb), C(c, c + nc);
+  return region_mask(A, B, C);
+}
+
+// Pattern of three explicit vertex lists: 1..20; 0 if not a hyper-triangle;
+// -1 if two of the sets are equal (the paper assumes distinct hyperedges).
+int oracle_classify(const int32_t* a, int na, const int32_t* b, int nb, const int32_t* c,
+                    int nc) {
+  VSet A(a, a + na), B(b, b + nb), C(c, c + nc);
+  if (A == B || B == C || A == C) return -1;
+  if (!intersects(A, B) || !intersects(B, C) || !intersects(A, C)) return 0;
+  return pattern_map().of_mask[region_mask(A, B, C)];
+}
+
+// Exact counts.  mode 0: Exact-bs shaped; mode 1: all triples.
+// Only triangles whose smallest hyperedge id lies in [i_lo, i_hi) are counted
+// (pass 0, ne for the whole graph); wedge statistics always cover the needed part.
+// counts[21]: [0] = T, [p] = H[p].  stats[ST_N] as in the enum above.
+// Returns 0, or a negative input error (-2 empty hyperedge, -3 vertex out of
+// range, -4 repeated vertex, -5 duplicate hyperedge, -6 bad argument,
+// -7 pattern table inconsistent, -8 unclassifiable triple).
+int oracle_count(int32_t nv, int32_t ne, const int64_t* e_ptr, const int32_t* e_idx, int mode,
+                 int nthreads, int32_t i_lo, int32_t i_hi, uint64_t* counts, uint64_t* stats,
+                 double* seconds) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!counts || !stats || nv < 0 || ne < 0 || i_lo < 0 || i_hi > ne || i_lo > i_hi) return -6;
+  if (!oracle_pattern_table_ok()) return -7;
+  std::memset(counts, 0, sizeof(uint64_t) * 21);
+  std::memset(stats, 0, sizeof(uint64_t) * ST_N);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+  Graph g;
+  int rc = load(g, nv, ne, e_ptr, e_idx);
+  if (rc) return rc;
+  const auto& pm = pattern_map();
+  int bad = 0;
+
+  if (mode == 1) {
+    // brute force: every unordered triple of distinct hyperedges
+    uint64_t H[21] = {0};
+    uint64_t open = 0, connected = 0, W = 0, Wc = 0;
+    uint64_t maxdeg = 0;
+    for (int32_t i = 0; i < ne; ++i) {
+      uint64_t deg = 0;
+      for (int32_t j = 0; j < ne; ++j) {
+        if (j == i || !intersects(g.e[i], g.e[j])) continue;
+        ++deg;
+        if (g.e[i] == g.e[j]) return -5;
+        if (j > i) {
+          ++W;
+          size_t w = common(g.e[i], g.e[j]);
+          if (w == std::min(g.e[i].size(), g.e[j].size())) ++Wc;
+        }
+      }
+      maxdeg = std::max(maxdeg, deg);
+      connected += deg * (deg - (deg ? 1 : 0)) / 2;
+    }
+    for (int32_t i = i_lo; i < i_hi; ++i)
+      for (int32_t j = i + 1; j < ne; ++j)
+        for (int32_t k = j + 1; k < ne; ++k) {
+          int ij = intersects(g.e[i], g.e[j]), jk = intersects(g.e[j], g.e[k]),
+              ik = intersects(g.e[i], g.e[k]);
+          int n = ij + jk + ik;
+          if (n == 2) ++open;
+          if (n != 3) continue;
+          int p = pm.of_mask[region_mask(g.e[i], g.e[j], g.e[k])];
+          if (p == 0) { bad = 1; continue; }
+          ++H[p];
+        }
+    for (int p = 1; p <= 20; ++p) { counts[p] = H[p]; counts[0] += H[p]; }
+    stats[ST_W] = W; stats[ST_WC] = Wc; stats[ST_WT] = W - Wc;
+    stats[ST_CONNECTED] = connected; stats[ST_OPEN] = open; stats[ST_MAXDEG] = maxdeg;
+    stats[ST_T] = counts[0];
+    if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return bad ? -8 : 0;
+  }
+  if (mode != 0) return -6;
+
+  // Projection graph (Sec. 2 / Algorithm 1): N(e_x) for every hyperedge that the
+  // requested range needs: the range itself and the larger-id neighbours of it.
+  const bool whole = (i_lo == 0 && i_hi == ne);
+  std::vector<std::vector<int32_t>> N(ne);
+  std::vector<char> need(ne, whole ? 1 : 0);
+  if (!whole) {
+    for (int32_t i = i_lo; i < i_hi; ++i) {
+      need[i] = 1;
+      for (int32_t v : g.e[i])
+        for (int32_t j : g.Ev[v])
+          if (j > i) need[j] = 1;
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int32_t x = 0; x < ne; ++x)
+    if (need[x]) N[x] = neighbours(g, x);
+
+  uint64_t W = 0, Wc = 0, connected = 0, maxdeg = 0;
+  int dup = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : W, Wc, connected) reduction(max : maxdeg) reduction(| : dup)
+  for (int32_t x = 0; x < ne; ++x) {
+    if (!need[x]) continue;
+    uint64_t d = N[x].size();
+    connected += d * (d - (d ? 1 : 0)) / 2;
+    maxdeg = std::max(maxdeg, d);
+    for (int32_t y : N[x]) {
+      if (y < x) continue;
+      ++W;
+      size_t w = common(g.e[x], g.e[y]);                      // omega_xy (Def. 2.2)
+      if (w == g.e[x].size() && w == g.e[y].size()) dup = 1;   // equal hyperedges
+      if (w == std::min(g.e[x].size(), g.e[y].size())) ++Wc;  // inclusion type (Def. 2.3)
+    }
+  }
+  if (dup) return -5;
+
+  int nth = 1;
+#ifdef _OPENMP
+  nth = omp_get_max_threads();
+#endif
+  std::vector<uint64_t> Hs((size_t)nth * 21, 0);
+#pragma omp parallel
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    uint64_t* H = &Hs[(size_t)tid * 21];
+#pragma omp for schedule(dynamic, 64) reduction(| : bad)
+    for (int32_t i = i_lo; i < i_hi; ++i) {
+      const auto& Ni = N[i];
+      for (size_t a = 0; a < Ni.size(); ++a) {
+        int32_t j = Ni[a];
+        if (j <= i) continue;
+        for (size_t b = a + 1; b < Ni.size(); ++b) {
+          int32_t k = Ni[b];                                     // i < j < k
+          if (!adjacent(N, j, k)) continue;                      // e_j cap e_k empty
+          int p = pm.of_mask[region_mask(g.e[i], g.e[j], g.e[k])];
+          if (p == 0) { bad = 1; continue; }
+          ++H[p];
+        }
+      }
+    }
+  }
+  for (int t = 0; t < nth; ++t)
+    for (int p = 1; p <= 20; ++p) counts[p] += Hs[(size_t)t * 21 + p];
+  for (int p = 1; p <= 20; ++p) counts[0] += counts[p];
+  stats[ST_W] = W; stats[ST_WC] = Wc; stats[ST_WT] = W - Wc;
+  stats[ST_CONNECTED] = connected; stats[ST_MAXDEG] = maxdeg; stats[ST_T] = counts[0];
+  // every closed triple is counted three times in sum C(deg, 2), every open one once
+  stats[ST_OPEN] = whole ? connected - 3 * counts[0] : 0;
+  if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return bad ? -8 : 0;
+}
+
+int oracle_max_threads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+}  // extern "C"

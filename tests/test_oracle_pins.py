@@ -1,0 +1,340 @@
+"""Pins of the oracle to things other than itself: the paper's worked examples,
+Algorithm 5's O(1) rules, closed forms, brute force and invariants.  CPU only."""
+import itertools
+import math
+import random
+
+import numpy as np
+import pytest
+
+from conftest import csr_of, load_json
+
+
+@pytest.fixture(scope="module")
+def orc(native_cpu):
+    import oracle
+
+    return oracle
+
+
+# ---------------------------------------------------------------- helpers written from Sec. 2
+
+def pairwise_connected(a, b, c):
+    return bool(a & b) and bool(b & c) and bool(a & c)
+
+
+def is_inclusion(x, y):
+    """Def. 2.3: the hyperwedge is of the inclusion type iff one set is inside the other."""
+    return x <= y or y <= x
+
+
+def alg5_pattern(ei, ej, ek):
+    """Patterns 1-8 from the O(1) tests of Algorithm 5 (Sec. 3.3), None for class TTT.
+
+    omega_xy = |e_x cap e_y| (Def. 2.2).  Written from the text of Sec. 3.3:
+    CCC: a chain of inclusions -> 1.  TCC: e_k inside both members of the
+    intersection-type wedge (i, j): 3 if omega_ij > |e_k| else 2; e_k containing
+    both: 4 if omega_ki + omega_kj - omega_ij = |e_k| else 5.  TTC: inclusion
+    wedge (i, j) with e_i the larger: 6 if omega_ik = omega_jk, else 7 if
+    omega_ij + omega_ik - omega_jk = |e_i|, else 8.
+    """
+    S = [set(ei), set(ej), set(ek)]
+    w = lambda x, y: len(S[x] & S[y])  # noqa: E731
+    pairs = [(0, 1, 2), (1, 2, 0), (0, 2, 1)]
+    inc = [p for p in pairs if is_inclusion(S[p[0]], S[p[1]])]
+    if len(inc) == 3:
+        return 1
+    if len(inc) == 2:
+        i, j, k = next(p for p in pairs if p not in inc)
+        if S[k] <= S[i] and S[k] <= S[j]:
+            return 3 if w(i, j) > len(S[k]) else 2
+        return 4 if w(k, i) + w(k, j) - w(i, j) == len(S[k]) else 5
+    if len(inc) == 1:
+        x, y, k = inc[0]
+        i, j = (x, y) if len(S[x]) > len(S[y]) else (y, x)
+        if w(i, k) == w(j, k):
+            return 6
+        return 7 if w(i, j) + w(i, k) - w(j, k) == len(S[i]) else 8
+    return None
+
+
+def random_triangles(n, universe, max_size, seed):
+    rnd = random.Random(seed)
+    out = []
+    while len(out) < n:
+        t = [set(rnd.sample(range(universe), rnd.randint(1, max_size))) for _ in range(3)]
+        if t[0] != t[1] and t[1] != t[2] and t[0] != t[2] and pairwise_connected(*t):
+            out.append(t)
+    return out
+
+
+def brute_force_py(edges):
+    """All triples with Python sets: (T, open, connected, W, W_c)."""
+    E = [set(e) for e in edges]
+    n = len(E)
+    adj = [[bool(E[i] & E[j]) and i != j for j in range(n)] for i in range(n)]
+    T = op = 0
+    for i, j, k in itertools.combinations(range(n), 3):
+        c = adj[i][j] + adj[j][k] + adj[i][k]
+        T += c == 3
+        op += c == 2
+    deg = [sum(r) for r in adj]
+    W = sum(deg) // 2
+    Wc = sum(1 for i, j in itertools.combinations(range(n), 2) if adj[i][j] and is_inclusion(E[i], E[j]))
+    return T, op, sum(d * (d - 1) // 2 for d in deg), W, Wc
+
+
+def line_graph_adjacency(e_ptr, e_idx, nv):
+    ne = len(e_ptr) - 1
+    H = np.zeros((ne, nv), dtype=np.int64)
+    for i in range(ne):
+        H[i, e_idx[e_ptr[i]:e_ptr[i + 1]]] = 1
+    A = (H @ H.T > 0).astype(np.int64)
+    np.fill_diagonal(A, 0)
+    return A
+
+
+# ---------------------------------------------------------------- pattern table
+
+def test_pattern_table_consistent(orc):
+    assert orc.table_ok()
+    seen = {orc.pattern_of_mask(m) for m in range(128)}
+    assert seen == set(range(0, 21))
+
+
+def test_pattern_table_covers_exactly_the_hyper_triangles(orc):
+    # a labelled mask is a hyper-triangle of distinct hyperedges iff the pattern is non-zero
+    regions = {"a": (1, 0, 0), "b": (0, 1, 0), "c": (0, 0, 1), "d": (1, 1, 0), "e": (0, 1, 1),
+               "f": (1, 0, 1), "g": (1, 1, 1)}
+    for m in range(128):
+        sets = [set(), set(), set()]
+        for r, (name, inn) in enumerate(regions.items()):
+            if m >> r & 1:
+                for s in range(3):
+                    if inn[s]:
+                        sets[s].add(name)
+        valid = pairwise_connected(*sets) and len({frozenset(s) for s in sets}) == 3
+        assert (orc.pattern_of_mask(m) != 0) == valid, m
+
+
+# ---------------------------------------------------------------- the paper's examples
+
+def test_email_example_printed_triangles(orc):
+    d = load_json("paper_examples.json")["email"]
+    E = d["hyperedges"]
+    for (i, j, k), p in d["printed_triangles"]:
+        assert orc.classify(E[i - 1], E[j - 1], E[k - 1]) == p
+
+
+def test_email_example_census(orc):
+    d = load_json("paper_examples.json")["email"]
+    E = d["hyperedges"]
+    e_ptr, e_idx = csr_of(E)
+    r = orc.count(e_ptr, e_idx, 200)
+    b = orc.count(e_ptr, e_idx, 200, mode="brute")
+    assert r.counts.tolist() == b.counts.tolist()
+    # the three printed triangles are all the triangles of this hypergraph
+    assert r.T == len(d["printed_triangles"]) == r.H(5)
+    T, op, con, W, Wc = brute_force_py(E)
+    assert (r.T, r.open, r.connected, r.W, r.W_c) == (T, op, con, W, Wc)
+
+
+def test_coauthor_example_printed_triangles(orc):
+    d = load_json("paper_examples.json")["coauthorship"]
+    E = d["hyperedges"]
+    for (i, j, k), p in d["printed_triangles"]:
+        assert orc.classify(E[i - 1], E[j - 1], E[k - 1]) == p
+
+
+def test_coauthor_example_census(orc):
+    d = load_json("paper_examples.json")["coauthorship"]
+    E = d["hyperedges"]
+    e_ptr, e_idx = csr_of(E)
+    r = orc.count(e_ptr, e_idx, 20)
+    T, op, con, W, Wc = brute_force_py(E)
+    assert (r.T, r.open, r.W, r.W_c) == (T, op, W, Wc)
+    # every triangle is classified like the printed ones: patterns 10 and 12 only
+    assert r.H(10) + r.H(12) == r.T
+
+
+# ---------------------------------------------------------------- Algorithm 5 and classes
+
+@pytest.mark.parametrize("seed", range(4))
+def test_algorithm5_rules_pin_patterns_1_to_8(orc, seed):
+    hits = 0
+    for t in random_triangles(3000, 9, 6, seed):
+        want = alg5_pattern(*t)
+        got = orc.classify(*t)
+        if want is None:
+            assert got >= 9
+        else:
+            hits += 1
+            assert got == want, (t, got, want)
+    assert hits > 100
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_class_membership(orc, seed):
+    import oracle
+
+    for t in random_triangles(2000, 12, 7, seed):
+        p = orc.classify(*t)
+        n_inc = sum(is_inclusion(x, y) for x, y in ((t[0], t[1]), (t[1], t[2]), (t[0], t[2])))
+        want = {3: "CCC", 2: "TCC", 1: "TTC", 0: "TTT"}[n_inc]
+        assert oracle.CLASS_OF_PATTERN[p] == want
+        if want == "TTT":  # Sec. 3.2: DenseTTT iff the three share a vertex
+            assert (p in oracle.DENSE_TTT) == bool(t[0] & t[1] & t[2])
+
+
+def test_all_twenty_patterns_occur(orc):
+    seen = set()
+    for t in random_triangles(20000, 10, 7, 11):
+        seen.add(orc.classify(*t))
+    assert seen == set(range(1, 21))
+
+
+# ---------------------------------------------------------------- closed forms
+
+def test_ordinary_graph_is_patterns_17_and_9(orc):
+    # every hyperedge of size 2: a triangle of the graph has regions d, e, f only
+    # (pattern 17); three edges at one vertex have a, b, c, g (pattern 9)
+    rnd = random.Random(5)
+    n = 40
+    edges = sorted({tuple(sorted(rnd.sample(range(n), 2))) for _ in range(250)})
+    A = np.zeros((n, n), dtype=np.int64)
+    for a, b in edges:
+        A[a, b] = A[b, a] = 1
+    tri = int(np.trace(A @ A @ A)) // 6
+    stars = sum(math.comb(int(d), 3) for d in A.sum(1))
+    e_ptr, e_idx = csr_of(edges)
+    r = orc.count(e_ptr, e_idx, n)
+    assert r.H(17) == tri and r.H(9) == stars and r.T == tri + stars
+
+
+def test_graph_with_private_vertices_is_pattern_20(orc):
+    # each edge {a,b} of a graph plus a private vertex: graph triangles have all of
+    # a..f and no g (pattern 20); stars stay pattern 9
+    rnd = random.Random(6)
+    n = 30
+    edges = sorted({tuple(sorted(rnd.sample(range(n), 2))) for _ in range(150)})
+    A = np.zeros((n, n), dtype=np.int64)
+    for a, b in edges:
+        A[a, b] = A[b, a] = 1
+    hyper = [[a, b, n + k] for k, (a, b) in enumerate(edges)]
+    e_ptr, e_idx = csr_of(hyper)
+    r = orc.count(e_ptr, e_idx, n + len(edges))
+    stars = sum(math.comb(int(d), 3) for d in A.sum(1))
+    assert r.H(20) == int(np.trace(A @ A @ A)) // 6 and r.H(9) == stars
+    assert r.T == r.H(20) + stars
+
+
+@pytest.mark.parametrize("n", [3, 7, 25])
+def test_sunflower_is_pattern_9(orc, n):
+    # n hyperedges sharing exactly vertex 0, disjoint petals: regions a, b, c, g
+    edges = [[0] + [1 + 3 * k, 2 + 3 * k] for k in range(n)]
+    e_ptr, e_idx = csr_of(edges)
+    r = orc.count(e_ptr, e_idx, 1 + 3 * n)
+    assert r.H(9) == math.comb(n, 3) == r.T
+
+
+@pytest.mark.parametrize("n", [3, 8, 20])
+def test_nested_chain_is_pattern_1(orc, n):
+    edges = [list(range(k + 1)) for k in range(n)]
+    e_ptr, e_idx = csr_of(edges)
+    r = orc.count(e_ptr, e_idx, n)
+    assert r.H(1) == math.comb(n, 3) == r.T
+    assert r.W_c == math.comb(n, 2) == r.W
+
+
+def test_hub_and_members_is_pattern_5(orc):
+    # one big hyperedge strictly containing pairwise-intersecting smaller ones (the
+    # organizer-account structure of the e-mail case study): big + two members = 5
+    members = [[1, 2], [2, 3], [3, 1]]
+    big = [1, 2, 3, 4]
+    e_ptr, e_idx = csr_of([big] + members)
+    r = orc.count(e_ptr, e_idx, 5)
+    assert r.H(5) == 3 and r.H(17) == 1 and r.T == 4
+
+
+# ---------------------------------------------------------------- brute force and invariants
+
+@pytest.mark.parametrize("seed", range(6))
+def test_exact_bs_matches_brute_force(orc, seed):
+    import hgen
+
+    rnd = random.Random(seed)
+    spec = hgen.HypergraphSpec(rnd.randint(6, 40), rnd.randint(5, 120), seed, hgen.SIZE_UNIFORM, 1,
+                               rnd.randint(2, 8), zipf_s=rnd.uniform(0.3, 1.5), name="t")
+    try:
+        e_ptr, e_idx = hgen.generate(spec)
+    except RuntimeError:
+        pytest.skip("generator exhausted the tiny universe")
+    r = orc.count(e_ptr, e_idx, spec.num_vertices)
+    b = orc.count(e_ptr, e_idx, spec.num_vertices, mode="brute")
+    assert r.counts.tolist() == b.counts.tolist()
+    assert (r.W, r.W_c, r.connected, r.open, r.max_deg) == (b.W, b.W_c, b.connected, b.open,
+                                                             b.max_deg)
+    edges = [e_idx[e_ptr[i]:e_ptr[i + 1]].tolist() for i in range(len(e_ptr) - 1)]
+    assert (r.T, r.open, r.connected, r.W, r.W_c) == brute_force_py(edges)
+
+
+def test_total_is_line_graph_trace(orc):
+    import hgen
+
+    e_ptr, e_idx = hgen.generate(hgen.TINY_PLAIN)
+    e_ptr, e_idx = hgen.prefix(e_ptr, e_idx, 400)
+    A = line_graph_adjacency(e_ptr, e_idx, 1000)
+    r = orc.count(e_ptr, e_idx, 1000)
+    assert r.T == int(np.trace(A @ A @ A)) // 6
+    deg = A.sum(1)
+    assert r.connected == int((deg * (deg - 1) // 2).sum()) and r.W == int(A.sum()) // 2
+    assert r.open == r.connected - 3 * r.T
+
+
+def test_relabelling_invariance(orc):
+    import hgen
+
+    e_ptr, e_idx = hgen.generate(hgen.TINY_PLAIN)
+    e_ptr, e_idx = hgen.prefix(e_ptr, e_idx, 500)
+    r = orc.count(e_ptr, e_idx, 1000)
+    rng = np.random.default_rng(0)
+    vperm = rng.permutation(1000)
+    eorder = rng.permutation(len(e_ptr) - 1)
+    edges = [sorted(vperm[e_idx[e_ptr[i]:e_ptr[i + 1]]].tolist()) for i in eorder]
+    p2, i2 = csr_of(edges)
+    r2 = orc.count(p2, i2, 1000)
+    assert r.counts.tolist() == r2.counts.tolist()
+    assert (r.W, r.W_c, r.open) == (r2.W, r2.W_c, r2.open)
+
+
+def test_range_sample_adds_up(orc):
+    import hgen
+
+    e_ptr, e_idx = hgen.generate(hgen.TINY_PLAIN)
+    e_ptr, e_idx = hgen.prefix(e_ptr, e_idx, 600)
+    whole = orc.count(e_ptr, e_idx, 1000)
+    parts = [orc.count(e_ptr, e_idx, 1000, i_range=(a, b)).counts
+             for a, b in ((0, 100), (100, 350), (350, 600))]
+    assert (parts[0] + parts[1] + parts[2]).tolist() == whole.counts.tolist()
+
+
+def test_input_errors(orc):
+    with pytest.raises(ValueError, match="duplicate hyperedge"):
+        orc.count(*csr_of([[1, 2], [2, 3], [1, 2]]), 5)
+    with pytest.raises(ValueError, match="out of range"):
+        orc.count(np.array([0, 2]), np.array([0, 9]), 5)
+    with pytest.raises(ValueError, match="repeated vertex"):
+        orc.count(np.array([0, 2]), np.array([3, 3]), 5)
+    with pytest.raises(ValueError, match="empty hyperedge"):
+        orc.count(np.array([0, 0, 1]), np.array([3]), 5)
+
+
+# ---------------------------------------------------------------- clustering coefficient
+
+def test_clustering_coefficient(orc):
+    d = load_json("paper_examples.json")["email"]
+    r = orc.count(*csr_of(d["hyperedges"]), 200)
+    assert orc.clustering_coeff(r.counts, r.open, [1.0] * 20) == 3.0 * r.T / r.open
+    cc = orc.pattern_wise_cc(r.counts, r.open)
+    assert cc[4] == 3.0 * 3 / r.open and sum(cc) == pytest.approx(3.0 * r.T / r.open)
+    assert math.isnan(orc.clustering_coeff(r.counts, 0, [1.0] * 20))
