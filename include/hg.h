@@ -1,0 +1,160 @@
+/*
+ * hg.h - C ABI of the GB300 exact hyper-triangle counting library (libhg).
+ *
+ * Method: Yin et al., "Efficient Computation of Hyper-triangles on
+ * Hypergraphs", PVLDB 18(3), 2024.  Step one builds every hyperwedge (a pair of
+ * hyperedges sharing >= 1 vertex, Def. 2.2) with omega_ij = |e_i cap e_j|
+ * (Sec. 3.1, Algorithm 2); step two closes hyperwedges into hyper-triangles
+ * (Def. 2.4), classifies each by the emptiness of its seven Venn regions and
+ * reduces into per-pattern counts H[p] (Sec. 2, Table 1) and the fine-grained
+ * clustering coefficient (Def. 5.1).
+ *
+ * Conventions for every entry point:
+ *   - Ids are int32, offsets int64.  A hypergraph is given as a hyperedge->vertex
+ *     CSR: edge_ptr[|E|+1] (edge_ptr[0] = 0, non-decreasing, edge_ptr[|E|] = nnz)
+ *     and edge_vtx[nnz]; row i lists the vertices of e_i strictly ascending.
+ *   - Every call returns an hg_status; none aborts, prints or traps.  CUDA errors
+ *     of asynchronous work surface at the next call that synchronises.
+ *   - One handle is used by one host thread at a time; all device work of a handle
+ *     is ordered on the CUDA stream given at load time.
+ *   - Device memory of a handle comes from the allocator installed with
+ *     hg_set_allocator at the time of the call (default: cudaMallocAsync on the
+ *     handle's stream) and is released by hg_free.
+ */
+#ifndef HG_H_
+#define HG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hg_graph hg_graph; /* opaque; owns the device copy of one hypergraph */
+
+typedef enum hg_status {
+  HG_OK = 0,
+  HG_ERR_INVALID_ARG = 1,          /* null pointer, negative size, bad edge_ptr shape */
+  HG_ERR_EMPTY_HYPEREDGE = 2,      /* a hyperedge with no vertex (Def. 2.1 forbids it) */
+  HG_ERR_DUP_VERTEX = 3,           /* a vertex listed twice in one hyperedge */
+  HG_ERR_VERTEX_RANGE = 4,         /* vertex id outside [0, num_vertices) */
+  HG_ERR_UNSORTED = 5,             /* a hyperedge's vertex list is not ascending */
+  HG_ERR_DUPLICATE_HYPEREDGE = 6,  /* two equal hyperedges (the paper assumes none, Sec. 2) */
+  HG_ERR_OOM = 7,                  /* the allocator returned no memory */
+  HG_ERR_CUDA = 8,                 /* a CUDA runtime call failed */
+  HG_ERR_TIMEOUT = 9,              /* a bounded device wait gave up */
+  HG_ERR_STATE = 10,               /* call out of order (e.g. counting before hg_build_wedges) */
+  HG_ERR_UNSUPPORTED = 11,         /* input beyond this build's limits */
+  HG_ERR_NO_DEVICE = 12,           /* no usable sm_103 device */
+  HG_ERR_INTERNAL = 13             /* a consistency check of the library failed */
+} hg_status;
+
+/*
+ * Device allocator hooks.  alloc returns a device pointer of at least `bytes`
+ * bytes usable on `stream` (a cudaStream_t), or NULL; free releases it.  ctx is
+ * passed back unchanged.  Passing two NULLs restores the default
+ * (cudaMallocAsync / cudaFreeAsync on the handle's stream).  The setting is
+ * process-wide and is read at each allocation.
+ */
+typedef void* (*hg_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*hg_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+hg_status hg_set_allocator(hg_alloc_fn alloc, hg_free_fn free_fn, void* ctx);
+
+/*
+ * Load and validate a hypergraph (Def. 2.1; Sec. 3.1 builds the per-vertex lists
+ * E_v, Algorithm 2).
+ *   num_vertices, num_edges  |V| >= 1 and |E| >= 0.
+ *   edge_ptr, edge_vtx       the hyperedge->vertex CSR described above; host
+ *                            pointers if inputs_on_device == 0, device pointers
+ *                            otherwise.  They stay owned by the caller and are
+ *                            copied; they may be freed when the call returns.
+ *   cuda_stream              cudaStream_t for all work of the handle (NULL = legacy
+ *                            default stream).
+ *   out                      receives the new handle on HG_OK, NULL otherwise.
+ * Builds the vertex->hyperedge lists on the device.  Returns HG_ERR_EMPTY_HYPEREDGE,
+ * HG_ERR_DUP_VERTEX, HG_ERR_UNSORTED or HG_ERR_VERTEX_RANGE for malformed input,
+ * before any counting work.  Synchronises the stream.
+ */
+hg_status hg_load_csr(int32_t num_vertices, int32_t num_edges, const int64_t* edge_ptr,
+                      const int32_t* edge_vtx, int inputs_on_device, void* cuda_stream,
+                      hg_graph** out);
+
+/* Optional tuning of hg_build_wedges; zero fields mean "choose automatically". */
+typedef struct hg_tuning {
+  int32_t dense_min_size;  /* hyperedges with at least this many vertices form the
+                              dense tensor-core tile set; -1 disables the dense path */
+  int32_t dense_max_count; /* cap on the size of the dense set (0 = 1% of |E|) */
+  int32_t reserved[6];
+} hg_tuning;
+
+typedef struct hg_wedge_stats {
+  uint64_t W;           /* hyperwedges: unordered pairs of hyperedges sharing a vertex */
+  uint64_t W_t;         /* intersection type (Def. 2.3) */
+  uint64_t W_c;         /* inclusion type: one hyperedge contains the other */
+  uint64_t connected;   /* sum over hyperedges of C(deg, 2), deg = |N(e_i)| (Sec. 2) */
+  uint64_t max_deg;     /* max |N(e_i)| */
+  uint64_t max_out_deg; /* max out-degree after degree ordering */
+  uint64_t dense_edges; /* hyperedges handled by the dense tile path */
+  uint64_t reserved;
+} hg_wedge_stats;
+
+/*
+ * Step one (Sec. 3.1, Algorithm 2): omega_ij = |e_i cap e_j| for every hyperwedge,
+ * its type (Def. 2.3), then the degree-ordered orientation used by step two.
+ * opt may be NULL.  out may be NULL.  Rejects equal hyperedges with
+ * HG_ERR_DUPLICATE_HYPEREDGE.  May be called again; it rebuilds.  Synchronises.
+ */
+hg_status hg_build_wedges(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out);
+
+/*
+ * Step two (Sec. 3.2-3.3; Algorithms 3-5 compute the same counts per class):
+ * every hyper-triangle {e_i, e_j, e_k} (three pairwise-intersecting hyperedges,
+ * Def. 2.4) is found once and classified into pattern p in 1..20 from the
+ * emptiness of its seven Venn regions (Sec. 2).
+ *   counts[21]  out: counts[0] = total hyper-triangles, counts[p] = H[p].
+ * Requires hg_build_wedges.  Synchronises.
+ */
+hg_status hg_count_patterns(hg_graph* g, uint64_t counts[21]);
+
+/*
+ * Fine-grained hypergraph clustering coefficient (Def. 5.1):
+ *   cc = 3 * sum_{p=1..20} eps[p-1] * H[p] / open,
+ * evaluated on the host in IEEE double with the sum taken in order p = 1..20;
+ * open = hyper-triples with exactly two of their three pairs connected
+ * ("open hyper-triangles"), = connected - 3 * total.  cc is NaN when open == 0.
+ * eps: 20 weights in [0, 1] (not checked).  Any output pointer may be NULL.
+ * Requires hg_count_patterns on the same handle.  No device work.
+ */
+hg_status hg_clustering_coeff(hg_graph* g, const double eps[20], double* cc,
+                              uint64_t* open_triples, uint64_t* connected_triples);
+
+/* Release the handle and every device buffer it owns (stream-ordered). */
+hg_status hg_free(hg_graph* g);
+
+/*
+ * The library's pattern table: lut[m] = pattern 1..20 of a labelled region mask
+ * m (bit r set = region r of (a)..(g) non-empty, Sec. 2), 0 where m is not a
+ * hyper-triangle of three distinct hyperedges.  Host only; no device needed.
+ */
+hg_status hg_pattern_table(uint8_t lut[128]);
+
+/* Static description of a status code. */
+const char* hg_status_str(hg_status s);
+
+/*
+ * Per-kernel device times of the last hg_build_wedges / hg_count_patterns on
+ * this handle, when timing was switched on with hg_set_timing(g, 1) (CUDA events
+ * on the handle's stream around each launch).  names[i] points to static
+ * strings; ms[i] is the summed time of that kernel in the last call.  *n is the
+ * capacity in and the number written out.
+ */
+hg_status hg_set_timing(hg_graph* g, int enable);
+hg_status hg_kernel_times(hg_graph* g, const char** names, float* ms, int32_t* launches,
+                          int32_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HG_H_ */

@@ -1,0 +1,612 @@
+// C ABI of libhg: argument checks, device memory, and the order of the kernels
+// of the two-step framework (Sec. 3.1 step one, Sec. 3.2-3.3 step two, Def. 5.1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "hg_internal.cuh"
+
+using namespace hg;
+
+namespace {
+
+// ---------------------------------------------------------------- allocator
+
+struct AllocatorHooks {
+  hg_alloc_fn alloc = nullptr;
+  hg_free_fn free_fn = nullptr;
+  void* ctx = nullptr;
+};
+std::mutex g_alloc_mu;
+AllocatorHooks g_hooks;
+
+struct Block {
+  void* p;
+  size_t bytes;
+  hg_free_fn free_fn;  // the hook that owns it (nullptr = cudaFreeAsync)
+  void* ctx;
+};
+
+// Device block of counters and flags shared by the kernels of one handle.
+struct Small {
+  int err;
+  int32_t pad0;
+  int32_t counters[16];       // work-fetch counters
+  int32_t bucket_count[8];    // [0..2] wedge buckets, [4..7] close buckets
+  unsigned long long wc;      // inclusion-type wedges
+  unsigned long long max_cand;
+  int32_t max_size;
+  int32_t pad1;
+  unsigned long long deg_stats[3];   // sum C(deg,2), max deg, sum deg
+  unsigned long long out_stats[3];   // sum C(d+,2), max d+, sum d+
+  unsigned long long wide_max[2];    // close bucket 3: max d+, max |e_u|
+  unsigned long long hist[24];       // pattern histogram (bin 0 = unclassifiable)
+};
+
+struct KTime {
+  const char* name;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct hg_graph {
+  int device = 0;
+  int nsm = 0;
+  cudaStream_t stream = nullptr;
+  int32_t nv = 0, ne = 0;
+  int64_t nnz = 0;
+  // load stage
+  int64_t* e_ptr = nullptr;
+  int32_t* e_idx = nullptr;
+  int32_t* esize = nullptr;
+  int64_t* v_ptr = nullptr;
+  int32_t* v_idx = nullptr;
+  int64_t* cand = nullptr;
+  int32_t max_size = 0;
+  int64_t max_cand = 0;
+  Small* small = nullptr;
+  void* scan_tmp = nullptr;
+  std::vector<Block> load_blocks;
+  // build stage
+  std::vector<Block> build_blocks;
+  int32_t* deg = nullptr;
+  Oriented ori{};
+  int packed = 0;
+  uint64_t two_w = 0;
+  bool built = false;
+  hg_wedge_stats stats{};
+  // count stage
+  std::vector<Block> count_blocks;
+  bool counted = false;
+  uint64_t counts[21] = {0};
+  // timing
+  bool timing = false;
+  std::vector<KTime> pending;
+  std::vector<std::pair<const char*, std::pair<float, int>>> times;  // static names
+};
+
+namespace {
+
+void* dev_alloc(hg_graph* g, std::vector<Block>& owner, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 256);
+  AllocatorHooks h;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    h = g_hooks;
+  }
+  void* p = nullptr;
+  if (h.alloc) {
+    p = h.alloc(bytes, (void*)g->stream, h.ctx);
+  } else if (cudaMallocAsync(&p, bytes, g->stream) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) owner.push_back(Block{p, bytes, h.alloc ? h.free_fn : nullptr, h.ctx});
+  return p;
+}
+
+void release(hg_graph* g, std::vector<Block>& owner) {
+  for (auto& b : owner) {
+    if (b.free_fn) b.free_fn(b.p, b.bytes, (void*)g->stream, b.ctx);
+    else cudaFreeAsync(b.p, g->stream);
+  }
+  owner.clear();
+}
+
+hg_status cuda_status(cudaError_t e) { return e == cudaSuccess ? HG_OK : HG_ERR_CUDA; }
+
+#define HG_CUDA(call)                                        \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return HG_ERR_CUDA;               \
+  } while (0)
+
+#define HG_TRY(st)                     \
+  do {                                 \
+    hg_status s_ = (st);               \
+    if (s_ != HG_OK) return s_;        \
+  } while (0)
+
+hg_status dev_err_status(int e) {
+  switch (e) {
+    case DE_OK: return HG_OK;
+    case DE_EMPTY: return HG_ERR_EMPTY_HYPEREDGE;
+    case DE_RANGE: return HG_ERR_VERTEX_RANGE;
+    case DE_DUPV: return HG_ERR_DUP_VERTEX;
+    case DE_UNSORTED: return HG_ERR_UNSORTED;
+    case DE_DUPEDGE: return HG_ERR_DUPLICATE_HYPEREDGE;
+    case DE_PTR: return HG_ERR_INVALID_ARG;
+    default: return HG_ERR_INTERNAL;
+  }
+}
+
+// Read back the small block and check the error word.
+hg_status sync_small(hg_graph* g, Small* host) {
+  HG_CUDA(cudaMemcpyAsync(host, g->small, sizeof(Small), cudaMemcpyDeviceToHost, g->stream));
+  HG_CUDA(cudaStreamSynchronize(g->stream));
+  HG_CUDA(cudaGetLastError());
+  return dev_err_status(host->err);
+}
+
+void t_begin(hg_graph* g, const char* name) {
+  if (!g->timing) return;
+  KTime k{name, nullptr, nullptr};
+  cudaEventCreate(&k.a);
+  cudaEventCreate(&k.b);
+  cudaEventRecord(k.a, g->stream);
+  g->pending.push_back(k);
+}
+
+void t_end(hg_graph* g) {
+  if (!g->timing || g->pending.empty()) return;
+  cudaEventRecord(g->pending.back().b, g->stream);
+}
+
+// Called after a synchronising point: fold the pending event pairs into g->times.
+void t_collect(hg_graph* g) {
+  for (auto& k : g->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, k.a, k.b) != cudaSuccess) {
+      cudaGetLastError();
+      ms = 0.f;
+    }
+    bool found = false;
+    for (auto& t : g->times)
+      if (std::strcmp(t.first, k.name) == 0) {
+        t.second.first += ms;
+        t.second.second += 1;
+        found = true;
+      }
+    if (!found) g->times.push_back({k.name, {ms, 1}});
+    cudaEventDestroy(k.a);
+    cudaEventDestroy(k.b);
+  }
+  g->pending.clear();
+}
+
+DevGraph dev_graph(const hg_graph* g) {
+  DevGraph d;
+  d.nv = g->nv;
+  d.ne = g->ne;
+  d.nnz = g->nnz;
+  d.e_ptr = g->e_ptr;
+  d.e_idx = g->e_idx;
+  d.esize = g->esize;
+  d.v_ptr = g->v_ptr;
+  d.v_idx = g->v_idx;
+  return d;
+}
+
+// ---------------------------------------------------------------- pattern table
+//
+// Pattern of a labelled region mask (bit r = region r of (a)..(g), Sec. 2) from
+// set relations.  Each hyperedge is the union of its non-empty regions, so
+// equality, containment and intersection of hyperedges are the same relations
+// on their sets of non-empty regions.
+//   class by the number of inclusion-type pairs (Def. 2.3): 3 CCC, 2 TCC, 1 TTC,
+//   0 TTT (Sec. 2);
+//   TCC: the third hyperedge lies inside both others (2 if it equals their
+//        intersection, else 3) or contains both (4 if it equals their union,
+//        else 5) - the tests of Algorithm 5;
+//   TTC: with big containing small and z the third, 6 if big and small meet z
+//        in the same vertices, 7 if big = small + (big cap z), else 8 -
+//        Algorithm 5's omega tests;
+//   TTT: region g non-empty gives 9-16, empty gives 17-20 (Sec. 3.2); inside a
+//        subclass, ascending number of non-empty pairwise regions (d, e, f),
+//        then of single regions (a, b, c).
+int pattern_of(int m) {
+  const int U = (1 << 0) | (1 << 3) | (1 << 5) | (1 << 6);
+  const int V = (1 << 1) | (1 << 3) | (1 << 4) | (1 << 6);
+  const int W = (1 << 2) | (1 << 4) | (1 << 5) | (1 << 6);
+  const int S[3] = {m & U, m & V, m & W};
+  auto sub = [](int x, int y) { return (x & ~y) == 0; };
+  auto incl = [&](int x, int y) { return sub(S[x], S[y]) || sub(S[y], S[x]); };
+  for (int x = 0; x < 3; ++x)
+    for (int y = x + 1; y < 3; ++y) {
+      if (!(S[x] & S[y])) return 0;   // not a hyper-triangle
+      if (S[x] == S[y]) return 0;     // equal hyperedges
+    }
+  const int pairs[3][3] = {{0, 1, 2}, {1, 2, 0}, {0, 2, 1}};  // (x, y, third)
+  int nc = 0;
+  for (auto& p : pairs) nc += incl(p[0], p[1]);
+  if (nc == 3) return 1;
+  if (nc == 2) {
+    for (auto& p : pairs) {
+      if (incl(p[0], p[1])) continue;
+      const int x = S[p[0]], y = S[p[1]], z = S[p[2]];
+      if (sub(z, x) && sub(z, y)) return z == (x & y) ? 2 : 3;
+      return z == (x | y) ? 4 : 5;
+    }
+  }
+  if (nc == 1) {
+    for (auto& p : pairs) {
+      if (!incl(p[0], p[1])) continue;
+      const int big = sub(S[p[1]], S[p[0]]) ? S[p[0]] : S[p[1]];
+      const int small = big == S[p[0]] ? S[p[1]] : S[p[0]];
+      const int z = S[p[2]];
+      if ((big & z) == (small & z)) return 6;
+      if (big == (small | (big & z))) return 7;
+      return 8;
+    }
+  }
+  const int pw = ((m >> 3) & 1) + ((m >> 4) & 1) + ((m >> 5) & 1);
+  const int sg = (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1);
+  if ((m >> 6) & 1) {
+    static const int dense[4][4] = {{0, 0, 0, 9}, {0, 0, 0, 10}, {0, 0, 11, 12}, {13, 14, 15, 16}};
+    return dense[pw][sg];
+  }
+  return pw == 3 ? 17 + sg : 0;
+}
+
+void build_lut(uint8_t lut[128]) {
+  for (int m = 0; m < 128; ++m) lut[m] = (uint8_t)pattern_of(m);
+}
+
+hg_status check_device(int* dev, int* nsm) {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return HG_ERR_NO_DEVICE;
+  }
+  HG_CUDA(cudaGetDevice(dev));
+  cudaDeviceProp p;
+  HG_CUDA(cudaGetDeviceProperties(&p, *dev));
+  if (p.major != 10 || p.minor != 3) return HG_ERR_NO_DEVICE;  // built for sm_103a only
+  *nsm = p.multiProcessorCount;
+  return HG_OK;
+}
+
+template <typename T>
+T* alloc_t(hg_graph* g, std::vector<Block>& owner, int64_t n) {
+  return static_cast<T*>(dev_alloc(g, owner, (size_t)std::max<int64_t>(n, 1) * sizeof(T)));
+}
+
+hg_status load_impl(hg_graph* g, const int64_t* edge_ptr, const int32_t* edge_vtx, int on_dev) {
+  cudaStream_t s = g->stream;
+  const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  g->small = alloc_t<Small>(g, g->load_blocks, 1);
+  g->e_ptr = alloc_t<int64_t>(g, g->load_blocks, (int64_t)g->ne + 1);
+  g->e_idx = alloc_t<int32_t>(g, g->load_blocks, g->nnz);
+  g->esize = alloc_t<int32_t>(g, g->load_blocks, g->ne);
+  g->v_ptr = alloc_t<int64_t>(g, g->load_blocks, (int64_t)g->nv + 1);
+  g->v_idx = alloc_t<int32_t>(g, g->load_blocks, g->nnz);
+  g->cand = alloc_t<int64_t>(g, g->load_blocks, g->ne);
+  int32_t* vdeg = alloc_t<int32_t>(g, g->load_blocks, g->nv);
+  const int64_t scan_n = std::max<int64_t>(std::max<int64_t>(g->nv, g->ne), 1);
+  g->scan_tmp = dev_alloc(g, g->load_blocks, scan_tmp_bytes(scan_n));
+  if (!g->small || !g->e_ptr || !g->e_idx || !g->esize || !g->v_ptr || !g->v_idx || !g->cand ||
+      !vdeg || !g->scan_tmp)
+    return HG_ERR_OOM;
+  HG_CUDA(cudaMemsetAsync(g->small, 0, sizeof(Small), s));
+  HG_CUDA(cudaMemcpyAsync(g->e_ptr, edge_ptr, sizeof(int64_t) * ((size_t)g->ne + 1), kind, s));
+  if (g->nnz > 0)
+    HG_CUDA(cudaMemcpyAsync(g->e_idx, edge_vtx, sizeof(int32_t) * (size_t)g->nnz, kind, s));
+  Small h;
+  launch_check_ptr(g->e_ptr, g->ne, g->nnz, &g->small->err, s);
+  HG_TRY(sync_small(g, &h));
+  HG_CUDA(cudaMemsetAsync(vdeg, 0, sizeof(int32_t) * (size_t)g->nv, s));
+  DevGraph d = dev_graph(g);
+  launch_validate_rows(d, g->esize, vdeg, &g->small->err, s);
+  HG_TRY(sync_small(g, &h));
+  scan_i32_to_i64(vdeg, g->v_ptr, g->nv, g->scan_tmp, s);
+  HG_CUDA(cudaMemsetAsync(vdeg, 0, sizeof(int32_t) * (size_t)g->nv, s));  // reused as cursors
+  launch_scatter(d, vdeg, g->v_idx, s);
+  launch_candidates(d, g->cand, &g->small->max_cand, &g->small->max_size, s);
+  HG_TRY(sync_small(g, &h));
+  g->max_cand = (int64_t)h.max_cand;
+  g->max_size = h.max_size;
+  return HG_OK;
+}
+
+hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
+  (void)opt;
+  cudaStream_t s = g->stream;
+  release(g, g->count_blocks);
+  release(g, g->build_blocks);
+  g->built = false;
+  g->counted = false;
+  const int64_t ne = g->ne;
+  g->packed = (ne < (int64_t(1) << 24) && g->max_size < 256) ? 1 : 0;
+  Small h;
+  HG_CUDA(cudaMemsetAsync(g->small, 0, sizeof(Small), s));
+  g->deg = alloc_t<int32_t>(g, g->build_blocks, ne);
+  int32_t* rows = alloc_t<int32_t>(g, g->build_blocks, 3 * ne);
+  g->ori.row_ptr = alloc_t<int64_t>(g, g->build_blocks, ne + 1);
+  g->ori.dplus = alloc_t<int32_t>(g, g->build_blocks, ne);
+  if (!g->deg || !rows || !g->ori.row_ptr || !g->ori.dplus) return HG_ERR_OOM;
+  WedgeBuckets wb;
+  for (int k = 0; k < 3; ++k) wb.rows[k] = rows + k * ne;
+  wb.count = g->small->bucket_count;
+  launch_bucket_rows(g->cand, g->ne, wb, s);
+  HG_TRY(sync_small(g, &h));
+  int32_t nb[3] = {h.bucket_count[0], h.bucket_count[1], h.bucket_count[2]};
+  unsigned long long* scratch = nullptr;
+  if (nb[2] > 0) {
+    scratch = static_cast<unsigned long long*>(
+        dev_alloc(g, g->build_blocks, wedge_heavy_scratch_bytes(g->max_cand, g->nsm)));
+    if (!scratch) return HG_ERR_OOM;
+  }
+  DevGraph d = dev_graph(g);
+  HG_CUDA(cudaMemsetAsync(g->deg, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1), s));
+  HG_CUDA(cudaMemsetAsync(g->ori.dplus, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1), s));
+  HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
+  t_begin(g, "wedge_count");
+  launch_wedge_pass(0, d, wb, nb, g->max_cand, g->deg, &g->small->wc, g->ori, g->packed, scratch,
+                    &g->small->err, g->small->counters, s, g->nsm);
+  t_end(g);
+  t_begin(g, "wedge_scan");
+  scan_i32_to_i64(g->deg, g->ori.row_ptr, ne, g->scan_tmp, s);
+  reduce_deg_stats(g->deg, ne, g->small->deg_stats, s);
+  t_end(g);
+  HG_TRY(sync_small(g, &h));
+  int64_t two_w = 0;
+  HG_CUDA(cudaMemcpyAsync(&two_w, g->ori.row_ptr + ne, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  HG_CUDA(cudaStreamSynchronize(s));
+  g->two_w = (uint64_t)two_w;
+  if (g->packed) {
+    g->ori.packed = alloc_t<uint32_t>(g, g->build_blocks, two_w);
+    if (!g->ori.packed) return HG_ERR_OOM;
+  } else {
+    g->ori.nbr = alloc_t<int32_t>(g, g->build_blocks, two_w);
+    g->ori.omega = alloc_t<int32_t>(g, g->build_blocks, two_w);
+    if (!g->ori.nbr || !g->ori.omega) return HG_ERR_OOM;
+  }
+  HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
+  t_begin(g, "wedge_emit");
+  launch_wedge_pass(1, d, wb, nb, g->max_cand, g->deg, &g->small->wc, g->ori, g->packed, scratch,
+                    &g->small->err, g->small->counters, s, g->nsm);
+  reduce_deg_stats(g->ori.dplus, ne, g->small->out_stats, s);
+  t_end(g);
+  HG_TRY(sync_small(g, &h));
+  t_collect(g);
+  hg_wedge_stats& st = g->stats;
+  std::memset(&st, 0, sizeof(st));
+  st.W = (uint64_t)two_w / 2;
+  st.W_c = h.wc;
+  st.W_t = st.W - st.W_c;
+  st.connected = h.deg_stats[0];
+  st.max_deg = h.deg_stats[1];
+  st.max_out_deg = h.out_stats[1];
+  if (h.deg_stats[2] != (unsigned long long)two_w || h.out_stats[2] != st.W || (two_w & 1))
+    return HG_ERR_INTERNAL;
+  g->built = true;
+  if (out) *out = st;
+  return HG_OK;
+}
+
+hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
+  cudaStream_t s = g->stream;
+  release(g, g->count_blocks);
+  g->counted = false;
+  const int64_t ne = g->ne;
+  Small h;
+  int32_t* lists = alloc_t<int32_t>(g, g->count_blocks, 4 * ne);
+  if (!lists) return HG_ERR_OOM;
+  HG_CUDA(cudaMemsetAsync(g->small->bucket_count + 4, 0, sizeof(int32_t) * 4, s));
+  HG_CUDA(cudaMemsetAsync(g->small->wide_max, 0, sizeof(g->small->wide_max), s));
+  HG_CUDA(cudaMemsetAsync(g->small->hist, 0, sizeof(g->small->hist), s));
+  HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
+  uint8_t lut[128];
+  build_lut(lut);
+  close_set_lut(lut, s);
+  CloseBuckets cb;
+  for (int k = 0; k < 4; ++k) cb.lists[k] = lists + k * ne;
+  cb.count = g->small->bucket_count + 4;
+  DevGraph d = dev_graph(g);
+  t_begin(g, "close_bucket");
+  launch_bucket_close(d, g->ori, cb, g->small->wide_max, s);
+  t_end(g);
+  HG_TRY(sync_small(g, &h));
+  int32_t n[4];
+  for (int k = 0; k < 4; ++k) n[k] = h.bucket_count[4 + k];
+  void* scratch = nullptr;
+  int64_t dmax = (int64_t)h.wide_max[0], words = ((int64_t)h.wide_max[1] + 31) / 32, cap = 0;
+  if (n[3] > 0) {
+    cap = 16;
+    while (cap < 4 * dmax) cap *= 2;
+    scratch = dev_alloc(g, g->count_blocks, close_wide_scratch_bytes(cap, words, dmax, g->nsm));
+    if (!scratch) return HG_ERR_OOM;
+  }
+  static const char* names[4] = {"close_warp256", "close_warp512", "close_warp1024", "close_wide"};
+  for (int k = 3; k >= 0; --k) {
+    if (n[k] <= 0) continue;
+    t_begin(g, names[k]);
+    launch_close(k, d, g->ori, g->packed, cb.lists[k], n[k], cb.count + k, cap, words, dmax,
+                 scratch, g->small->hist, g->small->counters + k, s, g->nsm);
+    t_end(g);
+  }
+  HG_TRY(sync_small(g, &h));
+  t_collect(g);
+  if (h.hist[0] != 0) return HG_ERR_INTERNAL;
+  for (int k = 21; k < 24; ++k)
+    if (h.hist[k] != 0) return HG_ERR_INTERNAL;
+  uint64_t total = 0;
+  for (int p = 1; p <= 20; ++p) {
+    g->counts[p] = h.hist[p];
+    total += h.hist[p];
+  }
+  g->counts[0] = total;
+  g->counted = true;
+  if (counts) std::memcpy(counts, g->counts, sizeof(g->counts));
+  return HG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hg_status hg_set_allocator(hg_alloc_fn alloc, hg_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return HG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_hooks.alloc = alloc;
+  g_hooks.free_fn = free_fn;
+  g_hooks.ctx = ctx;
+  return HG_OK;
+}
+
+hg_status hg_load_csr(int32_t num_vertices, int32_t num_edges, const int64_t* edge_ptr,
+                      const int32_t* edge_vtx, int inputs_on_device, void* cuda_stream,
+                      hg_graph** out) {
+  if (!out) return HG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (num_vertices < 1 || num_edges < 0 || !edge_ptr) return HG_ERR_INVALID_ARG;
+  int dev = 0, nsm = 0;
+  HG_TRY(check_device(&dev, &nsm));
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int64_t nnz = 0;
+  if (inputs_on_device) {
+    HG_CUDA(cudaMemcpyAsync(&nnz, edge_ptr + num_edges, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    HG_CUDA(cudaStreamSynchronize(s));
+  } else {
+    nnz = edge_ptr[num_edges];
+  }
+  if (nnz < 0 || (nnz > 0 && !edge_vtx)) return HG_ERR_INVALID_ARG;
+  hg_graph* g = new hg_graph();
+  g->device = dev;
+  g->nsm = nsm;
+  g->stream = s;
+  g->nv = num_vertices;
+  g->ne = num_edges;
+  g->nnz = nnz;
+  hg_status st = load_impl(g, edge_ptr, edge_vtx, inputs_on_device);
+  if (st != HG_OK) {
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    release(g, g->load_blocks);
+    cudaStreamSynchronize(s);
+    delete g;
+    return st;
+  }
+  *out = g;
+  return HG_OK;
+}
+
+hg_status hg_build_wedges(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
+  if (!g) return HG_ERR_INVALID_ARG;
+  hg_status st = build_impl(g, opt, out);
+  if (st != HG_OK) {
+    cudaStreamSynchronize(g->stream);
+    cudaGetLastError();
+    g->pending.clear();
+    g->built = false;
+  }
+  return st;
+}
+
+hg_status hg_count_patterns(hg_graph* g, uint64_t counts[21]) {
+  if (!g) return HG_ERR_INVALID_ARG;
+  if (!g->built) return HG_ERR_STATE;
+  hg_status st = count_impl(g, counts);
+  if (st != HG_OK) {
+    cudaStreamSynchronize(g->stream);
+    cudaGetLastError();
+    g->pending.clear();
+  }
+  return st;
+}
+
+hg_status hg_clustering_coeff(hg_graph* g, const double eps[20], double* cc,
+                              uint64_t* open_triples, uint64_t* connected_triples) {
+  if (!g || !eps) return HG_ERR_INVALID_ARG;
+  if (!g->counted) return HG_ERR_STATE;
+  const uint64_t connected = g->stats.connected;
+  const uint64_t open = connected - 3 * g->counts[0];
+  // Def. 5.1: 3 * sum_p eps_p |triangles of pattern p| / |open hyper-triangles|
+  double num = 0.0;
+  for (int p = 1; p <= 20; ++p) num += eps[p - 1] * (double)g->counts[p];
+  if (cc) *cc = open == 0 ? NAN : 3.0 * num / (double)open;
+  if (open_triples) *open_triples = open;
+  if (connected_triples) *connected_triples = connected;
+  return HG_OK;
+}
+
+hg_status hg_free(hg_graph* g) {
+  if (!g) return HG_ERR_INVALID_ARG;
+  cudaStream_t s = g->stream;
+  release(g, g->count_blocks);
+  release(g, g->build_blocks);
+  release(g, g->load_blocks);
+  cudaError_t e = cudaStreamSynchronize(s);
+  for (auto& k : g->pending) {
+    cudaEventDestroy(k.a);
+    cudaEventDestroy(k.b);
+  }
+  delete g;
+  return cuda_status(e);
+}
+
+hg_status hg_pattern_table(uint8_t lut[128]) {
+  if (!lut) return HG_ERR_INVALID_ARG;
+  build_lut(lut);
+  return HG_OK;
+}
+
+const char* hg_status_str(hg_status s) {
+  switch (s) {
+    case HG_OK: return "ok";
+    case HG_ERR_INVALID_ARG: return "invalid argument";
+    case HG_ERR_EMPTY_HYPEREDGE: return "empty hyperedge";
+    case HG_ERR_DUP_VERTEX: return "vertex repeated inside a hyperedge";
+    case HG_ERR_VERTEX_RANGE: return "vertex id out of range";
+    case HG_ERR_UNSORTED: return "hyperedge vertex list not ascending";
+    case HG_ERR_DUPLICATE_HYPEREDGE: return "two hyperedges are equal";
+    case HG_ERR_OOM: return "out of device memory";
+    case HG_ERR_CUDA: return "CUDA runtime error";
+    case HG_ERR_TIMEOUT: return "device wait timed out";
+    case HG_ERR_STATE: return "call out of order";
+    case HG_ERR_UNSUPPORTED: return "input beyond supported limits";
+    case HG_ERR_NO_DEVICE: return "no sm_103 CUDA device";
+    case HG_ERR_INTERNAL: return "internal consistency check failed";
+  }
+  return "unknown status";
+}
+
+hg_status hg_set_timing(hg_graph* g, int enable) {
+  if (!g) return HG_ERR_INVALID_ARG;
+  g->timing = enable != 0;
+  return HG_OK;
+}
+
+hg_status hg_kernel_times(hg_graph* g, const char** names, float* ms, int32_t* launches,
+                          int32_t* n) {
+  if (!g || !n) return HG_ERR_INVALID_ARG;
+  int32_t cap = *n, k = 0;
+  for (auto& t : g->times) {
+    if (k >= cap) break;
+    if (names) names[k] = t.first;
+    if (ms) ms[k] = t.second.first;
+    if (launches) launches[k] = t.second.second;
+    ++k;
+  }
+  *n = k;
+  g->times.clear();
+  return HG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,99 @@
+// Internal declarations shared by the CUDA translation units of libhg.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "hg.h"
+
+namespace hg {
+
+constexpr int kWarp = 32;
+
+// Error words written by kernels (first writer wins via atomicCAS).
+enum DevErr : int {
+  DE_OK = 0,
+  DE_EMPTY = 1,
+  DE_RANGE = 2,
+  DE_DUPV = 3,
+  DE_UNSORTED = 4,
+  DE_DUPEDGE = 5,
+  DE_PTR = 6,       // edge_ptr not monotone / out of [0, nnz]
+  DE_INTERNAL = 7,  // a kernel-side consistency check failed
+};
+
+__device__ __forceinline__ void dev_fail(int* err, int code) { atomicCAS(err, 0, code); }
+
+// Oriented wedge entries.  Packed: (nbr << 8) | omega, used when |E| < 2^24 and
+// every omega < 256; otherwise nbr and omega live in two int32 arrays.
+struct Oriented {
+  int64_t* row_ptr;   // [ne+1] start of row i (capacity deg(i))
+  int32_t* dplus;     // [ne] used length of row i
+  uint32_t* packed;   // [2W] packed entries, or nullptr
+  int32_t* nbr;       // [2W] wide entries, or nullptr
+  int32_t* omega;     // [2W]
+};
+
+struct DevGraph {
+  int32_t nv, ne;
+  int64_t nnz;
+  const int64_t* e_ptr;
+  const int32_t* e_idx;
+  const int32_t* esize;
+  const int64_t* v_ptr;
+  const int32_t* v_idx;
+};
+
+// ---------------- launch wrappers (implemented in the .cu files) ----------------
+
+// k_scan.cu
+// out[0..n] = exclusive prefix sums of in[0..n) (out[n] = total); tmp >= scan_tmp_bytes(n).
+size_t scan_tmp_bytes(int64_t n);
+void scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s);
+void scan_i64_to_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s);
+// acc[0] += sum C(x,2), acc[1] = max x, acc[2] += sum x  over x in a[0..n)
+void reduce_deg_stats(const int32_t* a, int64_t n, unsigned long long* acc, cudaStream_t s);
+
+// k_load.cu
+void launch_check_ptr(const int64_t* e_ptr, int32_t ne, int64_t nnz, int* err, cudaStream_t s);
+void launch_validate_rows(const DevGraph& g, int32_t* esize, int32_t* vdeg, int* err,
+                          cudaStream_t s);
+void launch_scatter(const DevGraph& g, int32_t* cursor, int32_t* v_idx, cudaStream_t s);
+// cand[i] = sum_{v in e_i} (|E_v| - 1); also bucket rows by cand into lists
+void launch_candidates(const DevGraph& g, int64_t* cand, unsigned long long* max_cand,
+                       int32_t* max_size, cudaStream_t s);
+
+// k_wedge.cu
+struct WedgeBuckets {
+  int32_t* rows[3];  // light (warp), medium (block, smem), heavy (block, global scratch)
+  int32_t* count;    // [3] device counters
+};
+void launch_bucket_rows(const int64_t* cand, int32_t ne, WedgeBuckets b, cudaStream_t s);
+int wedge_light_max_cand();
+int wedge_medium_max_cand();
+// mode 0: count (deg, W_c, dup check); mode 1: emit oriented entries
+void launch_wedge_pass(int mode, const DevGraph& g, const WedgeBuckets& b, const int32_t* nb,
+                       int64_t heavy_max_cand, int32_t* deg, unsigned long long* wc,
+                       const Oriented& o, int packed, unsigned long long* scratch,
+                       int* err, int32_t* work_counter, cudaStream_t s, int nsm);
+size_t wedge_heavy_scratch_bytes(int64_t heavy_max_cand, int nsm);
+
+// k_close.cu
+struct CloseBuckets {
+  int32_t* lists[4];  // warp cap 256, warp cap 512, warp cap 1024, block (global scratch)
+  int32_t* count;     // [4]
+};
+void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,
+                         unsigned long long* wide_max, cudaStream_t s);
+void close_set_lut(const uint8_t lut[128], cudaStream_t s);
+// n: list length (host copy); n_p: the same on the device; counter: zeroed fetch counter
+void launch_close(int bucket, const DevGraph& g, const Oriented& o, int packed,
+                  const int32_t* list, int32_t n, const int32_t* n_p, int64_t wide_cap,
+                  int64_t wide_words, int64_t wide_dmax, void* scratch, unsigned long long* hist,
+                  int32_t* counter, cudaStream_t s, int nsm);
+size_t close_wide_scratch_bytes(int64_t cap, int64_t words, int64_t dmax, int nsm);
+
+}  // namespace hg

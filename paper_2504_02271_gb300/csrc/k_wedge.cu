@@ -1,0 +1,327 @@
+// K1/K2: hyperwedge construction and degree-ordered orientation (step one,
+// Sec. 3.1, Algorithm 2).
+//
+// For each hyperedge e_i the kernels gather, for every vertex v of e_i, the
+// hyperedges j != i of E_v, and accumulate omega_ij = |e_i cap e_j| (the number
+// of shared vertices, Def. 2.2) in a hash table keyed by j.  That is row i of
+// the sparse product H * H^T without its diagonal.  Two passes run over the same
+// accumulation:
+//   pass 0 (count): deg(i) = number of distinct j, the inclusion-type count
+//            W_c (omega_ij = min(|e_i|, |e_j|), Def. 2.3) and the duplicate-
+//            hyperedge check (omega_ij = |e_i| = |e_j|);
+//   pass 1 (emit):  after every deg(j) is known, keep only the j ranked above i
+//            in the order (deg, id) and write (j, omega_ij) into row i of the
+//            oriented line graph.
+// Algorithm 2 merges the sorted E_v lists one id at a time on a CPU; here the
+// accumulation is a hash table in shared memory (one warp per light row, one
+// block per medium row) or in global scratch (one block per heavy row).
+#include "hg_internal.cuh"
+
+namespace hg {
+namespace {
+
+constexpr unsigned long long kEmpty = ~0ull;
+constexpr unsigned kFull = 0xffffffffu;
+
+constexpr int kLightCapLog2 = 9;     // 512 slots, rows with cand <= 256
+constexpr int kLightWarps = 8;
+constexpr int kMediumCapLog2 = 13;   // 8192 slots (64 KiB), rows with cand <= 4096
+constexpr int kBlockThreads = 256;
+
+__device__ __forceinline__ uint32_t slot_of(uint32_t key, int cap_log2) {
+  return (key * 0x9E3779B1u) >> (32 - cap_log2);
+}
+
+// omega accumulation: slot = (j << 32) | count
+__device__ __forceinline__ void ht_add(unsigned long long* T, int cap_log2, uint32_t j) {
+  const uint32_t mask = (1u << cap_log2) - 1u;
+  uint32_t s = slot_of(j, cap_log2);
+  const unsigned long long key = (unsigned long long)j << 32;
+  while (true) {
+    unsigned long long cur = *((volatile unsigned long long*)&T[s]);
+    if (cur == kEmpty) {
+      cur = atomicCAS(&T[s], kEmpty, key | 1ull);
+      if (cur == kEmpty) return;
+    }
+    if ((uint32_t)(cur >> 32) == j) {
+      atomicAdd(&T[s], 1ull);
+      return;
+    }
+    s = (s + 1u) & mask;
+  }
+}
+
+__device__ __forceinline__ bool ranked_above(int32_t di, int32_t i, int32_t dj, int32_t j) {
+  return di < dj || (di == dj && i < j);
+}
+
+template <bool PACKED>
+__device__ __forceinline__ void put_entry(const Oriented& o, int64_t at, uint32_t j, uint32_t om) {
+  if (PACKED) {
+    o.packed[at] = (j << 8) | om;
+  } else {
+    o.nbr[at] = (int32_t)j;
+    o.omega[at] = (int32_t)om;
+  }
+}
+
+// One warp per row; the table lives in shared memory.
+template <int MODE, bool PACKED>
+__global__ void __launch_bounds__(kLightWarps * 32)
+    k_wedge_light(DevGraph g, const int32_t* __restrict__ rows, const int32_t* __restrict__ nrows_p,
+                  int32_t* __restrict__ deg, unsigned long long* __restrict__ wc, Oriented o,
+                  int* __restrict__ err, int32_t* __restrict__ counter) {
+  constexpr int CAP = 1 << kLightCapLog2;
+  __shared__ unsigned long long tab[kLightWarps][CAP];
+  __shared__ unsigned long long blk_wc;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long* T = tab[w];
+  const int32_t nrows = *nrows_p;
+  if (threadIdx.x == 0) blk_wc = 0;
+  __syncthreads();
+  unsigned long long my_wc = 0;
+  while (true) {
+    int r = 0;
+    if (lane == 0) r = atomicAdd(counter, 1);
+    r = __shfl_sync(kFull, r, 0);
+    if (r >= nrows) break;
+    const int32_t i = rows[r];
+    for (int s = lane; s < CAP; s += 32) T[s] = kEmpty;
+    __syncwarp();
+    const int64_t b = g.e_ptr[i], e = g.e_ptr[i + 1];
+    for (int64_t p = b; p < e; ++p) {
+      const int32_t v = g.e_idx[p];
+      const int64_t vb = g.v_ptr[v], ve = g.v_ptr[v + 1];
+      for (int64_t q = vb + lane; q < ve; q += 32) {
+        const int32_t j = g.v_idx[q];
+        if (j != i) ht_add(T, kLightCapLog2, (uint32_t)j);
+      }
+    }
+    __syncwarp();
+    const int32_t szi = (int32_t)(e - b);
+    if (MODE == 0) {
+      int distinct = 0;
+      for (int s = lane; s < CAP; s += 32) {
+        const unsigned long long x = T[s];
+        if (x == kEmpty) continue;
+        ++distinct;
+        const int32_t j = (int32_t)(x >> 32), om = (int32_t)(x & 0xffffffffu);
+        if (j > i) {
+          const int32_t szj = g.esize[j];
+          if (om == szi && om == szj) dev_fail(err, DE_DUPEDGE);
+          if (om == min(szi, szj)) ++my_wc;
+        }
+      }
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) distinct += __shfl_down_sync(kFull, distinct, d);
+      if (lane == 0) deg[i] = distinct;
+    } else {
+      const int32_t di = deg[i];
+      const int64_t base = o.row_ptr[i];
+      int32_t written = 0;
+      for (int s0 = 0; s0 < CAP; s0 += 32) {
+        const unsigned long long x = T[s0 + lane];
+        bool emit = false;
+        uint32_t j = 0, om = 0;
+        if (x != kEmpty) {
+          j = (uint32_t)(x >> 32);
+          om = (uint32_t)(x & 0xffffffffu);
+          emit = ranked_above(di, i, deg[j], (int32_t)j);
+        }
+        const unsigned bal = __ballot_sync(kFull, emit);
+        if (emit) put_entry<PACKED>(o, base + written + __popc(bal & ((1u << lane) - 1u)), j, om);
+        written += __popc(bal);
+      }
+      if (lane == 0) o.dplus[i] = written;
+    }
+    __syncwarp();
+  }
+  if (MODE == 0) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) my_wc += __shfl_down_sync(kFull, my_wc, d);
+    if (lane == 0) atomicAdd(&blk_wc, my_wc);
+    __syncthreads();
+    if (threadIdx.x == 0 && blk_wc) atomicAdd(wc, blk_wc);
+  }
+}
+
+// One block per row; the table is in dynamic shared memory (SMEM) or in a
+// per-block slice of global scratch.
+template <int MODE, bool PACKED, bool SMEM>
+__global__ void __launch_bounds__(kBlockThreads)
+    k_wedge_block(DevGraph g, const int32_t* __restrict__ rows, const int32_t* __restrict__ nrows_p,
+                  int cap_log2, unsigned long long* __restrict__ gscratch,
+                  int32_t* __restrict__ deg, unsigned long long* __restrict__ wc, Oriented o,
+                  int* __restrict__ err, int32_t* __restrict__ counter) {
+  extern __shared__ unsigned long long dyn[];
+  unsigned long long* T = SMEM ? dyn : gscratch + ((size_t)blockIdx.x << cap_log2);
+  const uint32_t CAP = 1u << cap_log2;
+  __shared__ int32_t s_row;
+  __shared__ int32_t s_cnt;
+  __shared__ unsigned long long s_wc;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  constexpr int kWarps = kBlockThreads / 32;
+  const int32_t nrows = *nrows_p;
+  if (threadIdx.x == 0) s_wc = 0;
+  unsigned long long my_wc = 0;
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_row = atomicAdd(counter, 1);
+      s_cnt = 0;
+    }
+    __syncthreads();
+    const int32_t r = s_row;
+    if (r >= nrows) break;
+    const int32_t i = rows[r];
+    for (uint32_t s = threadIdx.x; s < CAP; s += kBlockThreads) T[s] = kEmpty;
+    __syncthreads();
+    const int64_t b = g.e_ptr[i], e = g.e_ptr[i + 1];
+    for (int64_t p = b + w; p < e; p += kWarps) {
+      const int32_t v = g.e_idx[p];
+      const int64_t vb = g.v_ptr[v], ve = g.v_ptr[v + 1];
+      for (int64_t q = vb + lane; q < ve; q += 32) {
+        const int32_t j = g.v_idx[q];
+        if (j != i) ht_add(T, cap_log2, (uint32_t)j);
+      }
+    }
+    __syncthreads();
+    const int32_t szi = (int32_t)(e - b);
+    if (MODE == 0) {
+      int distinct = 0;
+      for (uint32_t s = threadIdx.x; s < CAP; s += kBlockThreads) {
+        const unsigned long long x = T[s];
+        if (x == kEmpty) continue;
+        ++distinct;
+        const int32_t j = (int32_t)(x >> 32), om = (int32_t)(x & 0xffffffffu);
+        if (j > i) {
+          const int32_t szj = g.esize[j];
+          if (om == szi && om == szj) dev_fail(err, DE_DUPEDGE);
+          if (om == min(szi, szj)) ++my_wc;
+        }
+      }
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) distinct += __shfl_down_sync(kFull, distinct, d);
+      if (lane == 0) atomicAdd(&s_cnt, distinct);
+      __syncthreads();
+      if (threadIdx.x == 0) deg[i] = s_cnt;
+    } else {
+      const int32_t di = deg[i];
+      const int64_t base = o.row_ptr[i];
+      for (uint32_t s = threadIdx.x; s < CAP; s += kBlockThreads) {
+        const unsigned long long x = T[s];
+        if (x == kEmpty) continue;
+        const uint32_t j = (uint32_t)(x >> 32), om = (uint32_t)(x & 0xffffffffu);
+        if (ranked_above(di, i, deg[j], (int32_t)j)) {
+          const int32_t pos = atomicAdd(&s_cnt, 1);
+          put_entry<PACKED>(o, base + pos, j, om);
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) o.dplus[i] = s_cnt;
+    }
+  }
+  if (MODE == 0) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) my_wc += __shfl_down_sync(kFull, my_wc, d);
+    if (lane == 0) atomicAdd(&s_wc, my_wc);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_wc) atomicAdd(wc, s_wc);
+  }
+}
+
+// Sort rows into the three buckets by their gather count.
+__global__ void k_bucket_rows(const int64_t* __restrict__ cand, int32_t ne, WedgeBuckets b,
+                              int64_t light_max, int64_t medium_max) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < ne;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    int bucket = -1;
+    if (i < ne) {
+      const int64_t c = cand[i];
+      if (c > 0) bucket = c <= light_max ? 0 : (c <= medium_max ? 1 : 2);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const unsigned bal = __ballot_sync(kFull, bucket == k);
+      if (!bal) continue;
+      int32_t at = 0;
+      const int leader = __ffs(bal) - 1;
+      if (lane == leader) at = atomicAdd(&b.count[k], __popc(bal));
+      at = __shfl_sync(kFull, at, leader);
+      if (bucket == k) b.rows[k][at + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
+    }
+  }
+}
+
+int cap_log2_for(int64_t cand) {
+  int l = 4;
+  while ((int64_t(1) << l) < 2 * cand) ++l;
+  return l;
+}
+
+template <int MODE, bool PACKED>
+void launch_all(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb, int64_t heavy_max,
+                int32_t* deg, unsigned long long* wc, const Oriented& o,
+                unsigned long long* scratch, int* err, int32_t* counters, cudaStream_t s,
+                int nsm) {
+  // counters[0..2] are zeroed by the caller
+  if (nb[0] > 0) {
+    int blocks = (nb[0] + kLightWarps - 1) / kLightWarps;
+    blocks = blocks < nsm * 4 ? blocks : nsm * 4;
+    k_wedge_light<MODE, PACKED><<<blocks, kLightWarps * 32, 0, s>>>(g, b.rows[0], b.count + 0, deg,
+                                                                    wc, o, err, counters + 0);
+  }
+  if (nb[1] > 0) {
+    const size_t smem = sizeof(unsigned long long) << kMediumCapLog2;
+    cudaFuncSetAttribute(k_wedge_block<MODE, PACKED, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int blocks = nb[1] < nsm * 3 ? nb[1] : nsm * 3;
+    k_wedge_block<MODE, PACKED, true><<<blocks, kBlockThreads, smem, s>>>(
+        g, b.rows[1], b.count + 1, kMediumCapLog2, nullptr, deg, wc, o, err, counters + 1);
+  }
+  if (nb[2] > 0) {
+    int blocks = nb[2] < nsm * 2 ? nb[2] : nsm * 2;
+    k_wedge_block<MODE, PACKED, false><<<blocks, kBlockThreads, 0, s>>>(
+        g, b.rows[2], b.count + 2, cap_log2_for(heavy_max), scratch, deg, wc, o, err,
+        counters + 2);
+  }
+}
+
+}  // namespace
+
+int wedge_light_max_cand() { return (1 << kLightCapLog2) / 2; }
+int wedge_medium_max_cand() { return (1 << kMediumCapLog2) / 2; }
+
+size_t wedge_heavy_scratch_bytes(int64_t heavy_max_cand, int nsm) {
+  if (heavy_max_cand <= 0) return 0;
+  return (sizeof(unsigned long long) << cap_log2_for(heavy_max_cand)) * (size_t)(nsm * 2);
+}
+
+void launch_bucket_rows(const int64_t* cand, int32_t ne, WedgeBuckets b, cudaStream_t s) {
+  if (ne == 0) return;
+  int64_t blocks = (ne + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_bucket_rows<<<(unsigned)blocks, 256, 0, s>>>(cand, ne, b, wedge_light_max_cand(),
+                                                 wedge_medium_max_cand());
+}
+
+void launch_wedge_pass(int mode, const DevGraph& g, const WedgeBuckets& b, const int32_t* nb,
+                       int64_t heavy_max_cand, int32_t* deg, unsigned long long* wc,
+                       const Oriented& o, int packed, unsigned long long* scratch, int* err,
+                       int32_t* work_counter, cudaStream_t s, int nsm) {
+  if (mode == 0) {
+    if (packed)
+      launch_all<0, true>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, s, nsm);
+    else
+      launch_all<0, false>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, s, nsm);
+  } else {
+    if (packed)
+      launch_all<1, true>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, s, nsm);
+    else
+      launch_all<1, false>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, s, nsm);
+  }
+}
+
+}  // namespace hg

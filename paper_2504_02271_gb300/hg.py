@@ -1,0 +1,251 @@
+"""Thin ctypes binding of libhg (include/hg.h).
+
+Argument marshalling only: every step of the counting path runs in the CUDA
+kernels of ``libhg.so``.  The functions keep the C names.  Device memory comes
+from PyTorch's caching allocator (installed through ``hg_set_allocator``) and
+work runs on the CUDA stream passed at load time (default: torch's current
+stream).  If the library is missing the import of this module fails: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhg.so")
+
+STATUS = {
+    0: "HG_OK", 1: "HG_ERR_INVALID_ARG", 2: "HG_ERR_EMPTY_HYPEREDGE", 3: "HG_ERR_DUP_VERTEX",
+    4: "HG_ERR_VERTEX_RANGE", 5: "HG_ERR_UNSORTED", 6: "HG_ERR_DUPLICATE_HYPEREDGE",
+    7: "HG_ERR_OOM", 8: "HG_ERR_CUDA", 9: "HG_ERR_TIMEOUT", 10: "HG_ERR_STATE",
+    11: "HG_ERR_UNSUPPORTED", 12: "HG_ERR_NO_DEVICE", 13: "HG_ERR_INTERNAL",
+}
+HG_OK = 0
+
+# every entry point declared in include/hg.h
+EXPORTED = ("hg_set_allocator", "hg_load_csr", "hg_build_wedges", "hg_count_patterns",
+            "hg_clustering_coeff", "hg_free", "hg_status_str", "hg_set_timing", "hg_kernel_times",
+            "hg_pattern_table")
+
+
+class HgError(RuntimeError):
+    def __init__(self, fn: str, status: int, text: str):
+        super().__init__(f"{fn}: {STATUS.get(status, status)} ({text})")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("dense_min_size", ctypes.c_int32), ("dense_max_count", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class _WedgeStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("W", "W_t", "W_c", "connected", "max_deg",
+                                                 "max_out_deg", "dense_edges", "reserved")]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                            ctypes.c_void_p)
+
+
+def _open():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libhg.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.hg_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, vp]
+    lib.hg_load_csr.argtypes = [i32, i32, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)]
+    lib.hg_build_wedges.argtypes = [vp, ctypes.POINTER(_Tuning), ctypes.POINTER(_WedgeStats)]
+    lib.hg_count_patterns.argtypes = [vp, vp]
+    lib.hg_clustering_coeff.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_uint64),
+                                        ctypes.POINTER(ctypes.c_uint64)]
+    lib.hg_free.argtypes = [vp]
+    lib.hg_status_str.argtypes = [ctypes.c_int]
+    lib.hg_status_str.restype = ctypes.c_char_p
+    lib.hg_set_timing.argtypes = [vp, ctypes.c_int]
+    lib.hg_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p),
+                                    ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32),
+                                    ctypes.POINTER(i32)]
+    lib.hg_pattern_table.argtypes = [vp]
+    for name in EXPORTED:
+        if name != "hg_status_str":
+            getattr(lib, name).restype = ctypes.c_int
+    del i64
+    return lib
+
+
+_lib = _open()
+
+
+def _check(fn: str, status: int) -> None:
+    if status != HG_OK:
+        raise HgError(fn, status, hg_status_str(status))
+
+
+def hg_status_str(status: int) -> str:
+    return _lib.hg_status_str(int(status)).decode()
+
+
+# ------------------------------------------------------------------ allocator
+
+_torch_hooks = None
+
+
+def use_torch_allocator() -> None:
+    """Route libhg's device allocations through PyTorch's caching allocator."""
+    global _torch_hooks
+    import torch
+
+    def _alloc(nbytes, stream, _ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      int(stream or 0))
+        except Exception:  # out of memory -> NULL -> HG_ERR_OOM
+            return None
+
+    def _free(ptr, _nbytes, _stream, _ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    hooks = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+    _check("hg_set_allocator", _lib.hg_set_allocator(hooks[0], hooks[1], None))
+    _torch_hooks = hooks
+
+
+def use_default_allocator() -> None:
+    """Back to cudaMallocAsync / cudaFreeAsync on the handle's stream."""
+    global _torch_hooks
+    _check("hg_set_allocator", _lib.hg_set_allocator(_ALLOC_FN(), _FREE_FN(), None))
+    _torch_hooks = None
+
+
+def hg_set_allocator(alloc, free, ctx=None) -> None:
+    """Install raw ctypes hooks (see include/hg.h); pass None, None for the default."""
+    if alloc is None and free is None:
+        use_default_allocator()
+        return
+    _check("hg_set_allocator", _lib.hg_set_allocator(alloc, free, ctx))
+
+
+# ------------------------------------------------------------------ handle API
+
+@dataclass
+class Graph:
+    """An hg_graph handle plus what the binding needs to keep alive."""
+
+    ptr: int
+    stream: int
+    num_vertices: int
+    num_edges: int
+    nnz: int
+
+    def __del__(self):
+        if self.ptr:
+            try:
+                _lib.hg_free(ctypes.c_void_p(self.ptr))
+            except Exception:
+                pass
+            self.ptr = 0
+
+
+def _as_ptr(x, dtype):
+    """(pointer, on_device, keepalive) for a numpy array or a torch tensor."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            want = {np.int64: torch.int64, np.int32: torch.int32}[dtype]
+            if x.dtype != want or not x.is_contiguous():
+                x = x.to(want).contiguous()
+            return x.data_ptr(), bool(x.is_cuda), x
+    except ImportError:
+        pass
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, False, a
+
+
+def _default_stream() -> int:
+    import torch
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+def hg_load_csr(num_vertices: int, num_edges: int, edge_ptr, edge_vtx, stream: int | None = None
+                ) -> Graph:
+    """Validate and upload a hyperedge->vertex CSR; returns a Graph handle."""
+    p_ptr, p_dev, keep1 = _as_ptr(edge_ptr, np.int64)
+    v_ptr, v_dev, keep2 = _as_ptr(edge_vtx, np.int32)
+    if p_dev != v_dev:
+        raise ValueError("edge_ptr and edge_vtx must both be on the host or both on the device")
+    if stream is None:
+        stream = _default_stream()
+    out = ctypes.c_void_p()
+    st = _lib.hg_load_csr(int(num_vertices), int(num_edges), p_ptr, v_ptr, 1 if p_dev else 0,
+                          ctypes.c_void_p(stream), ctypes.byref(out))
+    del keep1, keep2
+    _check("hg_load_csr", st)
+    nnz = int(edge_ptr[-1])
+    return Graph(int(out.value), int(stream), int(num_vertices), int(num_edges), nnz)
+
+
+def hg_build_wedges(g: Graph, dense_min_size: int = 0, dense_max_count: int = 0) -> dict:
+    """Step one: hyperwedges, their types and the degree orientation; returns the stats."""
+    tun = _Tuning(int(dense_min_size), int(dense_max_count))
+    st = _WedgeStats()
+    _check("hg_build_wedges",
+           _lib.hg_build_wedges(ctypes.c_void_p(g.ptr), ctypes.byref(tun), ctypes.byref(st)))
+    return {n: int(getattr(st, n)) for n, _ in _WedgeStats._fields_ if n != "reserved"}
+
+
+def hg_count_patterns(g: Graph) -> np.ndarray:
+    """Step two: uint64[21] with [0] = total hyper-triangles and [p] = H[p]."""
+    out = np.zeros(21, dtype=np.uint64)
+    _check("hg_count_patterns", _lib.hg_count_patterns(ctypes.c_void_p(g.ptr), out.ctypes.data))
+    return out
+
+
+def hg_clustering_coeff(g: Graph, eps) -> tuple[float, int, int]:
+    """(cc, open hyper-triangles, connected triples) for weights eps[20] (Def. 5.1)."""
+    e = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+    if e.shape != (20,):
+        raise ValueError("eps must have 20 entries")
+    cc = ctypes.c_double()
+    op = ctypes.c_uint64()
+    co = ctypes.c_uint64()
+    _check("hg_clustering_coeff",
+           _lib.hg_clustering_coeff(ctypes.c_void_p(g.ptr), e.ctypes.data, ctypes.byref(cc),
+                                    ctypes.byref(op), ctypes.byref(co)))
+    return float(cc.value), int(op.value), int(co.value)
+
+
+def hg_pattern_table() -> np.ndarray:
+    """uint8[128]: pattern (1..20, 0 = none) of each labelled 7-bit region mask."""
+    out = np.zeros(128, dtype=np.uint8)
+    _check("hg_pattern_table", _lib.hg_pattern_table(out.ctypes.data))
+    return out
+
+
+def hg_free(g: Graph) -> None:
+    if g.ptr:
+        p, g.ptr = g.ptr, 0
+        _check("hg_free", _lib.hg_free(ctypes.c_void_p(p)))
+
+
+def hg_set_timing(g: Graph, enable: bool) -> None:
+    _check("hg_set_timing", _lib.hg_set_timing(ctypes.c_void_p(g.ptr), 1 if enable else 0))
+
+
+def hg_kernel_times(g: Graph) -> dict[str, tuple[float, int]]:
+    """{kernel group: (summed ms, launches)} since the last read."""
+    cap = 64
+    names = (ctypes.c_char_p * cap)()
+    ms = (ctypes.c_float * cap)()
+    launches = (ctypes.c_int32 * cap)()
+    n = ctypes.c_int32(cap)
+    _check("hg_kernel_times", _lib.hg_kernel_times(ctypes.c_void_p(g.ptr), names, ms, launches,
+                                                   ctypes.byref(n)))
+    return {names[k].decode(): (float(ms[k]), int(launches[k])) for k in range(n.value)}

@@ -1,0 +1,122 @@
+"""CUDA path vs the oracle, element by element (every pattern count, the total and
+the wedge statistics), through the C ABI.  Integers: bit-exact."""
+import numpy as np
+import pytest
+
+from conftest import csr_of, load_json
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_count(hg, nv, e_ptr, e_idx, **kw):
+    import torch
+
+    stream = torch.cuda.Stream()
+    g = hg.hg_load_csr(nv, len(e_ptr) - 1, e_ptr, e_idx, stream=stream.cuda_stream)
+    try:
+        stats = hg.hg_build_wedges(g, **kw)
+        counts = hg.hg_count_patterns(g)
+        cc1, open_, connected = hg.hg_clustering_coeff(g, [1.0] * 20)
+    finally:
+        hg.hg_free(g)
+    stats["open"] = open_
+    stats["connected2"] = connected
+    stats["cc1"] = cc1
+    return counts, stats
+
+
+def check_against_oracle(hg, nv, e_ptr, e_idx, ref=None):
+    import oracle
+
+    counts, st = gpu_count(hg, nv, e_ptr, e_idx)
+    if ref is None:
+        ref = oracle.count(e_ptr, e_idx, nv)
+    assert counts.tolist() == [int(x) for x in ref.counts]
+    assert st["W"] == ref.W and st["W_c"] == ref.W_c and st["W_t"] == ref.W_t
+    assert st["connected"] == ref.connected and st["max_deg"] == ref.max_deg
+    assert st["open"] == ref.open
+    return counts, st
+
+
+def test_paper_email_example(hglib):
+    # Sec. 6.2 (e-mail case study): three hyper-triangles, all pattern 5
+    d = load_json("paper_examples.json")["email"]
+    e_ptr, e_idx = csr_of(d["hyperedges"])
+    counts, st = check_against_oracle(hglib, 200, e_ptr, e_idx)
+    assert int(counts[5]) == 3 and int(counts[0]) == 3
+
+
+def test_paper_coauthor_example(hglib):
+    d = load_json("paper_examples.json")["coauthorship"]
+    e_ptr, e_idx = csr_of(d["hyperedges"])
+    check_against_oracle(hglib, 20, e_ptr, e_idx)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_small(hglib, seed):
+    import hgen
+
+    rng = np.random.default_rng(seed)
+    spec = hgen.HypergraphSpec(
+        num_vertices=int(rng.integers(5, 60)), num_edges=int(rng.integers(3, 400)), seed=seed,
+        size_dist=hgen.SIZE_UNIFORM, size_lo=1, size_hi=int(rng.integers(2, 12)),
+        zipf_s=float(rng.uniform(0.5, 1.5)), name="random_small")
+    try:
+        e_ptr, e_idx = hgen.generate(spec)
+    except RuntimeError:
+        pytest.skip("generator could not draw enough distinct hyperedges")
+    check_against_oracle(hglib, spec.num_vertices, e_ptr, e_idx)
+
+
+def test_wide_hyperedges(hglib):
+    # lowest-ranked hyperedges with more than 32 vertices take the block kernel
+    import hgen
+
+    spec = hgen.HypergraphSpec(400, 300, 7, hgen.SIZE_UNIFORM, 20, 90, zipf_s=0.3, name="wide")
+    e_ptr, e_idx = hgen.generate(spec)
+    check_against_oracle(hglib, spec.num_vertices, e_ptr, e_idx)
+
+
+def test_heavy_wedge_rows(hglib):
+    # a hub vertex in 6000 hyperedges: rows gather > 4096 candidates (global-scratch block)
+    rng = np.random.default_rng(3)
+    edges = []
+    for k in range(6000):
+        edges.append([0, 1 + 2 * k, 2 + 2 * k] if k % 3 else [0, 1 + 2 * k])
+    for k in range(200):
+        a, b = rng.choice(12000, 2, replace=False) + 1
+        edges.append([int(a), int(b)])
+    uniq = {tuple(sorted(set(e))) for e in edges}
+    e_ptr, e_idx = csr_of(sorted(uniq))
+    check_against_oracle(hglib, 13000, e_ptr, e_idx)
+
+
+def test_tiny_plain_full(hglib):
+    import hgen
+
+    gold = load_json("workloads.json")["tiny_plain"]
+    e_ptr, e_idx = hgen.generate(hgen.TINY_PLAIN)
+    assert hgen.csr_hash(e_ptr, e_idx) == gold["csr_hash"]
+    counts, st = gpu_count(hglib, gold["num_vertices"], e_ptr, e_idx)
+    assert counts.tolist() == gold["counts"]
+    assert st["W"] == gold["W"] and st["W_c"] == gold["W_c"] and st["open"] == gold["open"]
+
+
+@pytest.mark.parametrize("name", ["coauthor_prefix50k", "tag_heavy_prefix1000",
+                                  "tag_heavy_prefix2000", "coauthor"])
+def test_workload_golden(hglib, name):
+    import hgen
+
+    data = load_json("workloads.json")
+    if name not in data:
+        pytest.skip(f"no stored oracle values for {name}")
+    gold = data[name]
+    spec = hgen.WORKLOADS[gold["workload"]]
+    e_ptr, e_idx = hgen.generate(spec)
+    if gold["prefix_edges"] is not None:
+        e_ptr, e_idx = hgen.prefix(e_ptr, e_idx, gold["prefix_edges"])
+    assert hgen.csr_hash(e_ptr, e_idx) == gold["csr_hash"]
+    counts, st = gpu_count(hglib, gold["num_vertices"], e_ptr, e_idx)
+    assert counts.tolist() == gold["counts"]
+    for k in ("W", "W_c", "W_t", "connected", "open", "max_deg"):
+        assert st[k] == gold[k], k

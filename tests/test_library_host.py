@@ -1,0 +1,63 @@
+"""Host-side checks of libhg that need no GPU: it builds, loads, exports every
+entry point of include/hg.h, and its pattern table agrees with the oracle's
+independently written one."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def lib(native_cpu):
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location(
+        "_hg_build", os.path.join(ROOT, "paper_2504_02271_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build()
+    import paper_2504_02271_gb300 as hg
+
+    return hg
+
+
+def declared_entry_points():
+    text = open(os.path.join(ROOT, "include", "hg.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hg_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_entry_points()
+    assert "hg_load_csr" in names and "hg_count_patterns" in names
+    so = ctypes.CDLL(lib.hg.LIB_PATH)
+    for n in names:
+        assert hasattr(so, n), n
+    assert set(names) <= set(lib.hg.EXPORTED)
+
+
+def test_pattern_table_matches_oracle(lib):
+    import oracle
+
+    lut = lib.hg_pattern_table()
+    assert [int(x) for x in lut] == [oracle.pattern_of_mask(m) for m in range(128)]
+
+
+def test_status_strings(lib):
+    for s in range(14):
+        assert lib.hg_status_str(s) not in ("", "unknown status")
+    assert lib.hg_status_str(99) == "unknown status"
+
+
+def test_no_cpu_fallback_without_gpu(lib):
+    import numpy as np
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lib.HgError) as e:
+        lib.hg_load_csr(3, 1, np.array([0, 2]), np.array([0, 1]), stream=0)
+    assert e.value.name == "HG_ERR_NO_DEVICE"
