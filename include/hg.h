@@ -129,6 +129,28 @@ hg_status hg_count_patterns(hg_graph* g, uint64_t counts[21]);
 hg_status hg_clustering_coeff(hg_graph* g, const double eps[20], double* cc,
                               uint64_t* open_triples, uint64_t* connected_triples);
 
+/*
+ * Work done by the last hg_count_patterns of a handle (counted by the kernels):
+ *   probes       sum over oriented wedges u->v of |out(v)|: out-list entries
+ *                streamed and looked up in u's table (every hyper-triangle is
+ *                one successful probe);
+ *   gathers      entries of E_y read to build the Omega_ux vertex masks;
+ *   out_entries  oriented wedges (= W);
+ *   teams        hyperedges u that owned a closing team (out-degree >= 2);
+ *   bucket_teams the same per team shape (warp tables of 256/512/1024 slots, block).
+ */
+typedef struct hg_close_stats {
+  uint64_t probes;
+  uint64_t gathers;
+  uint64_t out_entries;
+  uint64_t teams;
+  uint64_t bucket_teams[4];
+} hg_close_stats;
+hg_status hg_close_stats_get(hg_graph* g, hg_close_stats* out);
+
+/* Process-wide number of kernel launches libhg has issued so far. */
+hg_status hg_kernel_launches(uint64_t* n);
+
 /* Release the handle and every device buffer it owns (stream-ordered). */
 hg_status hg_free(hg_graph* g);
 

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -46,6 +47,7 @@ struct Small {
   unsigned long long out_stats[3];   // sum C(d+,2), max d+, sum d+
   unsigned long long wide_max[2];    // close bucket 3: max d+, max |e_u|
   unsigned long long hist[24];       // pattern histogram (bin 0 = unclassifiable)
+  unsigned long long work[2];        // closure: probes, E_y entries scanned for masks
 };
 
 struct KTime {
@@ -85,11 +87,17 @@ struct hg_graph {
   std::vector<Block> count_blocks;
   bool counted = false;
   uint64_t counts[21] = {0};
+  hg_close_stats cstats{};
   // timing
   bool timing = false;
   std::vector<KTime> pending;
   std::vector<std::pair<const char*, std::pair<float, int>>> times;  // static names
 };
+
+namespace hg {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+}  // namespace hg
 
 namespace {
 
@@ -411,6 +419,7 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   HG_CUDA(cudaMemsetAsync(g->small->bucket_count + 4, 0, sizeof(int32_t) * 4, s));
   HG_CUDA(cudaMemsetAsync(g->small->wide_max, 0, sizeof(g->small->wide_max), s));
   HG_CUDA(cudaMemsetAsync(g->small->hist, 0, sizeof(g->small->hist), s));
+  HG_CUDA(cudaMemsetAsync(g->small->work, 0, sizeof(g->small->work), s));
   HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
   uint8_t lut[128];
   build_lut(lut);
@@ -438,7 +447,7 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
     if (n[k] <= 0) continue;
     t_begin(g, names[k]);
     launch_close(k, d, g->ori, g->packed, cb.lists[k], n[k], cb.count + k, cap, words, dmax,
-                 scratch, g->small->hist, g->small->counters + k, s, g->nsm);
+                 scratch, g->small->hist, g->small->work, g->small->counters + k, s, g->nsm);
     t_end(g);
   }
   HG_TRY(sync_small(g, &h));
@@ -452,6 +461,11 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
     total += h.hist[p];
   }
   g->counts[0] = total;
+  g->cstats.probes = h.work[0];
+  g->cstats.gathers = h.work[1];
+  g->cstats.out_entries = g->stats.W;
+  g->cstats.teams = (uint64_t)n[0] + n[1] + n[2] + n[3];
+  for (int k = 0; k < 4; ++k) g->cstats.bucket_teams[k] = (uint64_t)n[k];
   g->counted = true;
   if (counts) std::memcpy(counts, g->counts, sizeof(g->counts));
   return HG_OK;
@@ -559,6 +573,19 @@ hg_status hg_free(hg_graph* g) {
   }
   delete g;
   return cuda_status(e);
+}
+
+hg_status hg_close_stats_get(hg_graph* g, hg_close_stats* out) {
+  if (!g || !out) return HG_ERR_INVALID_ARG;
+  if (!g->counted) return HG_ERR_STATE;
+  *out = g->cstats;
+  return HG_OK;
+}
+
+hg_status hg_kernel_launches(uint64_t* n) {
+  if (!n) return HG_ERR_INVALID_ARG;
+  *n = hg::g_launches.load(std::memory_order_relaxed);
+  return HG_OK;
 }
 
 hg_status hg_pattern_table(uint8_t lut[128]) {

@@ -49,6 +49,9 @@ struct DevGraph {
 
 // ---------------- launch wrappers (implemented in the .cu files) ----------------
 
+// process-wide count of kernel launches made by the library (defined in hg_api.cu)
+void note_launch(int n = 1);
+
 // k_scan.cu
 // out[0..n] = exclusive prefix sums of in[0..n) (out[n] = total); tmp >= scan_tmp_bytes(n).
 size_t scan_tmp_bytes(int64_t n);
@@ -89,11 +92,12 @@ struct CloseBuckets {
 void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,
                          unsigned long long* wide_max, cudaStream_t s);
 void close_set_lut(const uint8_t lut[128], cudaStream_t s);
-// n: list length (host copy); n_p: the same on the device; counter: zeroed fetch counter
+// n: list length (host copy); n_p: the same on the device; counter: zeroed fetch counter;
+// work[0] += probes (entries of out(v) streamed), work[1] += E_y entries scanned for masks
 void launch_close(int bucket, const DevGraph& g, const Oriented& o, int packed,
                   const int32_t* list, int32_t n, const int32_t* n_p, int64_t wide_cap,
                   int64_t wide_words, int64_t wide_dmax, void* scratch, unsigned long long* hist,
-                  int32_t* counter, cudaStream_t s, int nsm);
+                  unsigned long long* work, int32_t* counter, cudaStream_t s, int nsm);
 size_t close_wide_scratch_bytes(int64_t cap, int64_t words, int64_t dmax, int nsm);
 
 }  // namespace hg

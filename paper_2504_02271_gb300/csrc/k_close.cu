@@ -70,7 +70,7 @@ template <int CAP_LOG2, int WARPS, bool PACKED>
 __global__ void __launch_bounds__(WARPS * 32)
     k_close_warp(DevGraph g, Oriented o, const int32_t* __restrict__ list,
                  const int32_t* __restrict__ n_p, unsigned long long* __restrict__ hist_out,
-                 int32_t* __restrict__ counter) {
+                 unsigned long long* __restrict__ work, int32_t* __restrict__ counter) {
   using TT = WarpTables<CAP_LOG2>;
   constexpr int CAP = TT::CAP;
   __shared__ TT tabs[WARPS];
@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(WARPS * 32)
   const int32_t n = *n_p;
   uint32_t* my_hist = hist[w][lane & (kHistCopies - 1)];
   uint64_t since_flush = 0;
+  unsigned long long probes = 0, gathers = 0;
 
   while (true) {
     int r = 0;
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(WARPS * 32)
     for (int p = 0; p < szu; ++p) {
       const int32_t y = __ldg(g.e_idx + eb + p);
       const int64_t yb = __ldg(g.v_ptr + y), ye = __ldg(g.v_ptr + y + 1);
+      gathers += (unsigned long long)(ye - yb);
       for (int64_t q = yb + lane; q < ye; q += 32) {
         const int32_t x = __ldg(g.v_idx + q);
         uint32_t s = slot_of((uint32_t)x, CAP_LOG2);
@@ -133,6 +135,7 @@ __global__ void __launch_bounds__(WARPS * 32)
       const int64_t vb = t.kbeg[k];
       const int32_t cnt = t.kcnt[k];
       since_flush += (uint64_t)cnt;
+      probes += (unsigned long long)cnt;
       for (int32_t j0 = 0; j0 < cnt; j0 += 4 * 32) {
         int32_t wv[4], om[4];
 #pragma unroll
@@ -172,6 +175,10 @@ __global__ void __launch_bounds__(WARPS * 32)
   for (int k = lane; k < kHistCopies * kBins; k += 32) {
     const uint32_t x = (&hist[w][0][0])[k];
     if (x) atomicAdd(&hist_out[k % kBins], (unsigned long long)x);
+  }
+  if (lane == 0) {  // warp-uniform totals
+    atomicAdd(&work[0], probes);
+    atomicAdd(&work[1], gathers);
   }
 }
 
@@ -215,7 +222,7 @@ __global__ void __launch_bounds__(kWideThreads)
     k_close_wide(DevGraph g, Oriented o, const int32_t* __restrict__ list,
                  const int32_t* __restrict__ n_p, int64_t cap_max, int64_t words_max,
                  int64_t dmax, char* __restrict__ scratch, unsigned long long* __restrict__ hist_out,
-                 int32_t* __restrict__ counter) {
+                 unsigned long long* __restrict__ work, int32_t* __restrict__ counter) {
   __shared__ uint32_t hist[kHistCopies][kBins];
   __shared__ uint8_t lut[128];
   __shared__ int32_t s_r;
@@ -228,6 +235,7 @@ __global__ void __launch_bounds__(kWideThreads)
   const int32_t n = *n_p;
   uint32_t* my_hist = hist[lane & (kHistCopies - 1)];
   uint64_t since_flush = 0;
+  unsigned long long probes = 0, gathers = 0;
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) s_r = atomicAdd(counter, 1);
@@ -260,6 +268,7 @@ __global__ void __launch_bounds__(kWideThreads)
     for (int p = w; p < szu; p += kW) {
       const int32_t y = __ldg(g.e_idx + eb + p);
       const int64_t yb = __ldg(g.v_ptr + y), ye = __ldg(g.v_ptr + y + 1);
+      if (lane == 0) gathers += (unsigned long long)(ye - yb);
       for (int64_t q = yb + lane; q < ye; q += 32) {
         const int32_t x = __ldg(g.v_idx + q);
         uint32_t s = slot_of((uint32_t)x, cl);
@@ -278,6 +287,7 @@ __global__ void __launch_bounds__(kWideThreads)
       const int64_t vb = t.kbeg[k];
       const int32_t cnt = t.kcnt[k];
       since_flush += (uint64_t)cnt;
+      if (lane == 0) probes += (unsigned long long)cnt;
       for (int32_t j = lane; j < cnt; j += 32) {
         int32_t wv, om;
         get_entry<PACKED>(o, vb + j, wv, om);
@@ -309,6 +319,10 @@ __global__ void __launch_bounds__(kWideThreads)
   if (threadIdx.x < kHistCopies * kBins) {
     const uint32_t x = (&hist[0][0])[threadIdx.x];
     if (x) atomicAdd(&hist_out[threadIdx.x % kBins], (unsigned long long)x);
+  }
+  if (lane == 0) {
+    atomicAdd(&work[0], probes);
+    atomicAdd(&work[1], gathers);
   }
 }
 
@@ -355,8 +369,8 @@ __global__ void k_bucket_close(DevGraph g, Oriented o, CloseBuckets b,
 
 template <int CAP_LOG2, int WARPS>
 void launch_warp(const DevGraph& g, const Oriented& o, int packed, const int32_t* list, int32_t n,
-                 const int32_t* n_p, unsigned long long* hist, int32_t* counter, cudaStream_t s,
-                 int nsm) {
+                 const int32_t* n_p, unsigned long long* hist, unsigned long long* work,
+                 int32_t* counter, cudaStream_t s, int nsm) {
   int per_sm = 0;
   if (packed) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_close_warp<CAP_LOG2, WARPS, true>,
@@ -368,10 +382,13 @@ void launch_warp(const DevGraph& g, const Oriented& o, int packed, const int32_t
   if (per_sm < 1) per_sm = 1;
   int blocks = (n + WARPS - 1) / WARPS;
   if (blocks > per_sm * nsm) blocks = per_sm * nsm;
+  note_launch();
   if (packed)
-    k_close_warp<CAP_LOG2, WARPS, true><<<blocks, WARPS * 32, 0, s>>>(g, o, list, n_p, hist, counter);
+    k_close_warp<CAP_LOG2, WARPS, true>
+        <<<blocks, WARPS * 32, 0, s>>>(g, o, list, n_p, hist, work, counter);
   else
-    k_close_warp<CAP_LOG2, WARPS, false><<<blocks, WARPS * 32, 0, s>>>(g, o, list, n_p, hist, counter);
+    k_close_warp<CAP_LOG2, WARPS, false>
+        <<<blocks, WARPS * 32, 0, s>>>(g, o, list, n_p, hist, work, counter);
 }
 
 }  // namespace
@@ -385,6 +402,7 @@ void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,
   if (g.ne == 0) return;
   int64_t blocks = (g.ne + 255) / 256;
   if (blocks > 4096) blocks = 4096;
+  note_launch();
   k_bucket_close<<<(unsigned)blocks, 256, 0, s>>>(g, o, b, wide_max);
 }
 
@@ -396,20 +414,23 @@ size_t close_wide_scratch_bytes(int64_t cap, int64_t words, int64_t dmax, int ns
 void launch_close(int bucket, const DevGraph& g, const Oriented& o, int packed,
                   const int32_t* list, int32_t n, const int32_t* n_p, int64_t wide_cap,
                   int64_t wide_words, int64_t wide_dmax, void* scratch, unsigned long long* hist,
-                  int32_t* counter, cudaStream_t s, int nsm) {
+                  unsigned long long* work, int32_t* counter, cudaStream_t s, int nsm) {
   if (n <= 0) return;
   switch (bucket) {
-    case 0: launch_warp<8, 8>(g, o, packed, list, n, n_p, hist, counter, s, nsm); break;
-    case 1: launch_warp<9, 4>(g, o, packed, list, n, n_p, hist, counter, s, nsm); break;
-    case 2: launch_warp<10, 2>(g, o, packed, list, n, n_p, hist, counter, s, nsm); break;
+    case 0: launch_warp<8, 8>(g, o, packed, list, n, n_p, hist, work, counter, s, nsm); break;
+    case 1: launch_warp<9, 4>(g, o, packed, list, n, n_p, hist, work, counter, s, nsm); break;
+    case 2: launch_warp<10, 2>(g, o, packed, list, n, n_p, hist, work, counter, s, nsm); break;
     default: {
       int blocks = n < nsm * 2 ? n : nsm * 2;
+      note_launch();
       if (packed)
         k_close_wide<true><<<blocks, kWideThreads, 0, s>>>(g, o, list, n_p, wide_cap, wide_words,
-                                                           wide_dmax, (char*)scratch, hist, counter);
+                                                           wide_dmax, (char*)scratch, hist, work,
+                                                           counter);
       else
         k_close_wide<false><<<blocks, kWideThreads, 0, s>>>(g, o, list, n_p, wide_cap, wide_words,
-                                                            wide_dmax, (char*)scratch, hist, counter);
+                                                            wide_dmax, (char*)scratch, hist, work,
+                                                            counter);
     }
   }
 }

@@ -105,23 +105,27 @@ int grid_for(int64_t work_items, int per_block) {
 }  // namespace
 
 void launch_check_ptr(const int64_t* e_ptr, int32_t ne, int64_t nnz, int* err, cudaStream_t s) {
+  note_launch();
   k_check_ptr<<<grid_for((int64_t)ne + 1, 256), 256, 0, s>>>(e_ptr, ne, nnz, err);
 }
 
 void launch_validate_rows(const DevGraph& g, int32_t* esize, int32_t* vdeg, int* err,
                           cudaStream_t s) {
   if (g.ne == 0) return;
+  note_launch();
   k_validate_rows<<<grid_for(g.ne, 8), 256, 0, s>>>(g, esize, vdeg, err);
 }
 
 void launch_scatter(const DevGraph& g, int32_t* cursor, int32_t* v_idx, cudaStream_t s) {
   if (g.ne == 0) return;
+  note_launch();
   k_scatter<<<grid_for(g.ne, 8), 256, 0, s>>>(g, cursor, v_idx);
 }
 
 void launch_candidates(const DevGraph& g, int64_t* cand, unsigned long long* max_cand,
                        int32_t* max_size, cudaStream_t s) {
   if (g.ne == 0) return;
+  note_launch();
   k_candidates<<<grid_for(g.ne, 8), 256, 0, s>>>(g, cand, max_cand, max_size);
 }
 

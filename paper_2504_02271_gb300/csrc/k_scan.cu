@@ -84,6 +84,7 @@ size_t level_bytes(int64_t n) {
 template <typename T>
 void scan_impl(const T* in, int64_t* out, int64_t n, char* tmp, cudaStream_t s) {
   if (n <= kTile) {
+    note_launch();
     k_tile_scan<T><<<1, kScanThreads, 0, s>>>(in, n, nullptr, out);
     return;
   }
@@ -91,6 +92,7 @@ void scan_impl(const T* in, int64_t* out, int64_t n, char* tmp, cudaStream_t s) 
   int64_t* sums = reinterpret_cast<int64_t*>(tmp);
   int64_t* sums_scan = sums + nb;
   char* next = tmp + (((size_t)(2 * nb + 1) * sizeof(int64_t) + 255) / 256) * 256;
+  note_launch(2);
   k_tile_sums<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
   scan_impl<int64_t>(sums, sums_scan, nb, next, s);
   k_tile_scan<T><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums_scan, out);
@@ -143,6 +145,7 @@ void reduce_deg_stats(const int32_t* a, int64_t n, unsigned long long* acc, cuda
   int64_t blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
+  note_launch();
   k_deg_stats<<<(unsigned)blocks, 256, 0, s>>>(a, n, acc);
 }
 

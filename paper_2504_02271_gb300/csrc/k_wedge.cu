@@ -270,6 +270,7 @@ void launch_all(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb, int
   if (nb[0] > 0) {
     int blocks = (nb[0] + kLightWarps - 1) / kLightWarps;
     blocks = blocks < nsm * 4 ? blocks : nsm * 4;
+    note_launch();
     k_wedge_light<MODE, PACKED><<<blocks, kLightWarps * 32, 0, s>>>(g, b.rows[0], b.count + 0, deg,
                                                                     wc, o, err, counters + 0);
   }
@@ -278,11 +279,13 @@ void launch_all(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb, int
     cudaFuncSetAttribute(k_wedge_block<MODE, PACKED, true>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int blocks = nb[1] < nsm * 3 ? nb[1] : nsm * 3;
+    note_launch();
     k_wedge_block<MODE, PACKED, true><<<blocks, kBlockThreads, smem, s>>>(
         g, b.rows[1], b.count + 1, kMediumCapLog2, nullptr, deg, wc, o, err, counters + 1);
   }
   if (nb[2] > 0) {
     int blocks = nb[2] < nsm * 2 ? nb[2] : nsm * 2;
+    note_launch();
     k_wedge_block<MODE, PACKED, false><<<blocks, kBlockThreads, 0, s>>>(
         g, b.rows[2], b.count + 2, cap_log2_for(heavy_max), scratch, deg, wc, o, err,
         counters + 2);
@@ -303,6 +306,7 @@ void launch_bucket_rows(const int64_t* cand, int32_t ne, WedgeBuckets b, cudaStr
   if (ne == 0) return;
   int64_t blocks = (ne + 255) / 256;
   if (blocks > 4096) blocks = 4096;
+  note_launch();
   k_bucket_rows<<<(unsigned)blocks, 256, 0, s>>>(cand, ne, b, wedge_light_max_cand(),
                                                  wedge_medium_max_cand());
 }

@@ -29,7 +29,7 @@ HG_OK = 0
 # every entry point declared in include/hg.h
 EXPORTED = ("hg_set_allocator", "hg_load_csr", "hg_build_wedges", "hg_count_patterns",
             "hg_clustering_coeff", "hg_free", "hg_status_str", "hg_set_timing", "hg_kernel_times",
-            "hg_pattern_table")
+            "hg_pattern_table", "hg_close_stats_get", "hg_kernel_launches")
 
 
 class HgError(RuntimeError):
@@ -47,6 +47,12 @@ class _Tuning(ctypes.Structure):
 class _WedgeStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("W", "W_t", "W_c", "connected", "max_deg",
                                                  "max_out_deg", "dense_edges", "reserved")]
+
+
+class _CloseStats(ctypes.Structure):
+    _fields_ = [("probes", ctypes.c_uint64), ("gathers", ctypes.c_uint64),
+                ("out_entries", ctypes.c_uint64), ("teams", ctypes.c_uint64),
+                ("bucket_teams", ctypes.c_uint64 * 4)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -74,6 +80,8 @@ def _open():
                                     ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32),
                                     ctypes.POINTER(i32)]
     lib.hg_pattern_table.argtypes = [vp]
+    lib.hg_close_stats_get.argtypes = [vp, ctypes.POINTER(_CloseStats)]
+    lib.hg_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
     for name in EXPORTED:
         if name != "hg_status_str":
             getattr(lib, name).restype = ctypes.c_int
@@ -220,6 +228,22 @@ def hg_clustering_coeff(g: Graph, eps) -> tuple[float, int, int]:
            _lib.hg_clustering_coeff(ctypes.c_void_p(g.ptr), e.ctypes.data, ctypes.byref(cc),
                                     ctypes.byref(op), ctypes.byref(co)))
     return float(cc.value), int(op.value), int(co.value)
+
+
+def hg_close_stats_get(g: Graph) -> dict:
+    """Work of the last hg_count_patterns: probes, gathers, out_entries, teams, bucket_teams."""
+    st = _CloseStats()
+    _check("hg_close_stats_get", _lib.hg_close_stats_get(ctypes.c_void_p(g.ptr), ctypes.byref(st)))
+    return {"probes": int(st.probes), "gathers": int(st.gathers),
+            "out_entries": int(st.out_entries), "teams": int(st.teams),
+            "bucket_teams": [int(x) for x in st.bucket_teams]}
+
+
+def hg_kernel_launches() -> int:
+    """Process-wide count of kernel launches issued by libhg."""
+    n = ctypes.c_uint64()
+    _check("hg_kernel_launches", _lib.hg_kernel_launches(ctypes.byref(n)))
+    return int(n.value)
 
 
 def hg_pattern_table() -> np.ndarray:
