@@ -85,7 +85,10 @@ typedef struct hg_tuning {
   int32_t dense_min_size;  /* hyperedges with at least this many vertices form the
                               dense tensor-core tile set; -1 disables the dense path */
   int32_t dense_max_count; /* cap on the size of the dense set (0 = 1% of |E|) */
-  int32_t reserved[6];
+  int32_t close_mode;      /* step two team shape: 0 = by out-degree and |e_u| (warp
+                              teams where they fit), 1 = block teams for every
+                              hyperedge; counts do not depend on it */
+  int32_t reserved[5];
 } hg_tuning;
 
 typedef struct hg_wedge_stats {
@@ -135,9 +138,12 @@ hg_status hg_clustering_coeff(hg_graph* g, const double eps[20], double* cc,
  *                streamed and looked up in u's table (every hyper-triangle is
  *                one successful probe);
  *   gathers      entries of E_y read to build the Omega_ux vertex masks;
- *   out_entries  oriented wedges (= W);
+ *   out_entries  entries of the teams' own out-lists out(u) (= oriented wedges
+ *                of hyperedges with out-degree >= 2);
  *   teams        hyperedges u that owned a closing team (out-degree >= 2);
- *   bucket_teams the same per team shape (warp tables of 256/512/1024 slots, block).
+ *   bucket_*     the same per team shape: warp teams for out-degree <= 64, <= 128,
+ *                <= 256, and block teams (index 3, which also takes what the warp
+ *                teams hand over).
  */
 typedef struct hg_close_stats {
   uint64_t probes;
@@ -145,6 +151,9 @@ typedef struct hg_close_stats {
   uint64_t out_entries;
   uint64_t teams;
   uint64_t bucket_teams[4];
+  uint64_t bucket_probes[4];
+  uint64_t bucket_gathers[4];
+  uint64_t bucket_out_entries[4];
 } hg_close_stats;
 hg_status hg_close_stats_get(hg_graph* g, hg_close_stats* out);
 

@@ -47,7 +47,7 @@ struct Small {
   unsigned long long out_stats[3];   // sum C(d+,2), max d+, sum d+
   unsigned long long wide_max[2];    // close bucket 3: max d+, max |e_u|
   unsigned long long hist[24];       // pattern histogram (bin 0 = unclassifiable)
-  unsigned long long work[2];        // closure: probes, E_y entries scanned for masks
+  unsigned long long work[4][3];     // closure per team shape: probes, E_y entries, out-entries
 };
 
 struct KTime {
@@ -80,6 +80,7 @@ struct hg_graph {
   int32_t* deg = nullptr;
   Oriented ori{};
   int packed = 0;
+  int close_mode = 0;
   uint64_t two_w = 0;
   bool built = false;
   hg_wedge_stats stats{};
@@ -333,7 +334,8 @@ hg_status load_impl(hg_graph* g, const int64_t* edge_ptr, const int32_t* edge_vt
 }
 
 hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
-  (void)opt;
+  g->close_mode = opt ? opt->close_mode : 0;
+  if (g->close_mode < 0 || g->close_mode > 1) return HG_ERR_INVALID_ARG;
   cudaStream_t s = g->stream;
   release(g, g->count_blocks);
   release(g, g->build_blocks);
@@ -414,9 +416,9 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   g->counted = false;
   const int64_t ne = g->ne;
   Small h;
-  int32_t* lists = alloc_t<int32_t>(g, g->count_blocks, 4 * ne);
+  int32_t* lists = alloc_t<int32_t>(g, g->count_blocks, 5 * ne);   // 4 buckets + overflow
   if (!lists) return HG_ERR_OOM;
-  HG_CUDA(cudaMemsetAsync(g->small->bucket_count + 4, 0, sizeof(int32_t) * 4, s));
+  HG_CUDA(cudaMemsetAsync(g->small->bucket_count + 3, 0, sizeof(int32_t) * 5, s));
   HG_CUDA(cudaMemsetAsync(g->small->wide_max, 0, sizeof(g->small->wide_max), s));
   HG_CUDA(cudaMemsetAsync(g->small->hist, 0, sizeof(g->small->hist), s));
   HG_CUDA(cudaMemsetAsync(g->small->work, 0, sizeof(g->small->work), s));
@@ -427,30 +429,44 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   CloseBuckets cb;
   for (int k = 0; k < 4; ++k) cb.lists[k] = lists + k * ne;
   cb.count = g->small->bucket_count + 4;
+  int32_t* overflow = lists + 4 * ne;
+  int32_t* n_overflow = g->small->bucket_count + 3;
   DevGraph d = dev_graph(g);
   t_begin(g, "close_bucket");
-  launch_bucket_close(d, g->ori, cb, g->small->wide_max, s);
+  // warp tables keep |e_x| in 16 bits: larger hyperedges send everything to block teams
+  launch_bucket_close(d, g->ori, cb, g->small->wide_max,
+                      g->close_mode == 1 || g->max_size >= 65536, s);
   t_end(g);
   HG_TRY(sync_small(g, &h));
   int32_t n[4];
   for (int k = 0; k < 4; ++k) n[k] = h.bucket_count[4 + k];
-  void* scratch = nullptr;
-  int64_t dmax = (int64_t)h.wide_max[0], words = ((int64_t)h.wide_max[1] + 31) / 32, cap = 0;
-  if (n[3] > 0) {
-    cap = 16;
-    while (cap < 4 * dmax) cap *= 2;
-    scratch = dev_alloc(g, g->count_blocks, close_wide_scratch_bytes(cap, words, dmax, g->nsm));
-    if (!scratch) return HG_ERR_OOM;
-  }
+  // block-kernel scratch: any out-degree and |e_u| of bucket 3, and the warp
+  // buckets' limits (out-degree 256, |e_u| 32) for hyperedges they hand over
+  const int64_t dmax = std::max<int64_t>((int64_t)h.wide_max[0], 256);
+  const int64_t words = std::max<int64_t>(((int64_t)h.wide_max[1] + 31) / 32, 1);
+  int64_t cap = 16;
+  while (cap < 4 * dmax) cap *= 2;
+  void* scratch = dev_alloc(g, g->count_blocks, close_wide_scratch_bytes(cap, words, dmax, g->nsm));
+  if (!scratch) return HG_ERR_OOM;
   static const char* names[4] = {"close_warp256", "close_warp512", "close_warp1024", "close_wide"};
   for (int k = 3; k >= 0; --k) {
     if (n[k] <= 0) continue;
     t_begin(g, names[k]);
     launch_close(k, d, g->ori, g->packed, cb.lists[k], n[k], cb.count + k, cap, words, dmax,
-                 scratch, g->small->hist, g->small->work, g->small->counters + k, s, g->nsm);
+                 scratch, g->small->hist, g->small->work[k], g->small->counters + k, overflow,
+                 n_overflow, s, g->nsm);
     t_end(g);
   }
   HG_TRY(sync_small(g, &h));
+  const int32_t n_over = h.bucket_count[3];
+  if (n_over > 0) {
+    t_begin(g, "close_wide");
+    launch_close(3, d, g->ori, g->packed, overflow, n_over, n_overflow, cap, words, dmax, scratch,
+                 g->small->hist, g->small->work[3], g->small->counters + 4, overflow, n_overflow, s,
+                 g->nsm);
+    t_end(g);
+    HG_TRY(sync_small(g, &h));
+  }
   t_collect(g);
   if (h.hist[0] != 0) return HG_ERR_INTERNAL;
   for (int k = 21; k < 24; ++k)
@@ -461,11 +477,18 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
     total += h.hist[p];
   }
   g->counts[0] = total;
-  g->cstats.probes = h.work[0];
-  g->cstats.gathers = h.work[1];
-  g->cstats.out_entries = g->stats.W;
+  std::memset(&g->cstats, 0, sizeof(g->cstats));
+  for (int k = 0; k < 4; ++k) {
+    g->cstats.bucket_probes[k] = h.work[k][0];
+    g->cstats.bucket_gathers[k] = h.work[k][1];
+    g->cstats.bucket_out_entries[k] = h.work[k][2];
+    g->cstats.probes += h.work[k][0];
+    g->cstats.gathers += h.work[k][1];
+    g->cstats.out_entries += h.work[k][2];
+  }
   g->cstats.teams = (uint64_t)n[0] + n[1] + n[2] + n[3];
   for (int k = 0; k < 4; ++k) g->cstats.bucket_teams[k] = (uint64_t)n[k];
+  g->cstats.bucket_teams[3] += (uint64_t)n_over;   // handed from the warp kernels
   g->counted = true;
   if (counts) std::memcpy(counts, g->counts, sizeof(g->counts));
   return HG_OK;

@@ -24,7 +24,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBins = 24;      // pattern 0 (invalid) .. 20, padded
-constexpr int kHistCopies = 4; // spread same-pattern increments of one warp
+constexpr int kHistCopies = 4; // spread same-pattern increments of the block kernel
 constexpr int kWideThreads = 256;
 
 __constant__ uint8_t c_lut[128];
@@ -53,38 +53,97 @@ __device__ __forceinline__ int region_bits(int szu, int szv, int szw, int wuv, i
 }
 
 // ------------------------------------------------------------------ warp per u
+//
+// One warp owns one hyperedge u with |e_u| <= 32 and out-degree <= D.  Shared
+// memory per warp holds a hash set of out(u) (load factor <= 1/2) with the
+// Omega_ux mask and |e_x| of each member, a 16*D-bit filter that rejects most
+// absent keys with one load (only keys that pass it walk the linear-probing
+// table), and per-neighbour arrays (row start, out-degree, mask, size).  The
+// closure walks the concatenation of the out(v) lists as one flat range: lane l
+// takes flat entries base + l + 32 q, so each load instruction reads 32
+// consecutive entries and every slot is full.  Hits are queued and classified
+// 32 at a time, so the classification runs with every lane active.  Shared-
+// memory traffic per probe is what bounds this kernel: a miss costs one load.
 
-template <int CAP_LOG2>
+constexpr int kUnroll = 4;
+constexpr int kQueue = 32 * kUnroll + 32;
+
+template <int D_LOG2, bool PACKED>
 struct WarpTables {
-  static constexpr int CAP = 1 << CAP_LOG2;
-  static constexpr int DMAX = CAP / 4;   // load factor <= 1/4
+  static constexpr int D = 1 << D_LOG2;      // max out-degree of u
+  static constexpr int CAP = 2 * D;          // hash slots
+  static constexpr int FWORDS = D / 2;       // filter words (16 * D bits)
   int32_t key[CAP];
   uint32_t mask[CAP];
-  int32_t size[CAP];
-  uint16_t kslot[DMAX];
-  int32_t kcnt[DMAX];
-  int64_t kbeg[DMAX];
+  uint16_t size[CAP];
+  uint32_t filt[FWORDS];
+  int64_t kbeg[D];
+  int32_t kcnt[D];
+  uint32_t kmask[D];
+  uint16_t ksz[D];
+  uint32_t queue[kQueue];                    // hits: (v index << 24) | (slot of w << 8) | omega
+  int32_t qom[PACKED ? 1 : kQueue];          // omega_vw when it may not fit 8 bits
 };
 
-template <int CAP_LOG2, int WARPS, bool PACKED>
-__global__ void __launch_bounds__(WARPS * 32)
+__device__ __forceinline__ uint32_t filt_bit(uint32_t key, int bits_log2) {
+  return (key * 0x85EBCA6Bu) >> (32 - bits_log2);
+}
+
+// Per-lane run-length accumulation of pattern increments (most lanes repeat the
+// same pattern many times): one shared atomic per run instead of per triangle.
+struct RunHist {
+  uint32_t pat = 0, run = 0;
+  __device__ __forceinline__ void add(uint32_t p, uint32_t* hist) {
+    if (p == pat && run < 0x7fffffffu) {
+      ++run;
+    } else {
+      if (run) atomicAdd(&hist[pat], run);
+      pat = p;
+      run = 1;
+    }
+  }
+  __device__ __forceinline__ void flush(uint32_t* hist) {
+    if (run) atomicAdd(&hist[pat], run);
+    run = 0;
+  }
+};
+
+// Classify queued hit number `at`: v = k-th out-neighbour, w = table slot.
+template <int D_LOG2, bool PACKED>
+__device__ __forceinline__ void classify_queued(const WarpTables<D_LOG2, PACKED>& t, int at,
+                                                int szu, const uint8_t* lut, uint32_t* hist,
+                                                RunHist& rh) {
+  const uint32_t e = t.queue[at];
+  const uint32_t k = e >> 24, sw = (e >> 8) & 0xffffu;
+  const int om = PACKED ? (int)(e & 0xffu) : t.qom[at];
+  const uint32_t muv = t.kmask[k], muw = t.mask[sw];
+  const int gg = __popc(muv & muw);
+  const int bits = region_bits(szu, t.ksz[k], t.size[sw], __popc(muv), __popc(muw), om, gg);
+  rh.add(lut[bits], hist);
+}
+
+template <int D_LOG2, int WARPS, bool PACKED>
+__global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
     k_close_warp(DevGraph g, Oriented o, const int32_t* __restrict__ list,
                  const int32_t* __restrict__ n_p, unsigned long long* __restrict__ hist_out,
-                 unsigned long long* __restrict__ work, int32_t* __restrict__ counter) {
-  using TT = WarpTables<CAP_LOG2>;
-  constexpr int CAP = TT::CAP;
-  __shared__ TT tabs[WARPS];
-  __shared__ uint32_t hist[WARPS][kHistCopies][kBins];
+                 unsigned long long* __restrict__ work, int32_t* __restrict__ counter,
+                 int32_t* __restrict__ overflow, int32_t* __restrict__ n_overflow) {
+  using TT = WarpTables<D_LOG2, PACKED>;
+  constexpr int CAP = TT::CAP, CAP_LOG2 = D_LOG2 + 1, FB_LOG2 = D_LOG2 + 4;
+  (void)overflow;
+  (void)n_overflow;   // linear probing at load <= 1/2 never overflows
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  TT* tabs = reinterpret_cast<TT*>(dyn_smem);   // WARPS tables
+  __shared__ uint32_t hist[WARPS][kBins];
   __shared__ uint8_t lut[128];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   TT& t = tabs[w];
   for (int k = threadIdx.x; k < 128; k += blockDim.x) lut[k] = c_lut[k];
-  for (int k = lane; k < kHistCopies * kBins; k += 32) (&hist[w][0][0])[k] = 0;
+  for (int k = lane; k < kBins; k += 32) hist[w][k] = 0;
   __syncthreads();
   const int32_t n = *n_p;
-  uint32_t* my_hist = hist[w][lane & (kHistCopies - 1)];
-  uint64_t since_flush = 0;
-  unsigned long long probes = 0, gathers = 0;
+  RunHist rh;
+  unsigned long long probes = 0, gathers = 0, outs = 0;
 
   while (true) {
     int r = 0;
@@ -98,87 +157,153 @@ __global__ void __launch_bounds__(WARPS * 32)
     const int32_t szu = (int32_t)(g.e_ptr[u + 1] - eb);
 
     for (int s = lane; s < CAP; s += 32) t.key[s] = -1;
+    for (int s = lane; s < TT::FWORDS; s += 32) t.filt[s] = 0;
+    // vertex y of e_u at lane p: its E_y range (one round trip for all p)
+    int64_t yb = 0, ye = 0;
+    if (lane < szu) {
+      const int32_t y = __ldg(g.e_idx + eb + lane);
+      yb = __ldg(g.v_ptr + y);
+      ye = __ldg(g.v_ptr + y + 1);
+    }
     __syncwarp();
-    // 1. out(u) into the table
+    // 1. out(u) into the table and the filter
+    int32_t my_cnt = 0;
+    for (int k = lane; k < du; k += 32) {
+      int32_t x, om;
+      get_entry<PACKED>(o, bu + k, x, om);
+      const int64_t xb = __ldg(o.row_ptr + x);
+      const int32_t xc = __ldg(o.dplus + x);
+      const int32_t xs = __ldg(g.esize + x);
+      uint32_t s = slot_of((uint32_t)x, CAP_LOG2);
+      while (atomicCAS(&t.key[s], -1, x) != -1) s = (s + 1) & (CAP - 1);
+      t.mask[s] = 0;
+      t.size[s] = (uint16_t)xs;
+      const uint32_t fb = filt_bit((uint32_t)x, FB_LOG2);
+      atomicOr(&t.filt[fb >> 5], 1u << (fb & 31));
+      t.kbeg[k] = xb;
+      t.kcnt[k] = xc;
+      my_cnt += xc;
+    }
+    __syncwarp();
+    // 2. Omega_ux masks: flat walk over the E_y lists of the vertices of e_u
+    {
+      const int64_t len = ye - yb;   // lanes >= szu hold 0
+      int64_t incl = len;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int64_t o2 = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += o2;
+      }
+      const int64_t total = __shfl_sync(kFull, incl, 31);
+      gathers += (unsigned long long)total;
+      for (int64_t f0 = 0; f0 < total; f0 += 32) {   // warp-uniform: all lanes shuffle
+        const int64_t f = f0 + lane;
+        int lo = 0, hi = 31;   // owner p: first lane whose inclusive prefix exceeds f
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {
+          const int mid = (lo + hi) >> 1;
+          const int64_t v = __shfl_sync(kFull, incl, mid);
+          if (v > f) hi = mid; else lo = mid + 1;
+        }
+        const int p = lo;
+        const int64_t start = __shfl_sync(kFull, yb, p) - (__shfl_sync(kFull, incl, p) -
+                                                          __shfl_sync(kFull, len, p));
+        if (f >= total) continue;
+        const int32_t x = __ldg(g.v_idx + start + f);
+        const uint32_t fb = filt_bit((uint32_t)x, FB_LOG2);
+        if (!((t.filt[fb >> 5] >> (fb & 31)) & 1u)) continue;
+        uint32_t s = slot_of((uint32_t)x, CAP_LOG2);
+        int32_t kk;
+        while ((kk = t.key[s]) != x && kk != -1) s = (s + 1) & (CAP - 1);
+        if (kk == x) atomicOr(&t.mask[s], 1u << p);   // lanes may be at different p
+      }
+    }
+    __syncwarp();
+    // per-neighbour copies of mask and size for the closure loop
     for (int k = lane; k < du; k += 32) {
       int32_t x, om;
       get_entry<PACKED>(o, bu + k, x, om);
       uint32_t s = slot_of((uint32_t)x, CAP_LOG2);
-      while (atomicCAS(&t.key[s], -1, x) != -1) s = (s + 1) & (CAP - 1);
-      t.mask[s] = 0;
-      t.size[s] = __ldg(g.esize + x);
-      t.kslot[k] = (uint16_t)s;
-      t.kbeg[k] = __ldg(o.row_ptr + x);
-      t.kcnt[k] = __ldg(o.dplus + x);
+      while (t.key[s] != x) s = (s + 1) & (CAP - 1);
+      t.kmask[k] = t.mask[s];
+      t.ksz[k] = t.size[s];
     }
+    int32_t F = my_cnt;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) F += __shfl_xor_sync(kFull, F, d);
+    probes += (unsigned long long)F;
+    outs += (unsigned long long)du;
     __syncwarp();
-    // 2. Omega_ux masks: for vertex y at position p of e_u, every x in E_y that is in out(u)
-    for (int p = 0; p < szu; ++p) {
-      const int32_t y = __ldg(g.e_idx + eb + p);
-      const int64_t yb = __ldg(g.v_ptr + y), ye = __ldg(g.v_ptr + y + 1);
-      gathers += (unsigned long long)(ye - yb);
-      for (int64_t q = yb + lane; q < ye; q += 32) {
-        const int32_t x = __ldg(g.v_idx + q);
-        uint32_t s = slot_of((uint32_t)x, CAP_LOG2);
-        int32_t kk;
-        while ((kk = t.key[s]) != x && kk != -1) s = (s + 1) & (CAP - 1);
-        if (kk == x) atomicOr(&t.mask[s], 1u << p);  // lanes may be at different p
-      }
+
+    // 3. closure over the flat range of all out(v), v in out(u)
+    int qn = 0;   // queued hits (the same on every lane)
+    int ck = 0, cj = lane;             // this lane's cursor: entry cj of out(v_ck)
+    int ccnt = du > 0 ? t.kcnt[0] : 0;
+    while (cj >= ccnt && ck < du) {
+      cj -= ccnt;
+      if (++ck < du) ccnt = t.kcnt[ck];
     }
-    __syncwarp();
-    // 3. close: for v in out(u), probe every w in out(v)
-    for (int k = 0; k < du; ++k) {
-      const int sv = t.kslot[k];
-      const uint32_t muv = t.mask[sv];
-      const int szv = t.size[sv];
-      const int wuv = __popc(muv);
-      const int64_t vb = t.kbeg[k];
-      const int32_t cnt = t.kcnt[k];
-      since_flush += (uint64_t)cnt;
-      probes += (unsigned long long)cnt;
-      for (int32_t j0 = 0; j0 < cnt; j0 += 4 * 32) {
-        int32_t wv[4], om[4];
+    int64_t cb = ck < du ? t.kbeg[ck] : 0;
+    for (int base = 0; base < F; base += 32 * kUnroll) {
+      int32_t ent_w[kUnroll], ent_om[kUnroll], ent_k[kUnroll];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int32_t j = j0 + q * 32 + lane;
-          wv[q] = -2;
-          om[q] = 0;
-          if (j < cnt) get_entry<PACKED>(o, vb + j, wv[q], om[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (wv[q] < 0) continue;
-          uint32_t s = slot_of((uint32_t)wv[q], CAP_LOG2);
-          int32_t kk;
-          while ((kk = t.key[s]) != wv[q] && kk != -1) s = (s + 1) & (CAP - 1);
-          if (kk != wv[q]) continue;
-          const uint32_t muw = t.mask[s];
-          const int szw = t.size[s];
-          const int gg = __popc(muv & muw);
-          const int bits = region_bits(szu, szv, szw, wuv, __popc(muw), om[q], gg);
-          atomicAdd(&my_hist[lut[bits]], 1u);
+      for (int q = 0; q < kUnroll; ++q) {
+        ent_k[q] = ck;
+        ent_w[q] = -1;
+        ent_om[q] = 0;
+        if (ck < du) get_entry<PACKED>(o, cb + cj, ent_w[q], ent_om[q]);
+        cj += 32;
+        while (cj >= ccnt && ck < du) {
+          cj -= ccnt;
+          if (++ck < du) {
+            ccnt = t.kcnt[ck];
+            cb = t.kbeg[ck];
+          }
         }
       }
-    }
-    if (since_flush > (1ull << 30)) {  // keep the 32-bit bins far from overflow
+      // probe; hits go to the warp's queue as (v index, slot of w, omega_vw)
+#pragma unroll
+      for (int q = 0; q < kUnroll; ++q) {
+        const int32_t x = ent_w[q];
+        bool hit = false;
+        uint32_t s = 0;
+        if (x >= 0) {
+          const uint32_t fb = filt_bit((uint32_t)x, FB_LOG2);
+          if ((t.filt[fb >> 5] >> (fb & 31)) & 1u) {
+            s = slot_of((uint32_t)x, CAP_LOG2);
+            int32_t kk;
+            while ((kk = t.key[s]) != x && kk != -1) s = (s + 1) & (CAP - 1);
+            hit = kk == x;
+          }
+        }
+        const unsigned bal = __ballot_sync(kFull, hit);
+        if (hit) {
+          const int at = qn + __popc(bal & ((1u << lane) - 1u));
+          t.queue[at] = ((uint32_t)ent_k[q] << 24) | (s << 8) |
+                        (PACKED ? (uint32_t)ent_om[q] : 0u);
+          if (!PACKED) t.qom[at] = ent_om[q];
+        }
+        qn += __popc(bal);
+      }
       __syncwarp();
-      for (int k = lane; k < kHistCopies * kBins; k += 32) {
-        const uint32_t x = (&hist[w][0][0])[k];
-        if (x) atomicAdd(&hist_out[k % kBins], (unsigned long long)x);
-        (&hist[w][0][0])[k] = 0;
+      // classify full rounds of 32 hits with every lane busy
+      while (qn >= 32) {
+        qn -= 32;
+        classify_queued<D_LOG2, PACKED>(t, qn + lane, szu, lut, hist[w], rh);
+        __syncwarp();
       }
-      since_flush = 0;
     }
+    if (lane < qn) classify_queued<D_LOG2, PACKED>(t, lane, szu, lut, hist[w], rh);
     __syncwarp();
   }
+  rh.flush(hist[w]);
   __syncwarp();
-  for (int k = lane; k < kHistCopies * kBins; k += 32) {
-    const uint32_t x = (&hist[w][0][0])[k];
-    if (x) atomicAdd(&hist_out[k % kBins], (unsigned long long)x);
-  }
-  if (lane == 0) {  // warp-uniform totals
+  for (int k = lane; k < kBins; k += 32)
+    if (hist[w][k]) atomicAdd(&hist_out[k], (unsigned long long)hist[w][k]);
+  if (lane == 0) {
     atomicAdd(&work[0], probes);
     atomicAdd(&work[1], gathers);
+    atomicAdd(&work[2], outs);
   }
 }
 
@@ -235,7 +360,7 @@ __global__ void __launch_bounds__(kWideThreads)
   const int32_t n = *n_p;
   uint32_t* my_hist = hist[lane & (kHistCopies - 1)];
   uint64_t since_flush = 0;
-  unsigned long long probes = 0, gathers = 0;
+  unsigned long long probes = 0, gathers = 0, outs = 0;
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) s_r = atomicAdd(counter, 1);
@@ -248,6 +373,7 @@ __global__ void __launch_bounds__(kWideThreads)
     const int64_t eb = g.e_ptr[u];
     const int32_t szu = (int32_t)(g.e_ptr[u + 1] - eb);
     const int32_t words = (szu + 31) / 32;
+    if (threadIdx.x == 0) outs += (unsigned long long)du;
     int cl = 4;
     while ((int64_t(1) << cl) < 4 * (int64_t)du) ++cl;
     const uint32_t cap = 1u << cl;
@@ -323,15 +449,16 @@ __global__ void __launch_bounds__(kWideThreads)
   if (lane == 0) {
     atomicAdd(&work[0], probes);
     atomicAdd(&work[1], gathers);
+    atomicAdd(&work[2], outs);
   }
 }
 
 // ------------------------------------------------------------------ bucketing
 
-constexpr int kWarpMaskBits = 32;
+constexpr int kWarpMaskBits = 32;   // warp tables keep Omega_ux in one 32-bit word
 
 __global__ void k_bucket_close(DevGraph g, Oriented o, CloseBuckets b,
-                               unsigned long long* __restrict__ wide_max) {
+                               unsigned long long* __restrict__ wide_max, bool all_block) {
   const int lane = threadIdx.x & 31;
   unsigned long long my_d = 0, my_s = 0;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < g.ne;
@@ -342,11 +469,12 @@ __global__ void k_bucket_close(DevGraph g, Oriented o, CloseBuckets b,
       const int32_t d = o.dplus[u];
       const int32_t sz = g.esize[u];
       if (d >= 2) {
-        if (sz <= kWarpMaskBits && d <= 64) bucket = 0;
+        if (all_block) bucket = 3;
+        else if (sz <= kWarpMaskBits && d <= 64) bucket = 0;
         else if (sz <= kWarpMaskBits && d <= 128) bucket = 1;
         else if (sz <= kWarpMaskBits && d <= 256) bucket = 2;
-        else {
-          bucket = 3;
+        else bucket = 3;
+        if (bucket == 3) {
           my_d = (unsigned long long)d > my_d ? (unsigned long long)d : my_d;
           my_s = (unsigned long long)sz > my_s ? (unsigned long long)sz : my_s;
         }
@@ -367,28 +495,35 @@ __global__ void k_bucket_close(DevGraph g, Oriented o, CloseBuckets b,
   atomicMax(&wide_max[1], my_s);
 }
 
-template <int CAP_LOG2, int WARPS>
-void launch_warp(const DevGraph& g, const Oriented& o, int packed, const int32_t* list, int32_t n,
-                 const int32_t* n_p, unsigned long long* hist, unsigned long long* work,
-                 int32_t* counter, cudaStream_t s, int nsm) {
+template <int D_LOG2, int WARPS, bool PACKED>
+void launch_warp_t(const DevGraph& g, const Oriented& o, const int32_t* list, int32_t n,
+                   const int32_t* n_p, unsigned long long* hist, unsigned long long* work,
+                   int32_t* counter, int32_t* overflow, int32_t* n_overflow, cudaStream_t s,
+                   int nsm) {
+  auto kern = k_close_warp<D_LOG2, WARPS, PACKED>;
+  const int smem = (int)(WARPS * sizeof(WarpTables<D_LOG2, PACKED>));
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   int per_sm = 0;
-  if (packed) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_close_warp<CAP_LOG2, WARPS, true>,
-                                                  WARPS * 32, 0);
-  } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_close_warp<CAP_LOG2, WARPS, false>,
-                                                  WARPS * 32, 0);
-  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
   if (per_sm < 1) per_sm = 1;
   int blocks = (n + WARPS - 1) / WARPS;
   if (blocks > per_sm * nsm) blocks = per_sm * nsm;
   note_launch();
+  kern<<<blocks, WARPS * 32, smem, s>>>(g, o, list, n_p, hist, work, counter, overflow,
+                                         n_overflow);
+}
+
+template <int D_LOG2, int WARPS>
+void launch_warp(const DevGraph& g, const Oriented& o, int packed, const int32_t* list, int32_t n,
+                 const int32_t* n_p, unsigned long long* hist, unsigned long long* work,
+                 int32_t* counter, int32_t* overflow, int32_t* n_overflow, cudaStream_t s,
+                 int nsm) {
   if (packed)
-    k_close_warp<CAP_LOG2, WARPS, true>
-        <<<blocks, WARPS * 32, 0, s>>>(g, o, list, n_p, hist, work, counter);
+    launch_warp_t<D_LOG2, WARPS, true>(g, o, list, n, n_p, hist, work, counter, overflow,
+                                       n_overflow, s, nsm);
   else
-    k_close_warp<CAP_LOG2, WARPS, false>
-        <<<blocks, WARPS * 32, 0, s>>>(g, o, list, n_p, hist, work, counter);
+    launch_warp_t<D_LOG2, WARPS, false>(g, o, list, n, n_p, hist, work, counter, overflow,
+                                        n_overflow, s, nsm);
 }
 
 }  // namespace
@@ -398,12 +533,12 @@ void close_set_lut(const uint8_t lut[128], cudaStream_t s) {
 }
 
 void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,
-                         unsigned long long* wide_max, cudaStream_t s) {
+                         unsigned long long* wide_max, bool all_block, cudaStream_t s) {
   if (g.ne == 0) return;
   int64_t blocks = (g.ne + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   note_launch();
-  k_bucket_close<<<(unsigned)blocks, 256, 0, s>>>(g, o, b, wide_max);
+  k_bucket_close<<<(unsigned)blocks, 256, 0, s>>>(g, o, b, wide_max, all_block);
 }
 
 size_t close_wide_scratch_bytes(int64_t cap, int64_t words, int64_t dmax, int nsm) {
@@ -414,12 +549,22 @@ size_t close_wide_scratch_bytes(int64_t cap, int64_t words, int64_t dmax, int ns
 void launch_close(int bucket, const DevGraph& g, const Oriented& o, int packed,
                   const int32_t* list, int32_t n, const int32_t* n_p, int64_t wide_cap,
                   int64_t wide_words, int64_t wide_dmax, void* scratch, unsigned long long* hist,
-                  unsigned long long* work, int32_t* counter, cudaStream_t s, int nsm) {
+                  unsigned long long* work, int32_t* counter, int32_t* overflow,
+                  int32_t* n_overflow, cudaStream_t s, int nsm) {
   if (n <= 0) return;
   switch (bucket) {
-    case 0: launch_warp<8, 8>(g, o, packed, list, n, n_p, hist, work, counter, s, nsm); break;
-    case 1: launch_warp<9, 4>(g, o, packed, list, n, n_p, hist, work, counter, s, nsm); break;
-    case 2: launch_warp<10, 2>(g, o, packed, list, n, n_p, hist, work, counter, s, nsm); break;
+    case 0:
+      launch_warp<6, 8>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow, s,
+                        nsm);
+      break;
+    case 1:
+      launch_warp<7, 6>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow, s,
+                        nsm);
+      break;
+    case 2:
+      launch_warp<8, 4>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow, s,
+                        nsm);
+      break;
     default: {
       int blocks = n < nsm * 2 ? n : nsm * 2;
       note_launch();

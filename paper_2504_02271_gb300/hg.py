@@ -41,7 +41,7 @@ class HgError(RuntimeError):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("dense_min_size", ctypes.c_int32), ("dense_max_count", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("close_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class _WedgeStats(ctypes.Structure):
@@ -52,7 +52,9 @@ class _WedgeStats(ctypes.Structure):
 class _CloseStats(ctypes.Structure):
     _fields_ = [("probes", ctypes.c_uint64), ("gathers", ctypes.c_uint64),
                 ("out_entries", ctypes.c_uint64), ("teams", ctypes.c_uint64),
-                ("bucket_teams", ctypes.c_uint64 * 4)]
+                ("bucket_teams", ctypes.c_uint64 * 4), ("bucket_probes", ctypes.c_uint64 * 4),
+                ("bucket_gathers", ctypes.c_uint64 * 4),
+                ("bucket_out_entries", ctypes.c_uint64 * 4)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -200,9 +202,10 @@ def hg_load_csr(num_vertices: int, num_edges: int, edge_ptr, edge_vtx, stream: i
     return Graph(int(out.value), int(stream), int(num_vertices), int(num_edges), nnz)
 
 
-def hg_build_wedges(g: Graph, dense_min_size: int = 0, dense_max_count: int = 0) -> dict:
+def hg_build_wedges(g: Graph, dense_min_size: int = 0, dense_max_count: int = 0,
+                    close_mode: int = 0) -> dict:
     """Step one: hyperwedges, their types and the degree orientation; returns the stats."""
-    tun = _Tuning(int(dense_min_size), int(dense_max_count))
+    tun = _Tuning(int(dense_min_size), int(dense_max_count), int(close_mode))
     st = _WedgeStats()
     _check("hg_build_wedges",
            _lib.hg_build_wedges(ctypes.c_void_p(g.ptr), ctypes.byref(tun), ctypes.byref(st)))
@@ -236,7 +239,10 @@ def hg_close_stats_get(g: Graph) -> dict:
     _check("hg_close_stats_get", _lib.hg_close_stats_get(ctypes.c_void_p(g.ptr), ctypes.byref(st)))
     return {"probes": int(st.probes), "gathers": int(st.gathers),
             "out_entries": int(st.out_entries), "teams": int(st.teams),
-            "bucket_teams": [int(x) for x in st.bucket_teams]}
+            "bucket_teams": [int(x) for x in st.bucket_teams],
+            "bucket_probes": [int(x) for x in st.bucket_probes],
+            "bucket_gathers": [int(x) for x in st.bucket_gathers],
+            "bucket_out_entries": [int(x) for x in st.bucket_out_entries]}
 
 
 def hg_kernel_launches() -> int:

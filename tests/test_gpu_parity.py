@@ -120,3 +120,17 @@ def test_workload_golden(hglib, name):
     assert counts.tolist() == gold["counts"]
     for k in ("W", "W_c", "W_t", "connected", "open", "max_deg"):
         assert st[k] == gold[k], k
+
+
+@pytest.mark.parametrize("name", ["tiny_plain", "coauthor_prefix50k"])
+def test_counts_do_not_depend_on_team_shape(hglib, name):
+    # every hyperedge through the block kernel gives the same counts as the
+    # out-degree/size buckets of warp kernels
+    import hgen
+
+    gold = load_json("workloads.json")[name]
+    e_ptr, e_idx = hgen.generate(hgen.WORKLOADS[gold["workload"]])
+    if gold["prefix_edges"] is not None:
+        e_ptr, e_idx = hgen.prefix(e_ptr, e_idx, gold["prefix_edges"])
+    counts, _ = gpu_count(hglib, gold["num_vertices"], e_ptr, e_idx, close_mode=1)
+    assert counts.tolist() == gold["counts"]
