@@ -160,6 +160,40 @@ hg_status hg_close_stats_get(hg_graph* g, hg_close_stats* out);
 /* Process-wide number of kernel launches libhg has issued so far. */
 hg_status hg_kernel_launches(uint64_t* n);
 
+/*
+ * Line-graph degrees without allocating.  The paper has no counterpart: this is
+ * for callers that cannot allocate device memory while they run - code in a
+ * host function enqueued on a stream (which may not make allocating CUDA
+ * calls), or a service whose device memory is a fixed arena owned by someone
+ * else.  It computes what the count pass of hg_build_wedges computes, from
+ * buffers the caller owns:
+ *   num_edges            |E| >= 0
+ *   edge_ptr, edge_vtx   device hyperedge->vertex CSR (as for hg_load_csr; rows
+ *                        ascending, already valid - this call does not validate)
+ *   vertex_ptr,          device vertex->hyperedge CSR of the same hypergraph
+ *   vertex_edge          (vertex_ptr[|V|+1] int64, vertex_edge[nnz] int32, any order
+ *                        inside a list)
+ *   degrees              device int32[|E|] out: |N(e_i)|, hyperedges sharing a vertex
+ *                        with e_i
+ *   inclusion_wedges     device uint64 out: inclusion-type hyperwedges (Def. 2.3)
+ *   cuda_stream          stream for the work; the call synchronises it.
+ * Scratch is one file-scope device array of 32 MiB (128 tables of 32,768 slots)
+ * that every device which loads this code keeps until the process exits.  A
+ * hyperedge whose vertices lie in more than 16,384 other (hyperedge, vertex)
+ * incidences does not fit a table: the call returns HG_ERR_UNSUPPORTED (and
+ * degrees are then incomplete).  Equal hyperedges give HG_ERR_DUPLICATE_HYPEREDGE.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Calls share
+ * the array and its previous contents: the call clears what must start at zero,
+ * and two calls whose work overlaps on the same GPU (for example on two streams)
+ * race on the array and corrupt each other.  No cudaMalloc, cudaFree or
+ * allocating library call is made.
+ */
+hg_status hg_wedge_degrees_noalloc(int32_t num_edges, const int64_t* edge_ptr,
+                                   const int32_t* edge_vtx, const int64_t* vertex_ptr,
+                                   const int32_t* vertex_edge, int32_t* degrees,
+                                   unsigned long long* inclusion_wedges, void* cuda_stream);
+
 /* Release the handle and every device buffer it owns (stream-ordered). */
 hg_status hg_free(hg_graph* g);
 

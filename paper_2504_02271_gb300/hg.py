@@ -29,7 +29,8 @@ HG_OK = 0
 # every entry point declared in include/hg.h
 EXPORTED = ("hg_set_allocator", "hg_load_csr", "hg_build_wedges", "hg_count_patterns",
             "hg_clustering_coeff", "hg_free", "hg_status_str", "hg_set_timing", "hg_kernel_times",
-            "hg_pattern_table", "hg_close_stats_get", "hg_kernel_launches")
+            "hg_pattern_table", "hg_close_stats_get", "hg_kernel_launches",
+            "hg_wedge_degrees_noalloc")
 
 
 class HgError(RuntimeError):
@@ -84,6 +85,7 @@ def _open():
     lib.hg_pattern_table.argtypes = [vp]
     lib.hg_close_stats_get.argtypes = [vp, ctypes.POINTER(_CloseStats)]
     lib.hg_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
+    lib.hg_wedge_degrees_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp]
     for name in EXPORTED:
         if name != "hg_status_str":
             getattr(lib, name).restype = ctypes.c_int
@@ -250,6 +252,24 @@ def hg_kernel_launches() -> int:
     n = ctypes.c_uint64()
     _check("hg_kernel_launches", _lib.hg_kernel_launches(ctypes.byref(n)))
     return int(n.value)
+
+
+def hg_wedge_degrees_noalloc(num_edges: int, edge_ptr, edge_vtx, vertex_ptr, vertex_edge,
+                             degrees, inclusion_wedges, stream: int | None = None) -> None:
+    """Line-graph degrees and the inclusion-wedge count into caller-owned device tensors.
+
+    For callers that cannot allocate device memory while they run: every argument
+    is a device tensor the caller already holds (int64 edge_ptr / vertex_ptr,
+    int32 edge_vtx / vertex_edge / degrees[|E|], one int64 for inclusion_wedges);
+    the library uses only its own fixed 32 MiB device array.  See include/hg.h.
+    """
+    if stream is None:
+        stream = _default_stream()
+    _check("hg_wedge_degrees_noalloc",
+           _lib.hg_wedge_degrees_noalloc(int(num_edges), edge_ptr.data_ptr(), edge_vtx.data_ptr(),
+                                         vertex_ptr.data_ptr(), vertex_edge.data_ptr(),
+                                         degrees.data_ptr(), inclusion_wedges.data_ptr(),
+                                         ctypes.c_void_p(stream)))
 
 
 def hg_pattern_table() -> np.ndarray:
