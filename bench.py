@@ -192,6 +192,25 @@ def close_algorithmic(cs, b, T):
     return nbytes, ops
 
 
+# ------------------------------------------------------------------ multi-rank aggregation
+
+def aggregate(units: float, seconds: float, dist=None, device=None):
+    """Whole-job (units, seconds): units summed over ranks, time = slowest rank.
+
+    The ranks are independent replicas (no exchange step in the counting path), so
+    the job's throughput is all ranks' work over the time of the last one to finish.
+    """
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(units), float(seconds)
+    import torch
+
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()), float(t.item())
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args):
@@ -287,15 +306,7 @@ def run_ours(args):
     clk = clocks.stop()
     barrier()
 
-    total_s = sum(step_ms) / 1000.0
-    if dist is not None:
-        t = torch.tensor([total_s, float(tri)], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_s, tri_all = float(tmax[0]), float(t[1])
-    else:
-        tri_all = float(tri)
+    tri_all, total_s = aggregate(float(tri), sum(step_ms) / 1000.0, dist, dev)
     value = tri_all / total_s
 
     # end to end through the C ABI from pinned host buffers
@@ -310,12 +321,9 @@ def run_ours(args):
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
         assert c2.tolist() == counts.tolist()
-    e2e_s = sum(e2e_ms) / 1000.0
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t[0])
-    e2e_value = int(counts[0]) * len(e2e_ms) * world / e2e_s
+    e2e_units, e2e_s = aggregate(float(int(counts[0]) * len(e2e_ms)), sum(e2e_ms) / 1000.0, dist,
+                                 dev)
+    e2e_value = e2e_units / e2e_s
 
     if rank != 0:
         if dist is not None:
