@@ -333,6 +333,65 @@ hg_status load_impl(hg_graph* g, const int64_t* edge_ptr, const int32_t* edge_vt
   return HG_OK;
 }
 
+// Heavy x heavy hyperwedges on the tensor cores: choose the heavy set,
+// fill its 0/1 e4m3 matrix, multiply.  Leaves dn->heavy_idx null when not used.
+constexpr int64_t kDenseMinRows = 256;                  // below this a tile pass does not pay
+constexpr int64_t kDenseMaxBytes = int64_t(8) << 30;    // matrix + omega budget
+
+hg_status dense_impl(hg_graph* g, const hg_tuning* opt, DenseInfo* dn) {
+  cudaStream_t s = g->stream;
+  *dn = DenseInfo{};
+  const int32_t want = opt ? opt->dense_min_size : 0;
+  if (want < 0 || g->ne == 0) return HG_OK;
+  const bool forced = want > 0;
+  const int32_t min_size = forced ? want : 32;
+  const int64_t cap = (opt && opt->dense_max_count > 0) ? opt->dense_max_count
+                                                        : std::max<int64_t>(g->ne / 100, 1);
+  if (g->max_size < min_size) return HG_OK;
+  // size histogram -> smallest threshold >= min_size keeping at most `cap` hyperedges
+  const int32_t max_bin = std::min<int32_t>(g->max_size, 1 << 20);
+  unsigned long long* hist = alloc_t<unsigned long long>(g, g->build_blocks, (int64_t)max_bin + 1);
+  if (!hist) return HG_ERR_OOM;
+  HG_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * ((size_t)max_bin + 1), s));
+  launch_size_hist(g->esize, g->ne, max_bin, hist, s);
+  std::vector<unsigned long long> h((size_t)max_bin + 1);
+  HG_CUDA(cudaMemcpyAsync(h.data(), hist, sizeof(unsigned long long) * h.size(),
+                          cudaMemcpyDeviceToHost, s));
+  HG_CUDA(cudaStreamSynchronize(s));
+  int64_t above = 0;
+  int32_t t = max_bin + 1;
+  for (int32_t k = max_bin; k >= min_size; --k) {
+    if (above + (int64_t)h[k] > cap) break;
+    above += (int64_t)h[k];
+    t = k;
+  }
+  if (above == 0 || (!forced && above < kDenseMinRows)) return HG_OK;
+  const int64_t rows_pad = dense_round_rows(above), k_pad = dense_round_k(g->nv);
+  if (rows_pad * (k_pad + rows_pad) > kDenseMaxBytes) return HG_OK;   // stays on the hash path
+  int32_t* heavy_idx = alloc_t<int32_t>(g, g->build_blocks, g->ne);
+  int32_t* ids = alloc_t<int32_t>(g, g->build_blocks, above);
+  uint8_t* a = alloc_t<uint8_t>(g, g->build_blocks, rows_pad * k_pad);
+  uint8_t* omega = alloc_t<uint8_t>(g, g->build_blocks, rows_pad * rows_pad);
+  if (!heavy_idx || !ids || !a || !omega) return HG_ERR_OOM;
+  int32_t* count = g->small->counters + 8;
+  HG_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t), s));
+  HG_CUDA(cudaMemsetAsync(a, 0, (size_t)(rows_pad * k_pad), s));
+  launch_pick_heavy(g->esize, g->ne, t, (int32_t)above, heavy_idx, ids, count, s);
+  launch_fill_dense(g->e_ptr, g->e_idx, ids, (int32_t)above, a, k_pad, s);
+  t_begin(g, "dense_omega");
+  HG_CUDA(launch_dense_omega(a, above, rows_pad, k_pad, omega, &g->small->err, s));
+  t_end(g);
+  Small hs;
+  HG_TRY(sync_small(g, &hs));
+  if (hs.counters[8] != (int32_t)above) return HG_ERR_INTERNAL;
+  dn->heavy_idx = heavy_idx;
+  dn->ids = ids;
+  dn->omega = omega;
+  dn->ld = rows_pad;
+  dn->nh = (int32_t)above;
+  return HG_OK;
+}
+
 hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   g->close_mode = opt ? opt->close_mode : 0;
   if (g->close_mode < 0 || g->close_mode > 1) return HG_ERR_INVALID_ARG;
@@ -363,12 +422,14 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
     if (!scratch) return HG_ERR_OOM;
   }
   DevGraph d = dev_graph(g);
+  DenseInfo dn{};
+  HG_TRY(dense_impl(g, opt, &dn));
   HG_CUDA(cudaMemsetAsync(g->deg, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1), s));
   HG_CUDA(cudaMemsetAsync(g->ori.dplus, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1), s));
   HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
   t_begin(g, "wedge_count");
   launch_wedge_pass(0, d, wb, nb, g->max_cand, g->deg, &g->small->wc, g->ori, g->packed, scratch,
-                    &g->small->err, g->small->counters, s, g->nsm);
+                    &g->small->err, g->small->counters, dn, s, g->nsm);
   t_end(g);
   t_begin(g, "wedge_scan");
   scan_i32_to_i64(g->deg, g->ori.row_ptr, ne, g->scan_tmp, s);
@@ -390,7 +451,7 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
   t_begin(g, "wedge_emit");
   launch_wedge_pass(1, d, wb, nb, g->max_cand, g->deg, &g->small->wc, g->ori, g->packed, scratch,
-                    &g->small->err, g->small->counters, s, g->nsm);
+                    &g->small->err, g->small->counters, dn, s, g->nsm);
   reduce_deg_stats(g->ori.dplus, ne, g->small->out_stats, s);
   t_end(g);
   HG_TRY(sync_small(g, &h));
@@ -403,6 +464,7 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   st.connected = h.deg_stats[0];
   st.max_deg = h.deg_stats[1];
   st.max_out_deg = h.out_stats[1];
+  st.dense_edges = (uint64_t)dn.nh;
   if (h.deg_stats[2] != (unsigned long long)two_w || h.out_stats[2] != st.W || (two_w & 1))
     return HG_ERR_INTERNAL;
   g->built = true;

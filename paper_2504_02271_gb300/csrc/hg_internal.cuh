@@ -69,6 +69,26 @@ void launch_scatter(const DevGraph& g, int32_t* cursor, int32_t* v_idx, cudaStre
 void launch_candidates(const DevGraph& g, int64_t* cand, unsigned long long* max_cand,
                        int32_t* max_size, cudaStream_t s);
 
+// k_dense.cu: heavy x heavy omega on the tensor cores
+struct DenseInfo {
+  const int32_t* heavy_idx;   // [ne] position in the heavy list or -1; nullptr = no dense path
+  const int32_t* ids;         // [nh] hyperedge id of each heavy position
+  const uint8_t* omega;       // [rows_pad x rows_pad] omega of heavy pairs
+  int64_t ld;                 // row stride of omega
+  int32_t nh;
+};
+size_t dense_smem_bytes();
+int64_t dense_round_rows(int64_t n);
+int64_t dense_round_k(int64_t k);
+void launch_size_hist(const int32_t* esize, int32_t ne, int32_t max_bin, unsigned long long* hist,
+                      cudaStream_t s);
+void launch_pick_heavy(const int32_t* esize, int32_t ne, int32_t min_size, int32_t cap,
+                       int32_t* heavy_idx, int32_t* ids, int32_t* count, cudaStream_t s);
+void launch_fill_dense(const int64_t* e_ptr, const int32_t* e_idx, const int32_t* ids, int32_t nh,
+                       uint8_t* a, int64_t lda, cudaStream_t s);
+cudaError_t launch_dense_omega(const uint8_t* a, int64_t rows, int64_t rows_pad, int64_t k_pad,
+                               uint8_t* omega, int* err, cudaStream_t s);
+
 // k_wedge.cu
 struct WedgeBuckets {
   int32_t* rows[3];  // light (warp), medium (block, smem), heavy (block, global scratch)
@@ -81,7 +101,8 @@ int wedge_medium_max_cand();
 void launch_wedge_pass(int mode, const DevGraph& g, const WedgeBuckets& b, const int32_t* nb,
                        int64_t heavy_max_cand, int32_t* deg, unsigned long long* wc,
                        const Oriented& o, int packed, unsigned long long* scratch,
-                       int* err, int32_t* work_counter, cudaStream_t s, int nsm);
+                       int* err, int32_t* work_counter, const DenseInfo& dense, cudaStream_t s,
+                       int nsm);
 size_t wedge_heavy_scratch_bytes(int64_t heavy_max_cand, int nsm);
 
 // k_close.cu

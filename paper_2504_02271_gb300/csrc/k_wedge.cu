@@ -51,6 +51,32 @@ __device__ __forceinline__ void ht_add(unsigned long long* T, int cap_log2, uint
   }
 }
 
+// add omega pairs known in advance (heavy x heavy, from the tensor-core tiles)
+__device__ __forceinline__ void ht_add_n(unsigned long long* T, int cap_log2, uint32_t j,
+                                         uint32_t n) {
+  const uint32_t mask = (1u << cap_log2) - 1u;
+  uint32_t s = slot_of(j, cap_log2);
+  const unsigned long long key = (unsigned long long)j << 32;
+  while (true) {
+    unsigned long long cur = *((volatile unsigned long long*)&T[s]);
+    if (cur == kEmpty) {
+      cur = atomicCAS(&T[s], kEmpty, key | n);
+      if (cur == kEmpty) return;
+    }
+    if ((uint32_t)(cur >> 32) == j) {
+      atomicAdd(&T[s], (unsigned long long)n);
+      return;
+    }
+    s = (s + 1u) & mask;
+  }
+}
+
+// Row i of a heavy hyperedge: its heavy neighbours come from the dense tiles, so the
+// gather skips them; light rows (and a graph without a dense path) gather everything.
+__device__ __forceinline__ bool gather_pair(const DenseInfo& dn, int32_t hi, int32_t j) {
+  return hi < 0 || dn.heavy_idx[j] < 0;
+}
+
 __device__ __forceinline__ bool ranked_above(int32_t di, int32_t i, int32_t dj, int32_t j) {
   return di < dj || (di == dj && i < j);
 }
@@ -70,7 +96,7 @@ template <int MODE, bool PACKED>
 __global__ void __launch_bounds__(kLightWarps * 32)
     k_wedge_light(DevGraph g, const int32_t* __restrict__ rows, const int32_t* __restrict__ nrows_p,
                   int32_t* __restrict__ deg, unsigned long long* __restrict__ wc, Oriented o,
-                  int* __restrict__ err, int32_t* __restrict__ counter) {
+                  int* __restrict__ err, int32_t* __restrict__ counter, DenseInfo dn) {
   constexpr int CAP = 1 << kLightCapLog2;
   __shared__ unsigned long long tab[kLightWarps][CAP];
   __shared__ unsigned long long blk_wc;
@@ -88,13 +114,20 @@ __global__ void __launch_bounds__(kLightWarps * 32)
     const int32_t i = rows[r];
     for (int s = lane; s < CAP; s += 32) T[s] = kEmpty;
     __syncwarp();
+    const int32_t hi = dn.heavy_idx ? dn.heavy_idx[i] : -1;
     const int64_t b = g.e_ptr[i], e = g.e_ptr[i + 1];
     for (int64_t p = b; p < e; ++p) {
       const int32_t v = g.e_idx[p];
       const int64_t vb = g.v_ptr[v], ve = g.v_ptr[v + 1];
       for (int64_t q = vb + lane; q < ve; q += 32) {
         const int32_t j = g.v_idx[q];
-        if (j != i) ht_add(T, kLightCapLog2, (uint32_t)j);
+        if (j != i && gather_pair(dn, hi, j)) ht_add(T, kLightCapLog2, (uint32_t)j);
+      }
+    }
+    if (hi >= 0) {
+      for (int32_t h = lane; h < dn.nh; h += 32) {
+        const uint32_t om = dn.omega[(int64_t)hi * dn.ld + h];
+        if (om && h != hi) ht_add_n(T, kLightCapLog2, (uint32_t)dn.ids[h], om);
       }
     }
     __syncwarp();
@@ -152,7 +185,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     k_wedge_block(DevGraph g, const int32_t* __restrict__ rows, const int32_t* __restrict__ nrows_p,
                   int cap_log2, unsigned long long* __restrict__ gscratch,
                   int32_t* __restrict__ deg, unsigned long long* __restrict__ wc, Oriented o,
-                  int* __restrict__ err, int32_t* __restrict__ counter) {
+                  int* __restrict__ err, int32_t* __restrict__ counter, DenseInfo dn) {
   extern __shared__ unsigned long long dyn[];
   unsigned long long* T = SMEM ? dyn : gscratch + ((size_t)blockIdx.x << cap_log2);
   const uint32_t CAP = 1u << cap_log2;
@@ -176,13 +209,20 @@ __global__ void __launch_bounds__(kBlockThreads)
     const int32_t i = rows[r];
     for (uint32_t s = threadIdx.x; s < CAP; s += kBlockThreads) T[s] = kEmpty;
     __syncthreads();
+    const int32_t hi = dn.heavy_idx ? dn.heavy_idx[i] : -1;
     const int64_t b = g.e_ptr[i], e = g.e_ptr[i + 1];
     for (int64_t p = b + w; p < e; p += kWarps) {
       const int32_t v = g.e_idx[p];
       const int64_t vb = g.v_ptr[v], ve = g.v_ptr[v + 1];
       for (int64_t q = vb + lane; q < ve; q += 32) {
         const int32_t j = g.v_idx[q];
-        if (j != i) ht_add(T, cap_log2, (uint32_t)j);
+        if (j != i && gather_pair(dn, hi, j)) ht_add(T, cap_log2, (uint32_t)j);
+      }
+    }
+    if (hi >= 0) {
+      for (int32_t h = threadIdx.x; h < dn.nh; h += kBlockThreads) {
+        const uint32_t om = dn.omega[(int64_t)hi * dn.ld + h];
+        if (om && h != hi) ht_add_n(T, cap_log2, (uint32_t)dn.ids[h], om);
       }
     }
     __syncthreads();
@@ -264,15 +304,15 @@ int cap_log2_for(int64_t cand) {
 template <int MODE, bool PACKED>
 void launch_all(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb, int64_t heavy_max,
                 int32_t* deg, unsigned long long* wc, const Oriented& o,
-                unsigned long long* scratch, int* err, int32_t* counters, cudaStream_t s,
-                int nsm) {
+                unsigned long long* scratch, int* err, int32_t* counters, const DenseInfo& dn,
+                cudaStream_t s, int nsm) {
   // counters[0..2] are zeroed by the caller
   if (nb[0] > 0) {
     int blocks = (nb[0] + kLightWarps - 1) / kLightWarps;
     blocks = blocks < nsm * 4 ? blocks : nsm * 4;
     note_launch();
     k_wedge_light<MODE, PACKED><<<blocks, kLightWarps * 32, 0, s>>>(g, b.rows[0], b.count + 0, deg,
-                                                                    wc, o, err, counters + 0);
+                                                                    wc, o, err, counters + 0, dn);
   }
   if (nb[1] > 0) {
     const size_t smem = sizeof(unsigned long long) << kMediumCapLog2;
@@ -281,14 +321,14 @@ void launch_all(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb, int
     int blocks = nb[1] < nsm * 3 ? nb[1] : nsm * 3;
     note_launch();
     k_wedge_block<MODE, PACKED, true><<<blocks, kBlockThreads, smem, s>>>(
-        g, b.rows[1], b.count + 1, kMediumCapLog2, nullptr, deg, wc, o, err, counters + 1);
+        g, b.rows[1], b.count + 1, kMediumCapLog2, nullptr, deg, wc, o, err, counters + 1, dn);
   }
   if (nb[2] > 0) {
     int blocks = nb[2] < nsm * 2 ? nb[2] : nsm * 2;
     note_launch();
     k_wedge_block<MODE, PACKED, false><<<blocks, kBlockThreads, 0, s>>>(
         g, b.rows[2], b.count + 2, cap_log2_for(heavy_max), scratch, deg, wc, o, err,
-        counters + 2);
+        counters + 2, dn);
   }
 }
 
@@ -314,17 +354,21 @@ void launch_bucket_rows(const int64_t* cand, int32_t ne, WedgeBuckets b, cudaStr
 void launch_wedge_pass(int mode, const DevGraph& g, const WedgeBuckets& b, const int32_t* nb,
                        int64_t heavy_max_cand, int32_t* deg, unsigned long long* wc,
                        const Oriented& o, int packed, unsigned long long* scratch, int* err,
-                       int32_t* work_counter, cudaStream_t s, int nsm) {
+                       int32_t* work_counter, const DenseInfo& dn, cudaStream_t s, int nsm) {
   if (mode == 0) {
     if (packed)
-      launch_all<0, true>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, s, nsm);
+      launch_all<0, true>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, dn, s,
+                          nsm);
     else
-      launch_all<0, false>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, s, nsm);
+      launch_all<0, false>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, dn, s,
+                           nsm);
   } else {
     if (packed)
-      launch_all<1, true>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, s, nsm);
+      launch_all<1, true>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, dn, s,
+                          nsm);
     else
-      launch_all<1, false>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, s, nsm);
+      launch_all<1, false>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, dn, s,
+                           nsm);
   }
 }
 

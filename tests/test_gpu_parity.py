@@ -134,3 +134,53 @@ def test_counts_do_not_depend_on_team_shape(hglib, name):
         e_ptr, e_idx = hgen.prefix(e_ptr, e_idx, gold["prefix_edges"])
     counts, _ = gpu_count(hglib, gold["num_vertices"], e_ptr, e_idx, close_mode=1)
     assert counts.tolist() == gold["counts"]
+
+
+def big_hyperedges(seed, ne, nv, lo, hi):
+    import hgen
+
+    spec = hgen.HypergraphSpec(nv, ne, seed, hgen.SIZE_UNIFORM, lo, hi, zipf_s=0.6, name="big")
+    return spec, *hgen.generate(spec)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_dense_tiles_match_oracle(hglib, seed):
+    # every hyperedge heavy: all omega come from the tensor-core tiles
+    import oracle
+
+    spec, e_ptr, e_idx = big_hyperedges(seed, 400, 4000, 40, 100)
+    counts, st = gpu_count(hglib, spec.num_vertices, e_ptr, e_idx, dense_min_size=40,
+                           dense_max_count=1000)
+    assert st["dense_edges"] == 400
+    ref = oracle.count(e_ptr, e_idx, spec.num_vertices)
+    assert counts.tolist() == [int(x) for x in ref.counts]
+    assert (st["W"], st["W_c"], st["connected"]) == (ref.W, ref.W_c, ref.connected)
+
+
+def test_dense_tiles_mixed_heavy_and_light(hglib):
+    # part of the hyperedges heavy: heavy x heavy from tiles, the rest hashed
+    import hgen
+
+    spec = hgen.HypergraphSpec(2000, 3000, 11, hgen.SIZE_LOGNORMAL, 2, 160, size_p1=2.5,
+                               size_p2=1.0, zipf_s=0.9, name="mixed")
+    e_ptr, e_idx = hgen.generate(spec)
+    off, st_off = gpu_count(hglib, spec.num_vertices, e_ptr, e_idx, dense_min_size=-1)
+    on, st_on = gpu_count(hglib, spec.num_vertices, e_ptr, e_idx, dense_min_size=24,
+                          dense_max_count=700)
+    assert st_off["dense_edges"] == 0 and 256 <= st_on["dense_edges"] <= 700
+    assert on.tolist() == off.tolist()
+    for k in ("W", "W_c", "connected", "max_deg", "open"):
+        assert st_on[k] == st_off[k], k
+
+
+def test_dense_tiles_tag_heavy_prefix(hglib):
+    import hgen
+
+    gold = load_json("workloads.json")["tag_heavy_prefix2000"]
+    e_ptr, e_idx = hgen.generate(hgen.TAG_HEAVY)
+    e_ptr, e_idx = hgen.prefix(e_ptr, e_idx, 2000)
+    counts, st = gpu_count(hglib, gold["num_vertices"], e_ptr, e_idx, dense_min_size=20,
+                           dense_max_count=1200)
+    assert st["dense_edges"] > 0
+    assert counts.tolist() == gold["counts"]
+    assert (st["W"], st["W_c"], st["connected"]) == (gold["W"], gold["W_c"], gold["connected"])
