@@ -49,6 +49,10 @@ def parse_args():
     ap.add_argument("--cpu-sample-edges", type=int, default=8000,
                     help="hyperedges whose owned triangles the CPU baseline counts")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--dense-min-size", type=int, default=0,
+                    help="hyperedges at least this large use the tensor-core tiles (0 auto, -1 off)")
+    ap.add_argument("--dense-max-count", type=int, default=0,
+                    help="cap on the tensor-core set (0 = 1%% of |E|)")
     return ap.parse_args()
 
 
@@ -148,6 +152,14 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def measured_tensor_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
 def source_sha(path):
     with open(path, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
@@ -171,7 +183,8 @@ def profiled_traffic(kernel, workload_name):
 
 
 # team shape of each closure kernel group -> index of its work counters
-CLOSE_GROUPS = {"close_warp256": 0, "close_warp512": 1, "close_warp1024": 2, "close_wide": 3}
+CLOSE_GROUPS = {"close_warp256": 0, "close_warp512": 1, "close_warp1024": 2, "close_block2048": 3,
+                "close_block8192": 4, "close_wide": 5}
 ISSUE_LANE_OPS_PER_CYCLE_PER_SM = 4 * 32   # 4 schedulers, one 32-lane instruction per cycle
 
 
@@ -252,7 +265,8 @@ def run_ours(args):
         try:
             if timing:
                 hg.hg_set_timing(g, True)
-            st = hg.hg_build_wedges(g)
+            st = hg.hg_build_wedges(g, dense_min_size=args.dense_min_size,
+                                    dense_max_count=args.dense_max_count)
             counts = hg.hg_count_patterns(g)
             cc = hg.hg_clustering_coeff(g, ones)
             kt = hg.hg_kernel_times(g) if timing else {}
@@ -341,7 +355,7 @@ def run_ours(args):
     achieved_ops = ops / (dom_ms / 1000.0) / 1e12
     achieved_gbs = nbytes / (dom_ms / 1000.0) / 1e9
     traffic = profiled_traffic(dom, cfg["workload"])
-    roof = {"bound": "alu", "kernel": f"{dom} (k_close_warp / k_close_wide)",
+    roof = {"bound": "alu", "kernel": f"{dom} (k_close_warp / k_close_block / k_close_wide)",
             "achieved": round(achieved_ops, 3), "peak": round(peak_ops, 2), "unit": "Tops/s",
             "frac": round(achieved_ops / peak_ops, 4),
             "peak_source": f"derived: 152 SMs x 128 lane-ops/cycle x {sm_mhz:.0f} MHz (median SM clock under load)",
@@ -349,6 +363,22 @@ def run_ours(args):
             "launch_ms": round(dom_ms, 4), "traffic": traffic,
             "hbm": {"achieved": round(achieved_gbs, 1), "peak": peak_hbm, "unit": "GB/s",
                     "frac": round(achieved_gbs / peak_hbm, 4), "peak_source": peak_kind}}
+
+    dense = None
+    if "dense_omega" in kernel_ms and st["dense_edges"]:
+        # algorithmic work of the tile product: 2 * nh * nh * |V| (multiply-adds of A A^T)
+        nh = st["dense_edges"]
+        flops = 2.0 * nh * nh * nv
+        d_ms = kernel_ms["dense_omega"][0] / kernel_ms["dense_omega"][1]
+        bf16 = measured_tensor_peak()
+        peak = bf16 * 2.0   # e4m3 dense rate = 2x bf16 (4.5 vs 2.25 PFLOP/s nominal)
+        ach = flops / (d_ms / 1000.0) / 1e12
+        dense = {"bound": "tensor", "kernel": "dense_omega (k_dense_omega, tcgen05 kind::f8f6f4)",
+                 "achieved": round(ach, 1), "peak": round(peak, 1), "unit": "TFLOP/s",
+                 "frac": round(ach / peak, 4),
+                 "peak_source": "measured bf16 burst x 2 (nominal e4m3/bf16 ratio)",
+                 "rows": nh, "k": nv, "launch_ms": round(d_ms, 4),
+                 "traffic": profiled_traffic("dense_omega", cfg["workload"])}
 
     cpu = None
     if world == 1 and not args.skip_cpu_baseline:
@@ -362,12 +392,15 @@ def run_ours(args):
         "config": dict(cfg, triangles_per_step=int(counts[0]), wedges=st["W"],
                        l2="256 MiB buffer written between steps, outside the per-step events",
                        inputs="int64/int32 CSR resident in HBM", parallelism=f"replicas x{world}",
-                       parity="counts equal stored oracle values" if parity else "not checked"),
+                       parity="counts equal stored oracle values" if parity else "not checked",
+                       dense_tiles={"min_size": args.dense_min_size, "max_count": args.dense_max_count,
+                                    "hyperedges": st["dense_edges"]}),
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
                 "h2d_bytes_per_step": int(e_ptr.nbytes + e_idx.nbytes),
                 "d2h_bytes_per_step": 21 * 8 + 8 * 8,
                 "ms_per_step": round(statistics.mean(e2e_ms), 4)},
         "roofline": roof,
+        "dense_roofline": dense,
         "kernel_ms_per_step": {n: round(v[0] / args.steps, 4) for n, v in sorted(kernel_ms.items())},
         "gpu_launches": int(launches),
         "clocks": clk,

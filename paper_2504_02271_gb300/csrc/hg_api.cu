@@ -38,7 +38,7 @@ struct Small {
   int err;
   int32_t pad0;
   int32_t counters[16];       // work-fetch counters
-  int32_t bucket_count[8];    // [0..2] wedge buckets, [4..7] close buckets
+  int32_t bucket_count[16];   // [0..2] wedge buckets, [3] handed-over teams, [4..9] close buckets
   unsigned long long wc;      // inclusion-type wedges
   unsigned long long max_cand;
   int32_t max_size;
@@ -47,7 +47,7 @@ struct Small {
   unsigned long long out_stats[3];   // sum C(d+,2), max d+, sum d+
   unsigned long long wide_max[2];    // close bucket 3: max d+, max |e_u|
   unsigned long long hist[24];       // pattern histogram (bin 0 = unclassifiable)
-  unsigned long long work[4][3];     // closure per team shape: probes, E_y entries, out-entries
+  unsigned long long work[kCloseBuckets][3];   // closure per team shape: probes, E_y entries, out-entries
 };
 
 struct KTime {
@@ -478,9 +478,9 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   g->counted = false;
   const int64_t ne = g->ne;
   Small h;
-  int32_t* lists = alloc_t<int32_t>(g, g->count_blocks, 5 * ne);   // 4 buckets + overflow
+  int32_t* lists = alloc_t<int32_t>(g, g->count_blocks, (kCloseBuckets + 1) * ne);  // + overflow
   if (!lists) return HG_ERR_OOM;
-  HG_CUDA(cudaMemsetAsync(g->small->bucket_count + 3, 0, sizeof(int32_t) * 5, s));
+  HG_CUDA(cudaMemsetAsync(g->small->bucket_count + 3, 0, sizeof(int32_t) * (1 + kCloseBuckets), s));
   HG_CUDA(cudaMemsetAsync(g->small->wide_max, 0, sizeof(g->small->wide_max), s));
   HG_CUDA(cudaMemsetAsync(g->small->hist, 0, sizeof(g->small->hist), s));
   HG_CUDA(cudaMemsetAsync(g->small->work, 0, sizeof(g->small->work), s));
@@ -489,9 +489,9 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   build_lut(lut);
   close_set_lut(lut, s);
   CloseBuckets cb;
-  for (int k = 0; k < 4; ++k) cb.lists[k] = lists + k * ne;
+  for (int k = 0; k < kCloseBuckets; ++k) cb.lists[k] = lists + k * ne;
   cb.count = g->small->bucket_count + 4;
-  int32_t* overflow = lists + 4 * ne;
+  int32_t* overflow = lists + kCloseBuckets * ne;
   int32_t* n_overflow = g->small->bucket_count + 3;
   DevGraph d = dev_graph(g);
   t_begin(g, "close_bucket");
@@ -500,8 +500,8 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
                       g->close_mode == 1 || g->max_size >= 65536, s);
   t_end(g);
   HG_TRY(sync_small(g, &h));
-  int32_t n[4];
-  for (int k = 0; k < 4; ++k) n[k] = h.bucket_count[4 + k];
+  int32_t n[kCloseBuckets];
+  for (int k = 0; k < kCloseBuckets; ++k) n[k] = h.bucket_count[4 + k];
   // block-kernel scratch: any out-degree and |e_u| of bucket 3, and the warp
   // buckets' limits (out-degree 256, |e_u| 32) for hyperedges they hand over
   const int64_t dmax = std::max<int64_t>((int64_t)h.wide_max[0], 256);
@@ -510,8 +510,10 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   while (cap < 4 * dmax) cap *= 2;
   void* scratch = dev_alloc(g, g->count_blocks, close_wide_scratch_bytes(cap, words, dmax, g->nsm));
   if (!scratch) return HG_ERR_OOM;
-  static const char* names[4] = {"close_warp256", "close_warp512", "close_warp1024", "close_wide"};
-  for (int k = 3; k >= 0; --k) {
+  static const char* names[kCloseBuckets] = {"close_warp256",   "close_warp512",
+                                             "close_warp1024",  "close_block2048",
+                                             "close_block8192", "close_wide"};
+  for (int k = kCloseBuckets - 1; k >= 0; --k) {
     if (n[k] <= 0) continue;
     t_begin(g, names[k]);
     launch_close(k, d, g->ori, g->packed, cb.lists[k], n[k], cb.count + k, cap, words, dmax,
@@ -523,9 +525,9 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   const int32_t n_over = h.bucket_count[3];
   if (n_over > 0) {
     t_begin(g, "close_wide");
-    launch_close(3, d, g->ori, g->packed, overflow, n_over, n_overflow, cap, words, dmax, scratch,
-                 g->small->hist, g->small->work[3], g->small->counters + 4, overflow, n_overflow, s,
-                 g->nsm);
+    launch_close(kWideBucket, d, g->ori, g->packed, overflow, n_over, n_overflow, cap, words, dmax,
+                 scratch, g->small->hist, g->small->work[kWideBucket], g->small->counters + 8,
+                 overflow, n_overflow, s, g->nsm);
     t_end(g);
     HG_TRY(sync_small(g, &h));
   }
@@ -540,7 +542,7 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   }
   g->counts[0] = total;
   std::memset(&g->cstats, 0, sizeof(g->cstats));
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < kCloseBuckets; ++k) {
     g->cstats.bucket_probes[k] = h.work[k][0];
     g->cstats.bucket_gathers[k] = h.work[k][1];
     g->cstats.bucket_out_entries[k] = h.work[k][2];
@@ -548,9 +550,11 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
     g->cstats.gathers += h.work[k][1];
     g->cstats.out_entries += h.work[k][2];
   }
-  g->cstats.teams = (uint64_t)n[0] + n[1] + n[2] + n[3];
-  for (int k = 0; k < 4; ++k) g->cstats.bucket_teams[k] = (uint64_t)n[k];
-  g->cstats.bucket_teams[3] += (uint64_t)n_over;   // handed from the warp kernels
+  for (int k = 0; k < kCloseBuckets; ++k) {
+    g->cstats.bucket_teams[k] = (uint64_t)n[k];
+    g->cstats.teams += (uint64_t)n[k];
+  }
+  g->cstats.bucket_teams[kWideBucket] += (uint64_t)n_over;   // handed from the warp kernels
   g->counted = true;
   if (counts) std::memcpy(counts, g->counts, sizeof(g->counts));
   return HG_OK;

@@ -106,9 +106,13 @@ void launch_wedge_pass(int mode, const DevGraph& g, const WedgeBuckets& b, const
 size_t wedge_heavy_scratch_bytes(int64_t heavy_max_cand, int nsm);
 
 // k_close.cu
+// close team shapes: warp teams (out-degree <= 64, 128, 256), block teams with shared
+// tables (<= 1024, <= 4096), block teams with global scratch (the rest)
+constexpr int kCloseBuckets = 6;
+constexpr int kWideBucket = 5;
 struct CloseBuckets {
-  int32_t* lists[4];  // warp cap 256, warp cap 512, warp cap 1024, block (global scratch)
-  int32_t* count;     // [4]
+  int32_t* lists[kCloseBuckets];
+  int32_t* count;     // [kCloseBuckets]
 };
 // all_block: send every hyperedge to the block kernel (bucket 3)
 void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,

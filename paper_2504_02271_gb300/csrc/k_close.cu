@@ -307,6 +307,263 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
   }
 }
 
+// ------------------------------------------------------------------ block per u (shared tables)
+//
+// One block owns one hyperedge u with |e_u| <= 32 and out-degree <= D.  The hash
+// set of out(u) (load factor <= 1/2) maps a key to its index k in out(u); per-k
+// arrays hold the Omega_ux mask, |e_x| and the place and length of out(x).  The
+// flat range of all out(v) entries is cut into WARPS slices of equal length (by a
+// prefix sum over the out-degrees); each warp walks its slice like the warp
+// kernel (32 consecutive entries per load, filter, queue, 32-wide
+// classification).
+
+template <int D_LOG2, int WARPS, bool PACKED>
+struct BlockTables {
+  static constexpr int D = 1 << D_LOG2;
+  static constexpr int CAP = 2 * D;
+  static constexpr int FWORDS = D / 2;
+  int32_t key[CAP];
+  uint16_t kidx[CAP];
+  uint32_t filt[FWORDS];
+  int64_t kbeg[D];
+  int32_t kcnt[D];
+  int32_t kpre[D + 1];       // exclusive prefix of kcnt
+  uint32_t kmask[D];
+  uint16_t ksz[D];
+  uint32_t queue[WARPS][kQueue];   // hits: (k_v << 16) | k_w ; omega in qom
+  uint8_t qom8[PACKED ? WARPS : 1][PACKED ? kQueue : 1];
+  int32_t qom[PACKED ? 1 : WARPS][PACKED ? 1 : kQueue];
+  int64_t ylen[32], yincl[32], ybeg[32];
+  int32_t u, du, szu;
+};
+
+template <int D_LOG2, int WARPS, bool PACKED>
+__device__ __forceinline__ int block_find(const BlockTables<D_LOG2, WARPS, PACKED>& t, int32_t x) {
+  constexpr int CAP = BlockTables<D_LOG2, WARPS, PACKED>::CAP;
+  uint32_t s = slot_of((uint32_t)x, D_LOG2 + 1);
+  int32_t kk;
+  while ((kk = t.key[s]) != x && kk != -1) s = (s + 1) & (CAP - 1);
+  return kk == x ? (int)t.kidx[s] : -1;
+}
+
+template <int D_LOG2, int WARPS, bool PACKED>
+__global__ void __launch_bounds__(WARPS * 32, 1)
+    k_close_block(DevGraph g, Oriented o, const int32_t* __restrict__ list,
+                  const int32_t* __restrict__ n_p, unsigned long long* __restrict__ hist_out,
+                  unsigned long long* __restrict__ work, int32_t* __restrict__ counter) {
+  using TT = BlockTables<D_LOG2, WARPS, PACKED>;
+  constexpr int CAP = TT::CAP, CAP_LOG2 = D_LOG2 + 1, FB_LOG2 = D_LOG2 + 4;
+  constexpr int NT = WARPS * 32;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  TT& t = *reinterpret_cast<TT*>(dyn_smem);
+  __shared__ uint32_t hist[WARPS][kBins];
+  __shared__ uint8_t lut[128];
+  __shared__ int32_t s_r;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = threadIdx.x; k < 128; k += NT) lut[k] = c_lut[k];
+  for (int k = threadIdx.x; k < WARPS * kBins; k += NT) (&hist[0][0])[k] = 0;
+  const int32_t n = *n_p;
+  RunHist rh;
+  unsigned long long probes = 0, gathers = 0, outs = 0, since_flush = 0;
+
+  while (true) {
+    __syncthreads();
+    if (since_flush > (1ull << 30)) {   // keep the 32-bit bins far from overflow
+      rh.flush(hist[w]);
+      __syncthreads();
+      for (int k = threadIdx.x; k < kBins; k += NT) {
+        unsigned long long x = 0;
+        for (int ww = 0; ww < WARPS; ++ww) {
+          x += hist[ww][k];
+          hist[ww][k] = 0;
+        }
+        if (x) atomicAdd(&hist_out[k], x);
+      }
+      since_flush = 0;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) s_r = atomicAdd(counter, 1);
+    __syncthreads();
+    const int32_t r = s_r;
+    if (r >= n) break;
+    const int32_t u = list[r];
+    const int32_t du = o.dplus[u];
+    const int64_t bu = o.row_ptr[u];
+    const int64_t eb = g.e_ptr[u];
+    const int32_t szu = (int32_t)(g.e_ptr[u + 1] - eb);
+    for (int s = threadIdx.x; s < CAP; s += NT) t.key[s] = -1;
+    for (int s = threadIdx.x; s < TT::FWORDS; s += NT) t.filt[s] = 0;
+    if (w == 0) {   // E_y ranges of the vertices of e_u and their prefix sums
+      int64_t yb = 0, len = 0;
+      if (lane < szu) {
+        const int32_t y = __ldg(g.e_idx + eb + lane);
+        yb = __ldg(g.v_ptr + y);
+        len = __ldg(g.v_ptr + y + 1) - yb;
+      }
+      int64_t incl = len;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int64_t o2 = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += o2;
+      }
+      t.ylen[lane] = len;
+      t.yincl[lane] = incl;
+      t.ybeg[lane] = yb;
+    }
+    __syncthreads();
+    // 1. out(u) into the table and the filter
+    for (int k = threadIdx.x; k < du; k += NT) {
+      int32_t x, om;
+      get_entry<PACKED>(o, bu + k, x, om);
+      uint32_t s = slot_of((uint32_t)x, CAP_LOG2);
+      while (atomicCAS(&t.key[s], -1, x) != -1) s = (s + 1) & (CAP - 1);
+      t.kidx[s] = (uint16_t)k;
+      const uint32_t fb = filt_bit((uint32_t)x, FB_LOG2);
+      atomicOr(&t.filt[fb >> 5], 1u << (fb & 31));
+      t.kbeg[k] = __ldg(o.row_ptr + x);
+      t.kcnt[k] = __ldg(o.dplus + x);
+      t.ksz[k] = (uint16_t)__ldg(g.esize + x);
+      t.kmask[k] = 0;
+    }
+    __syncthreads();
+    // 2. Omega_ux masks over the flat E_y range; prefix of the out-degrees (warp 0)
+    {
+      const int64_t total = t.yincl[31];
+      if (threadIdx.x == 0) gathers += (unsigned long long)total;
+      for (int64_t f = threadIdx.x; f < total; f += NT) {
+        int lo = 0, hi = 31;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (t.yincl[mid] > f) hi = mid; else lo = mid + 1;
+        }
+        const int p = lo;
+        const int32_t x = __ldg(g.v_idx + t.ybeg[p] + (f - (t.yincl[p] - t.ylen[p])));
+        const uint32_t fb = filt_bit((uint32_t)x, FB_LOG2);
+        if (!((t.filt[fb >> 5] >> (fb & 31)) & 1u)) continue;
+        const int k = block_find(t, x);
+        if (k >= 0) atomicOr(&t.kmask[k], 1u << p);
+      }
+    }
+    if (w == 0) {
+      int32_t run = 0;
+      for (int k0 = 0; k0 < du; k0 += 32) {
+        const int k = k0 + lane;
+        const int32_t c = k < du ? t.kcnt[k] : 0;
+        int32_t incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int32_t o2 = __shfl_up_sync(kFull, incl, d);
+          if (lane >= d) incl += o2;
+        }
+        if (k < du) t.kpre[k] = run + incl - c;
+        run += __shfl_sync(kFull, incl, 31);
+      }
+      if (lane == 0) t.kpre[du] = run;
+    }
+    __syncthreads();
+    const int32_t F = t.kpre[du];
+    since_flush += (unsigned long long)F;   // the same on every thread
+    if (threadIdx.x == 0) {
+      probes += (unsigned long long)F;
+      outs += (unsigned long long)du;
+    }
+    // 3. closure: warp w walks the flat slice [F*w/WARPS, F*(w+1)/WARPS)
+    const int32_t f_lo = (int32_t)((int64_t)F * w / WARPS), f_hi = (int32_t)((int64_t)F * (w + 1) / WARPS);
+    int qn = 0;
+    uint32_t* queue = t.queue[w];
+    // cursor of this lane: first entry f_lo + lane -> (ck, cj)
+    int ck = 0, cj = 0, ccnt = 0;
+    int64_t cb = 0;
+    {
+      const int32_t f0 = f_lo + lane;
+      int lo = 0, hi = du;   // last k with kpre[k] <= f0
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.kpre[mid] <= f0) lo = mid; else hi = mid - 1;
+      }
+      ck = lo;
+      if (f0 >= f_hi || ck >= du) {
+        ck = du;
+      } else {
+        cj = f0 - t.kpre[ck];
+        ccnt = t.kcnt[ck];
+        cb = t.kbeg[ck];
+      }
+    }
+    for (int32_t base = f_lo; base < f_hi; base += 32 * kUnroll) {
+      int32_t ent_w[kUnroll], ent_om[kUnroll], ent_k[kUnroll];
+#pragma unroll
+      for (int q = 0; q < kUnroll; ++q) {
+        ent_k[q] = ck;
+        ent_w[q] = -1;
+        ent_om[q] = 0;
+        if (ck < du && base + q * 32 + lane < f_hi) get_entry<PACKED>(o, cb + cj, ent_w[q], ent_om[q]);
+        cj += 32;
+        while (cj >= ccnt && ck < du) {
+          cj -= ccnt;
+          if (++ck < du) {
+            ccnt = t.kcnt[ck];
+            cb = t.kbeg[ck];
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kUnroll; ++q) {
+        const int32_t x = ent_w[q];
+        int kw = -1;
+        if (x >= 0) {
+          const uint32_t fb = filt_bit((uint32_t)x, FB_LOG2);
+          if ((t.filt[fb >> 5] >> (fb & 31)) & 1u) kw = block_find(t, x);
+        }
+        const bool hit = kw >= 0;
+        const unsigned bal = __ballot_sync(kFull, hit);
+        if (hit) {
+          const int at = qn + __popc(bal & ((1u << lane) - 1u));
+          queue[at] = ((uint32_t)ent_k[q] << 16) | (uint32_t)kw;
+          if (PACKED) t.qom8[w][at] = (uint8_t)ent_om[q];
+          else t.qom[w][at] = ent_om[q];
+        }
+        qn += __popc(bal);
+      }
+      __syncwarp();
+      while (qn >= 32) {
+        qn -= 32;
+        const int at = qn + lane;
+        const uint32_t e = queue[at];
+        const uint32_t kv = e >> 16, kw = e & 0xffffu;
+        const int om = PACKED ? (int)t.qom8[w][at] : t.qom[w][at];
+        const uint32_t muv = t.kmask[kv], muw = t.kmask[kw];
+        const int gg = __popc(muv & muw);
+        rh.add(lut[region_bits(szu, t.ksz[kv], t.ksz[kw], __popc(muv), __popc(muw), om, gg)],
+               hist[w]);
+        __syncwarp();
+      }
+    }
+    if (lane < qn) {
+      const uint32_t e = queue[lane];
+      const uint32_t kv = e >> 16, kw = e & 0xffffu;
+      const int om = PACKED ? (int)t.qom8[w][lane] : t.qom[w][lane];
+      const uint32_t muv = t.kmask[kv], muw = t.kmask[kw];
+      const int gg = __popc(muv & muw);
+      rh.add(lut[region_bits(szu, t.ksz[kv], t.ksz[kw], __popc(muv), __popc(muw), om, gg)],
+             hist[w]);
+    }
+    __syncwarp();
+  }
+  rh.flush(hist[w]);
+  __syncthreads();
+  for (int k = threadIdx.x; k < kBins; k += NT) {
+    unsigned long long x = 0;
+    for (int ww = 0; ww < WARPS; ++ww) x += hist[ww][k];
+    if (x) atomicAdd(&hist_out[k], x);
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(&work[0], probes);
+    atomicAdd(&work[1], gathers);
+    atomicAdd(&work[2], outs);
+  }
+}
+
 // ------------------------------------------------------------------ block per u (wide)
 // Any |e_u| (masks of `words` 32-bit words) and any out-degree; tables in global scratch.
 
@@ -469,19 +726,21 @@ __global__ void k_bucket_close(DevGraph g, Oriented o, CloseBuckets b,
       const int32_t d = o.dplus[u];
       const int32_t sz = g.esize[u];
       if (d >= 2) {
-        if (all_block) bucket = 3;
+        if (all_block) bucket = kWideBucket;
         else if (sz <= kWarpMaskBits && d <= 64) bucket = 0;
         else if (sz <= kWarpMaskBits && d <= 128) bucket = 1;
         else if (sz <= kWarpMaskBits && d <= 256) bucket = 2;
-        else bucket = 3;
-        if (bucket == 3) {
+        else if (sz <= kWarpMaskBits && d <= 1024) bucket = 3;
+        else if (sz <= kWarpMaskBits && d <= 4096) bucket = 4;
+        else bucket = kWideBucket;
+        if (bucket == kWideBucket) {
           my_d = (unsigned long long)d > my_d ? (unsigned long long)d : my_d;
           my_s = (unsigned long long)sz > my_s ? (unsigned long long)sz : my_s;
         }
       }
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < kCloseBuckets; ++k) {
       const unsigned bal = __ballot_sync(kFull, bucket == k);
       if (!bal) continue;
       int32_t at = 0;
@@ -526,6 +785,31 @@ void launch_warp(const DevGraph& g, const Oriented& o, int packed, const int32_t
                                         n_overflow, s, nsm);
 }
 
+template <int D_LOG2, int WARPS, bool PACKED>
+void launch_block_t(const DevGraph& g, const Oriented& o, const int32_t* list, int32_t n,
+                    const int32_t* n_p, unsigned long long* hist, unsigned long long* work,
+                    int32_t* counter, cudaStream_t s, int nsm) {
+  auto kern = k_close_block<D_LOG2, WARPS, PACKED>;
+  const int smem = (int)sizeof(BlockTables<D_LOG2, WARPS, PACKED>);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
+  if (per_sm < 1) per_sm = 1;
+  int blocks = n < per_sm * nsm ? n : per_sm * nsm;
+  note_launch();
+  kern<<<blocks, WARPS * 32, smem, s>>>(g, o, list, n_p, hist, work, counter);
+}
+
+template <int D_LOG2, int WARPS>
+void launch_block(const DevGraph& g, const Oriented& o, int packed, const int32_t* list, int32_t n,
+                  const int32_t* n_p, unsigned long long* hist, unsigned long long* work,
+                  int32_t* counter, cudaStream_t s, int nsm) {
+  if (packed)
+    launch_block_t<D_LOG2, WARPS, true>(g, o, list, n, n_p, hist, work, counter, s, nsm);
+  else
+    launch_block_t<D_LOG2, WARPS, false>(g, o, list, n, n_p, hist, work, counter, s, nsm);
+}
+
 }  // namespace
 
 void close_set_lut(const uint8_t lut[128], cudaStream_t s) {
@@ -564,6 +848,12 @@ void launch_close(int bucket, const DevGraph& g, const Oriented& o, int packed,
     case 2:
       launch_warp<8, 4>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow, s,
                         nsm);
+      break;
+    case 3:
+      launch_block<10, 16>(g, o, packed, list, n, n_p, hist, work, counter, s, nsm);
+      break;
+    case 4:
+      launch_block<12, 16>(g, o, packed, list, n, n_p, hist, work, counter, s, nsm);
       break;
     default: {
       int blocks = n < nsm * 2 ? n : nsm * 2;

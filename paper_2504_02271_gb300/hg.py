@@ -53,9 +53,9 @@ class _WedgeStats(ctypes.Structure):
 class _CloseStats(ctypes.Structure):
     _fields_ = [("probes", ctypes.c_uint64), ("gathers", ctypes.c_uint64),
                 ("out_entries", ctypes.c_uint64), ("teams", ctypes.c_uint64),
-                ("bucket_teams", ctypes.c_uint64 * 4), ("bucket_probes", ctypes.c_uint64 * 4),
-                ("bucket_gathers", ctypes.c_uint64 * 4),
-                ("bucket_out_entries", ctypes.c_uint64 * 4)]
+                ("bucket_teams", ctypes.c_uint64 * 6), ("bucket_probes", ctypes.c_uint64 * 6),
+                ("bucket_gathers", ctypes.c_uint64 * 6),
+                ("bucket_out_entries", ctypes.c_uint64 * 6)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

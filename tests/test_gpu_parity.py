@@ -184,3 +184,16 @@ def test_dense_tiles_tag_heavy_prefix(hglib):
     assert st["dense_edges"] > 0
     assert counts.tolist() == gold["counts"]
     assert (st["W"], st["W_c"], st["connected"]) == (gold["W"], gold["W_c"], gold["connected"])
+
+
+def test_block_teams_with_shared_tables(hglib):
+    # out-degrees of several hundred to a few thousand: block teams with shared tables
+    # (<= 1024 and <= 4096) against block teams with global tables (close_mode=1)
+    import hgen
+
+    spec = hgen.HypergraphSpec(40, 6000, 21, hgen.SIZE_UNIFORM, 3, 5, zipf_s=0.4, name="dense_small")
+    e_ptr, e_idx = hgen.generate(spec)
+    shared, st = gpu_count(hglib, spec.num_vertices, e_ptr, e_idx)
+    glob, _ = gpu_count(hglib, spec.num_vertices, e_ptr, e_idx, close_mode=1)
+    assert st["max_out_deg"] > 1024
+    assert shared.tolist() == glob.tolist()
