@@ -75,6 +75,13 @@ def _load():
         lib.oracle_pattern_of_mask.restype = ctypes.c_int
         lib.oracle_pattern_table_ok.restype = ctypes.c_int
         lib.oracle_max_threads.restype = ctypes.c_int
+        lib.oracle_philox4x32_10.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_philox4x32_10.restype = None
+        lib.oracle_sample_estimate.argtypes = [
+            ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+            ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+            ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]
+        lib.oracle_sample_estimate.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -149,6 +156,41 @@ def pattern_of_mask(mask: int) -> int:
 
 def table_ok() -> bool:
     return bool(_load().oracle_pattern_table_ok())
+
+
+def philox4x32_10(counter, key):
+    """Philox4x32-10 block (Salmon et al., SC'11): 4 output words of a counter and key."""
+    c = np.ascontiguousarray(np.asarray(counter, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    _load().oracle_philox4x32_10(c.ctypes.data, k.ctypes.data, out.ctypes.data)
+    return [int(x) for x in out]
+
+
+@dataclass
+class SampleEstimate:
+    raw: np.ndarray      # uint64[21]: triangles counted for the drawn hyperwedges ([0] = total)
+    est: np.ndarray      # float64[21]: raw * (W / samples) / sigma^3
+    W: int
+
+
+def sample_estimate(e_ptr, e_idx, num_vertices: int, seed: int, first: int, num: int,
+                    sigma: float = 1.0, identity_draws: bool = False, threads: int = 0
+                    ) -> SampleEstimate:
+    """Hyperwedge-sampling estimate of Algorithm 6 (Appro-bs) for samples first .. first+num-1."""
+    lib = _load()
+    e_ptr = np.ascontiguousarray(e_ptr, dtype=np.int64)
+    e_idx = np.ascontiguousarray(e_idx, dtype=np.int32)
+    raw = np.zeros(21, dtype=np.uint64)
+    est = np.zeros(21, dtype=np.float64)
+    W = ctypes.c_uint64(0)
+    rc = lib.oracle_sample_estimate(int(num_vertices), len(e_ptr) - 1, e_ptr.ctypes.data,
+                                    e_idx.ctypes.data, seed & (2**64 - 1), int(first), int(num),
+                                    float(sigma), 1 if identity_draws else 0, int(threads),
+                                    raw.ctypes.data, est.ctypes.data, ctypes.byref(W))
+    if rc != 0:
+        raise ValueError(f"oracle: {_ERR.get(rc, rc)}")
+    return SampleEstimate(raw, est, int(W.value))
 
 
 def clustering_coeff(counts, open_triples: int, eps) -> float:

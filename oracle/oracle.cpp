@@ -347,6 +347,116 @@ int oracle_count(int32_t nv, int32_t ne, const int64_t* e_ptr, const int32_t* e_
   return bad ? -8 : 0;
 }
 
+// ---------------------------------------------------------------- Appro-bs (Algorithm 6)
+//
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as
+// 1, 2, 3", SC'11): 10 rounds of two 32x32->64 multiplications on a 4-word
+// counter under a 2-word key that is bumped by the Weyl constants between rounds.
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0, n1 = (uint32_t)p1;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1, n3 = (uint32_t)p0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Hyperwedge sampling estimate (Algorithm 6 with sigma = 1):
+//   the hyperwedges are numbered in the order O of Sec. 2 (i ascending, then j
+//   ascending, i < j); sample n draws x = Philox4x32-10(counter = (n lo, n hi, 0, 0),
+//   key = (seed lo, seed hi)), r = x1 << 32 | x0 and takes hyperwedge
+//   m = floor(r * W / 2^64) (with replacement); the hyper-triangles counted for
+//   hyperwedge (i, j) are those {i, j, k} with k > j, i.e. the ones whose smallest
+//   hyperwedge in O is (i, j); raw[p] sums them over the samples and
+//   est[p] = raw[p] * (W / samples) / sigma^3 (p = 0 is the total).
+// identity_draws = 1 replaces the draw by m = n (every wedge once when the
+// samples are 0 .. W-1) - the special case that pins the estimate to the count.
+int oracle_sample_estimate(int32_t nv, int32_t ne, const int64_t* e_ptr, const int32_t* e_idx,
+                           uint64_t seed, uint64_t first, uint64_t num, double sigma,
+                           int identity_draws, int nthreads, uint64_t* raw, double* est,
+                           uint64_t* wedges) {
+  if (!raw || !est || num == 0) return -6;
+  if (!oracle_pattern_table_ok()) return -7;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+  Graph g;
+  int rc = load(g, nv, ne, e_ptr, e_idx);
+  if (rc) return rc;
+  std::vector<std::vector<int32_t>> N(ne);
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int32_t x = 0; x < ne; ++x) N[x] = neighbours(g, x);
+  // wedges in O order: prefix over i of |{j in N(i) : j > i}|
+  std::vector<uint64_t> start(ne + 1, 0);
+  for (int32_t i = 0; i < ne; ++i) {
+    uint64_t up = 0;
+    for (int32_t j : N[i]) up += j > i;
+    start[i + 1] = start[i] + up;
+  }
+  const uint64_t W = start[ne];
+  if (wedges) *wedges = W;
+  std::memset(raw, 0, sizeof(uint64_t) * 21);
+  if (W == 0) {
+    for (int p = 0; p <= 20; ++p) est[p] = 0.0;
+    return 0;
+  }
+  const auto& pm = pattern_map();
+  int nth = 1;
+#ifdef _OPENMP
+  nth = omp_get_max_threads();
+#endif
+  std::vector<uint64_t> Hs((size_t)nth * 21, 0);
+  int bad = 0;
+#pragma omp parallel
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    uint64_t* H = &Hs[(size_t)tid * 21];
+#pragma omp for schedule(dynamic, 1024) reduction(| : bad)
+    for (int64_t s = 0; s < (int64_t)num; ++s) {
+      const uint64_t n = first + (uint64_t)s;
+      uint64_t m;
+      if (identity_draws) {
+        m = n;
+        if (m >= W) continue;
+      } else {
+        const uint32_t ctr[4] = {(uint32_t)n, (uint32_t)(n >> 32), 0u, 0u};
+        const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        uint32_t x[4];
+        oracle_philox4x32_10(ctr, key, x);
+        const uint64_t r = ((uint64_t)x[1] << 32) | x[0];
+        m = (uint64_t)(((unsigned __int128)r * W) >> 64);
+      }
+      // the m-th hyperwedge (i, j) in O
+      const int32_t i = (int32_t)(std::upper_bound(start.begin(), start.end(), m) - start.begin()) - 1;
+      uint64_t rank = m - start[i];
+      int32_t j = -1;
+      for (int32_t x : N[i])
+        if (x > i && rank-- == 0) { j = x; break; }
+      // every hyperwedge (i, k) after (i, j) in O whose k meets e_j closes a triangle
+      for (int32_t k : N[i]) {
+        if (k <= j || !adjacent(N, j, k)) continue;
+        const int p = pm.of_mask[region_mask(g.e[i], g.e[j], g.e[k])];
+        if (p == 0) { bad = 1; continue; }
+        ++H[p];
+      }
+    }
+  }
+  for (int t = 0; t < nth; ++t)
+    for (int p = 1; p <= 20; ++p) raw[p] += Hs[(size_t)t * 21 + p];
+  for (int p = 1; p <= 20; ++p) raw[0] += raw[p];
+  const double scale = (double)W / (double)num;
+  const double s3 = sigma * sigma * sigma;
+  for (int p = 0; p <= 20; ++p) est[p] = ((double)raw[p] * scale) / s3;
+  return bad ? -8 : 0;
+}
+
 int oracle_max_threads() {
 #ifdef _OPENMP
   return omp_get_max_threads();
