@@ -121,6 +121,30 @@ hg_status hg_build_wedges(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out
 hg_status hg_count_patterns(hg_graph* g, uint64_t counts[21]);
 
 /*
+ * Hyperwedge-sampling estimate of the per-pattern counts (Sec. 4.1, Algorithm 6,
+ * "Appro-bs"), with vertex-sampling rate sigma = 1.
+ * The W hyperwedges (i, j), i < j, are numbered in the order O of Sec. 2 (by i,
+ * then j).  Sample n, for n = first_sample .. first_sample + num_samples - 1,
+ * draws hyperwedge m = floor(r * W / 2^64), where r = x1 * 2^32 + x0 and
+ * (x0, x1, x2, x3) is the Philox4x32-10 block (Salmon et al., SC'11) of counter
+ * (n mod 2^32, n div 2^32, 0, 0) under key (seed mod 2^32, seed div 2^32).
+ * For the drawn (i, j) every k > j adjacent to both closes a hyper-triangle; it
+ * is classified as in hg_count_patterns and counted.
+ *   raw[21]  out: raw[0] = hyper-triangles found over all samples, raw[p] per pattern.
+ *   est[21]  out: est[p] = raw[p] * (W / num_samples) / sigma^3 in IEEE double
+ *                 (0 when num_samples == 0).
+ * Disjoint sample ranges with the same seed are independent draws, so split runs
+ * sum to one run over the union (raw exactly).  Builds the sorted neighbour rows
+ * on the first call after hg_build_wedges (W extra entries of device memory).
+ * Requires hg_build_wedges.  sigma outside (0, 1] is HG_ERR_INVALID_ARG; sigma < 1
+ * is HG_ERR_UNSUPPORTED.  A hyperedge with more than 16,384 neighbours of larger
+ * index is HG_ERR_UNSUPPORTED.  Synchronises.
+ */
+hg_status hg_sample_estimate(hg_graph* g, uint64_t seed, uint64_t first_sample,
+                             uint64_t num_samples, double sigma, uint64_t raw[21],
+                             double est[21]);
+
+/*
  * Fine-grained hypergraph clustering coefficient (Def. 5.1):
  *   cc = 3 * sum_{p=1..20} eps[p-1] * H[p] / open,
  * evaluated on the host in IEEE double with the sum taken in order p = 1..20;

@@ -84,6 +84,17 @@ struct hg_graph {
   uint64_t two_w = 0;
   bool built = false;
   hg_wedge_stats stats{};
+  // what a later pass over the same hyperwedges needs (kept with build_blocks)
+  WedgeBuckets wb{};
+  int32_t nb[3] = {0, 0, 0};
+  unsigned long long* wscratch = nullptr;
+  DenseInfo dn{};
+  int32_t* upc = nullptr;          // |{j > i : omega_ij > 0}| per row
+  // sampling stage: rows of neighbours j > i sorted by j (order O of Sec. 2)
+  std::vector<Block> sample_blocks;
+  int64_t* up_ptr = nullptr;
+  Oriented up{};
+  bool upper_built = false;
   // count stage
   std::vector<Block> count_blocks;
   bool counted = false;
@@ -151,6 +162,7 @@ hg_status dev_err_status(int e) {
     case DE_UNSORTED: return HG_ERR_UNSORTED;
     case DE_DUPEDGE: return HG_ERR_DUPLICATE_HYPEREDGE;
     case DE_PTR: return HG_ERR_INVALID_ARG;
+    case DE_LIMIT: return HG_ERR_UNSUPPORTED;
     default: return HG_ERR_INTERNAL;
   }
 }
@@ -397,9 +409,11 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   if (g->close_mode < 0 || g->close_mode > 1) return HG_ERR_INVALID_ARG;
   cudaStream_t s = g->stream;
   release(g, g->count_blocks);
+  release(g, g->sample_blocks);
   release(g, g->build_blocks);
   g->built = false;
   g->counted = false;
+  g->upper_built = false;
   const int64_t ne = g->ne;
   g->packed = (ne < (int64_t(1) << 24) && g->max_size < 256) ? 1 : 0;
   Small h;
@@ -408,7 +422,8 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   int32_t* rows = alloc_t<int32_t>(g, g->build_blocks, 3 * ne);
   g->ori.row_ptr = alloc_t<int64_t>(g, g->build_blocks, ne + 1);
   g->ori.dplus = alloc_t<int32_t>(g, g->build_blocks, ne);
-  if (!g->deg || !rows || !g->ori.row_ptr || !g->ori.dplus) return HG_ERR_OOM;
+  g->upc = alloc_t<int32_t>(g, g->build_blocks, ne);
+  if (!g->deg || !rows || !g->ori.row_ptr || !g->ori.dplus || !g->upc) return HG_ERR_OOM;
   WedgeBuckets wb;
   for (int k = 0; k < 3; ++k) wb.rows[k] = rows + k * ne;
   wb.count = g->small->bucket_count;
@@ -426,10 +441,11 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   HG_TRY(dense_impl(g, opt, &dn));
   HG_CUDA(cudaMemsetAsync(g->deg, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1), s));
   HG_CUDA(cudaMemsetAsync(g->ori.dplus, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1), s));
+  HG_CUDA(cudaMemsetAsync(g->upc, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1), s));
   HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
   t_begin(g, "wedge_count");
   launch_wedge_pass(0, d, wb, nb, g->max_cand, g->deg, &g->small->wc, g->ori, g->packed, scratch,
-                    &g->small->err, g->small->counters, dn, s, g->nsm);
+                    &g->small->err, g->small->counters, dn, g->upc, s, g->nsm);
   t_end(g);
   t_begin(g, "wedge_scan");
   scan_i32_to_i64(g->deg, g->ori.row_ptr, ne, g->scan_tmp, s);
@@ -451,7 +467,7 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
   t_begin(g, "wedge_emit");
   launch_wedge_pass(1, d, wb, nb, g->max_cand, g->deg, &g->small->wc, g->ori, g->packed, scratch,
-                    &g->small->err, g->small->counters, dn, s, g->nsm);
+                    &g->small->err, g->small->counters, dn, nullptr, s, g->nsm);
   reduce_deg_stats(g->ori.dplus, ne, g->small->out_stats, s);
   t_end(g);
   HG_TRY(sync_small(g, &h));
@@ -467,8 +483,80 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   st.dense_edges = (uint64_t)dn.nh;
   if (h.deg_stats[2] != (unsigned long long)two_w || h.out_stats[2] != st.W || (two_w & 1))
     return HG_ERR_INTERNAL;
+  g->wb = wb;
+  for (int k = 0; k < 3; ++k) g->nb[k] = nb[k];
+  g->wscratch = scratch;
+  g->dn = dn;
   g->built = true;
   if (out) *out = st;
+  return HG_OK;
+}
+
+// Rows of neighbours j > i with omega_ij, sorted by j: the hyperwedges in the
+// order O of Sec. 2, row i starting at up_ptr[i].  Built on the first sampling call.
+hg_status upper_impl(hg_graph* g) {
+  cudaStream_t s = g->stream;
+  const int64_t ne = g->ne;
+  release(g, g->sample_blocks);
+  g->up_ptr = alloc_t<int64_t>(g, g->sample_blocks, ne + 1);
+  if (!g->up_ptr) return HG_ERR_OOM;
+  scan_i32_to_i64(g->upc, g->up_ptr, ne, g->scan_tmp, s);
+  int64_t w = 0;
+  HG_CUDA(cudaMemcpyAsync(&w, g->up_ptr + ne, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  HG_CUDA(cudaStreamSynchronize(s));
+  if ((uint64_t)w != g->stats.W) return HG_ERR_INTERNAL;
+  g->up = Oriented{};
+  g->up.row_ptr = g->up_ptr;
+  if (g->packed) {
+    g->up.packed = alloc_t<uint32_t>(g, g->sample_blocks, w);
+    if (!g->up.packed) return HG_ERR_OOM;
+  } else {
+    g->up.nbr = alloc_t<int32_t>(g, g->sample_blocks, w);
+    g->up.omega = alloc_t<int32_t>(g, g->sample_blocks, w);
+    if (!g->up.nbr || !g->up.omega) return HG_ERR_OOM;
+  }
+  DevGraph d = dev_graph(g);
+  HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
+  t_begin(g, "upper_emit");
+  launch_wedge_pass(2, d, g->wb, g->nb, g->max_cand, g->deg, &g->small->wc, g->up, g->packed,
+                    g->wscratch, &g->small->err, g->small->counters, g->dn, nullptr, s, g->nsm);
+  t_end(g);
+  t_begin(g, "upper_sort");
+  HG_CUDA(launch_sort_upper(g->up_ptr, g->ne, g->up, g->packed, &g->small->err, s, g->nsm));
+  t_end(g);
+  Small h;
+  HG_TRY(sync_small(g, &h));
+  t_collect(g);
+  g->upper_built = true;
+  return HG_OK;
+}
+
+hg_status sample_impl(hg_graph* g, uint64_t seed, uint64_t first, uint64_t num, double sigma,
+                      uint64_t raw[21], double est[21]) {
+  if (!g->upper_built) HG_TRY(upper_impl(g));
+  cudaStream_t s = g->stream;
+  uint8_t lut[128];
+  build_lut(lut);
+  sample_set_lut(lut, s);
+  HG_CUDA(cudaMemsetAsync(g->small->hist, 0, sizeof(g->small->hist), s));
+  DevGraph d = dev_graph(g);
+  t_begin(g, "sample");
+  launch_sample(d, g->up_ptr, g->up, g->packed, g->stats.W, seed, first, num, g->small->hist, s,
+                g->nsm);
+  t_end(g);
+  Small h;
+  HG_TRY(sync_small(g, &h));
+  t_collect(g);
+  if (h.hist[0] != 0) return HG_ERR_INTERNAL;
+  uint64_t total = 0;
+  for (int p = 1; p <= 20; ++p) total += h.hist[p];
+  raw[0] = total;
+  for (int p = 1; p <= 20; ++p) raw[p] = h.hist[p];
+  // Algorithm 6: each drawn hyperwedge stands for W / num of them; each hyper-triangle
+  // survives the vertex sampling of rate sigma with probability sigma^3
+  const double scale = num ? (double)g->stats.W / (double)num : 0.0;
+  const double s3 = sigma * sigma * sigma;
+  for (int p = 0; p <= 20; ++p) est[p] = num ? ((double)raw[p] * scale) / s3 : 0.0;
   return HG_OK;
 }
 
@@ -634,6 +722,22 @@ hg_status hg_count_patterns(hg_graph* g, uint64_t counts[21]) {
   return st;
 }
 
+hg_status hg_sample_estimate(hg_graph* g, uint64_t seed, uint64_t first_sample,
+                             uint64_t num_samples, double sigma, uint64_t raw[21],
+                             double est[21]) {
+  if (!g || !raw || !est || !(sigma > 0.0) || sigma > 1.0) return HG_ERR_INVALID_ARG;
+  if (!g->built) return HG_ERR_STATE;
+  if (sigma != 1.0) return HG_ERR_UNSUPPORTED;
+  if (num_samples > UINT64_MAX - first_sample) return HG_ERR_INVALID_ARG;
+  hg_status st = sample_impl(g, seed, first_sample, num_samples, sigma, raw, est);
+  if (st != HG_OK) {
+    cudaStreamSynchronize(g->stream);
+    cudaGetLastError();
+    g->pending.clear();
+  }
+  return st;
+}
+
 hg_status hg_clustering_coeff(hg_graph* g, const double eps[20], double* cc,
                               uint64_t* open_triples, uint64_t* connected_triples) {
   if (!g || !eps) return HG_ERR_INVALID_ARG;
@@ -653,6 +757,7 @@ hg_status hg_free(hg_graph* g) {
   if (!g) return HG_ERR_INVALID_ARG;
   cudaStream_t s = g->stream;
   release(g, g->count_blocks);
+  release(g, g->sample_blocks);
   release(g, g->build_blocks);
   release(g, g->load_blocks);
   cudaError_t e = cudaStreamSynchronize(s);

@@ -23,6 +23,7 @@ enum DevErr : int {
   DE_DUPEDGE = 5,
   DE_PTR = 6,       // edge_ptr not monotone / out of [0, nnz]
   DE_INTERNAL = 7,  // a kernel-side consistency check failed
+  DE_LIMIT = 8,     // an input row beyond a kernel's fixed capacity
 };
 
 __device__ __forceinline__ void dev_fail(int* err, int code) { atomicCAS(err, 0, code); }
@@ -97,12 +98,23 @@ struct WedgeBuckets {
 void launch_bucket_rows(const int64_t* cand, int32_t ne, WedgeBuckets b, cudaStream_t s);
 int wedge_light_max_cand();
 int wedge_medium_max_cand();
-// mode 0: count (deg, W_c, dup check); mode 1: emit oriented entries
+// mode 0: count (deg, W_c, dup check, upc = |{j > i}| if upc != null); mode 1: emit the
+// degree-oriented rows at o.row_ptr (lengths into o.dplus); mode 2: emit the rows of
+// neighbours j > i at o.row_ptr (exact offsets from a scan of upc)
 void launch_wedge_pass(int mode, const DevGraph& g, const WedgeBuckets& b, const int32_t* nb,
                        int64_t heavy_max_cand, int32_t* deg, unsigned long long* wc,
                        const Oriented& o, int packed, unsigned long long* scratch,
-                       int* err, int32_t* work_counter, const DenseInfo& dense, cudaStream_t s,
-                       int nsm);
+                       int* err, int32_t* work_counter, const DenseInfo& dense, int32_t* upc,
+                       cudaStream_t s, int nsm);
+
+// k_sample.cu
+int sample_sort_max_log2();
+void sample_set_lut(const uint8_t lut[128], cudaStream_t s);
+cudaError_t launch_sort_upper(const int64_t* up_ptr, int32_t ne, const Oriented& up, int packed,
+                              int* err, cudaStream_t s, int nsm);
+void launch_sample(const DevGraph& g, const int64_t* up_ptr, const Oriented& up, int packed,
+                   uint64_t W, uint64_t seed, uint64_t first, uint64_t num,
+                   unsigned long long* raw, cudaStream_t s, int nsm);
 size_t wedge_heavy_scratch_bytes(int64_t heavy_max_cand, int nsm);
 
 // k_close.cu

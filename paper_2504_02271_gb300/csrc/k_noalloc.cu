@@ -54,7 +54,7 @@ __device__ __forceinline__ void add_neighbour(unsigned long long* T, uint32_t j)
 // One block per hyperedge i (fetched from a counter): deg[i] = number of distinct
 // j != i sharing a vertex with e_i; inclusion wedges (j > i, omega_ij equal to the
 // smaller size) are summed into wc.  A row that gathers more than half a table of
-// (j, v) incidences is not processed and sets DE_INTERNAL + 1 (too large).
+// (j, v) incidences is not processed and sets DE_LIMIT.
 __global__ void __launch_bounds__(kThreads)
     k_wedge_degrees_noalloc(NoallocScratch* sc, int32_t ne, const int64_t* __restrict__ e_ptr,
                             const int32_t* __restrict__ e_idx, const int64_t* __restrict__ v_ptr,
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kThreads)
     for (uint32_t s = threadIdx.x; s < CAP; s += kThreads) T[s] = kEmptySlot;
     __syncthreads();
     if (s_cand > (unsigned long long)(CAP / 2)) {
-      if (threadIdx.x == 0) atomicCAS(&sc->err, 0, hg::DE_INTERNAL + 1);
+      if (threadIdx.x == 0) atomicCAS(&sc->err, 0, hg::DE_LIMIT);
       continue;
     }
     for (int64_t p = b + w; p < e; p += kWarps) {
@@ -173,7 +173,7 @@ extern "C" hg_status hg_wedge_degrees_noalloc(int32_t num_edges, const int64_t* 
     cudaGetLastError();
     return HG_ERR_CUDA;
   }
-  if (err == hg::DE_INTERNAL + 1) return HG_ERR_UNSUPPORTED;
+  if (err == hg::DE_LIMIT) return HG_ERR_UNSUPPORTED;
   if (err == hg::DE_DUPEDGE) return HG_ERR_DUPLICATE_HYPEREDGE;
   return err ? HG_ERR_INTERNAL : HG_OK;
 }

@@ -96,7 +96,8 @@ template <int MODE, bool PACKED>
 __global__ void __launch_bounds__(kLightWarps * 32)
     k_wedge_light(DevGraph g, const int32_t* __restrict__ rows, const int32_t* __restrict__ nrows_p,
                   int32_t* __restrict__ deg, unsigned long long* __restrict__ wc, Oriented o,
-                  int* __restrict__ err, int32_t* __restrict__ counter, DenseInfo dn) {
+                  int* __restrict__ err, int32_t* __restrict__ counter, DenseInfo dn,
+                  int32_t* __restrict__ upc) {
   constexpr int CAP = 1 << kLightCapLog2;
   __shared__ unsigned long long tab[kLightWarps][CAP];
   __shared__ unsigned long long blk_wc;
@@ -133,23 +134,31 @@ __global__ void __launch_bounds__(kLightWarps * 32)
     __syncwarp();
     const int32_t szi = (int32_t)(e - b);
     if (MODE == 0) {
-      int distinct = 0;
+      int distinct = 0, up = 0;
       for (int s = lane; s < CAP; s += 32) {
         const unsigned long long x = T[s];
         if (x == kEmpty) continue;
         ++distinct;
         const int32_t j = (int32_t)(x >> 32), om = (int32_t)(x & 0xffffffffu);
         if (j > i) {
+          ++up;
           const int32_t szj = g.esize[j];
           if (om == szi && om == szj) dev_fail(err, DE_DUPEDGE);
           if (om == min(szi, szj)) ++my_wc;
         }
       }
 #pragma unroll
-      for (int d = 16; d > 0; d >>= 1) distinct += __shfl_down_sync(kFull, distinct, d);
-      if (lane == 0) deg[i] = distinct;
+      for (int d = 16; d > 0; d >>= 1) {
+        distinct += __shfl_down_sync(kFull, distinct, d);
+        up += __shfl_down_sync(kFull, up, d);
+      }
+      if (lane == 0) {
+        deg[i] = distinct;
+        if (upc) upc[i] = up;
+      }
     } else {
-      const int32_t di = deg[i];
+      // MODE 1: the out-list of the degree orientation; MODE 2: the neighbours j > i
+      const int32_t di = MODE == 1 ? deg[i] : 0;
       const int64_t base = o.row_ptr[i];
       int32_t written = 0;
       for (int s0 = 0; s0 < CAP; s0 += 32) {
@@ -159,13 +168,13 @@ __global__ void __launch_bounds__(kLightWarps * 32)
         if (x != kEmpty) {
           j = (uint32_t)(x >> 32);
           om = (uint32_t)(x & 0xffffffffu);
-          emit = ranked_above(di, i, deg[j], (int32_t)j);
+          emit = MODE == 1 ? ranked_above(di, i, deg[j], (int32_t)j) : (int32_t)j > i;
         }
         const unsigned bal = __ballot_sync(kFull, emit);
         if (emit) put_entry<PACKED>(o, base + written + __popc(bal & ((1u << lane) - 1u)), j, om);
         written += __popc(bal);
       }
-      if (lane == 0) o.dplus[i] = written;
+      if (lane == 0 && MODE == 1) o.dplus[i] = written;
     }
     __syncwarp();
   }
@@ -185,12 +194,13 @@ __global__ void __launch_bounds__(kBlockThreads)
     k_wedge_block(DevGraph g, const int32_t* __restrict__ rows, const int32_t* __restrict__ nrows_p,
                   int cap_log2, unsigned long long* __restrict__ gscratch,
                   int32_t* __restrict__ deg, unsigned long long* __restrict__ wc, Oriented o,
-                  int* __restrict__ err, int32_t* __restrict__ counter, DenseInfo dn) {
+                  int* __restrict__ err, int32_t* __restrict__ counter, DenseInfo dn,
+                  int32_t* __restrict__ upc) {
   extern __shared__ unsigned long long dyn[];
   unsigned long long* T = SMEM ? dyn : gscratch + ((size_t)blockIdx.x << cap_log2);
   const uint32_t CAP = 1u << cap_log2;
   __shared__ int32_t s_row;
-  __shared__ int32_t s_cnt;
+  __shared__ int32_t s_cnt, s_up;
   __shared__ unsigned long long s_wc;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   constexpr int kWarps = kBlockThreads / 32;
@@ -202,6 +212,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     if (threadIdx.x == 0) {
       s_row = atomicAdd(counter, 1);
       s_cnt = 0;
+      s_up = 0;
     }
     __syncthreads();
     const int32_t r = s_row;
@@ -228,37 +239,48 @@ __global__ void __launch_bounds__(kBlockThreads)
     __syncthreads();
     const int32_t szi = (int32_t)(e - b);
     if (MODE == 0) {
-      int distinct = 0;
+      int distinct = 0, up = 0;
       for (uint32_t s = threadIdx.x; s < CAP; s += kBlockThreads) {
         const unsigned long long x = T[s];
         if (x == kEmpty) continue;
         ++distinct;
         const int32_t j = (int32_t)(x >> 32), om = (int32_t)(x & 0xffffffffu);
         if (j > i) {
+          ++up;
           const int32_t szj = g.esize[j];
           if (om == szi && om == szj) dev_fail(err, DE_DUPEDGE);
           if (om == min(szi, szj)) ++my_wc;
         }
       }
 #pragma unroll
-      for (int d = 16; d > 0; d >>= 1) distinct += __shfl_down_sync(kFull, distinct, d);
-      if (lane == 0) atomicAdd(&s_cnt, distinct);
+      for (int d = 16; d > 0; d >>= 1) {
+        distinct += __shfl_down_sync(kFull, distinct, d);
+        up += __shfl_down_sync(kFull, up, d);
+      }
+      if (lane == 0) {
+        atomicAdd(&s_cnt, distinct);
+        atomicAdd(&s_up, up);
+      }
       __syncthreads();
-      if (threadIdx.x == 0) deg[i] = s_cnt;
+      if (threadIdx.x == 0) {
+        deg[i] = s_cnt;
+        if (upc) upc[i] = s_up;
+      }
     } else {
-      const int32_t di = deg[i];
+      // MODE 1: the out-list of the degree orientation; MODE 2: the neighbours j > i
+      const int32_t di = MODE == 1 ? deg[i] : 0;
       const int64_t base = o.row_ptr[i];
       for (uint32_t s = threadIdx.x; s < CAP; s += kBlockThreads) {
         const unsigned long long x = T[s];
         if (x == kEmpty) continue;
         const uint32_t j = (uint32_t)(x >> 32), om = (uint32_t)(x & 0xffffffffu);
-        if (ranked_above(di, i, deg[j], (int32_t)j)) {
+        if (MODE == 1 ? ranked_above(di, i, deg[j], (int32_t)j) : (int32_t)j > i) {
           const int32_t pos = atomicAdd(&s_cnt, 1);
           put_entry<PACKED>(o, base + pos, j, om);
         }
       }
       __syncthreads();
-      if (threadIdx.x == 0) o.dplus[i] = s_cnt;
+      if (threadIdx.x == 0 && MODE == 1) o.dplus[i] = s_cnt;
     }
   }
   if (MODE == 0) {
@@ -305,14 +327,15 @@ template <int MODE, bool PACKED>
 void launch_all(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb, int64_t heavy_max,
                 int32_t* deg, unsigned long long* wc, const Oriented& o,
                 unsigned long long* scratch, int* err, int32_t* counters, const DenseInfo& dn,
-                cudaStream_t s, int nsm) {
+                int32_t* upc, cudaStream_t s, int nsm) {
   // counters[0..2] are zeroed by the caller
   if (nb[0] > 0) {
     int blocks = (nb[0] + kLightWarps - 1) / kLightWarps;
     blocks = blocks < nsm * 4 ? blocks : nsm * 4;
     note_launch();
     k_wedge_light<MODE, PACKED><<<blocks, kLightWarps * 32, 0, s>>>(g, b.rows[0], b.count + 0, deg,
-                                                                    wc, o, err, counters + 0, dn);
+                                                                    wc, o, err, counters + 0, dn,
+                                                                    upc);
   }
   if (nb[1] > 0) {
     const size_t smem = sizeof(unsigned long long) << kMediumCapLog2;
@@ -321,14 +344,15 @@ void launch_all(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb, int
     int blocks = nb[1] < nsm * 3 ? nb[1] : nsm * 3;
     note_launch();
     k_wedge_block<MODE, PACKED, true><<<blocks, kBlockThreads, smem, s>>>(
-        g, b.rows[1], b.count + 1, kMediumCapLog2, nullptr, deg, wc, o, err, counters + 1, dn);
+        g, b.rows[1], b.count + 1, kMediumCapLog2, nullptr, deg, wc, o, err, counters + 1, dn,
+        upc);
   }
   if (nb[2] > 0) {
     int blocks = nb[2] < nsm * 2 ? nb[2] : nsm * 2;
     note_launch();
     k_wedge_block<MODE, PACKED, false><<<blocks, kBlockThreads, 0, s>>>(
         g, b.rows[2], b.count + 2, cap_log2_for(heavy_max), scratch, deg, wc, o, err,
-        counters + 2, dn);
+        counters + 2, dn, upc);
   }
 }
 
@@ -354,22 +378,23 @@ void launch_bucket_rows(const int64_t* cand, int32_t ne, WedgeBuckets b, cudaStr
 void launch_wedge_pass(int mode, const DevGraph& g, const WedgeBuckets& b, const int32_t* nb,
                        int64_t heavy_max_cand, int32_t* deg, unsigned long long* wc,
                        const Oriented& o, int packed, unsigned long long* scratch, int* err,
-                       int32_t* work_counter, const DenseInfo& dn, cudaStream_t s, int nsm) {
+                       int32_t* work_counter, const DenseInfo& dn, int32_t* upc, cudaStream_t s,
+                       int nsm) {
+#define HG_WEDGE_PASS(M)                                                                        \
+  if (packed)                                                                                  \
+    launch_all<M, true>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, dn, \
+                        upc, s, nsm);                                                          \
+  else                                                                                         \
+    launch_all<M, false>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, dn, \
+                         upc, s, nsm);
   if (mode == 0) {
-    if (packed)
-      launch_all<0, true>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, dn, s,
-                          nsm);
-    else
-      launch_all<0, false>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, dn, s,
-                           nsm);
+    HG_WEDGE_PASS(0)
+  } else if (mode == 1) {
+    HG_WEDGE_PASS(1)
   } else {
-    if (packed)
-      launch_all<1, true>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, dn, s,
-                          nsm);
-    else
-      launch_all<1, false>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, dn, s,
-                           nsm);
+    HG_WEDGE_PASS(2)
   }
+#undef HG_WEDGE_PASS
 }
 
 }  // namespace hg

@@ -30,7 +30,7 @@ HG_OK = 0
 EXPORTED = ("hg_set_allocator", "hg_load_csr", "hg_build_wedges", "hg_count_patterns",
             "hg_clustering_coeff", "hg_free", "hg_status_str", "hg_set_timing", "hg_kernel_times",
             "hg_pattern_table", "hg_close_stats_get", "hg_kernel_launches",
-            "hg_wedge_degrees_noalloc")
+            "hg_wedge_degrees_noalloc", "hg_sample_estimate")
 
 
 class HgError(RuntimeError):
@@ -86,6 +86,8 @@ def _open():
     lib.hg_close_stats_get.argtypes = [vp, ctypes.POINTER(_CloseStats)]
     lib.hg_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
     lib.hg_wedge_degrees_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp]
+    u64 = ctypes.c_uint64
+    lib.hg_sample_estimate.argtypes = [vp, u64, u64, u64, ctypes.c_double, vp, vp]
     for name in EXPORTED:
         if name != "hg_status_str":
             getattr(lib, name).restype = ctypes.c_int
@@ -219,6 +221,18 @@ def hg_count_patterns(g: Graph) -> np.ndarray:
     out = np.zeros(21, dtype=np.uint64)
     _check("hg_count_patterns", _lib.hg_count_patterns(ctypes.c_void_p(g.ptr), out.ctypes.data))
     return out
+
+
+def hg_sample_estimate(g: Graph, seed: int, first_sample: int, num_samples: int,
+                       sigma: float = 1.0) -> tuple[np.ndarray, np.ndarray]:
+    """Hyperwedge-sampling estimate (Algorithm 6): (raw uint64[21], est float64[21])."""
+    raw = np.zeros(21, dtype=np.uint64)
+    est = np.zeros(21, dtype=np.float64)
+    _check("hg_sample_estimate",
+           _lib.hg_sample_estimate(ctypes.c_void_p(g.ptr), int(seed) & (2**64 - 1),
+                                   int(first_sample), int(num_samples), float(sigma),
+                                   raw.ctypes.data, est.ctypes.data))
+    return raw, est
 
 
 def hg_clustering_coeff(g: Graph, eps) -> tuple[float, int, int]:
