@@ -53,6 +53,10 @@ def parse_args():
                     help="hyperedges at least this large use the tensor-core tiles (0 auto, -1 off)")
     ap.add_argument("--dense-max-count", type=int, default=0,
                     help="cap on the tensor-core set (0 = 1%% of |E|)")
+    ap.add_argument("--batch-members", type=int, default=4096,
+                    help="--workload batched: members (seeds 100 ..) in the batch")
+    ap.add_argument("--per-graph-steps", type=int, default=2,
+                    help="--workload batched: timed steps of the one-handle-per-hypergraph form")
     return ap.parse_args()
 
 
@@ -413,6 +417,210 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------------ batches of hypergraphs
+
+def roofline_from_times(kernel_ms, cs, T, clk):
+    """ALU roofline of the closure kernel with the largest share (see close_algorithmic)."""
+    peak_hbm, peak_kind = measured_peaks()
+    groups = {n: v for n, v in kernel_ms.items() if n in CLOSE_GROUPS}
+    dom = max(groups, key=lambda n: groups[n][0])
+    dom_ms = groups[dom][0] / groups[dom][1]
+    nbytes, ops = close_algorithmic(cs, CLOSE_GROUPS[dom], T)
+    sm_mhz = ((clk or {}).get("sm_mhz") or 2070.0)
+    peak_ops = 152 * ISSUE_LANE_OPS_PER_CYCLE_PER_SM * sm_mhz * 1e6 / 1e12
+    achieved_ops = ops / (dom_ms / 1000.0) / 1e12
+    achieved_gbs = nbytes / (dom_ms / 1000.0) / 1e9
+    return {"bound": "alu", "kernel": f"{dom} (k_close_warp / k_close_block / k_close_wide)",
+            "achieved": round(achieved_ops, 3), "peak": round(peak_ops, 2), "unit": "Tops/s",
+            "frac": round(achieved_ops / peak_ops, 4),
+            "peak_source": f"derived: 152 SMs x 128 lane-ops/cycle x {sm_mhz:.0f} MHz (median SM clock under load)",
+            "algorithmic_ops_per_launch": int(ops), "algorithmic_bytes_per_launch": int(nbytes),
+            "launch_ms": round(dom_ms, 4), "traffic": None,
+            "hbm": {"achieved": round(achieved_gbs, 1), "peak": peak_hbm, "unit": "GB/s",
+                    "frac": round(achieved_gbs / peak_hbm, 4), "peak_source": peak_kind}}
+
+
+def run_batched(args):
+    """4,096 independent hypergraphs (|E| log-uniform in [100, 200000], |V| = |E|/4,
+    sizes power law 2.2 on [2, 50], Zipf(1.0), degree cap 100, seeds 100 ..): one
+    batch (hg_load_batch / hg_batch_*) against one handle per hypergraph."""
+    import numpy as np
+    import torch
+
+    import hgen
+
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        raise SystemExit("bench: --workload batched runs on one GPU (replicas: run one per GPU)")
+    torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    import paper_2504_02271_gb300 as hg
+
+    hg.use_torch_allocator()
+    G = args.batch_members
+    specs = [hgen.batched(s) for s in range(100, 100 + G)]
+    nv, eoff, eptr, evtx, used = hgen.generate_batch(specs, redraw=hgen.batched_redraw)
+    redrawn = [u.name for u in used if u.seed >= 2**32]
+    stream = torch.cuda.Stream()
+    d_ptr = torch.from_numpy(eptr).to(dev)
+    d_idx = torch.from_numpy(evtx).to(dev)
+    h_ptr = torch.from_numpy(eptr).pin_memory()
+    h_idx = torch.from_numpy(evtx).pin_memory()
+    # per-member device CSRs for the one-handle-per-hypergraph form (offsets from 0)
+    m_ptr = [torch.from_numpy(np.ascontiguousarray(eptr[eoff[m]:eoff[m + 1] + 1] - eptr[eoff[m]])).to(dev)
+             for m in range(G)]
+    m_idx = [d_idx[int(eptr[eoff[m]]):int(eptr[eoff[m + 1]])] for m in range(G)]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ones = [1.0] * 20
+    torch.cuda.synchronize()
+
+    def do_flush(k):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)
+
+    def batch_step(p, i, timing=False):
+        b = hg.hg_load_batch(nv, eoff, p, i, stream=stream.cuda_stream)
+        try:
+            waves = hg.hg_batch_waves(b)
+            if timing:
+                for w in waves:
+                    hg.hg_set_timing(w[0], True)
+            hg.hg_batch_build_wedges(b)
+            counts, stats = hg.hg_batch_count_patterns(b)
+            cc = hg.hg_batch_clustering_coeff(b, ones)
+            kt, cs = {}, None
+            for w in waves:
+                if timing:
+                    for n, (ms, c) in hg.hg_kernel_times(w[0]).items():
+                        a = kt.setdefault(n, [0.0, 0])
+                        a[0] += ms
+                        a[1] += c
+                one = hg.hg_close_stats_get(w[0])
+                if cs is None:
+                    cs = one
+                else:
+                    for k, v in one.items():
+                        cs[k] = [x + y for x, y in zip(cs[k], v)] if isinstance(v, list) else cs[k] + v
+        finally:
+            hg.hg_batch_free(b)
+        return counts, stats, cc, kt, cs, len(waves)
+
+    def per_graph_step():
+        out = np.zeros((G, 21), dtype=np.uint64)
+        for m in range(G):
+            g = hg.hg_load_csr(int(nv[m]), int(eoff[m + 1] - eoff[m]), m_ptr[m], m_idx[m],
+                               stream=stream.cuda_stream)
+            try:
+                hg.hg_build_wedges(g)
+                out[m] = hg.hg_count_patterns(g)
+                hg.hg_clustering_coeff(g, ones)
+            finally:
+                hg.hg_free(g)
+        return out
+
+    def timed(fn, k):
+        do_flush(k)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    counts = None
+    for k in range(args.warmup):
+        do_flush(k)
+        counts, stats, _, _, _, nwaves = batch_step(d_ptr, d_idx)
+    T = int(counts[:, 0].sum())
+
+    clocks = ClockSampler(dev)
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = hg.hg_kernel_launches()
+    step_ms, kernel_ms, cs = [], {}, None
+    for k in range(args.steps):
+        (c2, _, _, kt, cs, _), ms = timed(lambda: batch_step(d_ptr, d_idx, timing=True), k + 17)
+        assert np.array_equal(c2, counts)
+        step_ms.append(ms)
+        for n, (t, c) in kt.items():
+            a = kernel_ms.setdefault(n, [0.0, 0])
+            a[0] += t
+            a[1] += c
+    torch.cuda.synchronize()
+    launches = hg.hg_kernel_launches() - launches0
+    clk = clocks.stop()
+    value = T * len(step_ms) / (sum(step_ms) / 1000.0)
+
+    # the same members one handle at a time: identical counts, and its throughput
+    pg_counts, _ = timed(per_graph_step, 5)   # warm-up
+    if not np.array_equal(pg_counts, counts):
+        raise SystemExit("bench: batch counts differ from one-handle-per-hypergraph counts")
+    launches_pg0 = hg.hg_kernel_launches()
+    pg_ms = [timed(per_graph_step, 40 + k)[1] for k in range(max(1, args.per_graph_steps))]
+    launches_pg = (hg.hg_kernel_launches() - launches_pg0) // len(pg_ms)
+    pg_value = T * len(pg_ms) / (sum(pg_ms) / 1000.0)
+
+    # end to end from pinned host buffers (upload inside the timed region)
+    e2e_ms = []
+    for k in range(max(1, args.e2e_steps)):
+        (c3, _, _, _, _, _), ms = timed(lambda: batch_step(h_ptr, h_idx), 99 + k)
+        assert np.array_equal(c3, counts)
+        e2e_ms.append(ms)
+    e2e_value = T * len(e2e_ms) / (sum(e2e_ms) / 1000.0)
+
+    roof = roofline_from_times(kernel_ms, cs, T, clk)
+    cpu = None
+    if not args.skip_cpu_baseline:
+        import oracle
+
+        # bounded sample: whole members in seed order until about 15 s of oracle time
+        tri, secs, threads, done = 0, 0.0, 1, 0
+        for m in range(G):
+            if secs > 15.0:
+                break
+            p = eptr[eoff[m]:eoff[m + 1] + 1] - eptr[eoff[m]]
+            r = oracle.count(p, evtx[eptr[eoff[m]]:eptr[eoff[m + 1]]], int(nv[m]))
+            if r.counts.tolist() != counts[m].tolist():
+                raise SystemExit(f"bench: member {m} differs from the oracle")
+            tri, secs, threads, done = tri + r.T, secs + r.seconds, r.threads, m + 1
+        cpu = {"value": round(tri / secs, 1), "unit": UNIT, "cores": threads, "kind": "oracle",
+               "seconds": round(secs, 2), "triangles": tri,
+               "sample": f"members 0..{done - 1} of the batch, each counted whole (counts equal the GPU's)"}
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(statistics.mean(step_ms), 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"batched_{G}", "members": G, "seeds": f"100..{99 + G}",
+                   "member_edges": "log-uniform in [100, 200000]", "member_vertices": "|E|/4",
+                   "hyperedge_sizes": "truncated power law 2.2 on [2,50]",
+                   "vertex_popularity": "Zipf(1.0)", "degree_cap": 100,
+                   "redrawn_members": redrawn, "sum_edges": int(eoff[-1]), "sum_nnz": int(eptr[-1]),
+                   "waves": nwaves, "triangles_per_step": T,
+                   "wedges": int(stats["W"].sum()),
+                   "l2": "inputs (%.1f GB) larger than L2; 256 MiB buffer also written between steps"
+                         % ((eptr.nbytes + evtx.nbytes) / 1e9),
+                   "inputs": "concatenated int64/int32 CSRs resident in HBM",
+                   "parallelism": "replicas x1",
+                   "parity": "per-member counts equal one-handle-per-hypergraph counts"},
+        "per_graph": {"value": round(pg_value, 1), "unit": UNIT, "ms_per_step": round(statistics.mean(pg_ms), 3),
+                      "steps": len(pg_ms), "gpu_launches_per_step": int(launches_pg),
+                      "form": "hg_load_csr / hg_build_wedges / hg_count_patterns / hg_clustering_coeff per member"},
+        "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
+                "h2d_bytes_per_step": int(eptr.nbytes + evtx.nbytes),
+                "d2h_bytes_per_step": int(G * 21 * 8 + G * 64),
+                "ms_per_step": round(statistics.mean(e2e_ms), 3)},
+        "roofline": roof,
+        "kernel_ms_per_step": {n: round(v[0] / args.steps, 3) for n, v in sorted(kernel_ms.items())},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "close_stats": cs,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(e_ptr, e_idx, nv, sample_edges):
     import oracle
 
@@ -432,15 +640,36 @@ def run_reference(args):
         return
     import oracle
 
-    spec, e_ptr, e_idx, prefix = workload(args.workload)
-    cfg = workload_config(spec, e_ptr, prefix)
-    nv = spec.num_vertices
-    per_step = 2000
-    ne = len(e_ptr) - 1
+    if args.workload == "batched":
+        import hgen
 
-    def step(k):
-        lo = (k * per_step) % max(ne - per_step, 1)
-        return oracle.count(e_ptr, e_idx, nv, i_range=(lo, min(lo + per_step, ne)))
+        # per step: the next whole member of the batch (seeds 100 ..), in seed order
+        G = args.batch_members
+        cfg = {"workload": f"batched_{G}", "members": G, "seeds": f"100..{99 + G}"}
+        members = [hgen.batched(s) for s in range(100, 100 + G)]
+        per_step_desc = "one whole member of the batch (seed order, cycling)"
+
+        def step(k):
+            sp = members[k % G]
+            r = 0
+            while True:
+                try:
+                    p, i = hgen.generate(sp if r == 0 else hgen.batched_redraw(sp, r))
+                    break
+                except hgen.DedupExhausted:
+                    r += 1
+            return oracle.count(p, i, sp.num_vertices)
+    else:
+        spec, e_ptr, e_idx, prefix = workload(args.workload)
+        cfg = workload_config(spec, e_ptr, prefix)
+        nv = spec.num_vertices
+        per_step = 2000
+        ne = len(e_ptr) - 1
+        per_step_desc = f"triangles owned by {per_step} consecutive hyperedges"
+
+        def step(k):
+            lo = (k * per_step) % max(ne - per_step, 1)
+            return oracle.count(e_ptr, e_idx, nv, i_range=(lo, min(lo + per_step, ne)))
 
     for k in range(args.warmup):
         step(k)
@@ -459,7 +688,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic", "impl": "reference", "config": cfg,
         "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"per step: triangles owned by {per_step} consecutive hyperedges"},
+                         "sample": f"per step: {per_step_desc}"},
         "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -470,6 +699,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -119,6 +119,10 @@ _ERRORS = {-1: "bad argument", -2: "out of memory", -3: "not enough available ve
            -4: "could not draw a fresh hyperedge"}
 
 
+class DedupExhausted(RuntimeError):
+    """The generator found no fresh hyperedge after many redraws."""
+
+
 def generate(spec: HypergraphSpec) -> tuple[np.ndarray, np.ndarray]:
     """Return (e_ptr int64[|E|+1], e_idx int32[nnz]) for the spec."""
     lib = _load()
@@ -131,9 +135,58 @@ def generate(spec: HypergraphSpec) -> tuple[np.ndarray, np.ndarray]:
     np.cumsum(sizes, out=e_ptr[1:])
     e_idx = np.empty(int(e_ptr[-1]), dtype=np.int32)
     rc = lib.hgen_fill(ctypes.byref(p), sizes.ctypes.data, e_ptr.ctypes.data, e_idx.ctypes.data)
+    if rc == -4:
+        raise DedupExhausted(f"hgen_fill ({spec.name}): {_ERRORS.get(rc, rc)}")
     if rc != 0:
         raise RuntimeError(f"hgen_fill: {_ERRORS.get(rc, rc)}")
     return e_ptr, e_idx
+
+
+def generate_batch(specs: list[HypergraphSpec], threads: int = 0, redraw=None
+                   ) -> tuple[np.ndarray, np.ndarray, np.ndarray, np.ndarray, list[HypergraphSpec]]:
+    """Generate many hypergraphs into one concatenated layout:
+    (num_vertices int32[G], edge_off int64[G+1], edge_ptr int64[sum |E|+1],
+    edge_vtx int32[sum nnz], specs used), member m's hyperedges at edge_off[m] ..
+    edge_off[m+1]-1 with member-local vertex ids.  A member whose draw runs out of
+    fresh hyperedges is drawn again from redraw(spec, r), r = 1, 2, ... (first that
+    succeeds) when `redraw` is given.  Members are drawn in parallel threads (the C
+    generator keeps no shared state and ctypes releases the GIL); the output does not
+    depend on the thread count."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    workers = threads if threads > 0 else (os.cpu_count() or 1)
+
+    def run(sp0):
+        sp, r = sp0, 0
+        while True:
+            try:
+                return (sp, *generate(sp))
+            except DedupExhausted:
+                r += 1
+                if redraw is None or r > 64:
+                    raise
+                sp = redraw(sp0, r)
+
+    with ThreadPoolExecutor(workers) as ex:
+        parts = list(ex.map(run, specs))
+    G = len(parts)
+    edge_off = np.zeros(G + 1, dtype=np.int64)
+    np.cumsum([len(p[1]) - 1 for p in parts], out=edge_off[1:])
+    nnz = np.zeros(G + 1, dtype=np.int64)
+    np.cumsum([int(p[1][-1]) for p in parts], out=nnz[1:])
+    edge_ptr = np.empty(int(edge_off[-1]) + 1, dtype=np.int64)
+    edge_vtx = np.empty(int(nnz[-1]), dtype=np.int32)
+
+    def place(m):
+        sp, e_ptr, e_idx = parts[m]
+        edge_ptr[edge_off[m]:edge_off[m + 1]] = e_ptr[:-1] + nnz[m]
+        edge_vtx[nnz[m]:nnz[m + 1]] = e_idx
+
+    with ThreadPoolExecutor(workers) as ex:
+        list(ex.map(place, range(G)))
+    edge_ptr[-1] = nnz[-1]
+    nv = np.array([p[0].num_vertices for p in parts], dtype=np.int32)
+    return nv, edge_off, edge_ptr, edge_vtx, [p[0] for p in parts]
 
 
 def loguniform_int(seed: int, tag: int, lo: int, hi: int) -> int:
@@ -171,6 +224,12 @@ def batched(seed: int) -> HypergraphSpec:
                           degree_cap=100, name=f"batched_{seed}")
 
 
+def batched_redraw(spec: HypergraphSpec, r: int) -> HypergraphSpec:
+    """Batch member drawn again from seed + r * 2^32 (same sizes of |V| and |E|) when its
+    own seed runs out of fresh hyperedges under the degree cap."""
+    return replace(spec, seed=spec.seed + (r << 32))
+
+
 def served(member: int) -> HypergraphSpec:
     """One of the 64 resident hypergraphs of the serving workload."""
     seed = 5000 + member
@@ -180,3 +239,19 @@ def served(member: int) -> HypergraphSpec:
 
 
 WORKLOADS = {"tiny_plain": TINY_PLAIN, "coauthor": COAUTHOR, "tag_heavy": TAG_HEAVY}
+
+
+def hub(num_spokes: int, num_extra: int, seed: int) -> tuple[int, np.ndarray, np.ndarray]:
+    """A hub vertex 0 in `num_spokes` hyperedges ({0, a, b}, every third one {0, a}, with
+    fresh a, b), plus `num_extra` random pairs over the spoke vertices (duplicates
+    dropped); hyperedges sorted lexicographically.  Returns (num_vertices, e_ptr, e_idx)."""
+    rng = np.random.default_rng(seed)
+    edges = [[0, 1 + 2 * k, 2 + 2 * k] if k % 3 else [0, 1 + 2 * k] for k in range(num_spokes)]
+    for _ in range(num_extra):
+        a, b = rng.choice(2 * num_spokes, 2, replace=False) + 1
+        edges.append([int(a), int(b)])
+    uniq = sorted({tuple(sorted(set(e))) for e in edges})
+    e_ptr = np.zeros(len(uniq) + 1, dtype=np.int64)
+    e_ptr[1:] = np.cumsum([len(e) for e in uniq])
+    e_idx = np.array([v for e in uniq for v in e], dtype=np.int32)
+    return 2 * num_spokes + 1, e_ptr, e_idx

@@ -136,9 +136,9 @@ hg_status hg_count_patterns(hg_graph* g, uint64_t counts[21]);
  * Disjoint sample ranges with the same seed are independent draws, so split runs
  * sum to one run over the union (raw exactly).  Builds the sorted neighbour rows
  * on the first call after hg_build_wedges (W extra entries of device memory).
- * Requires hg_build_wedges.  sigma outside (0, 1] is HG_ERR_INVALID_ARG; sigma < 1
- * is HG_ERR_UNSUPPORTED.  A hyperedge with more than 16,384 neighbours of larger
- * index is HG_ERR_UNSUPPORTED.  Synchronises.
+ * Requires hg_build_wedges.  sigma outside (0, 1] is HG_ERR_INVALID_ARG; sigma < 1,
+ * or a wave handle of a batch, is HG_ERR_UNSUPPORTED.  A hyperedge with more than
+ * 16,384 neighbours of larger index is HG_ERR_UNSUPPORTED.  Synchronises.
  */
 hg_status hg_sample_estimate(hg_graph* g, uint64_t seed, uint64_t first_sample,
                              uint64_t num_samples, double sigma, uint64_t raw[21],
@@ -219,8 +219,66 @@ hg_status hg_wedge_degrees_noalloc(int32_t num_edges, const int64_t* edge_ptr,
                                    const int32_t* vertex_edge, int32_t* degrees,
                                    unsigned long long* inclusion_wedges, void* cuda_stream);
 
-/* Release the handle and every device buffer it owns (stream-ordered). */
+/* Release the handle and every device buffer it owns (stream-ordered).
+ * The wave handles of a batch belong to the batch: HG_ERR_STATE for them. */
 hg_status hg_free(hg_graph* g);
+
+/*
+ * Batches of independent hypergraphs.  The paper counts one hypergraph at a
+ * time; a batch counts many in the same kernel launches.  Members get disjoint
+ * vertex ranges, so the union's line graph is the disjoint union of theirs, every
+ * hyperwedge and hyper-triangle (Defs. 2.2, 2.4) lies in one member, and the
+ * closure kernels add each hyper-triangle to its member's 20 pattern bins.  Each
+ * member's results equal those of hg_load_csr / hg_build_wedges /
+ * hg_count_patterns on that member alone.
+ *
+ * Consecutive members are grouped into waves of at most max_wave_edges
+ * hyperedges (0 = 2^24 - 1, the limit of packed neighbour ids; a larger member
+ * is a wave of its own); each wave is one union handle resident on the device.
+ *
+ *   num_graphs    G >= 1.
+ *   num_vertices  [G] host: |V_m| >= 1.
+ *   edge_off      [G+1] host: member m owns hyperedges edge_off[m] .. edge_off[m+1]-1
+ *                 of the concatenated CSR; edge_off[0] = 0, non-decreasing; empty
+ *                 members are allowed.
+ *   edge_ptr      [edge_off[G]+1] int64, host or device (inputs_on_device): offsets
+ *                 into edge_vtx, edge_ptr[0] = 0, non-decreasing.
+ *   edge_vtx      vertex ids LOCAL to the member (0 .. |V_m|-1), each hyperedge
+ *                 ascending and duplicate-free; an id outside its member's range is
+ *                 HG_ERR_VERTEX_RANGE.  Other input errors as in hg_load_csr.
+ * The caller keeps its arrays; the batch holds device copies in union ids.
+ * Synchronises.  Free with hg_batch_free.
+ */
+typedef struct hg_batch hg_batch;
+hg_status hg_load_batch(int32_t num_graphs, const int32_t* num_vertices, const int64_t* edge_off,
+                        const int64_t* edge_ptr, const int32_t* edge_vtx, int inputs_on_device,
+                        int64_t max_wave_edges, void* cuda_stream, hg_batch** out);
+
+/* Step one (as hg_build_wedges) on every wave.  opt may be NULL.  Synchronises. */
+hg_status hg_batch_build_wedges(hg_batch* b, const hg_tuning* opt);
+
+/*
+ * Step two (as hg_count_patterns) on every wave.
+ *   counts  [G][21] out (may be NULL): counts[21 m] = member m's total, counts[21 m + p] = H[p].
+ *   stats   [G] out (may be NULL): W, W_t, W_c, connected, max_deg of member m
+ *           (max_out_deg and dense_edges are 0 per member).
+ * Requires hg_batch_build_wedges.  Synchronises.
+ */
+hg_status hg_batch_count_patterns(hg_batch* b, uint64_t* counts, hg_wedge_stats* stats);
+
+/* Def. 5.1 per member, as hg_clustering_coeff: cc, open, connected are [G] (each may
+ * be NULL).  Requires hg_batch_count_patterns.  No device work. */
+hg_status hg_batch_clustering_coeff(hg_batch* b, const double eps[20], double* cc,
+                                    uint64_t* open_triples, uint64_t* connected_triples);
+
+/* Number of waves, and wave k's handle (borrowed: for hg_set_timing, hg_kernel_times,
+ * hg_close_stats_get) with its first member and member count. */
+hg_status hg_batch_waves(hg_batch* b, int32_t* num_waves);
+hg_status hg_batch_wave(hg_batch* b, int32_t k, hg_graph** wave, int32_t* first_member,
+                        int32_t* num_members);
+
+/* Release the batch, its waves and their device buffers. */
+hg_status hg_batch_free(hg_batch* b);
 
 /*
  * The library's pattern table: lut[m] = pattern 1..20 of a labelled region mask

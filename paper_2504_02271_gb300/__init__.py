@@ -10,6 +10,8 @@ from .hg import (  # noqa: F401
     hg_kernel_launches, hg_kernel_times, hg_load_csr, hg_pattern_table, hg_sample_estimate, hg_set_allocator,
     hg_set_timing, hg_status_str,
     use_default_allocator, use_torch_allocator,
+    Batch, concat_members, hg_batch_build_wedges, hg_batch_clustering_coeff, hg_batch_count_patterns,
+    hg_batch_free, hg_batch_waves, hg_load_batch,
 )
 
 

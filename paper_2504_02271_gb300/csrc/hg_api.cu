@@ -100,6 +100,15 @@ struct hg_graph {
   bool counted = false;
   uint64_t counts[21] = {0};
   hg_close_stats cstats{};
+  // a wave of a batch: nm members, member m owning hyperedges [m_eoff[m], m_eoff[m+1])
+  // and union vertices [m_voff[m], m_voff[m+1])
+  int32_t nm = 0;
+  int32_t* m_eoff = nullptr;
+  int32_t* m_voff = nullptr;
+  int32_t* wcr = nullptr;                 // per-row inclusion wedges (build)
+  unsigned long long* mstats = nullptr;   // [nm][4]: sum deg, sum C(deg,2), W_c, max deg
+  unsigned long long* mhist = nullptr;    // [nm][24] pattern bins (count)
+  std::vector<unsigned long long> h_mstats, h_mhist;
   // timing
   bool timing = false;
   std::vector<KTime> pending;
@@ -221,6 +230,8 @@ DevGraph dev_graph(const hg_graph* g) {
   d.esize = g->esize;
   d.v_ptr = g->v_ptr;
   d.v_idx = g->v_idx;
+  d.m_eoff = g->m_eoff;
+  d.nm = g->nm;
   return d;
 }
 
@@ -308,7 +319,16 @@ T* alloc_t(hg_graph* g, std::vector<Block>& owner, int64_t n) {
   return static_cast<T*>(dev_alloc(g, owner, (size_t)std::max<int64_t>(n, 1) * sizeof(T)));
 }
 
-hg_status load_impl(hg_graph* g, const int64_t* edge_ptr, const int32_t* edge_vtx, int on_dev) {
+// Wave members for load_impl: host arrays of nm + 1 union offsets, and the
+// offset of the wave's first incidence in the caller's edge_ptr.
+struct WaveInput {
+  const int32_t* eoff;
+  const int32_t* voff;
+  int64_t base;
+};
+
+hg_status load_impl(hg_graph* g, const int64_t* edge_ptr, const int32_t* edge_vtx, int on_dev,
+                    const WaveInput* wave = nullptr) {
   cudaStream_t s = g->stream;
   const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   g->small = alloc_t<Small>(g, g->load_blocks, 1);
@@ -328,9 +348,23 @@ hg_status load_impl(hg_graph* g, const int64_t* edge_ptr, const int32_t* edge_vt
   HG_CUDA(cudaMemcpyAsync(g->e_ptr, edge_ptr, sizeof(int64_t) * ((size_t)g->ne + 1), kind, s));
   if (g->nnz > 0)
     HG_CUDA(cudaMemcpyAsync(g->e_idx, edge_vtx, sizeof(int32_t) * (size_t)g->nnz, kind, s));
+  if (wave) {
+    g->m_eoff = alloc_t<int32_t>(g, g->load_blocks, (int64_t)g->nm + 1);
+    g->m_voff = alloc_t<int32_t>(g, g->load_blocks, (int64_t)g->nm + 1);
+    if (!g->m_eoff || !g->m_voff) return HG_ERR_OOM;
+    HG_CUDA(cudaMemcpyAsync(g->m_eoff, wave->eoff, sizeof(int32_t) * ((size_t)g->nm + 1),
+                            cudaMemcpyHostToDevice, s));
+    HG_CUDA(cudaMemcpyAsync(g->m_voff, wave->voff, sizeof(int32_t) * ((size_t)g->nm + 1),
+                            cudaMemcpyHostToDevice, s));
+    launch_sub_base(g->e_ptr, g->ne, wave->base, s);
+  }
   Small h;
   launch_check_ptr(g->e_ptr, g->ne, g->nnz, &g->small->err, s);
   HG_TRY(sync_small(g, &h));
+  if (wave) {
+    launch_localize(dev_graph(g), g->m_voff, g->e_idx, &g->small->err, s);
+    HG_TRY(sync_small(g, &h));
+  }
   HG_CUDA(cudaMemsetAsync(vdeg, 0, sizeof(int32_t) * (size_t)g->nv, s));
   DevGraph d = dev_graph(g);
   launch_validate_rows(d, g->esize, vdeg, &g->small->err, s);
@@ -424,6 +458,14 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   g->ori.dplus = alloc_t<int32_t>(g, g->build_blocks, ne);
   g->upc = alloc_t<int32_t>(g, g->build_blocks, ne);
   if (!g->deg || !rows || !g->ori.row_ptr || !g->ori.dplus || !g->upc) return HG_ERR_OOM;
+  g->wcr = nullptr;
+  g->mstats = nullptr;
+  if (g->nm > 0) {
+    g->wcr = alloc_t<int32_t>(g, g->build_blocks, ne);
+    g->mstats = alloc_t<unsigned long long>(g, g->build_blocks, 4 * (int64_t)g->nm);
+    if (!g->wcr || !g->mstats) return HG_ERR_OOM;
+    HG_CUDA(cudaMemsetAsync(g->wcr, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1), s));
+  }
   WedgeBuckets wb;
   for (int k = 0; k < 3; ++k) wb.rows[k] = rows + k * ne;
   wb.count = g->small->bucket_count;
@@ -445,7 +487,8 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
   t_begin(g, "wedge_count");
   launch_wedge_pass(0, d, wb, nb, g->max_cand, g->deg, &g->small->wc, g->ori, g->packed, scratch,
-                    &g->small->err, g->small->counters, dn, g->upc, s, g->nsm);
+                    &g->small->err, g->small->counters, dn, RowCounts{g->upc, g->wcr}, s,
+                    g->nsm);
   t_end(g);
   t_begin(g, "wedge_scan");
   scan_i32_to_i64(g->deg, g->ori.row_ptr, ne, g->scan_tmp, s);
@@ -467,9 +510,15 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
   t_begin(g, "wedge_emit");
   launch_wedge_pass(1, d, wb, nb, g->max_cand, g->deg, &g->small->wc, g->ori, g->packed, scratch,
-                    &g->small->err, g->small->counters, dn, nullptr, s, g->nsm);
+                    &g->small->err, g->small->counters, dn, RowCounts{}, s, g->nsm);
   reduce_deg_stats(g->ori.dplus, ne, g->small->out_stats, s);
   t_end(g);
+  if (g->nm > 0) {
+    g->h_mstats.assign(4 * (size_t)g->nm, 0);
+    launch_member_stats(d, g->deg, g->wcr, g->mstats, s);
+    HG_CUDA(cudaMemcpyAsync(g->h_mstats.data(), g->mstats, sizeof(unsigned long long) * g->h_mstats.size(),
+                            cudaMemcpyDeviceToHost, s));
+  }
   HG_TRY(sync_small(g, &h));
   t_collect(g);
   hg_wedge_stats& st = g->stats;
@@ -519,7 +568,8 @@ hg_status upper_impl(hg_graph* g) {
   HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
   t_begin(g, "upper_emit");
   launch_wedge_pass(2, d, g->wb, g->nb, g->max_cand, g->deg, &g->small->wc, g->up, g->packed,
-                    g->wscratch, &g->small->err, g->small->counters, g->dn, nullptr, s, g->nsm);
+                    g->wscratch, &g->small->err, g->small->counters, g->dn, RowCounts{}, s,
+                    g->nsm);
   t_end(g);
   t_begin(g, "upper_sort");
   HG_CUDA(launch_sort_upper(g->up_ptr, g->ne, g->up, g->packed, &g->small->err, s, g->nsm));
@@ -573,6 +623,14 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   HG_CUDA(cudaMemsetAsync(g->small->hist, 0, sizeof(g->small->hist), s));
   HG_CUDA(cudaMemsetAsync(g->small->work, 0, sizeof(g->small->work), s));
   HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
+  // pattern bins: one set per member of a batch wave, else the handle's own
+  unsigned long long* hist = g->small->hist;
+  if (g->nm > 0) {
+    g->mhist = alloc_t<unsigned long long>(g, g->count_blocks, (int64_t)g->nm * 24);
+    if (!g->mhist) return HG_ERR_OOM;
+    HG_CUDA(cudaMemsetAsync(g->mhist, 0, sizeof(unsigned long long) * 24 * (size_t)g->nm, s));
+    hist = g->mhist;
+  }
   uint8_t lut[128];
   build_lut(lut);
   close_set_lut(lut, s);
@@ -605,7 +663,7 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
     if (n[k] <= 0) continue;
     t_begin(g, names[k]);
     launch_close(k, d, g->ori, g->packed, cb.lists[k], n[k], cb.count + k, cap, words, dmax,
-                 scratch, g->small->hist, g->small->work[k], g->small->counters + k, overflow,
+                 scratch, hist, g->small->work[k], g->small->counters + k, overflow,
                  n_overflow, s, g->nsm);
     t_end(g);
   }
@@ -614,12 +672,23 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   if (n_over > 0) {
     t_begin(g, "close_wide");
     launch_close(kWideBucket, d, g->ori, g->packed, overflow, n_over, n_overflow, cap, words, dmax,
-                 scratch, g->small->hist, g->small->work[kWideBucket], g->small->counters + 8,
+                 scratch, hist, g->small->work[kWideBucket], g->small->counters + 8,
                  overflow, n_overflow, s, g->nsm);
     t_end(g);
     HG_TRY(sync_small(g, &h));
   }
   t_collect(g);
+  if (g->nm > 0) {   // the wave's bins are the sums of its members'
+    g->h_mhist.assign(24 * (size_t)g->nm, 0);
+    HG_CUDA(cudaMemcpyAsync(g->h_mhist.data(), g->mhist, sizeof(unsigned long long) * g->h_mhist.size(),
+                            cudaMemcpyDeviceToHost, s));
+    HG_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < 24; ++k) {
+      unsigned long long x = 0;
+      for (int32_t m = 0; m < g->nm; ++m) x += g->h_mhist[24 * (size_t)m + k];
+      h.hist[k] = x;
+    }
+  }
   if (h.hist[0] != 0) return HG_ERR_INTERNAL;
   for (int k = 21; k < 24; ++k)
     if (h.hist[k] != 0) return HG_ERR_INTERNAL;
@@ -645,6 +714,98 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   g->cstats.bucket_teams[kWideBucket] += (uint64_t)n_over;   // handed from the warp kernels
   g->counted = true;
   if (counts) std::memcpy(counts, g->counts, sizeof(g->counts));
+  return HG_OK;
+}
+
+}  // namespace
+
+// A batch: member hypergraphs grouped into waves, each wave one union handle.
+struct hg_batch {
+  cudaStream_t stream = nullptr;
+  int32_t G = 0;
+  std::vector<hg_graph*> waves;
+  std::vector<int32_t> first;   // first member of each wave (+ G at the end)
+  bool built = false, counted = false;
+};
+
+namespace {
+
+hg_status free_graph(hg_graph* g) {
+  cudaStream_t s = g->stream;
+  release(g, g->count_blocks);
+  release(g, g->sample_blocks);
+  release(g, g->build_blocks);
+  release(g, g->load_blocks);
+  cudaError_t e = cudaStreamSynchronize(s);
+  for (auto& k : g->pending) {
+    cudaEventDestroy(k.a);
+    cudaEventDestroy(k.b);
+  }
+  delete g;
+  return cuda_status(e);
+}
+
+void free_batch(hg_batch* b) {
+  for (hg_graph* w : b->waves) free_graph(w);
+  delete b;
+}
+
+constexpr int64_t kDefaultWaveEdges = (int64_t(1) << 24) - 1;   // packed 24-bit neighbour ids
+
+hg_status load_batch_impl(hg_batch* b, const int32_t* num_vertices, const int64_t* edge_off,
+                          const int64_t* edge_ptr, const int32_t* edge_vtx, int on_dev,
+                          int64_t max_wave_edges, int dev, int nsm) {
+  cudaStream_t s = b->stream;
+  const int32_t G = b->G;
+  // greedy waves of consecutive members: at most max_wave_edges hyperedges (a
+  // larger member gets a wave of its own) and fewer than 2^31 union vertices
+  int32_t m = 0;
+  while (m < G) {
+    const int32_t m0 = m;
+    int64_t ne = 0, nv = 0;
+    while (m < G) {
+      const int64_t dne = edge_off[m + 1] - edge_off[m], dnv = num_vertices[m];
+      if (m > m0 && (ne + dne > max_wave_edges || nv + dnv > INT32_MAX)) break;
+      ne += dne;
+      nv += dnv;
+      ++m;
+    }
+    if (ne > INT32_MAX || nv > INT32_MAX) return HG_ERR_UNSUPPORTED;
+    b->first.push_back(m0);
+  }
+  b->first.push_back(G);
+  for (size_t k = 0; k + 1 < b->first.size(); ++k) {
+    const int32_t m0 = b->first[k], m1 = b->first[k + 1];
+    const int64_t e0 = edge_off[m0], e1 = edge_off[m1];
+    int64_t p0 = 0, p1 = 0;
+    if (on_dev) {
+      HG_CUDA(cudaMemcpyAsync(&p0, edge_ptr + e0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      HG_CUDA(cudaMemcpyAsync(&p1, edge_ptr + e1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      HG_CUDA(cudaStreamSynchronize(s));
+    } else {
+      p0 = edge_ptr[e0];
+      p1 = edge_ptr[e1];
+    }
+    if (p0 < 0 || p1 < p0 || (p1 > p0 && !edge_vtx)) return HG_ERR_INVALID_ARG;
+    std::vector<int32_t> eoff((size_t)(m1 - m0) + 1), voff((size_t)(m1 - m0) + 1);
+    int64_t nv = 0;
+    for (int32_t q = m0; q <= m1; ++q) {
+      eoff[(size_t)(q - m0)] = (int32_t)(edge_off[q] - e0);
+      voff[(size_t)(q - m0)] = (int32_t)nv;
+      if (q < m1) nv += num_vertices[q];
+    }
+    hg_graph* g = new hg_graph();
+    g->device = dev;
+    g->nsm = nsm;
+    g->stream = s;
+    g->nv = (int32_t)std::max<int64_t>(nv, 1);
+    g->ne = (int32_t)(e1 - e0);
+    g->nnz = p1 - p0;
+    g->nm = m1 - m0;
+    b->waves.push_back(g);
+    WaveInput wi{eoff.data(), voff.data(), p0};
+    HG_TRY(load_impl(g, edge_ptr + e0, edge_vtx ? edge_vtx + p0 : nullptr, on_dev, &wi));
+  }
   return HG_OK;
 }
 
@@ -727,7 +888,7 @@ hg_status hg_sample_estimate(hg_graph* g, uint64_t seed, uint64_t first_sample,
                              double est[21]) {
   if (!g || !raw || !est || !(sigma > 0.0) || sigma > 1.0) return HG_ERR_INVALID_ARG;
   if (!g->built) return HG_ERR_STATE;
-  if (sigma != 1.0) return HG_ERR_UNSUPPORTED;
+  if (sigma != 1.0 || g->nm > 0) return HG_ERR_UNSUPPORTED;
   if (num_samples > UINT64_MAX - first_sample) return HG_ERR_INVALID_ARG;
   hg_status st = sample_impl(g, seed, first_sample, num_samples, sigma, raw, est);
   if (st != HG_OK) {
@@ -755,18 +916,130 @@ hg_status hg_clustering_coeff(hg_graph* g, const double eps[20], double* cc,
 
 hg_status hg_free(hg_graph* g) {
   if (!g) return HG_ERR_INVALID_ARG;
-  cudaStream_t s = g->stream;
-  release(g, g->count_blocks);
-  release(g, g->sample_blocks);
-  release(g, g->build_blocks);
-  release(g, g->load_blocks);
-  cudaError_t e = cudaStreamSynchronize(s);
-  for (auto& k : g->pending) {
-    cudaEventDestroy(k.a);
-    cudaEventDestroy(k.b);
+  if (g->nm > 0) return HG_ERR_STATE;   // a wave belongs to its batch
+  return free_graph(g);
+}
+
+hg_status hg_load_batch(int32_t num_graphs, const int32_t* num_vertices, const int64_t* edge_off,
+                        const int64_t* edge_ptr, const int32_t* edge_vtx, int inputs_on_device,
+                        int64_t max_wave_edges, void* cuda_stream, hg_batch** out) {
+  if (!out) return HG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (num_graphs < 1 || !num_vertices || !edge_off || !edge_ptr || max_wave_edges < 0)
+    return HG_ERR_INVALID_ARG;
+  if (edge_off[0] != 0) return HG_ERR_INVALID_ARG;
+  for (int32_t m = 0; m < num_graphs; ++m)
+    if (num_vertices[m] < 1 || edge_off[m + 1] < edge_off[m] ||
+        edge_off[m + 1] - edge_off[m] > INT32_MAX)
+      return HG_ERR_INVALID_ARG;
+  int dev = 0, nsm = 0;
+  HG_TRY(check_device(&dev, &nsm));
+  hg_batch* b = new hg_batch();
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  b->G = num_graphs;
+  hg_status st = load_batch_impl(b, num_vertices, edge_off, edge_ptr, edge_vtx, inputs_on_device,
+                                 max_wave_edges > 0 ? max_wave_edges : kDefaultWaveEdges, dev, nsm);
+  if (st != HG_OK) {
+    cudaStreamSynchronize(b->stream);
+    cudaGetLastError();
+    free_batch(b);
+    cudaGetLastError();
+    return st;
   }
-  delete g;
-  return cuda_status(e);
+  *out = b;
+  return HG_OK;
+}
+
+hg_status hg_batch_build_wedges(hg_batch* b, const hg_tuning* opt) {
+  if (!b) return HG_ERR_INVALID_ARG;
+  b->built = b->counted = false;
+  for (hg_graph* g : b->waves) {
+    hg_status st = hg_build_wedges(g, opt, nullptr);
+    if (st != HG_OK) return st;
+  }
+  b->built = true;
+  return HG_OK;
+}
+
+hg_status hg_batch_count_patterns(hg_batch* b, uint64_t* counts, hg_wedge_stats* stats) {
+  if (!b) return HG_ERR_INVALID_ARG;
+  if (!b->built) return HG_ERR_STATE;
+  b->counted = false;
+  for (hg_graph* g : b->waves) {
+    hg_status st = hg_count_patterns(g, nullptr);
+    if (st != HG_OK) return st;
+  }
+  for (size_t k = 0; k < b->waves.size(); ++k) {
+    const hg_graph* g = b->waves[k];
+    for (int32_t q = 0; q < g->nm; ++q) {
+      const size_t m = (size_t)(b->first[k] + q);
+      const unsigned long long* h = g->h_mhist.data() + 24 * (size_t)q;
+      const unsigned long long* st = g->h_mstats.data() + 4 * (size_t)q;
+      uint64_t total = 0;
+      for (int p = 1; p <= 20; ++p) total += h[p];
+      if (counts) {
+        counts[21 * m] = total;
+        for (int p = 1; p <= 20; ++p) counts[21 * m + (size_t)p] = h[p];
+      }
+      if (st[0] & 1) return HG_ERR_INTERNAL;
+      if (stats) {
+        hg_wedge_stats& w = stats[m];
+        std::memset(&w, 0, sizeof(w));
+        w.W = st[0] / 2;
+        w.W_c = st[2];
+        w.W_t = w.W - w.W_c;
+        w.connected = st[1];
+        w.max_deg = st[3];
+      }
+    }
+  }
+  b->counted = true;
+  return HG_OK;
+}
+
+hg_status hg_batch_clustering_coeff(hg_batch* b, const double eps[20], double* cc,
+                                    uint64_t* open_triples, uint64_t* connected_triples) {
+  if (!b || !eps) return HG_ERR_INVALID_ARG;
+  if (!b->counted) return HG_ERR_STATE;
+  for (size_t k = 0; k < b->waves.size(); ++k) {
+    const hg_graph* g = b->waves[k];
+    for (int32_t q = 0; q < g->nm; ++q) {
+      const size_t m = (size_t)(b->first[k] + q);
+      const unsigned long long* h = g->h_mhist.data() + 24 * (size_t)q;
+      uint64_t total = 0;
+      for (int p = 1; p <= 20; ++p) total += h[p];
+      const uint64_t connected = g->h_mstats[4 * (size_t)q + 1];
+      const uint64_t open = connected - 3 * total;
+      // Def. 5.1, summed in order p = 1..20 in IEEE double, as hg_clustering_coeff
+      double num = 0.0;
+      for (int p = 1; p <= 20; ++p) num += eps[p - 1] * (double)h[p];
+      if (cc) cc[m] = open == 0 ? NAN : 3.0 * num / (double)open;
+      if (open_triples) open_triples[m] = open;
+      if (connected_triples) connected_triples[m] = connected;
+    }
+  }
+  return HG_OK;
+}
+
+hg_status hg_batch_waves(hg_batch* b, int32_t* num_waves) {
+  if (!b || !num_waves) return HG_ERR_INVALID_ARG;
+  *num_waves = (int32_t)b->waves.size();
+  return HG_OK;
+}
+
+hg_status hg_batch_wave(hg_batch* b, int32_t k, hg_graph** wave, int32_t* first_member,
+                        int32_t* num_members) {
+  if (!b || k < 0 || k >= (int32_t)b->waves.size()) return HG_ERR_INVALID_ARG;
+  if (wave) *wave = b->waves[(size_t)k];
+  if (first_member) *first_member = b->first[(size_t)k];
+  if (num_members) *num_members = b->first[(size_t)k + 1] - b->first[(size_t)k];
+  return HG_OK;
+}
+
+hg_status hg_batch_free(hg_batch* b) {
+  if (!b) return HG_ERR_INVALID_ARG;
+  free_batch(b);
+  return HG_OK;
 }
 
 hg_status hg_close_stats_get(hg_graph* g, hg_close_stats* out) {

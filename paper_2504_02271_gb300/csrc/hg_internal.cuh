@@ -46,7 +46,21 @@ struct DevGraph {
   const int32_t* esize;
   const int64_t* v_ptr;
   const int32_t* v_idx;
+  // a batch of disjoint member hypergraphs: member m owns hyperedges
+  // [m_eoff[m], m_eoff[m+1]); nm == 0 for a single hypergraph
+  const int32_t* m_eoff;
+  int32_t nm;
 };
+
+// member owning hyperedge u (0 for a single hypergraph)
+__device__ __forceinline__ int32_t member_of(const DevGraph& g, int32_t u) {
+  int32_t lo = 0, hi = g.nm > 0 ? g.nm - 1 : 0;
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(g.m_eoff + mid) <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
 
 // ---------------- launch wrappers (implemented in the .cu files) ----------------
 
@@ -98,14 +112,28 @@ struct WedgeBuckets {
 void launch_bucket_rows(const int64_t* cand, int32_t ne, WedgeBuckets b, cudaStream_t s);
 int wedge_light_max_cand();
 int wedge_medium_max_cand();
-// mode 0: count (deg, W_c, dup check, upc = |{j > i}| if upc != null); mode 1: emit the
-// degree-oriented rows at o.row_ptr (lengths into o.dplus); mode 2: emit the rows of
-// neighbours j > i at o.row_ptr (exact offsets from a scan of upc)
+// Per-row outputs of the count pass (each may be null): upc[i] = |{j > i}|,
+// wcr[i] = |{j > i : omega_ij = min(|e_i|, |e_j|)}| (inclusion-type hyperwedges).
+struct RowCounts {
+  int32_t* upc;
+  int32_t* wcr;
+};
+
+// mode 0: count (deg, W_c, dup check, RowCounts); mode 1: emit the degree-oriented rows
+// at o.row_ptr (lengths into o.dplus); mode 2: emit the rows of neighbours j > i at
+// o.row_ptr (exact offsets from a scan of upc)
 void launch_wedge_pass(int mode, const DevGraph& g, const WedgeBuckets& b, const int32_t* nb,
                        int64_t heavy_max_cand, int32_t* deg, unsigned long long* wc,
                        const Oriented& o, int packed, unsigned long long* scratch,
-                       int* err, int32_t* work_counter, const DenseInfo& dense, int32_t* upc,
+                       int* err, int32_t* work_counter, const DenseInfo& dense, RowCounts rc,
                        cudaStream_t s, int nsm);
+
+// k_batch.cu
+void launch_sub_base(int64_t* e_ptr, int32_t ne, int64_t base, cudaStream_t s);
+void launch_localize(const DevGraph& g, const int32_t* m_voff, int32_t* e_idx, int* err,
+                     cudaStream_t s);
+void launch_member_stats(const DevGraph& g, const int32_t* deg, const int32_t* wcr,
+                         unsigned long long* out, cudaStream_t s);
 
 // k_sample.cu
 int sample_sort_max_log2();

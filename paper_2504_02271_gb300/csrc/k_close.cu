@@ -108,6 +108,21 @@ struct RunHist {
   }
 };
 
+// Move a warp's shared bins (after its lanes' runs) into the global bins `out`.
+__device__ __forceinline__ void warp_flush(RunHist& rh, uint32_t* hist,
+                                           unsigned long long* __restrict__ out, int lane) {
+  rh.flush(hist);
+  __syncwarp();
+  for (int k = lane; k < kBins; k += 32) {
+    const uint32_t x = hist[k];
+    if (x) {
+      atomicAdd(&out[k], (unsigned long long)x);
+      hist[k] = 0;
+    }
+  }
+  __syncwarp();
+}
+
 // Classify queued hit number `at`: v = k-th out-neighbour, w = table slot.
 template <int D_LOG2, bool PACKED>
 __device__ __forceinline__ void classify_queued(const WarpTables<D_LOG2, PACKED>& t, int at,
@@ -143,7 +158,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
   __syncthreads();
   const int32_t n = *n_p;
   RunHist rh;
-  unsigned long long probes = 0, gathers = 0, outs = 0;
+  unsigned long long probes = 0, gathers = 0, outs = 0, since_flush = 0;
+  int32_t cur = 0;   // member whose bins the shared histogram holds
 
   while (true) {
     int r = 0;
@@ -151,6 +167,12 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
     r = __shfl_sync(kFull, r, 0);
     if (r >= n) break;
     const int32_t u = list[r];
+    const int32_t m = member_of(g, u);
+    if (m != cur || since_flush > (1ull << 30)) {   // 32-bit bins stay far from overflow
+      warp_flush(rh, hist[w], hist_out + (size_t)cur * kBins, lane);
+      cur = m;
+      since_flush = 0;
+    }
     const int32_t du = o.dplus[u];
     const int64_t bu = o.row_ptr[u];
     const int64_t eb = g.e_ptr[u];
@@ -232,6 +254,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) F += __shfl_xor_sync(kFull, F, d);
     probes += (unsigned long long)F;
+    since_flush += (unsigned long long)F;
     outs += (unsigned long long)du;
     __syncwarp();
 
@@ -296,10 +319,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
     if (lane < qn) classify_queued<D_LOG2, PACKED>(t, lane, szu, lut, hist[w], rh);
     __syncwarp();
   }
-  rh.flush(hist[w]);
-  __syncwarp();
-  for (int k = lane; k < kBins; k += 32)
-    if (hist[w][k]) atomicAdd(&hist_out[k], (unsigned long long)hist[w][k]);
+  warp_flush(rh, hist[w], hist_out + (size_t)cur * kBins, lane);
   if (lane == 0) {
     atomicAdd(&work[0], probes);
     atomicAdd(&work[1], gathers);
@@ -365,28 +385,34 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   const int32_t n = *n_p;
   RunHist rh;
   unsigned long long probes = 0, gathers = 0, outs = 0, since_flush = 0;
+  int32_t cur = 0;   // member whose bins the shared histograms hold
+  auto block_flush = [&]() {
+    rh.flush(hist[w]);
+    __syncthreads();
+    for (int k = threadIdx.x; k < kBins; k += NT) {
+      unsigned long long x = 0;
+      for (int ww = 0; ww < WARPS; ++ww) {
+        x += hist[ww][k];
+        hist[ww][k] = 0;
+      }
+      if (x) atomicAdd(&hist_out[(size_t)cur * kBins + k], x);
+    }
+    __syncthreads();
+  };
 
   while (true) {
     __syncthreads();
-    if (since_flush > (1ull << 30)) {   // keep the 32-bit bins far from overflow
-      rh.flush(hist[w]);
-      __syncthreads();
-      for (int k = threadIdx.x; k < kBins; k += NT) {
-        unsigned long long x = 0;
-        for (int ww = 0; ww < WARPS; ++ww) {
-          x += hist[ww][k];
-          hist[ww][k] = 0;
-        }
-        if (x) atomicAdd(&hist_out[k], x);
-      }
-      since_flush = 0;
-      __syncthreads();
-    }
     if (threadIdx.x == 0) s_r = atomicAdd(counter, 1);
     __syncthreads();
     const int32_t r = s_r;
     if (r >= n) break;
     const int32_t u = list[r];
+    const int32_t m = member_of(g, u);   // the same on every thread
+    if (m != cur || since_flush > (1ull << 30)) {   // 32-bit bins stay far from overflow
+      block_flush();
+      cur = m;
+      since_flush = 0;
+    }
     const int32_t du = o.dplus[u];
     const int64_t bu = o.row_ptr[u];
     const int64_t eb = g.e_ptr[u];
@@ -550,13 +576,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     }
     __syncwarp();
   }
-  rh.flush(hist[w]);
-  __syncthreads();
-  for (int k = threadIdx.x; k < kBins; k += NT) {
-    unsigned long long x = 0;
-    for (int ww = 0; ww < WARPS; ++ww) x += hist[ww][k];
-    if (x) atomicAdd(&hist_out[k], x);
-  }
+  block_flush();
   if (threadIdx.x == 0) {
     atomicAdd(&work[0], probes);
     atomicAdd(&work[1], gathers);
@@ -608,16 +628,29 @@ __global__ void __launch_bounds__(kWideThreads)
   __shared__ uint32_t hist[kHistCopies][kBins];
   __shared__ uint8_t lut[128];
   __shared__ int32_t s_r;
+  __shared__ unsigned long long s_since;   // probes since the last flush (block-wide)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   constexpr int kW = kWideThreads / 32;
+  static_assert(kHistCopies * kBins <= kWideThreads, "one thread per shared bin");
   WideScratch t = wide_carve(scratch + wide_block_bytes(cap_max, words_max, dmax) * blockIdx.x,
                              cap_max, words_max, dmax);
   for (int k = threadIdx.x; k < 128; k += blockDim.x) lut[k] = c_lut[k];
   for (int k = threadIdx.x; k < kHistCopies * kBins; k += blockDim.x) (&hist[0][0])[k] = 0;
   const int32_t n = *n_p;
   uint32_t* my_hist = hist[lane & (kHistCopies - 1)];
-  uint64_t since_flush = 0;
   unsigned long long probes = 0, gathers = 0, outs = 0;
+  int32_t cur = 0;   // member whose bins the shared histograms hold
+  if (threadIdx.x == 0) s_since = 0;
+  auto block_flush = [&]() {
+    __syncthreads();
+    if (threadIdx.x < kHistCopies * kBins) {
+      const uint32_t x = (&hist[0][0])[threadIdx.x];
+      if (x) atomicAdd(&hist_out[(size_t)cur * kBins + threadIdx.x % kBins], (unsigned long long)x);
+      (&hist[0][0])[threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) s_since = 0;
+    __syncthreads();
+  };
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) s_r = atomicAdd(counter, 1);
@@ -625,6 +658,11 @@ __global__ void __launch_bounds__(kWideThreads)
     const int32_t r = s_r;
     if (r >= n) break;
     const int32_t u = list[r];
+    const int32_t m = member_of(g, u);   // the same on every thread
+    if (m != cur || s_since > (1ull << 28)) {   // s_since is read after a barrier: uniform
+      block_flush();
+      cur = m;
+    }
     const int32_t du = o.dplus[u];
     const int64_t bu = o.row_ptr[u];
     const int64_t eb = g.e_ptr[u];
@@ -669,8 +707,10 @@ __global__ void __launch_bounds__(kWideThreads)
       for (int q = 0; q < words; ++q) wuv += __popc(muv[q]);
       const int64_t vb = t.kbeg[k];
       const int32_t cnt = t.kcnt[k];
-      since_flush += (uint64_t)cnt;
-      if (lane == 0) probes += (unsigned long long)cnt;
+      if (lane == 0) {
+        probes += (unsigned long long)cnt;
+        atomicAdd(&s_since, (unsigned long long)cnt);
+      }
       for (int32_t j = lane; j < cnt; j += 32) {
         int32_t wv, om;
         get_entry<PACKED>(o, vb + j, wv, om);
@@ -688,21 +728,8 @@ __global__ void __launch_bounds__(kWideThreads)
         atomicAdd(&my_hist[lut[bits]], 1u);
       }
     }
-    if (since_flush > (1ull << 28)) {
-      __syncthreads();
-      if (threadIdx.x < kHistCopies * kBins) {
-        const uint32_t x = (&hist[0][0])[threadIdx.x];
-        if (x) atomicAdd(&hist_out[threadIdx.x % kBins], (unsigned long long)x);
-        (&hist[0][0])[threadIdx.x] = 0;
-      }
-      since_flush = 0;
-    }
   }
-  __syncthreads();
-  if (threadIdx.x < kHistCopies * kBins) {
-    const uint32_t x = (&hist[0][0])[threadIdx.x];
-    if (x) atomicAdd(&hist_out[threadIdx.x % kBins], (unsigned long long)x);
-  }
+  block_flush();
   if (lane == 0) {
     atomicAdd(&work[0], probes);
     atomicAdd(&work[1], gathers);

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kLightWarps * 32)
     k_wedge_light(DevGraph g, const int32_t* __restrict__ rows, const int32_t* __restrict__ nrows_p,
                   int32_t* __restrict__ deg, unsigned long long* __restrict__ wc, Oriented o,
                   int* __restrict__ err, int32_t* __restrict__ counter, DenseInfo dn,
-                  int32_t* __restrict__ upc) {
+                  RowCounts rc) {
   constexpr int CAP = 1 << kLightCapLog2;
   __shared__ unsigned long long tab[kLightWarps][CAP];
   __shared__ unsigned long long blk_wc;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kLightWarps * 32)
     __syncwarp();
     const int32_t szi = (int32_t)(e - b);
     if (MODE == 0) {
-      int distinct = 0, up = 0;
+      int distinct = 0, up = 0, incl = 0;
       for (int s = lane; s < CAP; s += 32) {
         const unsigned long long x = T[s];
         if (x == kEmpty) continue;
@@ -144,17 +144,20 @@ __global__ void __launch_bounds__(kLightWarps * 32)
           ++up;
           const int32_t szj = g.esize[j];
           if (om == szi && om == szj) dev_fail(err, DE_DUPEDGE);
-          if (om == min(szi, szj)) ++my_wc;
+          if (om == min(szi, szj)) ++incl;
         }
       }
+      my_wc += (unsigned long long)incl;
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) {
         distinct += __shfl_down_sync(kFull, distinct, d);
         up += __shfl_down_sync(kFull, up, d);
+        incl += __shfl_down_sync(kFull, incl, d);
       }
       if (lane == 0) {
         deg[i] = distinct;
-        if (upc) upc[i] = up;
+        if (rc.upc) rc.upc[i] = up;
+        if (rc.wcr) rc.wcr[i] = incl;
       }
     } else {
       // MODE 1: the out-list of the degree orientation; MODE 2: the neighbours j > i
@@ -195,12 +198,12 @@ __global__ void __launch_bounds__(kBlockThreads)
                   int cap_log2, unsigned long long* __restrict__ gscratch,
                   int32_t* __restrict__ deg, unsigned long long* __restrict__ wc, Oriented o,
                   int* __restrict__ err, int32_t* __restrict__ counter, DenseInfo dn,
-                  int32_t* __restrict__ upc) {
+                  RowCounts rc) {
   extern __shared__ unsigned long long dyn[];
   unsigned long long* T = SMEM ? dyn : gscratch + ((size_t)blockIdx.x << cap_log2);
   const uint32_t CAP = 1u << cap_log2;
   __shared__ int32_t s_row;
-  __shared__ int32_t s_cnt, s_up;
+  __shared__ int32_t s_cnt, s_up, s_incl;
   __shared__ unsigned long long s_wc;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   constexpr int kWarps = kBlockThreads / 32;
@@ -213,6 +216,7 @@ __global__ void __launch_bounds__(kBlockThreads)
       s_row = atomicAdd(counter, 1);
       s_cnt = 0;
       s_up = 0;
+      s_incl = 0;
     }
     __syncthreads();
     const int32_t r = s_row;
@@ -239,7 +243,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     __syncthreads();
     const int32_t szi = (int32_t)(e - b);
     if (MODE == 0) {
-      int distinct = 0, up = 0;
+      int distinct = 0, up = 0, incl = 0;
       for (uint32_t s = threadIdx.x; s < CAP; s += kBlockThreads) {
         const unsigned long long x = T[s];
         if (x == kEmpty) continue;
@@ -249,22 +253,26 @@ __global__ void __launch_bounds__(kBlockThreads)
           ++up;
           const int32_t szj = g.esize[j];
           if (om == szi && om == szj) dev_fail(err, DE_DUPEDGE);
-          if (om == min(szi, szj)) ++my_wc;
+          if (om == min(szi, szj)) ++incl;
         }
       }
+      my_wc += (unsigned long long)incl;
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) {
         distinct += __shfl_down_sync(kFull, distinct, d);
         up += __shfl_down_sync(kFull, up, d);
+        incl += __shfl_down_sync(kFull, incl, d);
       }
       if (lane == 0) {
         atomicAdd(&s_cnt, distinct);
         atomicAdd(&s_up, up);
+        atomicAdd(&s_incl, incl);
       }
       __syncthreads();
       if (threadIdx.x == 0) {
         deg[i] = s_cnt;
-        if (upc) upc[i] = s_up;
+        if (rc.upc) rc.upc[i] = s_up;
+        if (rc.wcr) rc.wcr[i] = s_incl;
       }
     } else {
       // MODE 1: the out-list of the degree orientation; MODE 2: the neighbours j > i
@@ -327,7 +335,7 @@ template <int MODE, bool PACKED>
 void launch_all(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb, int64_t heavy_max,
                 int32_t* deg, unsigned long long* wc, const Oriented& o,
                 unsigned long long* scratch, int* err, int32_t* counters, const DenseInfo& dn,
-                int32_t* upc, cudaStream_t s, int nsm) {
+                RowCounts rc, cudaStream_t s, int nsm) {
   // counters[0..2] are zeroed by the caller
   if (nb[0] > 0) {
     int blocks = (nb[0] + kLightWarps - 1) / kLightWarps;
@@ -335,7 +343,7 @@ void launch_all(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb, int
     note_launch();
     k_wedge_light<MODE, PACKED><<<blocks, kLightWarps * 32, 0, s>>>(g, b.rows[0], b.count + 0, deg,
                                                                     wc, o, err, counters + 0, dn,
-                                                                    upc);
+                                                                    rc);
   }
   if (nb[1] > 0) {
     const size_t smem = sizeof(unsigned long long) << kMediumCapLog2;
@@ -345,14 +353,14 @@ void launch_all(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb, int
     note_launch();
     k_wedge_block<MODE, PACKED, true><<<blocks, kBlockThreads, smem, s>>>(
         g, b.rows[1], b.count + 1, kMediumCapLog2, nullptr, deg, wc, o, err, counters + 1, dn,
-        upc);
+        rc);
   }
   if (nb[2] > 0) {
     int blocks = nb[2] < nsm * 2 ? nb[2] : nsm * 2;
     note_launch();
     k_wedge_block<MODE, PACKED, false><<<blocks, kBlockThreads, 0, s>>>(
         g, b.rows[2], b.count + 2, cap_log2_for(heavy_max), scratch, deg, wc, o, err,
-        counters + 2, dn, upc);
+        counters + 2, dn, rc);
   }
 }
 
@@ -378,15 +386,15 @@ void launch_bucket_rows(const int64_t* cand, int32_t ne, WedgeBuckets b, cudaStr
 void launch_wedge_pass(int mode, const DevGraph& g, const WedgeBuckets& b, const int32_t* nb,
                        int64_t heavy_max_cand, int32_t* deg, unsigned long long* wc,
                        const Oriented& o, int packed, unsigned long long* scratch, int* err,
-                       int32_t* work_counter, const DenseInfo& dn, int32_t* upc, cudaStream_t s,
+                       int32_t* work_counter, const DenseInfo& dn, RowCounts rc, cudaStream_t s,
                        int nsm) {
 #define HG_WEDGE_PASS(M)                                                                        \
   if (packed)                                                                                  \
     launch_all<M, true>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, dn, \
-                        upc, s, nsm);                                                          \
+                        rc, s, nsm);                                                           \
   else                                                                                         \
     launch_all<M, false>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, dn, \
-                         upc, s, nsm);
+                         rc, s, nsm);
   if (mode == 0) {
     HG_WEDGE_PASS(0)
   } else if (mode == 1) {

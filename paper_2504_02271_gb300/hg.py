@@ -30,7 +30,9 @@ HG_OK = 0
 EXPORTED = ("hg_set_allocator", "hg_load_csr", "hg_build_wedges", "hg_count_patterns",
             "hg_clustering_coeff", "hg_free", "hg_status_str", "hg_set_timing", "hg_kernel_times",
             "hg_pattern_table", "hg_close_stats_get", "hg_kernel_launches",
-            "hg_wedge_degrees_noalloc", "hg_sample_estimate")
+            "hg_wedge_degrees_noalloc", "hg_sample_estimate", "hg_load_batch",
+            "hg_batch_build_wedges", "hg_batch_count_patterns", "hg_batch_clustering_coeff",
+            "hg_batch_waves", "hg_batch_wave", "hg_batch_free")
 
 
 class HgError(RuntimeError):
@@ -88,6 +90,14 @@ def _open():
     lib.hg_wedge_degrees_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp]
     u64 = ctypes.c_uint64
     lib.hg_sample_estimate.argtypes = [vp, u64, u64, u64, ctypes.c_double, vp, vp]
+    lib.hg_load_batch.argtypes = [i32, vp, vp, vp, vp, ctypes.c_int, i64, vp, ctypes.POINTER(vp)]
+    lib.hg_batch_build_wedges.argtypes = [vp, ctypes.POINTER(_Tuning)]
+    lib.hg_batch_count_patterns.argtypes = [vp, vp, vp]
+    lib.hg_batch_clustering_coeff.argtypes = [vp, vp, vp, vp, vp]
+    lib.hg_batch_waves.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.hg_batch_wave.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(i32),
+                                  ctypes.POINTER(i32)]
+    lib.hg_batch_free.argtypes = [vp]
     for name in EXPORTED:
         if name != "hg_status_str":
             getattr(lib, name).restype = ctypes.c_int
@@ -158,9 +168,10 @@ class Graph:
     num_vertices: int
     num_edges: int
     nnz: int
+    owned: bool = True   # False for the wave handles a Batch lends out
 
     def __del__(self):
-        if self.ptr:
+        if self.ptr and self.owned:
             try:
                 _lib.hg_free(ctypes.c_void_p(self.ptr))
             except Exception:
@@ -313,3 +324,120 @@ def hg_kernel_times(g: Graph) -> dict[str, tuple[float, int]]:
     _check("hg_kernel_times", _lib.hg_kernel_times(ctypes.c_void_p(g.ptr), names, ms, launches,
                                                    ctypes.byref(n)))
     return {names[k].decode(): (float(ms[k]), int(launches[k])) for k in range(n.value)}
+
+
+# ------------------------------------------------------------------ batches
+
+@dataclass
+class Batch:
+    """An hg_batch handle: many hypergraphs counted in the same launches."""
+
+    ptr: int
+    stream: int
+    num_graphs: int
+    keep: object = None
+
+    def __del__(self):
+        if self.ptr:
+            try:
+                _lib.hg_batch_free(ctypes.c_void_p(self.ptr))
+            except Exception:
+                pass
+            self.ptr = 0
+
+
+def concat_members(members):
+    """Member CSRs [(num_vertices, edge_ptr, edge_vtx), ...] -> the concatenated
+    (num_vertices[G], edge_off[G+1], edge_ptr, edge_vtx) layout of hg_load_batch
+    (vertex ids stay member-local)."""
+    nv = np.array([int(m[0]) for m in members], dtype=np.int32)
+    ne = np.array([len(m[1]) - 1 for m in members], dtype=np.int64)
+    edge_off = np.zeros(len(members) + 1, dtype=np.int64)
+    np.cumsum(ne, out=edge_off[1:])
+    nnz = np.array([int(m[1][-1]) for m in members], dtype=np.int64)
+    base = np.zeros(len(members) + 1, dtype=np.int64)
+    np.cumsum(nnz, out=base[1:])
+    edge_ptr = np.empty(int(edge_off[-1]) + 1, dtype=np.int64)
+    for k, m in enumerate(members):
+        edge_ptr[edge_off[k]:edge_off[k + 1]] = np.asarray(m[1][:-1], dtype=np.int64) + base[k]
+    edge_ptr[-1] = base[-1]
+    edge_vtx = (np.concatenate([np.asarray(m[2], dtype=np.int32) for m in members])
+                if len(members) else np.zeros(0, dtype=np.int32))
+    return nv, edge_off, edge_ptr, edge_vtx
+
+
+def hg_load_batch(num_vertices, edge_off, edge_ptr, edge_vtx, max_wave_edges: int = 0,
+                  stream: int | None = None) -> Batch:
+    """Upload a batch (layout of concat_members); edge_ptr/edge_vtx on host or device."""
+    nv = np.ascontiguousarray(num_vertices, dtype=np.int32)
+    eo = np.ascontiguousarray(edge_off, dtype=np.int64)
+    if len(eo) != len(nv) + 1:
+        raise ValueError("edge_off must have num_graphs + 1 entries")
+    p_ptr, p_dev, keep1 = _as_ptr(edge_ptr, np.int64)
+    v_ptr, v_dev, keep2 = _as_ptr(edge_vtx, np.int32)
+    if p_dev != v_dev:
+        raise ValueError("edge_ptr and edge_vtx must both be on the host or both on the device")
+    if stream is None:
+        stream = _default_stream()
+    out = ctypes.c_void_p()
+    st = _lib.hg_load_batch(len(nv), nv.ctypes.data, eo.ctypes.data, ctypes.c_void_p(p_ptr),
+                            ctypes.c_void_p(v_ptr), 1 if p_dev else 0, int(max_wave_edges),
+                            ctypes.c_void_p(stream), ctypes.byref(out))
+    del keep1, keep2
+    _check("hg_load_batch", st)
+    return Batch(int(out.value), int(stream), len(nv))
+
+
+def hg_batch_build_wedges(b: Batch, dense_min_size: int = 0, dense_max_count: int = 0,
+                          close_mode: int = 0) -> None:
+    tun = _Tuning(int(dense_min_size), int(dense_max_count), int(close_mode))
+    _check("hg_batch_build_wedges", _lib.hg_batch_build_wedges(ctypes.c_void_p(b.ptr),
+                                                               ctypes.byref(tun)))
+
+
+def hg_batch_count_patterns(b: Batch) -> tuple[np.ndarray, dict]:
+    """(counts uint64[G, 21], per-member wedge stats as uint64 arrays of length G)."""
+    counts = np.zeros((b.num_graphs, 21), dtype=np.uint64)
+    stats = (_WedgeStats * b.num_graphs)()
+    _check("hg_batch_count_patterns",
+           _lib.hg_batch_count_patterns(ctypes.c_void_p(b.ptr), counts.ctypes.data,
+                                        ctypes.cast(stats, ctypes.c_void_p)))
+    arr = np.ctypeslib.as_array(ctypes.cast(stats, ctypes.POINTER(ctypes.c_uint64)),
+                                shape=(b.num_graphs, 8)).copy()
+    names = [n for n, _ in _WedgeStats._fields_]
+    return counts, {n: arr[:, k] for k, n in enumerate(names) if n != "reserved"}
+
+
+def hg_batch_clustering_coeff(b: Batch, eps) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Per member (cc, open hyper-triangles, connected triples) for weights eps[20]."""
+    e = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+    if e.shape != (20,):
+        raise ValueError("eps must have 20 entries")
+    cc = np.zeros(b.num_graphs, dtype=np.float64)
+    op = np.zeros(b.num_graphs, dtype=np.uint64)
+    co = np.zeros(b.num_graphs, dtype=np.uint64)
+    _check("hg_batch_clustering_coeff",
+           _lib.hg_batch_clustering_coeff(ctypes.c_void_p(b.ptr), e.ctypes.data, cc.ctypes.data,
+                                          op.ctypes.data, co.ctypes.data))
+    return cc, op, co
+
+
+def hg_batch_waves(b: Batch) -> list[tuple[Graph, int, int]]:
+    """[(wave handle (borrowed), first member, member count), ...]."""
+    n = ctypes.c_int32()
+    _check("hg_batch_waves", _lib.hg_batch_waves(ctypes.c_void_p(b.ptr), ctypes.byref(n)))
+    out = []
+    for k in range(n.value):
+        w = ctypes.c_void_p()
+        f = ctypes.c_int32()
+        c = ctypes.c_int32()
+        _check("hg_batch_wave", _lib.hg_batch_wave(ctypes.c_void_p(b.ptr), k, ctypes.byref(w),
+                                                   ctypes.byref(f), ctypes.byref(c)))
+        out.append((Graph(int(w.value), b.stream, 0, 0, 0, owned=False), f.value, c.value))
+    return out
+
+
+def hg_batch_free(b: Batch) -> None:
+    if b.ptr:
+        p, b.ptr = b.ptr, 0
+        _check("hg_batch_free", _lib.hg_batch_free(ctypes.c_void_p(p)))

@@ -31,25 +31,37 @@ CASES = {
     "tag_heavy_prefix1000": (hgen.TAG_HEAVY, 1_000),
     "tag_heavy_prefix2000": (hgen.TAG_HEAVY, 2_000),
 }
+# hub hypergraphs (hgen.hub): name -> (spokes, extra pairs, seed)
+HUBS = {
+    "hub6000": (6000, 200, 3),
+    "hub3000": (3000, 0, 0),
+}
 
 
 def run(name: str) -> dict:
-    spec, pre = CASES[name]
-    e_ptr, e_idx = hgen.generate(spec)
-    if pre is not None:
-        e_ptr, e_idx = hgen.prefix(e_ptr, e_idx, pre)
+    if name in HUBS:
+        nv, e_ptr, e_idx = hgen.hub(*HUBS[name])
+        workload, pre = "hub", None
+    else:
+        spec, pre = CASES[name]
+        nv, workload = spec.num_vertices, spec.name
+        e_ptr, e_idx = hgen.generate(spec)
+        if pre is not None:
+            e_ptr, e_idx = hgen.prefix(e_ptr, e_idx, pre)
     t0 = time.time()
-    r = oracle.count(e_ptr, e_idx, spec.num_vertices)
+    r = oracle.count(e_ptr, e_idx, nv)
     entry = {
-        "workload": spec.name, "prefix_edges": pre, "num_vertices": spec.num_vertices,
+        "workload": workload, "prefix_edges": pre, "num_vertices": nv,
         "num_edges": len(e_ptr) - 1, "nnz": int(e_ptr[-1]),
         "csr_hash": hgen.csr_hash(e_ptr, e_idx),
         "counts": [int(x) for x in r.counts], "W": r.W, "W_t": r.W_t, "W_c": r.W_c,
         "connected": r.connected, "open": r.open, "max_deg": r.max_deg,
         "oracle_seconds": round(r.seconds, 2), "oracle_threads": r.threads,
     }
+    if name in HUBS:
+        entry["hub"] = list(HUBS[name])
     if pre is not None and pre <= 300:
-        b = oracle.count(e_ptr, e_idx, spec.num_vertices, mode="brute")
+        b = oracle.count(e_ptr, e_idx, nv, mode="brute")
         assert [int(x) for x in b.counts] == entry["counts"] and b.open == r.open
         entry["brute_force_agrees"] = True
     print(f"{name}: T={r.T} W={r.W} {time.time() - t0:.1f}s", flush=True)
@@ -61,7 +73,7 @@ def main(names: list[str]) -> None:
     if os.path.exists(OUT):
         with open(OUT) as f:
             data = json.load(f)
-    for n in names or list(CASES):
+    for n in names or list(CASES) + list(HUBS):
         data[n] = run(n)
         with open(OUT, "w") as f:
             json.dump(data, f, indent=1, sort_keys=True)
