@@ -419,13 +419,18 @@ def run_ours(args):
 
 # ------------------------------------------------------------------ batches of hypergraphs
 
-def roofline_from_times(kernel_ms, cs, T, clk):
-    """ALU roofline of the closure kernel with the largest share (see close_algorithmic)."""
+def roofline_from_times(kernel_ms, cs, T, clk, steps):
+    """ALU roofline of the closure kernel with the largest share (see close_algorithmic).
+
+    kernel_ms holds (summed ms, launches) over `steps` steps; cs and T are one step's
+    work, which that kernel does in launches / steps launches (one per wave)."""
     peak_hbm, peak_kind = measured_peaks()
     groups = {n: v for n, v in kernel_ms.items() if n in CLOSE_GROUPS}
     dom = max(groups, key=lambda n: groups[n][0])
-    dom_ms = groups[dom][0] / groups[dom][1]
+    dom_ms = groups[dom][0] / groups[dom][1]            # average launch duration
+    per_step = groups[dom][1] / steps                   # launches of it in one step
     nbytes, ops = close_algorithmic(cs, CLOSE_GROUPS[dom], T)
+    nbytes, ops = nbytes / per_step, ops / per_step     # per launch
     sm_mhz = ((clk or {}).get("sm_mhz") or 2070.0)
     peak_ops = 152 * ISSUE_LANE_OPS_PER_CYCLE_PER_SM * sm_mhz * 1e6 / 1e12
     achieved_ops = ops / (dom_ms / 1000.0) / 1e12
@@ -568,7 +573,7 @@ def run_batched(args):
         e2e_ms.append(ms)
     e2e_value = T * len(e2e_ms) / (sum(e2e_ms) / 1000.0)
 
-    roof = roofline_from_times(kernel_ms, cs, T, clk)
+    roof = roofline_from_times(kernel_ms, cs, T, clk, args.steps)
     cpu = None
     if not args.skip_cpu_baseline:
         import oracle

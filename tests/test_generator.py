@@ -71,3 +71,22 @@ def test_loguniform_sizes(gen):
     assert min(xs) >= 100 and max(xs) <= 200_000
     med = float(np.median(np.log(xs)))
     assert abs(med - (math.log(100) + math.log(200_000)) / 2) < 0.6
+
+
+def test_stored_hub_values_follow_the_sunflower_closed_form():
+    # hub(3000, 0, 0): 3000 hyperedges meeting pairwise in exactly {0}, each with a
+    # private vertex: every triple is a hyper-triangle with regions a, b, c, g
+    # non-empty (pattern 9), so H[9] = C(3000, 3), W = C(3000, 2) and no hyperwedge
+    # is of inclusion type.  Pins the stored oracle entry the GPU tests compare with.
+    from math import comb
+
+    import hgen
+
+    gold = load_json("workloads.json")["hub3000"]
+    nv, e_ptr, e_idx = hgen.hub(*gold["hub"])
+    assert hgen.csr_hash(e_ptr, e_idx) == gold["csr_hash"] and nv == gold["num_vertices"]
+    want = [0] * 21
+    want[0] = want[9] = comb(3000, 3)
+    assert gold["counts"] == want
+    assert (gold["W"], gold["W_c"], gold["W_t"]) == (comb(3000, 2), 0, comb(3000, 2))
+    assert gold["connected"] == 3000 * comb(2999, 2) and gold["open"] == 0

@@ -63,3 +63,23 @@ def test_estimate_is_unbiased(small):
     for p in [0] + [p for p in range(1, 21) if exact.counts[p] > exact.T // 50]:
         mean, se = ests[:, p].mean(), ests[:, p].std(ddof=1) / np.sqrt(len(ests))
         assert abs(mean - float(exact.counts[p])) < 4 * se + 1e-9, p
+
+
+def test_block_function_avalanche():
+    # flipping any one of the 128 counter bits changes about half of the 128 output
+    # bits (a dropped round or a wrong word order would leave many bits unchanged)
+    import oracle
+
+    rng = np.random.default_rng(7)
+    flips = []
+    for _ in range(24):
+        c = [int(x) for x in rng.integers(0, 2**32, 4, dtype=np.uint64)]
+        k = [int(x) for x in rng.integers(0, 2**32, 2, dtype=np.uint64)]
+        y0 = oracle.philox4x32_10(c, k)
+        for bit in range(128):
+            c2 = list(c)
+            c2[bit // 32] ^= 1 << (bit % 32)
+            y1 = oracle.philox4x32_10(c2, k)
+            flips.append(sum(bin(a ^ b).count("1") for a, b in zip(y0, y1)))
+    flips = np.array(flips)
+    assert abs(flips.mean() - 64.0) < 1.0 and flips.min() >= 30
