@@ -57,6 +57,10 @@ def parse_args():
                     help="--workload batched: members (seeds 100 ..) in the batch")
     ap.add_argument("--per-graph-steps", type=int, default=2,
                     help="--workload batched: timed steps of the one-handle-per-hypergraph form")
+    ap.add_argument("--queries", type=int, default=10_000, help="--workload served: stream length")
+    ap.add_argument("--plain-queries", type=int, default=1000,
+                    help="--workload served: queries replayed with batching off")
+    ap.add_argument("--serve-workers", type=int, default=4)
     return ap.parse_args()
 
 
@@ -626,6 +630,218 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ serving
+
+def served_stream(n, n_graphs, rate, seed=5):
+    """The query stream: Poisson arrivals at `rate`/s; kind and hypergraph uniform;
+    estimates draw samples k*1e6 .. k*1e6 + 1e6 - 1 under seed 2024 (query k)."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    kinds = rng.integers(0, 3, n)
+    gids = rng.integers(0, n_graphs, n)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n))
+    qs = [{"kind": int(kinds[k]), "graph": int(gids[k]), "seed": 2024,
+           "first_sample": k * 1_000_000, "num_samples": 1_000_000} for k in range(n)]
+    return qs, arrivals
+
+
+def serve_stream(hg, srv, ids, qs, arrivals, eps):
+    """Submit at the arrival times from a producer thread; collect every answer."""
+    import threading
+
+    tickets = [None] * len(qs)
+
+    def producer():
+        t0 = time.perf_counter()
+        for k, q in enumerate(qs):
+            delay = arrivals[k] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            tickets[k] = srv.submit(q["kind"], ids[q["graph"]], q["seed"], q["first_sample"],
+                                    q["num_samples"], eps)
+
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    return [srv.wait(t) for t in tickets]
+
+
+def latency_summary(res):
+    import numpy as np
+
+    lat = np.array([r["t_done"] - r["t_submit"] for r in res]) * 1000.0
+    span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+    return {"queries": len(res), "seconds": round(span, 3), "queries_per_s": round(len(res) / span, 1),
+            "p50_ms": round(float(np.percentile(lat, 50)), 2),
+            "p99_ms": round(float(np.percentile(lat, 99)), 2),
+            "max_ms": round(float(lat.max()), 2)}
+
+
+def run_served(args):
+    """64 resident hypergraphs (|E| log-uniform in [1000, 1000000], |V| = |E|/5, otherwise
+    the co-authorship shape), a Poisson stream of queries answered by hg_server."""
+    import numpy as np
+    import torch
+
+    import hgen
+    import oracle
+
+    torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    import paper_2504_02271_gb300 as hg
+
+    n_graphs, n_queries, rate = 64, args.queries, 2000.0
+    specs = [hgen.served(m) for m in range(n_graphs)]
+    nv, eoff, eptr, evtx, _ = hgen.generate_batch(specs)
+    gs = []
+    for m in range(n_graphs):
+        p = np.ascontiguousarray(eptr[eoff[m]:eoff[m + 1] + 1] - eptr[eoff[m]])
+        gs.append((int(nv[m]), p, np.ascontiguousarray(evtx[eptr[eoff[m]]:eptr[eoff[m + 1]]])))
+    qs, arrivals = served_stream(n_queries, n_graphs, rate)
+    eps = [1.0] * 20
+
+    # answers of the plain calls alone: exact ones per hypergraph (and the oracle's on
+    # the small ones); estimates for a sample of the queries
+    stream = torch.cuda.Stream()
+    alone = {}
+    for m, (n_v, p, i) in enumerate(gs):
+        g = hg.hg_load_csr(n_v, len(p) - 1, p, i, stream=stream.cuda_stream)
+        try:
+            hg.hg_build_wedges(g)
+            alone[m] = (hg.hg_count_patterns(g), hg.hg_clustering_coeff(g, eps))
+        finally:
+            hg.hg_free(g)
+    small = [m for m in range(n_graphs) if len(gs[m][1]) - 1 <= 3000]
+    for m in small:
+        r = oracle.count(gs[m][1], gs[m][2], gs[m][0])
+        if r.counts.tolist() != alone[m][0].tolist():
+            raise SystemExit(f"bench: hypergraph {m} differs from the oracle")
+
+    clocks = ClockSampler(dev)
+    clocks.start()
+    launches0 = hg.hg_kernel_launches()
+    t_reg = time.perf_counter()
+    srv = hg.Server(workers=args.serve_workers)
+    ids = [srv.add_graph(n_v, p, i) for n_v, p, i in gs]      # host buffers -> device
+    reg_s = time.perf_counter() - t_reg
+    res = serve_stream(hg, srv, ids, qs, arrivals, eps)
+    stats = srv.stats()
+    srv.close()
+    wall = time.perf_counter() - t_reg
+    launches = hg.hg_kernel_launches() - launches0
+    clk = clocks.stop()
+
+    # every exact answer equals the plain calls'; a sample of estimates too, some the oracle's
+    for q, r in zip(qs, res):
+        if r["status"] != 0:
+            raise SystemExit(f"bench: query failed with status {r['status']}")
+        if q["kind"] != 2:
+            c, (cc, op, co) = alone[q["graph"]]
+            if r["counts"].tolist() != c.tolist() or (q["kind"] == 1 and not (
+                    (np.isnan(cc) and np.isnan(r["cc"])) or cc == r["cc"])):
+                raise SystemExit("bench: a served exact answer differs from the plain calls")
+    est_idx = [k for k, q in enumerate(qs) if q["kind"] == 2]
+    rng = np.random.default_rng(11)
+    for k in rng.choice(est_idx, min(40, len(est_idx)), replace=False):
+        q, r = qs[k], res[k]
+        n_v, p, i = gs[q["graph"]]
+        g = hg.hg_load_csr(n_v, len(p) - 1, p, i, stream=stream.cuda_stream)
+        try:
+            hg.hg_build_wedges(g)
+            raw, est = hg.hg_sample_estimate(g, q["seed"], q["first_sample"], q["num_samples"])
+        finally:
+            hg.hg_free(g)
+        if raw.tolist() != r["counts"].tolist() or est.tolist() != r["est"].tolist():
+            raise SystemExit("bench: a served estimate differs from the plain call")
+    checked_oracle = 0
+    for k in est_idx:
+        q = qs[k]
+        if q["graph"] in small and checked_oracle < 3:
+            n_v, p, i = gs[q["graph"]]
+            ref = oracle.sample_estimate(p, i, n_v, seed=q["seed"], first=q["first_sample"],
+                                         num=q["num_samples"])
+            if ref.raw.tolist() != res[k]["counts"].tolist() or ref.est.tolist() != res[k]["est"].tolist():
+                raise SystemExit("bench: a served estimate differs from the oracle")
+            checked_oracle += 1
+
+    summary = latency_summary(res)
+    exact_batches = {}   # (worker, start time) of an exact batch -> its distinct hypergraphs
+    for r in res:
+        if r["kind"] != 2:
+            exact_batches.setdefault((r["worker"], r["t_start"]), set()).add(r["graph"])
+    computed_T = sum(int(alone[g][0][0]) for gset in exact_batches.values() for g in gset)
+    answered_T = sum(int(r["counts"][0]) for q, r in zip(qs, res) if q["kind"] != 2)
+
+    # the same stream's first queries with batching off (one worker, one query per batch)
+    n_plain = min(args.plain_queries, n_queries)
+    srv1 = hg.Server(workers=1, max_batch_queries=1)
+    ids1 = [srv1.add_graph(n_v, p, i) for n_v, p, i in gs]
+    res1 = serve_stream(hg, srv1, ids1, qs[:n_plain], arrivals[:n_plain], eps)
+    srv1.close()
+    for a, b in zip(res[:n_plain], res1):
+        if a["counts"].tolist() != b["counts"].tolist() or a["est"].tolist() != b["est"].tolist():
+            raise SystemExit("bench: answers differ between batched and unbatched serving")
+    plain = latency_summary(res1)
+
+    cpu = None
+    if not args.skip_cpu_baseline:
+        # the oracle answering the stream's queries in order, one at a time, for ~15 s;
+        # exact queries on hypergraphs above 200,000 hyperedges are skipped (one of them
+        # alone runs for minutes on the host)
+        secs, done, skipped, threads = 0.0, 0, 0, 1
+        t0 = time.perf_counter()
+        for q in qs:
+            if time.perf_counter() - t0 > 15.0:
+                break
+            n_v, p, i = gs[q["graph"]]
+            if q["kind"] != 2 and len(p) - 1 > 200_000:
+                skipped += 1
+                continue
+            if q["kind"] == 2:
+                r = oracle.sample_estimate(p, i, n_v, seed=q["seed"], first=q["first_sample"],
+                                           num=q["num_samples"])
+            else:
+                r = oracle.count(p, i, n_v)
+                threads = r.threads
+            done += 1
+        secs = time.perf_counter() - t0
+        cpu = {"value": round(done / secs, 3), "unit": "queries/s", "cores": threads,
+               "kind": "oracle", "seconds": round(secs, 2),
+               "sample": f"the stream's first {done} queries answered one at a time (skipping "
+                         f"{skipped} exact queries on hypergraphs above 200,000 hyperedges)"}
+
+    line = {
+        "metric": "queries answered/s (exact counts, clustering coefficients, 1e6-sample estimates) with p50/p99 latency",
+        "value": summary["queries_per_s"], "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": round(summary["seconds"] * 1000, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "served", "graphs": n_graphs, "sum_edges": int(eoff[-1]),
+                   "sum_nnz": int(eptr[-1]), "graph_edges": "log-uniform in [1000, 1000000]",
+                   "graph_vertices": "|E|/5, co-authorship shape, degree cap 100",
+                   "queries": n_queries, "arrivals": f"Poisson {rate:.0f}/s",
+                   "mix": "1/3 counts, 1/3 clustering coefficient, 1/3 estimate (1e6 Philox samples)",
+                   "workers": args.serve_workers,
+                   "parity": "exact answers equal the plain calls (and the oracle on hypergraphs "
+                             "with <= 3000 hyperedges); 40 estimates equal the plain call, 3 the oracle"},
+        "latency": summary,
+        "triangles": {"answered": answered_T, "computed": computed_T,
+                      "computed_per_s": round(computed_T / summary["seconds"], 1)},
+        "server": stats,
+        "unbatched": dict(plain, note="same server, workers=1, max_batch_queries=1, the stream's first "
+                                      f"{n_plain} queries at the same arrival times"),
+        "e2e": {"value": round(n_queries / wall, 1), "unit": "queries/s",
+                "h2d_bytes_per_step": int(eptr.nbytes + evtx.nbytes),
+                "d2h_bytes_per_step": int(n_queries * 416), "registration_s": round(reg_s, 3),
+                "seconds": round(wall, 3)},
+        "roofline": None,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def cpu_baseline(e_ptr, e_idx, nv, sample_edges):
     import oracle
 
@@ -706,6 +922,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_ours(args)
 

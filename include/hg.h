@@ -254,6 +254,17 @@ hg_status hg_load_batch(int32_t num_graphs, const int32_t* num_vertices, const i
                         const int64_t* edge_ptr, const int32_t* edge_vtx, int inputs_on_device,
                         int64_t max_wave_edges, void* cuda_stream, hg_batch** out);
 
+/*
+ * The same for members stored apart: member m's CSR is edge_ptrs[m][0 .. num_edges[m]]
+ * (offsets from 0) and edge_vtxs[m] (member-local ids), all on the host or all on the
+ * device.  The pointer arrays themselves are host arrays.  The members are gathered
+ * into the waves with one copy per member.
+ */
+hg_status hg_load_batch_members(int32_t num_graphs, const int32_t* num_vertices,
+                                const int32_t* num_edges, const int64_t* const* edge_ptrs,
+                                const int32_t* const* edge_vtxs, int inputs_on_device,
+                                int64_t max_wave_edges, void* cuda_stream, hg_batch** out);
+
 /* Step one (as hg_build_wedges) on every wave.  opt may be NULL.  Synchronises. */
 hg_status hg_batch_build_wedges(hg_batch* b, const hg_tuning* opt);
 
@@ -279,6 +290,94 @@ hg_status hg_batch_wave(hg_batch* b, int32_t k, hg_graph** wave, int32_t* first_
 
 /* Release the batch, its waves and their device buffers. */
 hg_status hg_batch_free(hg_batch* b);
+
+/*
+ * Serving: count, clustering-coefficient and sampled-estimate queries on hypergraphs
+ * kept resident on the device, answered with continuous batching.  (No counterpart
+ * in the paper, which answers one query on one hypergraph at a time.)
+ *
+ * Queries are admitted in arrival order.  A free worker takes the oldest waiting
+ * query with everything that can share its launches: an exact query takes every
+ * waiting exact query whose hypergraph is in the batch or still fits
+ * (max_batch_graphs, the device-memory budget), and the batch runs as one
+ * hg_load_batch_members / hg_batch_build_wedges / hg_batch_count_patterns with each
+ * distinct hypergraph evaluated once; an estimate query takes the waiting estimate
+ * queries on its hypergraph, which share one load and step one.  `workers` batches
+ * run at the same time, each on its own CUDA stream; a batch waits while its memory
+ * estimate does not fit the budget (unless nothing else is running).  Every answer
+ * equals the one the plain calls give for that query alone.
+ *
+ * Threads: submit / wait / drain / stats may be called from any thread.  The
+ * server's own threads allocate with cudaMallocAsync whatever hg_set_allocator set.
+ */
+typedef struct hg_server hg_server;
+
+typedef struct {
+  int32_t workers;            /* concurrent batches, each with its own stream (0 = 4) */
+  int32_t max_batch_graphs;   /* distinct hypergraphs in one exact batch (0 = 64) */
+  int64_t memory_budget;      /* device bytes of the batches in flight (0 = half of free) */
+  int32_t max_batch_queries;  /* queries in one batch (0 = no limit for exact batches, 256
+                                 for estimate groups); 1 = no batching */
+  int32_t reserved[3];
+} hg_server_options;
+
+typedef enum {
+  HG_Q_COUNTS = 0,       /* the 21 counts of hg_count_patterns */
+  HG_Q_CLUSTERING = 1,   /* the counts and Def. 5.1 with weights eps */
+  HG_Q_ESTIMATE = 2      /* hg_sample_estimate(seed, first_sample, num_samples, 1.0) */
+} hg_query_kind;
+
+typedef struct {
+  int32_t kind;          /* hg_query_kind */
+  int32_t graph;         /* id from hg_server_add_graph */
+  uint64_t seed, first_sample, num_samples;   /* HG_Q_ESTIMATE */
+  double eps[20];        /* HG_Q_CLUSTERING */
+} hg_query;
+
+typedef struct {
+  hg_status status;
+  int32_t kind, graph;
+  uint64_t counts[21];   /* exact counts, or the raw sample counts of an estimate */
+  double est[21];        /* HG_Q_ESTIMATE */
+  double cc;             /* HG_Q_CLUSTERING: cc, open, connected as hg_clustering_coeff */
+  uint64_t open, connected;
+  double t_submit, t_start, t_done;   /* seconds since hg_server_create */
+  int32_t batch_queries, batch_graphs, worker, reserved;
+} hg_result;
+
+typedef struct {
+  uint64_t submitted, batches, exact_batches, queries_batched;
+  uint64_t max_in_flight_bytes, max_concurrent_batches, budget_bytes;
+  double now;            /* seconds since hg_server_create */
+} hg_server_stats;
+
+/* Start the workers on the current device.  opt may be NULL (defaults). */
+hg_status hg_server_create(const hg_server_options* opt, hg_server** out);
+
+/*
+ * Register a hypergraph: its CSR (as hg_load_csr; host or device) is copied into
+ * server-owned device memory and stays there until hg_server_destroy.  Validates it
+ * and runs step one once to size its memory estimate.  Synchronises.
+ */
+hg_status hg_server_add_graph(hg_server* s, int32_t num_vertices, int32_t num_edges,
+                              const int64_t* edge_ptr, const int32_t* edge_vtx,
+                              int inputs_on_device, int32_t* graph_id);
+
+/* Queue a query (copied); returns at once with a ticket for hg_server_wait. */
+hg_status hg_server_submit(hg_server* s, const hg_query* q, uint64_t* ticket);
+
+/* Block until the ticket's query is answered, then hand its result over (each ticket
+ * once; an unknown or collected ticket is HG_ERR_INVALID_ARG).  The query's own
+ * outcome is out->status. */
+hg_status hg_server_wait(hg_server* s, uint64_t ticket, hg_result* out);
+
+/* Block until nothing is queued or running. */
+hg_status hg_server_drain(hg_server* s);
+
+hg_status hg_server_stats_get(hg_server* s, hg_server_stats* out);
+
+/* Answer what is queued, stop the workers, free the resident hypergraphs. */
+hg_status hg_server_destroy(hg_server* s);
 
 /*
  * The library's pattern table: lut[m] = pattern 1..20 of a labelled region mask

@@ -11,7 +11,8 @@ from .hg import (  # noqa: F401
     hg_set_timing, hg_status_str,
     use_default_allocator, use_torch_allocator,
     Batch, concat_members, hg_batch_build_wedges, hg_batch_clustering_coeff, hg_batch_count_patterns,
-    hg_batch_free, hg_batch_waves, hg_load_batch,
+    hg_batch_free, hg_batch_waves, hg_load_batch, hg_load_batch_members,
+    Server, HG_Q_COUNTS, HG_Q_CLUSTERING, HG_Q_ESTIMATE,
 )
 
 

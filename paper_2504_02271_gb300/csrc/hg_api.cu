@@ -116,16 +116,22 @@ struct hg_graph {
 };
 
 namespace hg {
+void alloc_bypass_hooks(bool on);
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 }  // namespace hg
 
 namespace {
 
+// Threads of the library's own runtime (the server's workers) allocate with
+// cudaMallocAsync even when the caller installed hooks: the hooks may call back into
+// an interpreter that those threads must not wait on.
+thread_local bool t_bypass_hooks = false;
+
 void* dev_alloc(hg_graph* g, std::vector<Block>& owner, size_t bytes) {
   bytes = std::max<size_t>(bytes, 256);
   AllocatorHooks h;
-  {
+  if (!t_bypass_hooks) {
     std::lock_guard<std::mutex> lk(g_alloc_mu);
     h = g_hooks;
   }
@@ -325,6 +331,11 @@ struct WaveInput {
   const int32_t* eoff;
   const int32_t* voff;
   int64_t base;
+  // members stored apart (hg_load_batch_members): member q of the wave has its own
+  // offsets m_eptr[q][0 .. ne_q] (from 0) and ids m_evtx[q]; noff = its first incidence
+  const int64_t* const* m_eptr = nullptr;
+  const int32_t* const* m_evtx = nullptr;
+  const int64_t* noff = nullptr;
 };
 
 hg_status load_impl(hg_graph* g, const int64_t* edge_ptr, const int32_t* edge_vtx, int on_dev,
@@ -345,9 +356,23 @@ hg_status load_impl(hg_graph* g, const int64_t* edge_ptr, const int32_t* edge_vt
       !vdeg || !g->scan_tmp)
     return HG_ERR_OOM;
   HG_CUDA(cudaMemsetAsync(g->small, 0, sizeof(Small), s));
-  HG_CUDA(cudaMemcpyAsync(g->e_ptr, edge_ptr, sizeof(int64_t) * ((size_t)g->ne + 1), kind, s));
-  if (g->nnz > 0)
-    HG_CUDA(cudaMemcpyAsync(g->e_idx, edge_vtx, sizeof(int32_t) * (size_t)g->nnz, kind, s));
+  if (wave && wave->m_eptr) {
+    // gather the members (in order: a member's last offset is overwritten by the next
+    // member's first), then shift offsets by each member's first incidence
+    for (int32_t q = 0; q < g->nm; ++q) {
+      const int64_t ne_q = wave->eoff[q + 1] - wave->eoff[q];
+      const int64_t nnz_q = wave->noff[q + 1] - wave->noff[q];
+      HG_CUDA(cudaMemcpyAsync(g->e_ptr + wave->eoff[q], wave->m_eptr[q],
+                              sizeof(int64_t) * (size_t)(ne_q + 1), kind, s));
+      if (nnz_q > 0)
+        HG_CUDA(cudaMemcpyAsync(g->e_idx + wave->noff[q], wave->m_evtx[q],
+                                sizeof(int32_t) * (size_t)nnz_q, kind, s));
+    }
+  } else {
+    HG_CUDA(cudaMemcpyAsync(g->e_ptr, edge_ptr, sizeof(int64_t) * ((size_t)g->ne + 1), kind, s));
+    if (g->nnz > 0)
+      HG_CUDA(cudaMemcpyAsync(g->e_idx, edge_vtx, sizeof(int32_t) * (size_t)g->nnz, kind, s));
+  }
   if (wave) {
     g->m_eoff = alloc_t<int32_t>(g, g->load_blocks, (int64_t)g->nm + 1);
     g->m_voff = alloc_t<int32_t>(g, g->load_blocks, (int64_t)g->nm + 1);
@@ -356,7 +381,15 @@ hg_status load_impl(hg_graph* g, const int64_t* edge_ptr, const int32_t* edge_vt
                             cudaMemcpyHostToDevice, s));
     HG_CUDA(cudaMemcpyAsync(g->m_voff, wave->voff, sizeof(int32_t) * ((size_t)g->nm + 1),
                             cudaMemcpyHostToDevice, s));
-    launch_sub_base(g->e_ptr, g->ne, wave->base, s);
+    if (wave->m_eptr) {
+      int64_t* noff = alloc_t<int64_t>(g, g->load_blocks, (int64_t)g->nm + 1);
+      if (!noff) return HG_ERR_OOM;
+      HG_CUDA(cudaMemcpyAsync(noff, wave->noff, sizeof(int64_t) * ((size_t)g->nm + 1),
+                              cudaMemcpyHostToDevice, s));
+      launch_add_member_base(g->e_ptr, g->ne, g->m_eoff, g->nm, noff, s);
+    } else {
+      launch_sub_base(g->e_ptr, g->ne, wave->base, s);
+    }
   }
   Small h;
   launch_check_ptr(g->e_ptr, g->ne, g->nnz, &g->small->err, s);
@@ -752,9 +785,14 @@ void free_batch(hg_batch* b) {
 
 constexpr int64_t kDefaultWaveEdges = (int64_t(1) << 24) - 1;   // packed 24-bit neighbour ids
 
+// member_ptr/member_vtx (both or neither): members stored apart, member m's offsets
+// member_ptr[m][0 .. ne_m] from 0; otherwise the concatenated edge_ptr / edge_vtx.
 hg_status load_batch_impl(hg_batch* b, const int32_t* num_vertices, const int64_t* edge_off,
                           const int64_t* edge_ptr, const int32_t* edge_vtx, int on_dev,
-                          int64_t max_wave_edges, int dev, int nsm) {
+                          int64_t max_wave_edges, int dev, int nsm,
+                          const int64_t* const* member_ptr = nullptr,
+                          const int32_t* const* member_vtx = nullptr,
+                          const int64_t* member_nnz = nullptr) {
   cudaStream_t s = b->stream;
   const int32_t G = b->G;
   // greedy waves of consecutive members: at most max_wave_edges hyperedges (a
@@ -778,6 +816,32 @@ hg_status load_batch_impl(hg_batch* b, const int32_t* num_vertices, const int64_
     const int32_t m0 = b->first[k], m1 = b->first[k + 1];
     const int64_t e0 = edge_off[m0], e1 = edge_off[m1];
     int64_t p0 = 0, p1 = 0;
+    if (member_ptr) {
+      std::vector<int32_t> eoff((size_t)(m1 - m0) + 1), voff((size_t)(m1 - m0) + 1);
+      std::vector<int64_t> noff((size_t)(m1 - m0) + 1);
+      int64_t nv = 0, nnz = 0;
+      for (int32_t q = m0; q <= m1; ++q) {
+        eoff[(size_t)(q - m0)] = (int32_t)(edge_off[q] - e0);
+        voff[(size_t)(q - m0)] = (int32_t)nv;
+        noff[(size_t)(q - m0)] = nnz;
+        if (q < m1) {
+          nv += num_vertices[q];
+          nnz += member_nnz[q];
+        }
+      }
+      hg_graph* g = new hg_graph();
+      g->device = dev;
+      g->nsm = nsm;
+      g->stream = s;
+      g->nv = (int32_t)std::max<int64_t>(nv, 1);
+      g->ne = (int32_t)(e1 - e0);
+      g->nnz = nnz;
+      g->nm = m1 - m0;
+      b->waves.push_back(g);
+      WaveInput wi{eoff.data(), voff.data(), 0, member_ptr + m0, member_vtx + m0, noff.data()};
+      HG_TRY(load_impl(g, nullptr, nullptr, on_dev, &wi));
+      continue;
+    }
     if (on_dev) {
       HG_CUDA(cudaMemcpyAsync(&p0, edge_ptr + e0, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
       HG_CUDA(cudaMemcpyAsync(&p1, edge_ptr + e1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -950,6 +1014,53 @@ hg_status hg_load_batch(int32_t num_graphs, const int32_t* num_vertices, const i
   return HG_OK;
 }
 
+hg_status hg_load_batch_members(int32_t num_graphs, const int32_t* num_vertices,
+                                const int32_t* num_edges, const int64_t* const* edge_ptrs,
+                                const int32_t* const* edge_vtxs, int inputs_on_device,
+                                int64_t max_wave_edges, void* cuda_stream, hg_batch** out) {
+  if (!out) return HG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (num_graphs < 1 || !num_vertices || !num_edges || !edge_ptrs || !edge_vtxs ||
+      max_wave_edges < 0)
+    return HG_ERR_INVALID_ARG;
+  int dev = 0, nsm = 0;
+  HG_TRY(check_device(&dev, &nsm));
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  std::vector<int64_t> edge_off((size_t)num_graphs + 1, 0), nnz((size_t)num_graphs, 0);
+  for (int32_t m = 0; m < num_graphs; ++m) {
+    if (num_vertices[m] < 1 || num_edges[m] < 0 || !edge_ptrs[m]) return HG_ERR_INVALID_ARG;
+    edge_off[(size_t)m + 1] = edge_off[(size_t)m] + num_edges[m];
+    int64_t first = 0, last = 0;
+    if (inputs_on_device) {
+      HG_CUDA(cudaMemcpyAsync(&first, edge_ptrs[m], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      HG_CUDA(cudaMemcpyAsync(&last, edge_ptrs[m] + num_edges[m], sizeof(int64_t),
+                              cudaMemcpyDeviceToHost, s));
+      HG_CUDA(cudaStreamSynchronize(s));
+    } else {
+      first = edge_ptrs[m][0];
+      last = edge_ptrs[m][num_edges[m]];
+    }
+    if (first != 0 || last < 0 || (last > 0 && !edge_vtxs[m])) return HG_ERR_INVALID_ARG;
+    nnz[(size_t)m] = last;
+  }
+  hg_batch* b = new hg_batch();
+  b->stream = s;
+  b->G = num_graphs;
+  hg_status st = load_batch_impl(b, num_vertices, edge_off.data(), nullptr, nullptr,
+                                 inputs_on_device,
+                                 max_wave_edges > 0 ? max_wave_edges : kDefaultWaveEdges, dev, nsm,
+                                 edge_ptrs, edge_vtxs, nnz.data());
+  if (st != HG_OK) {
+    cudaStreamSynchronize(s);
+    cudaGetLastError();
+    free_batch(b);
+    cudaGetLastError();
+    return st;
+  }
+  *out = b;
+  return HG_OK;
+}
+
 hg_status hg_batch_build_wedges(hg_batch* b, const hg_tuning* opt) {
   if (!b) return HG_ERR_INVALID_ARG;
   b->built = b->counted = false;
@@ -1104,3 +1215,7 @@ hg_status hg_kernel_times(hg_graph* g, const char** names, float* ms, int32_t* l
 }
 
 }  // extern "C"
+
+namespace hg {
+void alloc_bypass_hooks(bool on) { t_bypass_hooks = on; }
+}  // namespace hg

@@ -128,8 +128,13 @@ void launch_wedge_pass(int mode, const DevGraph& g, const WedgeBuckets& b, const
                        int* err, int32_t* work_counter, const DenseInfo& dense, RowCounts rc,
                        cudaStream_t s, int nsm);
 
+// hg_api.cu: allocations of the calling thread skip the caller-installed hooks
+void alloc_bypass_hooks(bool on);
+
 // k_batch.cu
 void launch_sub_base(int64_t* e_ptr, int32_t ne, int64_t base, cudaStream_t s);
+void launch_add_member_base(int64_t* e_ptr, int32_t ne, const int32_t* m_eoff, int32_t nm,
+                            const int64_t* noff, cudaStream_t s);
 void launch_localize(const DevGraph& g, const int32_t* m_voff, int32_t* e_idx, int* err,
                      cudaStream_t s);
 void launch_member_stats(const DevGraph& g, const int32_t* deg, const int32_t* wcr,

@@ -19,6 +19,19 @@ __global__ void k_sub_base(int64_t* __restrict__ e_ptr, int32_t ne, int64_t base
     e_ptr[i] -= base;
 }
 
+// Members gathered from separate CSRs: e_ptr[i] += noff[member of i] for i in [0, ne]
+// (position ne holds the last member's final offset, so it becomes the total).
+__global__ void k_add_member_base(int64_t* __restrict__ e_ptr, int32_t ne,
+                                  const int32_t* __restrict__ m_eoff, int32_t nm,
+                                  const int64_t* __restrict__ noff) {
+  DevGraph g{};
+  g.m_eoff = m_eoff;
+  g.nm = nm;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= ne;
+       i += (int64_t)gridDim.x * blockDim.x)
+    e_ptr[i] += noff[member_of(g, (int32_t)i)];
+}
+
 // Member-local vertex ids -> union ids (v + m_voff[m]); ids outside [0, |V_m|) set DE_RANGE.
 // Runs after the row pointers were checked, so every row range lies in [0, nnz).
 __global__ void k_localize(DevGraph g, const int32_t* __restrict__ m_voff, int32_t* __restrict__ e_idx,
@@ -84,6 +97,12 @@ void launch_sub_base(int64_t* e_ptr, int32_t ne, int64_t base, cudaStream_t s) {
   if (base == 0) return;
   note_launch();
   k_sub_base<<<grid_of((int64_t)ne + 1, 256), 256, 0, s>>>(e_ptr, ne, base);
+}
+
+void launch_add_member_base(int64_t* e_ptr, int32_t ne, const int32_t* m_eoff, int32_t nm,
+                            const int64_t* noff, cudaStream_t s) {
+  note_launch();
+  k_add_member_base<<<grid_of((int64_t)ne + 1, 256), 256, 0, s>>>(e_ptr, ne, m_eoff, nm, noff);
 }
 
 void launch_localize(const DevGraph& g, const int32_t* m_voff, int32_t* e_idx, int* err,

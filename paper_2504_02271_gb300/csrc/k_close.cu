@@ -17,6 +17,8 @@
 //   f = omega_uw - g, and g itself.
 // Their non-emptiness bits index a 128-entry table giving the pattern 1..20; a
 // block-local histogram is flushed to 64-bit global counters.
+#include <mutex>
+
 #include "hg_internal.cuh"
 
 namespace hg {
@@ -839,8 +841,19 @@ void launch_block(const DevGraph& g, const Oriented& o, int packed, const int32_
 
 }  // namespace
 
+// The table never changes, so it is written once per device (synchronously, before the
+// first kernel that reads it); concurrent host threads never rewrite constant memory
+// that a running kernel reads.
 void close_set_lut(const uint8_t lut[128], cudaStream_t s) {
-  cudaMemcpyToSymbolAsync(c_lut, lut, 128, 0, cudaMemcpyHostToDevice, s);
+  (void)s;
+  static std::mutex mu;
+  static uint64_t done = 0;   // bit d: device d holds the table
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done >> dev & 1) return;
+  if (cudaMemcpyToSymbol(c_lut, lut, 128, 0, cudaMemcpyHostToDevice) == cudaSuccess)
+    done |= uint64_t(1) << dev;
 }
 
 void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,

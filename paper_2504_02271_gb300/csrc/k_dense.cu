@@ -299,16 +299,16 @@ void launch_fill_dense(const int64_t* e_ptr, const int32_t* e_idx, const int32_t
 // Returns a CUDA error from the tensor-map encoding or the launch.
 cudaError_t launch_dense_omega(const uint8_t* a, int64_t rows, int64_t rows_pad, int64_t k_pad,
                                uint8_t* omega, int* err, cudaStream_t s) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
+  // looked up once (thread-safe static initialisation)
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() {
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
                                                      cudaEnableDefault, &q);
-    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-      return e != cudaSuccess ? e : cudaErrorNotSupported;
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess) fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode) return cudaErrorNotSupported;
   if (rows_pad % kBN || k_pad % kBK || ((uintptr_t)a & 255) || ((uintptr_t)omega & 15))
     return cudaErrorInvalidValue;
   CUtensorMap map;

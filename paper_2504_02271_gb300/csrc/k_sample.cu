@@ -9,6 +9,8 @@
 // (i, j) every k > j in both upper(i) and upper(j) closes the hyper-triangle
 // {i, j, k} whose smallest hyperwedge in O is (i, j); it is classified from its
 // seven Venn regions (g by a 3-way merge of the vertex lists) and counted.
+#include <mutex>
+
 #include "hg_internal.cuh"
 
 namespace hg {
@@ -195,8 +197,17 @@ constexpr int kSortMaxLog2 = 14;   // rows of up to 16,384 neighbours sort in sh
 
 int sample_sort_max_log2() { return kSortMaxLog2; }
 
+// Written once per device, synchronously (see close_set_lut).
 void sample_set_lut(const uint8_t lut[128], cudaStream_t s) {
-  cudaMemcpyToSymbolAsync(c_sample_lut, lut, 128, 0, cudaMemcpyHostToDevice, s);
+  (void)s;
+  static std::mutex mu;
+  static uint64_t done = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done >> dev & 1) return;
+  if (cudaMemcpyToSymbol(c_sample_lut, lut, 128, 0, cudaMemcpyHostToDevice) == cudaSuccess)
+    done |= uint64_t(1) << dev;
 }
 
 cudaError_t launch_sort_upper(const int64_t* up_ptr, int32_t ne, const Oriented& up, int packed,

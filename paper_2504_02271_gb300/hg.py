@@ -32,7 +32,9 @@ EXPORTED = ("hg_set_allocator", "hg_load_csr", "hg_build_wedges", "hg_count_patt
             "hg_pattern_table", "hg_close_stats_get", "hg_kernel_launches",
             "hg_wedge_degrees_noalloc", "hg_sample_estimate", "hg_load_batch",
             "hg_batch_build_wedges", "hg_batch_count_patterns", "hg_batch_clustering_coeff",
-            "hg_batch_waves", "hg_batch_wave", "hg_batch_free")
+            "hg_batch_waves", "hg_batch_wave", "hg_batch_free", "hg_load_batch_members",
+            "hg_server_create", "hg_server_add_graph", "hg_server_submit", "hg_server_wait",
+            "hg_server_drain", "hg_server_stats_get", "hg_server_destroy")
 
 
 class HgError(RuntimeError):
@@ -58,6 +60,35 @@ class _CloseStats(ctypes.Structure):
                 ("bucket_teams", ctypes.c_uint64 * 6), ("bucket_probes", ctypes.c_uint64 * 6),
                 ("bucket_gathers", ctypes.c_uint64 * 6),
                 ("bucket_out_entries", ctypes.c_uint64 * 6)]
+
+
+class _ServerOptions(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("max_batch_graphs", ctypes.c_int32),
+                ("memory_budget", ctypes.c_int64), ("max_batch_queries", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+class _Query(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("graph", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("first_sample", ctypes.c_uint64), ("num_samples", ctypes.c_uint64),
+                ("eps", ctypes.c_double * 20)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("kind", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("counts", ctypes.c_uint64 * 21), ("est", ctypes.c_double * 21),
+                ("cc", ctypes.c_double), ("open", ctypes.c_uint64), ("connected", ctypes.c_uint64),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("batch_queries", ctypes.c_int32),
+                ("batch_graphs", ctypes.c_int32), ("worker", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "batches", "exact_batches",
+                                                 "queries_batched", "max_in_flight_bytes",
+                                                 "max_concurrent_batches", "budget_bytes")] + \
+               [("now", ctypes.c_double)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -98,6 +129,15 @@ def _open():
     lib.hg_batch_wave.argtypes = [vp, i32, ctypes.POINTER(vp), ctypes.POINTER(i32),
                                   ctypes.POINTER(i32)]
     lib.hg_batch_free.argtypes = [vp]
+    lib.hg_load_batch_members.argtypes = [i32, vp, vp, vp, vp, ctypes.c_int, i64, vp,
+                                          ctypes.POINTER(vp)]
+    lib.hg_server_create.argtypes = [ctypes.POINTER(_ServerOptions), ctypes.POINTER(vp)]
+    lib.hg_server_add_graph.argtypes = [vp, i32, i32, vp, vp, ctypes.c_int, ctypes.POINTER(i32)]
+    lib.hg_server_submit.argtypes = [vp, ctypes.POINTER(_Query), ctypes.POINTER(u64)]
+    lib.hg_server_wait.argtypes = [vp, u64, ctypes.POINTER(_Result)]
+    lib.hg_server_drain.argtypes = [vp]
+    lib.hg_server_stats_get.argtypes = [vp, ctypes.POINTER(_ServerStats)]
+    lib.hg_server_destroy.argtypes = [vp]
     for name in EXPORTED:
         if name != "hg_status_str":
             getattr(lib, name).restype = ctypes.c_int
@@ -441,3 +481,107 @@ def hg_batch_free(b: Batch) -> None:
     if b.ptr:
         p, b.ptr = b.ptr, 0
         _check("hg_batch_free", _lib.hg_batch_free(ctypes.c_void_p(p)))
+
+
+def hg_load_batch_members(members, max_wave_edges: int = 0, stream: int | None = None) -> Batch:
+    """Batch of members stored apart: [(num_vertices, edge_ptr, edge_vtx), ...], each CSR
+    with offsets from 0 (numpy on the host or torch tensors on the device, not mixed)."""
+    keep, ptrs, idxs, devs = [], [], [], set()
+    for _, p, i in members:
+        pp, pd, k1 = _as_ptr(p, np.int64)
+        ip, idv, k2 = _as_ptr(i, np.int32)
+        devs.update((pd, idv))
+        keep += [k1, k2]
+        ptrs.append(pp)
+        idxs.append(ip)
+    if len(devs) > 1:
+        raise ValueError("member CSRs must all be on the host or all on the device")
+    nv = np.array([int(m[0]) for m in members], dtype=np.int32)
+    ne = np.array([len(m[1]) - 1 for m in members], dtype=np.int32)
+    pa = (ctypes.c_void_p * len(members))(*ptrs)
+    ia = (ctypes.c_void_p * len(members))(*idxs)
+    if stream is None:
+        stream = _default_stream()
+    out = ctypes.c_void_p()
+    st = _lib.hg_load_batch_members(len(members), nv.ctypes.data, ne.ctypes.data,
+                                    ctypes.cast(pa, ctypes.c_void_p), ctypes.cast(ia, ctypes.c_void_p),
+                                    1 if devs == {True} else 0, int(max_wave_edges),
+                                    ctypes.c_void_p(stream), ctypes.byref(out))
+    del keep
+    _check("hg_load_batch_members", st)
+    return Batch(int(out.value), int(stream), len(members))
+
+
+# ------------------------------------------------------------------ serving
+
+HG_Q_COUNTS, HG_Q_CLUSTERING, HG_Q_ESTIMATE = 0, 1, 2
+
+
+class Server:
+    """hg_server: queries on resident hypergraphs with continuous batching."""
+
+    def __init__(self, workers: int = 0, max_batch_graphs: int = 0, memory_budget: int = 0,
+                 max_batch_queries: int = 0):
+        opt = _ServerOptions(int(workers), int(max_batch_graphs), int(memory_budget),
+                             int(max_batch_queries))
+        out = ctypes.c_void_p()
+        _check("hg_server_create", _lib.hg_server_create(ctypes.byref(opt), ctypes.byref(out)))
+        self.ptr = int(out.value)
+
+    def add_graph(self, num_vertices: int, edge_ptr, edge_vtx) -> int:
+        p_ptr, p_dev, k1 = _as_ptr(edge_ptr, np.int64)
+        v_ptr, v_dev, k2 = _as_ptr(edge_vtx, np.int32)
+        if p_dev != v_dev:
+            raise ValueError("edge_ptr and edge_vtx must both be on the host or both on the device")
+        gid = ctypes.c_int32()
+        _check("hg_server_add_graph",
+               _lib.hg_server_add_graph(ctypes.c_void_p(self.ptr), int(num_vertices),
+                                        len(edge_ptr) - 1, ctypes.c_void_p(p_ptr),
+                                        ctypes.c_void_p(v_ptr), 1 if p_dev else 0,
+                                        ctypes.byref(gid)))
+        del k1, k2
+        return int(gid.value)
+
+    def submit(self, kind: int, graph: int, seed: int = 0, first_sample: int = 0,
+               num_samples: int = 0, eps=None) -> int:
+        q = _Query(int(kind), int(graph), int(seed) & (2**64 - 1), int(first_sample),
+                   int(num_samples))
+        if eps is not None:
+            for k, x in enumerate(eps):
+                q.eps[k] = float(x)
+        t = ctypes.c_uint64()
+        _check("hg_server_submit", _lib.hg_server_submit(ctypes.c_void_p(self.ptr), ctypes.byref(q),
+                                                         ctypes.byref(t)))
+        return int(t.value)
+
+    def wait(self, ticket: int) -> dict:
+        r = _Result()
+        _check("hg_server_wait", _lib.hg_server_wait(ctypes.c_void_p(self.ptr), int(ticket),
+                                                     ctypes.byref(r)))
+        return {"status": int(r.status), "kind": int(r.kind), "graph": int(r.graph),
+                "counts": np.array(list(r.counts), dtype=np.uint64),
+                "est": np.array(list(r.est), dtype=np.float64), "cc": float(r.cc),
+                "open": int(r.open), "connected": int(r.connected), "t_submit": r.t_submit,
+                "t_start": r.t_start, "t_done": r.t_done, "batch_queries": int(r.batch_queries),
+                "batch_graphs": int(r.batch_graphs), "worker": int(r.worker)}
+
+    def drain(self) -> None:
+        _check("hg_server_drain", _lib.hg_server_drain(ctypes.c_void_p(self.ptr)))
+
+    def stats(self) -> dict:
+        st = _ServerStats()
+        _check("hg_server_stats_get", _lib.hg_server_stats_get(ctypes.c_void_p(self.ptr),
+                                                               ctypes.byref(st)))
+        return {n: (float(getattr(st, n)) if n == "now" else int(getattr(st, n)))
+                for n, _ in _ServerStats._fields_}
+
+    def close(self) -> None:
+        if self.ptr:
+            p, self.ptr = self.ptr, 0
+            _check("hg_server_destroy", _lib.hg_server_destroy(ctypes.c_void_p(p)))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
