@@ -16,7 +16,11 @@ Parity status of each function:
     examples (Sec. 6.2), Algorithm 5's O(1) rules, closed forms and brute force;
   * the numbering of patterns 9, 11 and 13-20 inside the TTT class: parity
     unpinned (the paper prints that part of the numbering only in a figure
-    that is not available); class membership of every pattern is pinned.
+    that is not available); class membership of every pattern is pinned;
+  * the samplers (Algorithms 6 and 7): pinned by their every-hyperwedge-once
+    special cases (equal to the exact counts), split ranges, uniformity and
+    unbiasedness; Philox4x32-10's identity with other implementations is parity
+    unpinned (no published known-answer vectors are stored).
 """
 from __future__ import annotations
 
@@ -82,6 +86,14 @@ def _load():
             ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int, ctypes.c_int,
             ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]
         lib.oracle_sample_estimate.restype = ctypes.c_int
+        lib.oracle_subgraph.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_double,
+                                        ctypes.c_void_p]
+        lib.oracle_subgraph.restype = ctypes.c_int32
+        lib.oracle_sample_estimate_adv.argtypes = [
+            ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+            ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+            ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_sample_estimate_adv.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -191,6 +203,51 @@ def sample_estimate(e_ptr, e_idx, num_vertices: int, seed: int, first: int, num:
     if rc != 0:
         raise ValueError(f"oracle: {_ERR.get(rc, rc)}")
     return SampleEstimate(raw, est, int(W.value))
+
+
+def subgraph(num_edges: int, seed: int, sigma: float) -> np.ndarray:
+    """Ids (ascending) of the hyperedges kept in G' for sampling proportion sigma
+    (Algorithms 6-7, line 2): the ceil(sigma |E|) smallest Philox priorities."""
+    kept = np.zeros(max(num_edges, 1), dtype=np.int32)
+    n = _load().oracle_subgraph(int(num_edges), seed & (2**64 - 1), float(sigma), kept.ctypes.data)
+    if n < 0:
+        raise ValueError("oracle: bad argument")
+    return kept[:n].copy()
+
+
+@dataclass
+class AdvEstimate:
+    raw: np.ndarray       # uint64[21]
+    est: np.ndarray       # float64[21]
+    W: int
+    W_t: int
+    W_c: int
+    alphas: tuple         # samples of the TTT, CCC, TTC, TCC sets
+    edges: int            # |E'|
+
+
+CLASS_BITS = {"CCC": 1, "TCC": 2, "TTC": 4, "TTT": 8}
+
+
+def sample_estimate_adv(e_ptr, e_idx, num_vertices: int, seed: int, first: int, num: int,
+                        sigma: float = 1.0, class_mask: int = 15, identity_draws: bool = False,
+                        threads: int = 0) -> AdvEstimate:
+    """Appro-adv (Algorithm 7): per-class hyperwedge sampling from W^t and W^c."""
+    lib = _load()
+    e_ptr = np.ascontiguousarray(e_ptr, dtype=np.int64)
+    e_idx = np.ascontiguousarray(e_idx, dtype=np.int32)
+    raw = np.zeros(21, dtype=np.uint64)
+    est = np.zeros(21, dtype=np.float64)
+    info = np.zeros(8, dtype=np.uint64)
+    rc = lib.oracle_sample_estimate_adv(int(num_vertices), len(e_ptr) - 1, e_ptr.ctypes.data,
+                                        e_idx.ctypes.data, seed & (2**64 - 1), int(first), int(num),
+                                        float(sigma), int(class_mask), 1 if identity_draws else 0,
+                                        int(threads), raw.ctypes.data, est.ctypes.data,
+                                        info.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle: {_ERR.get(rc, rc)}")
+    return AdvEstimate(raw, est, int(info[0]), int(info[1]), int(info[2]),
+                       tuple(int(x) for x in info[3:7]), int(info[7]))
 
 
 def clustering_coeff(counts, open_triples: int, eps) -> float:

@@ -35,6 +35,7 @@
 // shows them only in a figure): ascending number of non-empty pairwise
 // regions (d, e, f), then ascending number of non-empty single regions.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstdint>
 #include <cstring>
@@ -365,7 +366,60 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-// Hyperwedge sampling estimate (Algorithm 6 with sigma = 1):
+// The sub-hypergraph G' of Algorithms 6 and 7 (line 2: sigma|E| hyperedges drawn
+// uniformly at random).  Reading: hyperedge i gets the priority
+// r_i = x1 << 32 | x0 of Philox4x32-10(counter = (i, 0, 1, 0), key = (seed lo, seed hi));
+// G' keeps the ceil(sigma * |E|) hyperedges with the smallest (r_i, i), renumbered
+// 0 .. |E'|-1 in ascending original id (so the order O is kept).  sigma = 1 keeps all.
+// Writes the kept ids, ascending, to kept[] (capacity ne) and returns how many.
+int32_t oracle_subgraph(int32_t ne, uint64_t seed, double sigma, int32_t* kept) {
+  if (ne < 0 || !(sigma > 0.0) || sigma > 1.0) return -1;
+  const int32_t keep = sigma == 1.0 ? ne : (int32_t)std::ceil(sigma * (double)ne);
+  std::vector<std::pair<uint64_t, int32_t>> pr((size_t)ne);
+  for (int32_t i = 0; i < ne; ++i) {
+    uint64_t r = 0;
+    if (sigma != 1.0) {
+      const uint32_t ctr[4] = {(uint32_t)i, 0u, 1u, 0u};
+      const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+      uint32_t x[4];
+      oracle_philox4x32_10(ctr, key, x);
+      r = ((uint64_t)x[1] << 32) | x[0];
+    }
+    pr[(size_t)i] = {r, i};
+  }
+  std::sort(pr.begin(), pr.end());
+  std::vector<int32_t> ids;
+  for (int32_t k = 0; k < keep; ++k) ids.push_back(pr[(size_t)k].second);
+  std::sort(ids.begin(), ids.end());
+  for (int32_t k = 0; k < keep; ++k) kept[k] = ids[(size_t)k];
+  return keep;
+}
+
+}  // extern "C"
+
+namespace {
+
+// CSR of G' (oracle_subgraph) with its hyperedges renumbered in ascending original id.
+int sub_csr(int32_t ne, const int64_t* e_ptr, const int32_t* e_idx, uint64_t seed, double sigma,
+            std::vector<int64_t>& sp, std::vector<int32_t>& si) {
+  std::vector<int32_t> kept((size_t)std::max(ne, 1));
+  const int32_t n = oracle_subgraph(ne, seed, sigma, kept.data());
+  if (n < 0) return -1;
+  sp.assign(1, 0);
+  si.clear();
+  for (int32_t k = 0; k < n; ++k) {
+    const int32_t i = kept[(size_t)k];
+    for (int64_t q = e_ptr[i]; q < e_ptr[i + 1]; ++q) si.push_back(e_idx[q]);
+    sp.push_back((int64_t)si.size());
+  }
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Hyperwedge sampling estimate (Algorithm 6):
 //   the hyperwedges are numbered in the order O of Sec. 2 (i ascending, then j
 //   ascending, i < j); sample n draws x = Philox4x32-10(counter = (n lo, n hi, 0, 0),
 //   key = (seed lo, seed hi)), r = x1 << 32 | x0 and takes hyperwedge
@@ -373,6 +427,8 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
 //   hyperwedge (i, j) are those {i, j, k} with k > j, i.e. the ones whose smallest
 //   hyperwedge in O is (i, j); raw[p] sums them over the samples and
 //   est[p] = raw[p] * (W / samples) / sigma^3 (p = 0 is the total).
+// With sigma < 1 all of this runs on the sub-hypergraph G' of oracle_subgraph
+// (W is then the number of hyperwedges of G').
 // identity_draws = 1 replaces the draw by m = n (every wedge once when the
 // samples are 0 .. W-1) - the special case that pins the estimate to the count.
 int oracle_sample_estimate(int32_t nv, int32_t ne, const int64_t* e_ptr, const int32_t* e_idx,
@@ -384,6 +440,14 @@ int oracle_sample_estimate(int32_t nv, int32_t ne, const int64_t* e_ptr, const i
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
+  std::vector<int64_t> sub_ptr;
+  std::vector<int32_t> sub_idx;
+  if (sigma != 1.0) {
+    if (sub_csr(ne, e_ptr, e_idx, seed, sigma, sub_ptr, sub_idx)) return -6;
+    ne = (int32_t)sub_ptr.size() - 1;
+    e_ptr = sub_ptr.data();
+    e_idx = sub_idx.data();
+  }
   Graph g;
   int rc = load(g, nv, ne, e_ptr, e_idx);
   if (rc) return rc;
@@ -454,6 +518,141 @@ int oracle_sample_estimate(int32_t nv, int32_t ne, const int64_t* e_ptr, const i
   const double scale = (double)W / (double)num;
   const double s3 = sigma * sigma * sigma;
   for (int p = 0; p <= 20; ++p) est[p] = ((double)raw[p] * scale) / s3;
+  return bad ? -8 : 0;
+}
+
+// Appro-adv (Algorithm 7).  On G' (oracle_subgraph), the hyperwedges split into
+// W^t (intersection type) and W^c (inclusion type) (Def. 2.3), each in the order O.
+// The alpha samples are shared out as in line 4, floors of exact integer quotients:
+//   alpha_1 = |W^t|^2 alpha / |W|^2     TTT class, drawn from W^t
+//   alpha_2 = |W^c|^2 alpha / |W|^2     CCC class, drawn from W^c
+//   alpha_3 = |W^t||W^c| alpha / |W|^2  TTC class, drawn from W^t
+//   alpha_4 = |W^t||W^c| alpha / |W|^2  TCC class, drawn from W^c.
+// Sample s (0 .. alpha_x - 1) of set x draws n = first + s from Philox4x32-10
+// (counter = (n lo, n hi, 1 + x, 0), key = seed), r = x1 << 32 | x0, and takes the
+// m-th hyperwedge of its type, m = floor(r |W^type| / 2^64).  For the drawn (i, j)
+// every k adjacent to both closes a hyper-triangle; it is counted when its class
+// (from its pattern: 1 CCC, 2-5 TCC, 6-8 TTC, 9-20 TTT) is the set's class and
+// (i, j) is, among the triangle's hyperwedges of the drawn type, the first in O
+// (reading: the triangle's owner, so that every triangle of the class is counted
+// once over W^type).  est[p] = raw[p] * (|W^type| / alpha_x) / sigma^3 for p in the
+// set's class; est[0] = sum of est[1..20] in order.  class_mask (bit 0 CCC, 1 TCC,
+// 2 TTC, 3 TTT) selects the sets that are drawn (targeted estimation).
+// identity_draws = 1 draws every hyperwedge of the type once (alpha_x = |W^type|,
+// m = s): the estimate is then the exact count of each selected class.
+// info[8] = W, W_t, W_c, alpha_1..alpha_4, |E'|.
+int oracle_sample_estimate_adv(int32_t nv, int32_t ne, const int64_t* e_ptr,
+                               const int32_t* e_idx, uint64_t seed, uint64_t first, uint64_t num,
+                               double sigma, int class_mask, int identity_draws, int nthreads,
+                               uint64_t* raw, double* est, uint64_t* info) {
+  if (!raw || !est || !info) return -6;
+  if (!oracle_pattern_table_ok()) return -7;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+  std::vector<int64_t> sub_ptr;
+  std::vector<int32_t> sub_idx;
+  if (sigma != 1.0) {
+    if (sub_csr(ne, e_ptr, e_idx, seed, sigma, sub_ptr, sub_idx)) return -6;
+    ne = (int32_t)sub_ptr.size() - 1;
+    e_ptr = sub_ptr.data();
+    e_idx = sub_idx.data();
+  }
+  Graph g;
+  int rc = load(g, nv, ne, e_ptr, e_idx);
+  if (rc) return rc;
+  std::vector<std::vector<int32_t>> N(ne);
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int32_t x = 0; x < ne; ++x) N[x] = neighbours(g, x);
+  // inclusion type of a hyperwedge (Def. 2.3): the intersection is the smaller hyperedge
+  auto inclusion = [&](int32_t a, int32_t b) {
+    size_t common = 0;
+    for (int32_t v : g.e[a]) common += g.e[b].count(v);
+    return common == std::min(g.e[a].size(), g.e[b].size());
+  };
+  // per type, the wedges (i, j), j > i, in O: row starts and the row lists
+  std::vector<std::vector<int32_t>> up[2];   // [0] intersection, [1] inclusion
+  up[0].assign(ne, {});
+  up[1].assign(ne, {});
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int32_t i = 0; i < ne; ++i)
+    for (int32_t j : N[i])
+      if (j > i) up[inclusion(i, j) ? 1 : 0][i].push_back(j);
+  std::vector<uint64_t> start[2];
+  for (int t = 0; t < 2; ++t) {
+    start[t].assign(ne + 1, 0);
+    for (int32_t i = 0; i < ne; ++i) start[t][i + 1] = start[t][i] + up[t][i].size();
+  }
+  const uint64_t Wt = start[0][ne], Wc = start[1][ne], W = Wt + Wc;
+  uint64_t alpha[4] = {0, 0, 0, 0};
+  if (W > 0) {
+    const unsigned __int128 den = (unsigned __int128)W * W;
+    alpha[0] = (uint64_t)((unsigned __int128)Wt * Wt * num / den);
+    alpha[1] = (uint64_t)((unsigned __int128)Wc * Wc * num / den);
+    alpha[2] = alpha[3] = (uint64_t)((unsigned __int128)Wt * Wc * num / den);
+  }
+  const int set_type[4] = {0, 1, 0, 1};     // the type each set draws from
+  const int set_class[4] = {3, 0, 2, 1};    // TTT, CCC, TTC, TCC
+  static const int kClassOf[21] = {-1, 0, 1, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3};
+  if (identity_draws)
+    for (int x = 0; x < 4; ++x) alpha[x] = start[set_type[x]][ne];
+  info[0] = W; info[1] = Wt; info[2] = Wc;
+  for (int x = 0; x < 4; ++x) info[3 + x] = alpha[x];
+  info[7] = (uint64_t)ne;
+  std::memset(raw, 0, sizeof(uint64_t) * 21);
+  for (int p = 0; p <= 20; ++p) est[p] = 0.0;
+  const auto& pm = pattern_map();
+  int bad = 0;
+  for (int x = 0; x < 4; ++x) {
+    if (!(class_mask >> set_class[x] & 1) || alpha[x] == 0) continue;
+    const int t = set_type[x];
+    const uint64_t Wx = start[t][ne];
+    uint64_t H[21] = {0};
+#pragma omp parallel for schedule(dynamic, 1024) reduction(+ : H[:21]) reduction(| : bad)
+    for (int64_t s = 0; s < (int64_t)alpha[x]; ++s) {
+      uint64_t m;
+      if (identity_draws) {
+        m = (uint64_t)s;
+      } else {
+        const uint64_t n = first + (uint64_t)s;
+        const uint32_t ctr[4] = {(uint32_t)n, (uint32_t)(n >> 32), (uint32_t)(1 + x), 0u};
+        const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+        uint32_t xr[4];
+        oracle_philox4x32_10(ctr, key, xr);
+        const uint64_t r = ((uint64_t)xr[1] << 32) | xr[0];
+        m = (uint64_t)(((unsigned __int128)r * Wx) >> 64);
+      }
+      const int32_t i =
+          (int32_t)(std::upper_bound(start[t].begin(), start[t].end(), m) - start[t].begin()) - 1;
+      const int32_t j = up[t][i][(size_t)(m - start[t][i])];
+      for (int32_t k : N[i]) {
+        if (k == j || !adjacent(N, j, k)) continue;
+        const int p = pm.of_mask[region_mask(g.e[i], g.e[j], g.e[k])];
+        if (p == 0) { bad = 1; continue; }
+        if (kClassOf[p] != set_class[x]) continue;
+        // the triangle's hyperwedges in O: (a,b) < (a,c) < (b,c) for a < b < c
+        int32_t v[3] = {i, j, k};
+        std::sort(v, v + 3);
+        const int32_t pairs[3][2] = {{v[0], v[1]}, {v[0], v[2]}, {v[1], v[2]}};
+        for (auto& pq : pairs) {
+          if ((inclusion(pq[0], pq[1]) ? 1 : 0) != t) continue;
+          if (pq[0] == std::min(i, j) && pq[1] == std::max(i, j)) ++H[p];
+          break;   // only the first hyperwedge of the drawn type owns the triangle
+        }
+      }
+    }
+    const double scale = (double)Wx / (double)alpha[x];
+    const double s3 = sigma * sigma * sigma;
+    for (int p = 1; p <= 20; ++p) {
+      if (kClassOf[p] != set_class[x]) continue;
+      raw[p] = H[p];
+      est[p] = ((double)H[p] * scale) / s3;
+    }
+  }
+  for (int p = 1; p <= 20; ++p) {
+    raw[0] += raw[p];
+    est[0] += est[p];
+  }
   return bad ? -8 : 0;
 }
 

@@ -83,3 +83,103 @@ def test_block_function_avalanche():
             flips.append(sum(bin(a ^ b).count("1") for a, b in zip(y0, y1)))
     flips = np.array(flips)
     assert abs(flips.mean() - 64.0) < 1.0 and flips.min() >= 30
+
+
+# ------------------------------------------------------------------ Appro-adv (Algorithm 7)
+
+CLASS_OF = {1: "CCC", **{p: "TCC" for p in range(2, 6)}, **{p: "TTC" for p in range(6, 9)},
+            **{p: "TTT" for p in range(9, 21)}}
+
+
+def test_adv_every_wedge_once_gives_the_exact_class_counts(small):
+    # every hyperwedge of each type drawn once: each triangle of a class is counted by
+    # exactly one of its hyperwedges of the drawn type, so the estimate is the count
+    import oracle
+
+    e_ptr, e_idx, nv = small
+    exact = oracle.count(e_ptr, e_idx, nv)
+    a = oracle.sample_estimate_adv(e_ptr, e_idx, nv, seed=0, first=0, num=1, identity_draws=True)
+    assert (a.W, a.W_t, a.W_c) == (exact.W, exact.W_t, exact.W_c)
+    assert a.alphas == (exact.W_t, exact.W_c, exact.W_t, exact.W_c)
+    assert a.raw.tolist() == exact.counts.tolist()
+    assert a.est.tolist() == [float(x) for x in exact.counts]
+    # one class at a time: that class's counts, zeros elsewhere
+    for cls, bit in oracle.CLASS_BITS.items():
+        b = oracle.sample_estimate_adv(e_ptr, e_idx, nv, seed=0, first=0, num=1, class_mask=bit,
+                                       identity_draws=True)
+        want = [int(exact.counts[p]) if CLASS_OF[p] == cls else 0 for p in range(1, 21)]
+        assert b.raw[1:].tolist() == want, cls
+
+
+def test_adv_sample_split_and_targeted_classes(small):
+    import oracle
+
+    e_ptr, e_idx, nv = small
+    full = oracle.sample_estimate_adv(e_ptr, e_idx, nv, seed=5, first=100, num=20_000)
+    W, Wt, Wc = full.W, full.W_t, full.W_c
+    a1, a2, a3, a4 = full.alphas
+    assert a3 == a4 and a1 * W * W <= Wt * Wt * 20_000 < (a1 + 1) * W * W
+    assert a2 * W * W <= Wc * Wc * 20_000 < (a2 + 1) * W * W
+    assert 20_000 - 4 <= a1 + a2 + a3 + a4 <= 20_000   # (W_t + W_c)^2 = W^2
+    for cls, bit in oracle.CLASS_BITS.items():
+        one = oracle.sample_estimate_adv(e_ptr, e_idx, nv, seed=5, first=100, num=20_000,
+                                         class_mask=bit)
+        for p in range(1, 21):
+            want = full.est[p] if CLASS_OF[p] == cls else 0.0
+            assert one.est[p] == want, (cls, p)
+
+
+def test_adv_estimate_is_unbiased(small):
+    import oracle
+
+    e_ptr, e_idx, nv = small
+    exact = oracle.count(e_ptr, e_idx, nv)
+    ests = np.array([oracle.sample_estimate_adv(e_ptr, e_idx, nv, seed=s, first=0, num=400).est
+                     for s in range(300)])
+    for p in [0] + [p for p in range(1, 21) if exact.counts[p] > exact.T // 50]:
+        mean, se = ests[:, p].mean(), ests[:, p].std(ddof=1) / np.sqrt(len(ests))
+        assert abs(mean - float(exact.counts[p])) < 4 * se + 1e-9, p
+
+
+# ------------------------------------------------------------------ sigma < 1 (line 2)
+
+def test_subgraph_selection(small):
+    import math
+
+    import oracle
+
+    e_ptr, e_idx, nv = small
+    ne = len(e_ptr) - 1
+    assert oracle.subgraph(ne, 3, 1.0).tolist() == list(range(ne))
+    seen = np.zeros(ne)
+    for seed in range(400):
+        k = oracle.subgraph(ne, seed, 0.3)
+        assert len(k) == math.ceil(0.3 * ne) and np.all(np.diff(k) > 0)
+        seen[k] += 1
+    assert oracle.subgraph(ne, 1, 0.3).tolist() != oracle.subgraph(ne, 2, 0.3).tolist()
+    # each hyperedge kept with probability ceil(0.3 |E|) / |E|: binomial(400, q) per edge
+    q = math.ceil(0.3 * ne) / ne
+    z = (seen - 400 * q) / math.sqrt(400 * q * (1 - q))
+    assert abs(z.mean()) < 0.3 and np.abs(z).max() < 5.0
+
+
+def test_sigma_estimates_run_on_the_sub_hypergraph(small):
+    # every hyperwedge of G' once: raw = the exact counts of the explicitly built G',
+    # est = raw / sigma^3 (Algorithms 6 and 7, line 2 and the final scaling)
+    import oracle
+
+    e_ptr, e_idx, nv = small
+    sigma = 0.5
+    kept = oracle.subgraph(len(e_ptr) - 1, 77, sigma)
+    rows = [e_idx[e_ptr[i]:e_ptr[i + 1]] for i in kept]
+    sp = np.zeros(len(rows) + 1, dtype=np.int64)
+    sp[1:] = np.cumsum([len(r) for r in rows])
+    si = np.concatenate(rows).astype(np.int32)
+    sub = oracle.count(sp, si, nv)
+    bs = oracle.sample_estimate(e_ptr, e_idx, nv, seed=77, first=0, num=sub.W, sigma=sigma,
+                                identity_draws=True)
+    assert bs.W == sub.W and bs.raw.tolist() == sub.counts.tolist()
+    assert bs.est.tolist() == [float(x) / sigma ** 3 for x in sub.counts]
+    adv = oracle.sample_estimate_adv(e_ptr, e_idx, nv, seed=77, first=0, num=1, sigma=sigma,
+                                     identity_draws=True)
+    assert adv.edges == len(kept) and adv.raw.tolist() == sub.counts.tolist()
