@@ -136,13 +136,47 @@ hg_status hg_count_patterns(hg_graph* g, uint64_t counts[21]);
  * Disjoint sample ranges with the same seed are independent draws, so split runs
  * sum to one run over the union (raw exactly).  Builds the sorted neighbour rows
  * on the first call after hg_build_wedges (W extra entries of device memory).
- * Requires hg_build_wedges.  sigma outside (0, 1] is HG_ERR_INVALID_ARG; sigma < 1,
- * or a wave handle of a batch, is HG_ERR_UNSUPPORTED.  A hyperedge with more than
- * 16,384 neighbours of larger index is HG_ERR_UNSUPPORTED.  Synchronises.
+ * sigma in (0, 1] (line 2 of Algorithm 6): with sigma < 1 everything above runs on
+ * the sub-hypergraph G' of the ceil(sigma |E|) hyperedges with the smallest
+ * priorities r_i = x1 * 2^32 + x0 of Philox4x32-10(counter (i, 0, 1, 0), key as
+ * above) (ties by id), renumbered in id order; W is then G''s, and est[p] =
+ * raw[p] * (W / num_samples) / sigma^3.  G' is built on the device and kept on the
+ * handle for the last (seed, sigma).
+ * Requires hg_build_wedges.  sigma outside (0, 1] is HG_ERR_INVALID_ARG; a wave handle
+ * of a batch is HG_ERR_UNSUPPORTED.  A hyperedge with more than 16,384 neighbours of
+ * larger index is HG_ERR_UNSUPPORTED.  Synchronises.
  */
 hg_status hg_sample_estimate(hg_graph* g, uint64_t seed, uint64_t first_sample,
                              uint64_t num_samples, double sigma, uint64_t raw[21],
                              double est[21]);
+
+/*
+ * Class-targeted sampling estimate (Sec. 4.2, Algorithm 7, "Appro-adv").  On G (or on
+ * G' for sigma < 1, as above) the hyperwedges split into W^t (intersection type) and
+ * W^c (inclusion type) (Def. 2.3), each numbered in the order O.  The num_samples = alpha
+ * draws are shared out as in line 4, as exact integer floors:
+ *   set 1: alpha_1 = |W^t|^2 alpha / |W|^2 draws from W^t, counting the TTT class (9-20)
+ *   set 2: alpha_2 = |W^c|^2 alpha / |W|^2 draws from W^c, counting CCC (1)
+ *   set 3: alpha_3 = |W^t||W^c| alpha / |W|^2 draws from W^t, counting TTC (6-8)
+ *   set 4: alpha_4 = alpha_3 draws from W^c, counting TCC (2-5).
+ * Draw s of set x uses n = first_sample + s and Philox4x32-10(counter (n lo, n hi, 1 + x,
+ * 0), key (seed lo, seed hi)); r = x1 * 2^32 + x0 picks the hyperwedge
+ * m = floor(r |W^type| / 2^64) of that type.  For the drawn (i, j), every k adjacent to
+ * both closes a hyper-triangle, counted when it is of the set's class and (i, j) is, among
+ * its hyperwedges of the drawn type, the first in O (so each triangle of the class is
+ * counted once over W^type).
+ *   class_mask  bit 0 CCC, 1 TCC, 2 TTC, 3 TTT: the sets drawn (targeted estimation);
+ *               unselected classes stay 0.
+ *   raw[21], est[21]  out: per pattern; est[p] = raw[p] (|W^type| / alpha_x) / sigma^3 in
+ *               IEEE double; raw[0], est[0] = the sums over p = 1..20 in order.
+ *   info[8]     out (may be NULL): W, W^t, W^c, alpha_1..alpha_4, |E'|.
+ * Builds, on the first call after hg_build_wedges, the upper rows split by type and every
+ * neighbour row sorted (3W more entries).  Limits and errors as hg_sample_estimate, plus
+ * every neighbour row at most 16,384 long; class_mask > 15 is HG_ERR_INVALID_ARG.
+ */
+hg_status hg_sample_estimate_adv(hg_graph* g, uint64_t seed, uint64_t first_sample,
+                                 uint64_t num_samples, double sigma, uint32_t class_mask,
+                                 uint64_t raw[21], double est[21], uint64_t info[8]);
 
 /*
  * Fine-grained hypergraph clustering coefficient (Def. 5.1):

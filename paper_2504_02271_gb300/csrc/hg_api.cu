@@ -95,6 +95,16 @@ struct hg_graph {
   int64_t* up_ptr = nullptr;
   Oriented up{};
   bool upper_built = false;
+  // Algorithm 7: the upper rows split by type, and every neighbour row sorted
+  bool adv_built = false;
+  int64_t* t_ptr = nullptr;
+  int64_t* c_ptr = nullptr;
+  Oriented t_ent{}, c_ent{}, full{};
+  uint64_t Wt = 0, Wc = 0;
+  // the sub-hypergraph G' for sigma < 1 (Algorithms 6-7, line 2), kept for its seed
+  hg_graph* sub = nullptr;
+  uint64_t sub_seed = 0;
+  double sub_sigma = 1.0;
   // count stage
   std::vector<Block> count_blocks;
   bool counted = false;
@@ -471,16 +481,28 @@ hg_status dense_impl(hg_graph* g, const hg_tuning* opt, DenseInfo* dn) {
   return HG_OK;
 }
 
+hg_status free_graph(hg_graph* g);
+
+// Drop what the samplers built on this handle (upper rows, Algorithm 7 rows, G').
+void release_sampling(hg_graph* g) {
+  release(g, g->sample_blocks);
+  g->upper_built = false;
+  g->adv_built = false;
+  if (g->sub) {
+    free_graph(g->sub);
+    g->sub = nullptr;
+  }
+}
+
 hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   g->close_mode = opt ? opt->close_mode : 0;
   if (g->close_mode < 0 || g->close_mode > 1) return HG_ERR_INVALID_ARG;
   cudaStream_t s = g->stream;
   release(g, g->count_blocks);
-  release(g, g->sample_blocks);
+  release_sampling(g);
   release(g, g->build_blocks);
   g->built = false;
   g->counted = false;
-  g->upper_built = false;
   const int64_t ne = g->ne;
   g->packed = (ne < (int64_t(1) << 24) && g->max_size < 256) ? 1 : 0;
   Small h;
@@ -491,13 +513,13 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   g->ori.dplus = alloc_t<int32_t>(g, g->build_blocks, ne);
   g->upc = alloc_t<int32_t>(g, g->build_blocks, ne);
   if (!g->deg || !rows || !g->ori.row_ptr || !g->ori.dplus || !g->upc) return HG_ERR_OOM;
-  g->wcr = nullptr;
+  g->wcr = alloc_t<int32_t>(g, g->build_blocks, ne);
+  if (!g->wcr) return HG_ERR_OOM;
+  HG_CUDA(cudaMemsetAsync(g->wcr, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1), s));
   g->mstats = nullptr;
   if (g->nm > 0) {
-    g->wcr = alloc_t<int32_t>(g, g->build_blocks, ne);
     g->mstats = alloc_t<unsigned long long>(g, g->build_blocks, 4 * (int64_t)g->nm);
-    if (!g->wcr || !g->mstats) return HG_ERR_OOM;
-    HG_CUDA(cudaMemsetAsync(g->wcr, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1), s));
+    if (!g->mstats) return HG_ERR_OOM;
   }
   WedgeBuckets wb;
   for (int k = 0; k < 3; ++k) wb.rows[k] = rows + k * ne;
@@ -611,6 +633,214 @@ hg_status upper_impl(hg_graph* g) {
   HG_TRY(sync_small(g, &h));
   t_collect(g);
   g->upper_built = true;
+  return HG_OK;
+}
+
+// Algorithm 7's rows: the upper rows split by hyperwedge type (order kept), and
+// every neighbour row N(i) sorted by id (offsets: the scan of the full degrees).
+hg_status adv_impl(hg_graph* g) {
+  if (!g->upper_built) HG_TRY(upper_impl(g));
+  cudaStream_t s = g->stream;
+  const int64_t ne = g->ne;
+  int32_t* cnt_t = alloc_t<int32_t>(g, g->sample_blocks, ne);
+  g->t_ptr = alloc_t<int64_t>(g, g->sample_blocks, ne + 1);
+  g->c_ptr = alloc_t<int64_t>(g, g->sample_blocks, ne + 1);
+  if (!cnt_t || !g->t_ptr || !g->c_ptr) return HG_ERR_OOM;
+  launch_type_counts(g->upc, g->wcr, g->ne, cnt_t, s);
+  scan_i32_to_i64(cnt_t, g->t_ptr, ne, g->scan_tmp, s);
+  scan_i32_to_i64(g->wcr, g->c_ptr, ne, g->scan_tmp, s);
+  int64_t wt = 0, wc = 0;
+  HG_CUDA(cudaMemcpyAsync(&wt, g->t_ptr + ne, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  HG_CUDA(cudaMemcpyAsync(&wc, g->c_ptr + ne, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  HG_CUDA(cudaStreamSynchronize(s));
+  if ((uint64_t)wt + (uint64_t)wc != g->stats.W || (uint64_t)wc != g->stats.W_c) return HG_ERR_INTERNAL;
+  g->Wt = (uint64_t)wt;
+  g->Wc = (uint64_t)wc;
+  g->t_ent = Oriented{};
+  g->c_ent = Oriented{};
+  g->full = Oriented{};
+  g->full.row_ptr = g->ori.row_ptr;
+  if (g->packed) {
+    g->t_ent.packed = alloc_t<uint32_t>(g, g->sample_blocks, wt);
+    g->c_ent.packed = alloc_t<uint32_t>(g, g->sample_blocks, wc);
+    g->full.packed = alloc_t<uint32_t>(g, g->sample_blocks, (int64_t)g->two_w);
+    if (!g->t_ent.packed || !g->c_ent.packed || !g->full.packed) return HG_ERR_OOM;
+  } else {
+    g->t_ent.nbr = alloc_t<int32_t>(g, g->sample_blocks, wt);
+    g->t_ent.omega = alloc_t<int32_t>(g, g->sample_blocks, wt);
+    g->c_ent.nbr = alloc_t<int32_t>(g, g->sample_blocks, wc);
+    g->c_ent.omega = alloc_t<int32_t>(g, g->sample_blocks, wc);
+    g->full.nbr = alloc_t<int32_t>(g, g->sample_blocks, (int64_t)g->two_w);
+    g->full.omega = alloc_t<int32_t>(g, g->sample_blocks, (int64_t)g->two_w);
+    if (!g->t_ent.nbr || !g->t_ent.omega || !g->c_ent.nbr || !g->c_ent.omega || !g->full.nbr ||
+        !g->full.omega)
+      return HG_ERR_OOM;
+  }
+  DevGraph d = dev_graph(g);
+  t_begin(g, "adv_split");
+  launch_split_types(d, g->up_ptr, g->up, g->packed, g->t_ptr, g->t_ent, g->c_ptr, g->c_ent, s);
+  t_end(g);
+  HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
+  t_begin(g, "full_emit");
+  launch_wedge_pass(3, d, g->wb, g->nb, g->max_cand, g->deg, &g->small->wc, g->full, g->packed,
+                    g->wscratch, &g->small->err, g->small->counters, g->dn, RowCounts{}, s,
+                    g->nsm);
+  t_end(g);
+  t_begin(g, "full_sort");
+  HG_CUDA(launch_sort_upper(g->ori.row_ptr, g->ne, g->full, g->packed, &g->small->err, s, g->nsm));
+  t_end(g);
+  Small h;
+  HG_TRY(sync_small(g, &h));
+  t_collect(g);
+  g->adv_built = true;
+  return HG_OK;
+}
+
+// G' (Algorithms 6-7, line 2): the ceil(sigma |E|) hyperedges with the smallest Philox
+// priorities (ties by id), renumbered in id order, as a handle of its own with step one
+// built.  The k-th smallest priority is found by a 4-pass radix select (16-bit digits).
+hg_status subgraph_impl(hg_graph* g, uint64_t seed, double sigma) {
+  if (g->sub && g->sub_seed == seed && g->sub_sigma == sigma) return HG_OK;
+  if (g->sub) {
+    free_graph(g->sub);
+    g->sub = nullptr;
+  }
+  cudaStream_t s = g->stream;
+  const int32_t ne = g->ne;
+  const int64_t keep = (int64_t)std::ceil(sigma * (double)ne);
+  std::vector<Block> tmp;
+  struct Releaser {
+    hg_graph* g;
+    std::vector<Block>& b;
+    ~Releaser() { release(g, b); }
+  } rel{g, tmp};
+  unsigned long long* pr = alloc_t<unsigned long long>(g, tmp, ne);
+  unsigned int* hist = alloc_t<unsigned int>(g, tmp, 65536);
+  int32_t* flags = alloc_t<int32_t>(g, tmp, ne);
+  int64_t* rank = alloc_t<int64_t>(g, tmp, (int64_t)ne + 1);
+  int32_t* ids = alloc_t<int32_t>(g, tmp, keep);
+  int32_t* sizes = alloc_t<int32_t>(g, tmp, keep);
+  int64_t* sub_ptr = alloc_t<int64_t>(g, tmp, keep + 1);
+  if (!pr || !hist || !flags || !rank || !ids || !sizes || !sub_ptr) return HG_ERR_OOM;
+  launch_priority(ne, seed, pr, s);
+  unsigned long long prefix = 0, pmask = 0;
+  int64_t less = 0;   // priorities below the current prefix range
+  std::vector<unsigned int> h(65536);
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 48 - 16 * pass;
+    HG_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned int) * 65536, s));
+    launch_digit_hist(pr, ne, shift, pmask, prefix, hist, s);
+    HG_CUDA(cudaMemcpyAsync(h.data(), hist, sizeof(unsigned int) * 65536, cudaMemcpyDeviceToHost, s));
+    HG_CUDA(cudaStreamSynchronize(s));
+    int64_t cum = 0;
+    int d = 0;
+    for (; d < 65536; ++d) {
+      if (less + cum + (int64_t)h[(size_t)d] >= keep) break;
+      cum += h[(size_t)d];
+    }
+    if (d == 65536) return HG_ERR_INTERNAL;
+    less += cum;
+    prefix |= (unsigned long long)d << shift;
+    pmask |= 0xffffull << shift;
+  }
+  const unsigned long long T = prefix;   // the keep-th smallest priority
+  const int64_t need = keep - less;      // how many priorities equal to T are kept
+  launch_equal_flags(pr, ne, T, flags, s);
+  scan_i32_to_i64(flags, rank, ne, g->scan_tmp, s);
+  launch_keep_flags(pr, ne, T, rank, need, flags, s);
+  scan_i32_to_i64(flags, rank, ne, g->scan_tmp, s);
+  launch_compact_kept(flags, rank, g->esize, ne, ids, sizes, s);
+  int64_t kept = 0;
+  HG_CUDA(cudaMemcpyAsync(&kept, rank + ne, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  HG_CUDA(cudaStreamSynchronize(s));
+  if (kept != keep) return HG_ERR_INTERNAL;
+  scan_i32_to_i64(sizes, sub_ptr, keep, g->scan_tmp, s);
+  int64_t nnz = 0;
+  HG_CUDA(cudaMemcpyAsync(&nnz, sub_ptr + keep, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  HG_CUDA(cudaStreamSynchronize(s));
+  int32_t* sub_idx = alloc_t<int32_t>(g, tmp, nnz);
+  if (!sub_idx) return HG_ERR_OOM;
+  launch_gather_rows(g->e_ptr, g->e_idx, ids, (int32_t)keep, sub_ptr, sub_idx, s);
+  hg_graph* sub = new hg_graph();
+  sub->device = g->device;
+  sub->nsm = g->nsm;
+  sub->stream = s;
+  sub->nv = g->nv;
+  sub->ne = (int32_t)keep;
+  sub->nnz = nnz;
+  hg_status st = load_impl(sub, sub_ptr, sub_idx, 1);
+  if (st == HG_OK) st = build_impl(sub, nullptr, nullptr);
+  if (st != HG_OK) {
+    cudaStreamSynchronize(s);
+    free_graph(sub);
+    return st;
+  }
+  g->sub = sub;
+  g->sub_seed = seed;
+  g->sub_sigma = sigma;
+  return HG_OK;
+}
+
+hg_status sample_adv_impl(hg_graph* g, uint64_t seed, uint64_t first, uint64_t num, double sigma,
+                          uint32_t class_mask, uint64_t raw[21], double est[21], uint64_t info[8]) {
+  if (!g->adv_built) HG_TRY(adv_impl(g));
+  cudaStream_t s = g->stream;
+  uint8_t lut[128];
+  build_lut(lut);
+  sample_set_lut(lut, s);
+  const uint64_t Wt = g->Wt, Wc = g->Wc, W = Wt + Wc;
+  uint64_t alpha[4] = {0, 0, 0, 0};
+  if (W > 0) {   // Algorithm 7, line 4: exact floors
+    const unsigned __int128 den = (unsigned __int128)W * W;
+    alpha[0] = (uint64_t)((unsigned __int128)Wt * Wt * num / den);
+    alpha[1] = (uint64_t)((unsigned __int128)Wc * Wc * num / den);
+    alpha[2] = alpha[3] = (uint64_t)((unsigned __int128)Wt * Wc * num / den);
+  }
+  static const int kType[4] = {0, 1, 0, 1};    // intersection, inclusion, intersection, inclusion
+  static const int kClass[4] = {3, 0, 2, 1};   // TTT, CCC, TTC, TCC
+  static const int kClassOf[21] = {-1, 0, 1, 1, 1, 1, 2, 2, 2, 3, 3, 3,
+                                   3,  3, 3, 3, 3, 3, 3, 3, 3};
+  if (info) {
+    info[0] = W;
+    info[1] = Wt;
+    info[2] = Wc;
+    for (int x = 0; x < 4; ++x) info[3 + x] = alpha[x];
+    info[7] = (uint64_t)g->ne;
+  }
+  for (int p = 0; p <= 20; ++p) {
+    raw[p] = 0;
+    est[p] = 0.0;
+  }
+  DevGraph d = dev_graph(g);
+  const double s3 = sigma * sigma * sigma;
+  for (int x = 0; x < 4; ++x) {
+    if (!(class_mask >> kClass[x] & 1u) || alpha[x] == 0) continue;
+    const bool incl = kType[x] == 1;
+    const uint64_t Wx = incl ? Wc : Wt;
+    HG_CUDA(cudaMemsetAsync(g->small->hist, 0, sizeof(g->small->hist), s));
+    t_begin(g, "sample_adv");
+    launch_sample_adv(d, incl ? g->c_ptr : g->t_ptr, incl ? g->c_ent : g->t_ent, Wx, kType[x],
+                      kClass[x], (uint32_t)(1 + x), g->ori.row_ptr, g->full, g->packed, seed,
+                      first, alpha[x], g->small->hist, s, g->nsm);
+    t_end(g);
+    Small h;
+    HG_TRY(sync_small(g, &h));
+    if (h.hist[0] != 0) return HG_ERR_INTERNAL;
+    const double scale = (double)Wx / (double)alpha[x];
+    for (int p = 1; p <= 20; ++p) {
+      if (kClassOf[p] != kClass[x]) {
+        if (h.hist[p] != 0) return HG_ERR_INTERNAL;
+        continue;
+      }
+      raw[p] = h.hist[p];
+      est[p] = ((double)h.hist[p] * scale) / s3;
+    }
+  }
+  t_collect(g);
+  for (int p = 1; p <= 20; ++p) {
+    raw[0] += raw[p];
+    est[0] += est[p];
+  }
   return HG_OK;
 }
 
@@ -766,7 +996,7 @@ namespace {
 hg_status free_graph(hg_graph* g) {
   cudaStream_t s = g->stream;
   release(g, g->count_blocks);
-  release(g, g->sample_blocks);
+  release_sampling(g);
   release(g, g->build_blocks);
   release(g, g->load_blocks);
   cudaError_t e = cudaStreamSynchronize(s);
@@ -952,9 +1182,39 @@ hg_status hg_sample_estimate(hg_graph* g, uint64_t seed, uint64_t first_sample,
                              double est[21]) {
   if (!g || !raw || !est || !(sigma > 0.0) || sigma > 1.0) return HG_ERR_INVALID_ARG;
   if (!g->built) return HG_ERR_STATE;
-  if (sigma != 1.0 || g->nm > 0) return HG_ERR_UNSUPPORTED;
+  if (g->nm > 0) return HG_ERR_UNSUPPORTED;
   if (num_samples > UINT64_MAX - first_sample) return HG_ERR_INVALID_ARG;
-  hg_status st = sample_impl(g, seed, first_sample, num_samples, sigma, raw, est);
+  hg_status st = HG_OK;
+  hg_graph* h = g;
+  if (sigma != 1.0) {
+    st = subgraph_impl(g, seed, sigma);
+    h = g->sub;
+  }
+  if (st == HG_OK) st = sample_impl(h, seed, first_sample, num_samples, sigma, raw, est);
+  if (st != HG_OK) {
+    cudaStreamSynchronize(g->stream);
+    cudaGetLastError();
+    g->pending.clear();
+  }
+  return st;
+}
+
+hg_status hg_sample_estimate_adv(hg_graph* g, uint64_t seed, uint64_t first_sample,
+                                 uint64_t num_samples, double sigma, uint32_t class_mask,
+                                 uint64_t raw[21], double est[21], uint64_t info[8]) {
+  if (!g || !raw || !est || !(sigma > 0.0) || sigma > 1.0 || class_mask > 15u)
+    return HG_ERR_INVALID_ARG;
+  if (!g->built) return HG_ERR_STATE;
+  if (g->nm > 0) return HG_ERR_UNSUPPORTED;
+  if (num_samples > UINT64_MAX - first_sample) return HG_ERR_INVALID_ARG;
+  hg_status st = HG_OK;
+  hg_graph* h = g;
+  if (sigma != 1.0) {
+    st = subgraph_impl(g, seed, sigma);
+    h = g->sub;
+  }
+  if (st == HG_OK)
+    st = sample_adv_impl(h, seed, first_sample, num_samples, sigma, class_mask, raw, est, info);
   if (st != HG_OK) {
     cudaStreamSynchronize(g->stream);
     cudaGetLastError();

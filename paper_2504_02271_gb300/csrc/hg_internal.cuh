@@ -121,7 +121,8 @@ struct RowCounts {
 
 // mode 0: count (deg, W_c, dup check, RowCounts); mode 1: emit the degree-oriented rows
 // at o.row_ptr (lengths into o.dplus); mode 2: emit the rows of neighbours j > i at
-// o.row_ptr (exact offsets from a scan of upc)
+// o.row_ptr (exact offsets from a scan of upc); mode 3: emit every neighbour at
+// o.row_ptr (exact offsets from a scan of deg)
 void launch_wedge_pass(int mode, const DevGraph& g, const WedgeBuckets& b, const int32_t* nb,
                        int64_t heavy_max_cand, int32_t* deg, unsigned long long* wc,
                        const Oriented& o, int packed, unsigned long long* scratch,
@@ -148,6 +149,29 @@ cudaError_t launch_sort_upper(const int64_t* up_ptr, int32_t ne, const Oriented&
 void launch_sample(const DevGraph& g, const int64_t* up_ptr, const Oriented& up, int packed,
                    uint64_t W, uint64_t seed, uint64_t first, uint64_t num,
                    unsigned long long* raw, cudaStream_t s, int nsm);
+// Appro-adv (Algorithm 7)
+void launch_type_counts(const int32_t* upc, const int32_t* wcr, int32_t ne, int32_t* cnt_t,
+                        cudaStream_t s);
+void launch_split_types(const DevGraph& g, const int64_t* up_ptr, const Oriented& up, int packed,
+                        const int64_t* t_ptr, const Oriented& t, const int64_t* c_ptr,
+                        const Oriented& c, cudaStream_t s);
+void launch_sample_adv(const DevGraph& g, const int64_t* set_ptr, const Oriented& set_ent,
+                       uint64_t Wx, int type, int cls, uint32_t stream, const int64_t* full_ptr,
+                       const Oriented& full, int packed, uint64_t seed, uint64_t first,
+                       uint64_t num, unsigned long long* raw, cudaStream_t s, int nsm);
+// the sub-hypergraph G' of Algorithms 6-7 (sigma < 1)
+void launch_priority(int32_t ne, uint64_t seed, unsigned long long* pr, cudaStream_t s);
+void launch_digit_hist(const unsigned long long* pr, int32_t ne, int shift,
+                       unsigned long long pmask, unsigned long long prefix, unsigned int* hist,
+                       cudaStream_t s);
+void launch_equal_flags(const unsigned long long* pr, int32_t ne, unsigned long long T,
+                        int32_t* eq, cudaStream_t s);
+void launch_keep_flags(const unsigned long long* pr, int32_t ne, unsigned long long T,
+                       const int64_t* eq_rank, int64_t need, int32_t* keep, cudaStream_t s);
+void launch_compact_kept(const int32_t* keep, const int64_t* pos, const int32_t* esize, int32_t ne,
+                         int32_t* ids, int32_t* sizes, cudaStream_t s);
+void launch_gather_rows(const int64_t* e_ptr, const int32_t* e_idx, const int32_t* ids, int32_t nk,
+                        const int64_t* sub_ptr, int32_t* sub_idx, cudaStream_t s);
 size_t wedge_heavy_scratch_bytes(int64_t heavy_max_cand, int nsm);
 
 // k_close.cu

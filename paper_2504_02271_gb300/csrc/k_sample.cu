@@ -191,6 +191,238 @@ __global__ void __launch_bounds__(kSampleWarps * 32)
   }
 }
 
+// ------------------------------------------------------------------ Appro-adv (Algorithm 7)
+
+// cnt_t[i] = upper entries of intersection type = upc[i] - wcr[i]
+__global__ void k_type_counts(const int32_t* __restrict__ upc, const int32_t* __restrict__ wcr,
+                              int32_t ne, int32_t* __restrict__ cnt_t) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne;
+       i += (int64_t)gridDim.x * blockDim.x)
+    cnt_t[i] = upc[i] - wcr[i];
+}
+
+__device__ __forceinline__ void put_up(const Oriented& o, int packed, int64_t at, int32_t j,
+                                       int32_t om) {
+  if (packed) {
+    o.packed[at] = ((uint32_t)j << 8) | (uint32_t)om;
+  } else {
+    o.nbr[at] = j;
+    o.omega[at] = om;
+  }
+}
+
+// One warp per row: the sorted upper row split, order kept, into its intersection-type
+// entries (t) and inclusion-type entries (c) (Def. 2.3: omega_ij = min(|e_i|, |e_j|)).
+__global__ void k_split_types(const DevGraph g, const int64_t* __restrict__ up_ptr, Oriented up,
+                              int packed, const int64_t* __restrict__ t_ptr, Oriented t,
+                              const int64_t* __restrict__ c_ptr, Oriented c) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < g.ne; i += warps) {
+    const int64_t b = up_ptr[i], e = up_ptr[i + 1];
+    const int32_t szi = g.esize[i];
+    int64_t nt = t_ptr[i], nc = c_ptr[i];
+    for (int64_t p0 = b; p0 < e; p0 += 32) {
+      const int64_t p = p0 + lane;
+      int32_t j = 0, om = 0;
+      bool incl = false;
+      if (p < e) {
+        up_entry(up, packed, p, j, om);
+        incl = om == min(szi, g.esize[j]);
+      }
+      const unsigned bc = __ballot_sync(kFull, p < e && incl);
+      const unsigned bt = __ballot_sync(kFull, p < e && !incl);
+      const unsigned below = (1u << lane) - 1u;
+      if (p < e) {
+        if (incl) put_up(c, packed, nc + __popc(bc & below), j, om);
+        else put_up(t, packed, nt + __popc(bt & below), j, om);
+      }
+      nt += __popc(bt);
+      nc += __popc(bc);
+    }
+  }
+}
+
+// pattern -> class (0 CCC, 1 TCC, 2 TTC, 3 TTT; Sec. 2)
+__constant__ int8_t c_class_of[24] = {-1, 0, 1, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3,
+                                      3,  3, 3, 3, 3, 3, 3, 3, -1, -1, -1};
+
+struct AdvSet {
+  const int64_t* ptr;   // rows of the drawn type
+  Oriented ent;
+  uint64_t Wx;          // hyperwedges of that type
+  int type;             // 0 intersection, 1 inclusion
+  int cls;              // class counted
+  uint32_t stream;      // Philox counter word 2
+};
+
+__device__ __forceinline__ int wedge_type(int om, int sa, int sb) { return om == min(sa, sb); }
+
+// One warp per draw of set `st`: the drawn (i, j), every k in N(i) cap N(j); the
+// triangle counts when its class is st.cls and (i, j) is its first hyperwedge of
+// type st.type in O.  raw[0..23] += per-pattern counts.
+__global__ void __launch_bounds__(kSampleWarps * 32)
+    k_sample_adv(DevGraph g, AdvSet st, const int64_t* __restrict__ full_ptr, Oriented full,
+                 int packed, uint64_t seed, uint64_t first, uint64_t num,
+                 unsigned long long* __restrict__ raw) {
+  __shared__ uint32_t hist[kSampleWarps][24];
+  __shared__ uint8_t lut[128];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = threadIdx.x; k < 128; k += blockDim.x) lut[k] = c_sample_lut[k];
+  for (int k = lane; k < 24; k += 32) hist[w][k] = 0;
+  __syncthreads();
+  const uint64_t warps = (uint64_t)gridDim.x * kSampleWarps;
+  for (uint64_t s = (uint64_t)blockIdx.x * kSampleWarps + w; s < num; s += warps) {
+    const uint64_t n = first + s;
+    uint32_t c[4] = {(uint32_t)n, (uint32_t)(n >> 32), st.stream, 0u};
+    philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint64_t r = ((uint64_t)c[1] << 32) | c[0];
+    const uint64_t m = __umul64hi(r, st.Wx);
+    int32_t lo = 0, hi = g.ne - 1;   // row: last i with ptr[i] <= m
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (__ldg(st.ptr + mid) <= (int64_t)m) lo = mid; else hi = mid - 1;
+    }
+    const int32_t i = lo;
+    int32_t j, wij;
+    up_entry(st.ent, packed, (int64_t)m, j, wij);
+    const int64_t ei = g.e_ptr[i], ej = g.e_ptr[j];
+    const int szi = (int)(g.e_ptr[i + 1] - ei), szj = (int)(g.e_ptr[j + 1] - ej);
+    // walk the shorter neighbour row, search the longer one
+    int64_t ab = __ldg(full_ptr + i), ae = __ldg(full_ptr + i + 1);
+    int64_t bb = __ldg(full_ptr + j), be = __ldg(full_ptr + j + 1);
+    const bool swap = (ae - ab) > (be - bb);
+    if (swap) {
+      int64_t t0 = ab, t1 = ae;
+      ab = bb;
+      ae = be;
+      bb = t0;
+      be = t1;
+    }
+    for (int64_t a = ab + lane; a < ae; a += 32) {
+      int32_t k, wa;
+      up_entry(full, packed, a, k, wa);
+      if (k == i || k == j) continue;
+      int64_t l = bb, h = be;
+      while (l < h) {
+        const int64_t mid = (l + h) >> 1;
+        int32_t x, om;
+        up_entry(full, packed, mid, x, om);
+        if (x < k) l = mid + 1; else h = mid;
+      }
+      if (l >= be) continue;
+      int32_t x, wb;
+      up_entry(full, packed, l, x, wb);
+      if (x != k) continue;
+      const int wik = swap ? wb : wa, wjk = swap ? wa : wb;
+      const int64_t ek = g.e_ptr[k];
+      const int szk = (int)(g.e_ptr[k + 1] - ek);
+      const int gg = triple_common(g.e_idx + ei, szi, g.e_idx + ej, szj, g.e_idx + ek, szk);
+      const int ra = szi - wij - wik + gg, rb = szj - wij - wjk + gg, rc = szk - wik - wjk + gg;
+      const int bits = (ra > 0) | ((rb > 0) << 1) | ((rc > 0) << 2) | ((wij > gg) << 3) |
+                       ((wjk > gg) << 4) | ((wik > gg) << 5) | ((gg > 0) << 6);
+      const int pat = lut[bits];
+      if (c_class_of[pat] != st.cls) continue;
+      // the triangle's hyperwedges in O, (a,b) < (a,c) < (b,c) for a < b < c; the
+      // first of the drawn type must be (i, j)
+      const int tij = wedge_type(wij, szi, szj), tik = wedge_type(wik, szi, szk),
+                tjk = wedge_type(wjk, szj, szk);
+      int32_t v0 = i, v1 = j, v2 = k;
+      int t01 = tij, t02 = tik, t12 = tjk;   // types of the pairs (v0,v1), (v0,v2), (v1,v2)
+      // sort the three ids, carrying the pair types along
+      if (v0 > v1) { int32_t q = v0; v0 = v1; v1 = q; int tq = t02; t02 = t12; t12 = tq; }
+      if (v1 > v2) { int32_t q = v1; v1 = v2; v2 = q; int tq = t01; t01 = t02; t02 = tq; }
+      if (v0 > v1) { int32_t q = v0; v0 = v1; v1 = q; int tq = t02; t02 = t12; t12 = tq; }
+      int32_t oa, ob;
+      if (t01 == st.type) { oa = v0; ob = v1; }
+      else if (t02 == st.type) { oa = v0; ob = v2; }
+      else { oa = v1; ob = v2; }
+      if (oa == min(i, j) && ob == max(i, j)) atomicAdd(&hist[w][pat], 1u);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < 24; k += blockDim.x) {
+    unsigned long long x = 0;
+    for (int ww = 0; ww < kSampleWarps; ++ww) x += hist[ww][k];
+    if (x) atomicAdd(&raw[k], x);
+  }
+}
+
+// ------------------------------------------------------------------ the sub-hypergraph G'
+
+// Priority of hyperedge i: Philox4x32-10(counter (i, 0, 1, 0), key seed), x1 << 32 | x0.
+__global__ void k_priority(int32_t ne, uint64_t seed, unsigned long long* __restrict__ pr) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t c[4] = {(uint32_t)i, 0u, 1u, 0u};
+    philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    pr[i] = ((unsigned long long)c[1] << 32) | c[0];
+  }
+}
+
+// Radix-select pass: histogram of the 16-bit digit at `shift` over the priorities whose
+// higher bits equal `prefix` (mask `pmask`).
+__global__ void k_digit_hist(const unsigned long long* __restrict__ pr, int32_t ne, int shift,
+                             unsigned long long pmask, unsigned long long prefix,
+                             unsigned int* __restrict__ hist) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long x = pr[i];
+    if ((x & pmask) == prefix) atomicAdd(&hist[(x >> shift) & 0xffffu], 1u);
+  }
+}
+
+// keep[i] = 1 for priorities below the threshold T, and for those equal to T while
+// their rank among the equal ones (in id order, eq_rank = exclusive scan) is < need
+__global__ void k_equal_flags(const unsigned long long* __restrict__ pr, int32_t ne,
+                              unsigned long long T, int32_t* __restrict__ eq) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne;
+       i += (int64_t)gridDim.x * blockDim.x)
+    eq[i] = pr[i] == T;
+}
+
+__global__ void k_keep_flags(const unsigned long long* __restrict__ pr, int32_t ne,
+                             unsigned long long T, const int64_t* __restrict__ eq_rank,
+                             int64_t need, int32_t* __restrict__ keep) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long x = pr[i];
+    keep[i] = x < T || (x == T && eq_rank[i] < need);
+  }
+}
+
+// kept hyperedges in id order: position = exclusive scan of keep; their sizes
+__global__ void k_compact_kept(const int32_t* __restrict__ keep, const int64_t* __restrict__ pos,
+                               const int32_t* __restrict__ esize, int32_t ne,
+                               int32_t* __restrict__ ids, int32_t* __restrict__ sizes) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (keep[i]) {
+      ids[pos[i]] = (int32_t)i;
+      sizes[pos[i]] = esize[i];
+    }
+}
+
+// one warp per kept hyperedge: copy its vertex row into the sub-hypergraph's CSR
+__global__ void k_gather_rows(const int64_t* __restrict__ e_ptr, const int32_t* __restrict__ e_idx,
+                              const int32_t* __restrict__ ids, int32_t nk,
+                              const int64_t* __restrict__ sub_ptr, int32_t* __restrict__ sub_idx) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int32_t q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nk; q += warps) {
+    const int32_t i = ids[q];
+    const int64_t b = e_ptr[i], len = e_ptr[i + 1] - b, o = sub_ptr[q];
+    for (int64_t t = lane; t < len; t += 32) sub_idx[o + t] = e_idx[b + t];
+  }
+}
+
+int grid_n(int64_t items, int per_block) {
+  int64_t b = (items + per_block - 1) / per_block;
+  if (b > 65535) b = 65535;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
 }  // namespace
 
 constexpr int kSortMaxLog2 = 14;   // rows of up to 16,384 neighbours sort in shared memory
@@ -231,6 +463,76 @@ void launch_sample(const DevGraph& g, const int64_t* up_ptr, const Oriented& up,
   note_launch();
   k_sample<<<(unsigned)blocks, kSampleWarps * 32, 0, s>>>(g, up_ptr, up, packed, W, seed, first,
                                                           num, raw);
+}
+
+void launch_type_counts(const int32_t* upc, const int32_t* wcr, int32_t ne, int32_t* cnt_t,
+                        cudaStream_t s) {
+  if (ne == 0) return;
+  note_launch();
+  k_type_counts<<<grid_n(ne, 256), 256, 0, s>>>(upc, wcr, ne, cnt_t);
+}
+
+void launch_split_types(const DevGraph& g, const int64_t* up_ptr, const Oriented& up, int packed,
+                        const int64_t* t_ptr, const Oriented& t, const int64_t* c_ptr,
+                        const Oriented& c, cudaStream_t s) {
+  if (g.ne == 0) return;
+  note_launch();
+  k_split_types<<<grid_n(g.ne, 8), 256, 0, s>>>(g, up_ptr, up, packed, t_ptr, t, c_ptr, c);
+}
+
+void launch_sample_adv(const DevGraph& g, const int64_t* set_ptr, const Oriented& set_ent,
+                       uint64_t Wx, int type, int cls, uint32_t stream, const int64_t* full_ptr,
+                       const Oriented& full, int packed, uint64_t seed, uint64_t first,
+                       uint64_t num, unsigned long long* raw, cudaStream_t s, int nsm) {
+  if (num == 0 || Wx == 0) return;
+  AdvSet st{set_ptr, set_ent, Wx, type, cls, stream};
+  uint64_t blocks = (num + kSampleWarps - 1) / kSampleWarps;
+  if (blocks > (uint64_t)nsm * 16) blocks = (uint64_t)nsm * 16;
+  note_launch();
+  k_sample_adv<<<(unsigned)blocks, kSampleWarps * 32, 0, s>>>(g, st, full_ptr, full, packed, seed,
+                                                               first, num, raw);
+}
+
+void launch_priority(int32_t ne, uint64_t seed, unsigned long long* pr, cudaStream_t s) {
+  if (ne == 0) return;
+  note_launch();
+  k_priority<<<grid_n(ne, 256), 256, 0, s>>>(ne, seed, pr);
+}
+
+void launch_digit_hist(const unsigned long long* pr, int32_t ne, int shift,
+                       unsigned long long pmask, unsigned long long prefix, unsigned int* hist,
+                       cudaStream_t s) {
+  if (ne == 0) return;
+  note_launch();
+  k_digit_hist<<<grid_n(ne, 256), 256, 0, s>>>(pr, ne, shift, pmask, prefix, hist);
+}
+
+void launch_equal_flags(const unsigned long long* pr, int32_t ne, unsigned long long T,
+                        int32_t* eq, cudaStream_t s) {
+  if (ne == 0) return;
+  note_launch();
+  k_equal_flags<<<grid_n(ne, 256), 256, 0, s>>>(pr, ne, T, eq);
+}
+
+void launch_keep_flags(const unsigned long long* pr, int32_t ne, unsigned long long T,
+                       const int64_t* eq_rank, int64_t need, int32_t* keep, cudaStream_t s) {
+  if (ne == 0) return;
+  note_launch();
+  k_keep_flags<<<grid_n(ne, 256), 256, 0, s>>>(pr, ne, T, eq_rank, need, keep);
+}
+
+void launch_compact_kept(const int32_t* keep, const int64_t* pos, const int32_t* esize, int32_t ne,
+                         int32_t* ids, int32_t* sizes, cudaStream_t s) {
+  if (ne == 0) return;
+  note_launch();
+  k_compact_kept<<<grid_n(ne, 256), 256, 0, s>>>(keep, pos, esize, ne, ids, sizes);
+}
+
+void launch_gather_rows(const int64_t* e_ptr, const int32_t* e_idx, const int32_t* ids, int32_t nk,
+                        const int64_t* sub_ptr, int32_t* sub_idx, cudaStream_t s) {
+  if (nk == 0) return;
+  note_launch();
+  k_gather_rows<<<grid_n(nk, 8), 256, 0, s>>>(e_ptr, e_idx, ids, nk, sub_ptr, sub_idx);
 }
 
 }  // namespace hg

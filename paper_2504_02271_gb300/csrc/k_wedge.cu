@@ -160,7 +160,8 @@ __global__ void __launch_bounds__(kLightWarps * 32)
         if (rc.wcr) rc.wcr[i] = incl;
       }
     } else {
-      // MODE 1: the out-list of the degree orientation; MODE 2: the neighbours j > i
+      // MODE 1: the out-list of the degree orientation; MODE 2: the neighbours j > i;
+      // MODE 3: every neighbour
       const int32_t di = MODE == 1 ? deg[i] : 0;
       const int64_t base = o.row_ptr[i];
       int32_t written = 0;
@@ -171,7 +172,8 @@ __global__ void __launch_bounds__(kLightWarps * 32)
         if (x != kEmpty) {
           j = (uint32_t)(x >> 32);
           om = (uint32_t)(x & 0xffffffffu);
-          emit = MODE == 1 ? ranked_above(di, i, deg[j], (int32_t)j) : (int32_t)j > i;
+          emit = MODE == 1 ? ranked_above(di, i, deg[j], (int32_t)j)
+                           : (MODE == 2 ? (int32_t)j > i : true);
         }
         const unsigned bal = __ballot_sync(kFull, emit);
         if (emit) put_entry<PACKED>(o, base + written + __popc(bal & ((1u << lane) - 1u)), j, om);
@@ -275,14 +277,16 @@ __global__ void __launch_bounds__(kBlockThreads)
         if (rc.wcr) rc.wcr[i] = s_incl;
       }
     } else {
-      // MODE 1: the out-list of the degree orientation; MODE 2: the neighbours j > i
+      // MODE 1: the out-list of the degree orientation; MODE 2: the neighbours j > i;
+      // MODE 3: every neighbour
       const int32_t di = MODE == 1 ? deg[i] : 0;
       const int64_t base = o.row_ptr[i];
       for (uint32_t s = threadIdx.x; s < CAP; s += kBlockThreads) {
         const unsigned long long x = T[s];
         if (x == kEmpty) continue;
         const uint32_t j = (uint32_t)(x >> 32), om = (uint32_t)(x & 0xffffffffu);
-        if (MODE == 1 ? ranked_above(di, i, deg[j], (int32_t)j) : (int32_t)j > i) {
+        if (MODE == 1 ? ranked_above(di, i, deg[j], (int32_t)j)
+                      : (MODE == 2 ? (int32_t)j > i : true)) {
           const int32_t pos = atomicAdd(&s_cnt, 1);
           put_entry<PACKED>(o, base + pos, j, om);
         }
@@ -399,8 +403,10 @@ void launch_wedge_pass(int mode, const DevGraph& g, const WedgeBuckets& b, const
     HG_WEDGE_PASS(0)
   } else if (mode == 1) {
     HG_WEDGE_PASS(1)
-  } else {
+  } else if (mode == 2) {
     HG_WEDGE_PASS(2)
+  } else {
+    HG_WEDGE_PASS(3)
   }
 #undef HG_WEDGE_PASS
 }

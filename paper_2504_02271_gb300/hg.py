@@ -34,7 +34,8 @@ EXPORTED = ("hg_set_allocator", "hg_load_csr", "hg_build_wedges", "hg_count_patt
             "hg_batch_build_wedges", "hg_batch_count_patterns", "hg_batch_clustering_coeff",
             "hg_batch_waves", "hg_batch_wave", "hg_batch_free", "hg_load_batch_members",
             "hg_server_create", "hg_server_add_graph", "hg_server_submit", "hg_server_wait",
-            "hg_server_drain", "hg_server_stats_get", "hg_server_destroy")
+            "hg_server_drain", "hg_server_stats_get", "hg_server_destroy",
+            "hg_sample_estimate_adv")
 
 
 class HgError(RuntimeError):
@@ -121,6 +122,8 @@ def _open():
     lib.hg_wedge_degrees_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp]
     u64 = ctypes.c_uint64
     lib.hg_sample_estimate.argtypes = [vp, u64, u64, u64, ctypes.c_double, vp, vp]
+    lib.hg_sample_estimate_adv.argtypes = [vp, u64, u64, u64, ctypes.c_double, ctypes.c_uint32,
+                                           vp, vp, vp]
     lib.hg_load_batch.argtypes = [i32, vp, vp, vp, vp, ctypes.c_int, i64, vp, ctypes.POINTER(vp)]
     lib.hg_batch_build_wedges.argtypes = [vp, ctypes.POINTER(_Tuning)]
     lib.hg_batch_count_patterns.argtypes = [vp, vp, vp]
@@ -284,6 +287,21 @@ def hg_sample_estimate(g: Graph, seed: int, first_sample: int, num_samples: int,
                                    int(first_sample), int(num_samples), float(sigma),
                                    raw.ctypes.data, est.ctypes.data))
     return raw, est
+
+
+def hg_sample_estimate_adv(g: Graph, seed: int, first_sample: int, num_samples: int,
+                           sigma: float = 1.0, class_mask: int = 15) -> tuple[np.ndarray, np.ndarray, dict]:
+    """Appro-adv (Algorithm 7): (raw uint64[21], est float64[21], info)."""
+    raw = np.zeros(21, dtype=np.uint64)
+    est = np.zeros(21, dtype=np.float64)
+    info = np.zeros(8, dtype=np.uint64)
+    _check("hg_sample_estimate_adv",
+           _lib.hg_sample_estimate_adv(ctypes.c_void_p(g.ptr), int(seed) & (2**64 - 1),
+                                       int(first_sample), int(num_samples), float(sigma),
+                                       int(class_mask), raw.ctypes.data, est.ctypes.data,
+                                       info.ctypes.data))
+    keys = ("W", "W_t", "W_c", "alpha_1", "alpha_2", "alpha_3", "alpha_4", "edges")
+    return raw, est, {k: int(v) for k, v in zip(keys, info)}
 
 
 def hg_clustering_coeff(g: Graph, eps) -> tuple[float, int, int]:

@@ -124,11 +124,16 @@ def test_argument_and_state_errors(hglib):
             hglib.hg_sample_estimate(g, 1, 0, 10)
         assert ei.value.name == "HG_ERR_STATE"
         hglib.hg_build_wedges(g)
-        for sigma, name in ((0.0, "HG_ERR_INVALID_ARG"), (1.5, "HG_ERR_INVALID_ARG"),
-                            (0.5, "HG_ERR_UNSUPPORTED")):
+        for sigma in (0.0, 1.5, -0.5):
             with pytest.raises(hglib.HgError) as ei:
                 hglib.hg_sample_estimate(g, 1, 0, 10, sigma=sigma)
-            assert ei.value.name == name
+            assert ei.value.name == "HG_ERR_INVALID_ARG"
+            with pytest.raises(hglib.HgError) as ei:
+                hglib.hg_sample_estimate_adv(g, 1, 0, 10, sigma=sigma)
+            assert ei.value.name == "HG_ERR_INVALID_ARG"
+        with pytest.raises(hglib.HgError) as ei:
+            hglib.hg_sample_estimate_adv(g, 1, 0, 10, class_mask=16)
+        assert ei.value.name == "HG_ERR_INVALID_ARG"
         with pytest.raises(hglib.HgError) as ei:
             hglib.hg_sample_estimate(g, 1, 2**64 - 5, 10)
         assert ei.value.name == "HG_ERR_INVALID_ARG"
@@ -139,3 +144,97 @@ def test_argument_and_state_errors(hglib):
         assert raw.tolist() == raw2.tolist()
     finally:
         hglib.hg_free(g)
+
+
+# ------------------------------------------------------------------ Appro-adv and sigma < 1
+
+def gpu_adv(hg, nv, e_ptr, e_idx, runs, **build):
+    import torch
+
+    stream = torch.cuda.Stream()
+    g = hg.hg_load_csr(nv, len(e_ptr) - 1, e_ptr, e_idx, stream=stream.cuda_stream)
+    try:
+        hg.hg_build_wedges(g, **build)
+        out = []
+        for r in runs:
+            if r[0] == "bs":
+                _, seed, first, num, sigma = r
+                out.append(hg.hg_sample_estimate(g, seed, first, num, sigma=sigma))
+            else:
+                _, seed, first, num, sigma, mask = r
+                out.append(hg.hg_sample_estimate_adv(g, seed, first, num, sigma=sigma,
+                                                     class_mask=mask))
+    finally:
+        hg.hg_free(g)
+    return out
+
+
+def check_adv(hg, nv, e_ptr, e_idx, runs, **build):
+    import oracle
+
+    out = gpu_adv(hg, nv, e_ptr, e_idx, runs, **build)
+    for r, got in zip(runs, out):
+        if r[0] == "bs":
+            _, seed, first, num, sigma = r
+            ref = oracle.sample_estimate(e_ptr, e_idx, nv, seed=seed, first=first, num=num,
+                                         sigma=sigma)
+            assert got[0].tolist() == ref.raw.tolist(), r
+            assert got[1].tolist() == ref.est.tolist(), r
+        else:
+            _, seed, first, num, sigma, mask = r
+            ref = oracle.sample_estimate_adv(e_ptr, e_idx, nv, seed=seed, first=first, num=num,
+                                             sigma=sigma, class_mask=mask)
+            raw, est, info = got
+            assert raw.tolist() == ref.raw.tolist(), r
+            assert est.tolist() == ref.est.tolist(), r
+            assert (info["W"], info["W_t"], info["W_c"], info["edges"]) == \
+                (ref.W, ref.W_t, ref.W_c, ref.edges), r
+            assert (info["alpha_1"], info["alpha_2"], info["alpha_3"], info["alpha_4"]) == ref.alphas
+    return out
+
+
+def test_adv_tiny_plain(hglib):
+    import hgen
+
+    e_ptr, e_idx = hgen.prefix(*hgen.generate(hgen.TINY_PLAIN), 300)
+    runs = [("adv", 9, 0, 30_000, 1.0, 15), ("adv", 9, 0, 30_000, 1.0, 8),
+            ("adv", 9, 0, 30_000, 1.0, 1 | 2 | 4), ("adv", 2**64 - 3, 2**36, 5_000, 1.0, 15),
+            ("adv", 4, 0, 1, 1.0, 15)]
+    out = check_adv(hglib, 1000, e_ptr, e_idx, runs)
+    assert out[0][0][0] > 0
+
+
+@pytest.mark.parametrize("name", ["tiny_plain", "coauthor_prefix50k", "tag_heavy_prefix2000"])
+def test_adv_workloads(hglib, name):
+    gold, e_ptr, e_idx = workload(name)
+    check_adv(hglib, gold["num_vertices"], e_ptr, e_idx,
+              [("adv", 2024, 0, 100_000, 1.0, 15), ("adv", 3, 10**9, 20_000, 1.0, 2 | 4)])
+
+
+def test_adv_unpacked_and_dense_tiles(hglib):
+    import hgen
+
+    spec = hgen.HypergraphSpec(3000, 300, 4, hgen.SIZE_UNIFORM, 200, 300, zipf_s=0.6, name="big")
+    e_ptr, e_idx = hgen.generate(spec)
+    check_adv(hglib, spec.num_vertices, e_ptr, e_idx, [("adv", 3, 0, 10_000, 1.0, 15)])
+    spec = hgen.HypergraphSpec(4000, 400, 1, hgen.SIZE_UNIFORM, 40, 100, zipf_s=0.6, name="big")
+    e_ptr, e_idx = hgen.generate(spec)
+    check_adv(hglib, spec.num_vertices, e_ptr, e_idx, [("adv", 12, 0, 10_000, 1.0, 15)],
+              dense_min_size=40, dense_max_count=1000)
+
+
+@pytest.mark.parametrize("sigma", [0.5, 0.3, 0.05])
+def test_sigma_sub_hypergraph(hglib, sigma):
+    # Algorithms 6 and 7 on G' (the ceil(sigma |E|) smallest Philox priorities)
+    import hgen
+
+    e_ptr, e_idx = hgen.prefix(*hgen.generate(hgen.TINY_PLAIN), 1500)
+    runs = [("bs", 31, 0, 40_000, sigma), ("adv", 31, 0, 40_000, sigma, 15),
+            ("bs", 32, 7, 40_000, sigma), ("bs", 31, 7, 10_000, 1.0), ("adv", 32, 0, 20_000, sigma, 8)]
+    check_adv(hglib, 1000, e_ptr, e_idx, runs)
+
+
+def test_sigma_on_coauthor_prefix(hglib):
+    gold, e_ptr, e_idx = workload("coauthor_prefix50k")
+    check_adv(hglib, gold["num_vertices"], e_ptr, e_idx,
+              [("bs", 5, 0, 200_000, 0.4), ("adv", 5, 0, 200_000, 0.4, 15)])
