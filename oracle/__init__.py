@@ -94,6 +94,11 @@ def _load():
             ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int, ctypes.c_int,
             ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         lib.oracle_sample_estimate_adv.restype = ctypes.c_int
+        lib.oracle_enumerate.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_uint64,
+                                         ctypes.POINTER(ctypes.c_uint64)]
+        lib.oracle_enumerate.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -203,6 +208,27 @@ def sample_estimate(e_ptr, e_idx, num_vertices: int, seed: int, first: int, num:
     if rc != 0:
         raise ValueError(f"oracle: {_ERR.get(rc, rc)}")
     return SampleEstimate(raw, est, int(W.value))
+
+
+def enumerate_pattern(e_ptr, e_idx, num_vertices: int, pattern: int, mode: str = "exact_bs",
+                      threads: int = 0) -> np.ndarray:
+    """int32[T_p, 3]: the hyper-triangles of `pattern` (0 = all) as i < j < k, sorted."""
+    lib = _load()
+    e_ptr = np.ascontiguousarray(e_ptr, dtype=np.int64)
+    e_idx = np.ascontiguousarray(e_idx, dtype=np.int32)
+    m = {"exact_bs": 0, "brute": 1}[mode]
+    total = ctypes.c_uint64(0)
+    rc = lib.oracle_enumerate(int(num_vertices), len(e_ptr) - 1, e_ptr.ctypes.data, e_idx.ctypes.data,
+                              m, int(pattern), int(threads), None, 0, ctypes.byref(total))
+    if rc != 0:
+        raise ValueError(f"oracle: {_ERR.get(rc, rc)}")
+    out = np.zeros((int(total.value), 3), dtype=np.int32)
+    rc = lib.oracle_enumerate(int(num_vertices), len(e_ptr) - 1, e_ptr.ctypes.data, e_idx.ctypes.data,
+                              m, int(pattern), int(threads), out.ctypes.data, int(total.value),
+                              ctypes.byref(total))
+    if rc != 0:
+        raise ValueError(f"oracle: {_ERR.get(rc, rc)}")
+    return out
 
 
 def subgraph(num_edges: int, seed: int, sigma: float) -> np.ndarray:

@@ -35,6 +35,7 @@
 // shows them only in a figure): ascending number of non-empty pairwise
 // regions (d, e, f), then ascending number of non-empty single regions.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <chrono>
 #include <cstdint>
@@ -653,6 +654,73 @@ int oracle_sample_estimate_adv(int32_t nv, int32_t ne, const int64_t* e_ptr,
     raw[0] += raw[p];
     est[0] += est[p];
   }
+  return bad ? -8 : 0;
+}
+
+// The hyper-triangles of one pattern (the problem statement of Sec. 2: compute the
+// hyper-triangles of a given pattern p; 0 = every pattern), as triples i < j < k in
+// lexicographic order.  mode 0 enumerates like Exact-bs (Algorithm 1), mode 1 tries every
+// triple.  The first min(total, capacity) triples go to out[3 * t ..]; *total = how many.
+int oracle_enumerate(int32_t nv, int32_t ne, const int64_t* e_ptr, const int32_t* e_idx, int mode,
+                     int pattern, int nthreads, int32_t* out, uint64_t capacity,
+                     uint64_t* total) {
+  if (!total || pattern < 0 || pattern > 20 || (capacity > 0 && !out)) return -6;
+  if (!oracle_pattern_table_ok()) return -7;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+  Graph g;
+  int rc = load(g, nv, ne, e_ptr, e_idx);
+  if (rc) return rc;
+  const auto& pm = pattern_map();
+  std::vector<std::vector<int32_t>> N(ne);
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int32_t x = 0; x < ne; ++x) N[x] = neighbours(g, x);
+  int nth = 1;
+#ifdef _OPENMP
+  nth = omp_get_max_threads();
+#endif
+  std::vector<std::vector<std::array<int32_t, 3>>> found((size_t)nth);
+  int bad = 0;
+#pragma omp parallel
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    auto& mine = found[(size_t)tid];
+#pragma omp for schedule(dynamic, 16) reduction(| : bad)
+    for (int32_t i = 0; i < ne; ++i) {
+      if (mode == 1) {   // every triple i < j < k
+        for (int32_t j = i + 1; j < ne; ++j)
+          for (int32_t k = j + 1; k < ne; ++k) {
+            if (!adjacent(N, i, j) || !adjacent(N, j, k) || !adjacent(N, i, k)) continue;
+            const int p = pm.of_mask[region_mask(g.e[i], g.e[j], g.e[k])];
+            if (p == 0) { bad = 1; continue; }
+            if (pattern == 0 || p == pattern) mine.push_back({i, j, k});
+          }
+      } else {           // pairs of neighbours of e_i above i that meet
+        const auto& Ni = N[i];
+        for (size_t a = 0; a < Ni.size(); ++a) {
+          const int32_t j = Ni[a];
+          if (j <= i) continue;
+          for (size_t b = a + 1; b < Ni.size(); ++b) {
+            const int32_t k = Ni[b];
+            if (!adjacent(N, j, k)) continue;
+            const int p = pm.of_mask[region_mask(g.e[i], g.e[j], g.e[k])];
+            if (p == 0) { bad = 1; continue; }
+            if (pattern == 0 || p == pattern) mine.push_back({i, j, k});
+          }
+        }
+      }
+    }
+  }
+  std::vector<std::array<int32_t, 3>> all;
+  for (auto& f : found) all.insert(all.end(), f.begin(), f.end());
+  std::sort(all.begin(), all.end());
+  *total = all.size();
+  for (uint64_t t = 0; t < std::min<uint64_t>(capacity, all.size()); ++t)
+    for (int c = 0; c < 3; ++c) out[3 * t + (uint64_t)c] = all[(size_t)t][(size_t)c];
   return bad ? -8 : 0;
 }
 

@@ -338,3 +338,64 @@ def test_clustering_coefficient(orc):
     cc = orc.pattern_wise_cc(r.counts, r.open)
     assert cc[4] == 3.0 * 3 / r.open and sum(cc) == pytest.approx(3.0 * r.T / r.open)
     assert math.isnan(orc.clustering_coeff(r.counts, 0, [1.0] * 20))
+
+
+# ------------------------------------------------------------------ single-pattern enumeration
+
+def test_enumeration_reproduces_the_printed_case_study_triangles():
+    # Sec. 6.2: the printed hyper-triangles (1-based hyperedge labels) of the e-mail case
+    # study are all of its pattern-5 triangles; the co-authorship ones are among theirs
+    import oracle
+
+    for name in ("email", "coauthorship"):
+        d = load_json("paper_examples.json")[name]
+        e_ptr, e_idx = csr_of(d["hyperedges"])
+        nv = 1 + max(v for e in d["hyperedges"] for v in e)
+        for tri, p in d["printed_triangles"]:
+            got = {tuple(t) for t in oracle.enumerate_pattern(e_ptr, e_idx, nv, p).tolist()}
+            assert tuple(x - 1 for x in tri) in got, (name, tri, p)
+    d = load_json("paper_examples.json")["email"]
+    e_ptr, e_idx = csr_of(d["hyperedges"])
+    nv = 1 + max(v for e in d["hyperedges"] for v in e)
+    got = oracle.enumerate_pattern(e_ptr, e_idx, nv, 5).tolist()
+    assert got == sorted([x - 1 for x in t] for t, _ in d["printed_triangles"])
+
+
+def random_hypergraph(seed, nv, ne):
+    import hgen
+
+    spec = hgen.HypergraphSpec(nv, ne, 500 + seed, hgen.SIZE_UNIFORM, 1, 7, zipf_s=0.9, name="t")
+    e_ptr, e_idx = hgen.generate(spec)
+    return e_ptr, e_idx, nv
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_enumeration_equals_brute_force_and_counts(seed):
+    import oracle
+
+    e_ptr, e_idx, nv = random_hypergraph(seed, 60, 120)
+    counts = oracle.count(e_ptr, e_idx, nv).counts
+    for p in range(0, 21):
+        a = oracle.enumerate_pattern(e_ptr, e_idx, nv, p)
+        b = oracle.enumerate_pattern(e_ptr, e_idx, nv, p, mode="brute")
+        assert a.tolist() == b.tolist()
+        assert len(a) == int(counts[p])
+        for i, j, k in a.tolist():
+            assert i < j < k
+            if p:
+                rows = [set(e_idx[e_ptr[x]:e_ptr[x + 1]].tolist()) for x in (i, j, k)]
+                assert oracle.classify(*rows) == p
+
+
+def test_enumeration_closed_form_sunflower():
+    # n hyperedges meeting pairwise in exactly {0}, each with a private vertex: every
+    # triple is a pattern-9 hyper-triangle, so the list is all C(n, 3) triples
+    from itertools import combinations
+
+    import oracle
+
+    n = 14
+    e_ptr, e_idx = csr_of([[0, 1 + x] for x in range(n)])
+    got = oracle.enumerate_pattern(e_ptr, e_idx, n + 1, 9).tolist()
+    assert got == [list(t) for t in combinations(range(n), 3)]
+    assert oracle.enumerate_pattern(e_ptr, e_idx, n + 1, 17).tolist() == []
