@@ -179,6 +179,21 @@ hg_status hg_sample_estimate_adv(hg_graph* g, uint64_t seed, uint64_t first_samp
                                  uint64_t raw[21], double est[21], uint64_t info[8]);
 
 /*
+ * The hyper-triangles of one pattern (Sec. 2, problem statement: compute the
+ * hyper-triangles of a given pattern p).  Every hyper-triangle {e_i, e_j, e_k},
+ * i < j < k, of pattern `pattern` (1..20; 0 = every pattern) is found once, from its
+ * smallest hyperwedge (i, j) in the order O, and written as the three ids (i, j, k).
+ *   triples   [capacity][3] int32, on the device (triples_on_device = 1) or the host;
+ *             the first min(total, capacity) triples found are written, in no fixed
+ *             order (each triple ascending).
+ *   total     out: the number of hyper-triangles of the pattern (= H[pattern], or T).
+ * Uses the sorted upper rows of hg_sample_estimate (built on first use).  Requires
+ * hg_build_wedges; a wave handle of a batch is HG_ERR_UNSUPPORTED.  Synchronises.
+ */
+hg_status hg_enumerate_pattern(hg_graph* g, int32_t pattern, int32_t* triples, uint64_t capacity,
+                               int triples_on_device, uint64_t* total);
+
+/*
  * Fine-grained hypergraph clustering coefficient (Def. 5.1):
  *   cc = 3 * sum_{p=1..20} eps[p-1] * H[p] / open,
  * evaluated on the host in IEEE double with the sum taken in order p = 1..20;

@@ -48,6 +48,7 @@ struct Small {
   unsigned long long wide_max[2];    // close bucket 3: max d+, max |e_u|
   unsigned long long hist[24];       // pattern histogram (bin 0 = unclassifiable)
   unsigned long long work[kCloseBuckets][3];   // closure per team shape: probes, E_y entries, out-entries
+  unsigned long long found;                    // triples of hg_enumerate_pattern
 };
 
 struct KTime {
@@ -1215,6 +1216,53 @@ hg_status hg_sample_estimate_adv(hg_graph* g, uint64_t seed, uint64_t first_samp
   }
   if (st == HG_OK)
     st = sample_adv_impl(h, seed, first_sample, num_samples, sigma, class_mask, raw, est, info);
+  if (st != HG_OK) {
+    cudaStreamSynchronize(g->stream);
+    cudaGetLastError();
+    g->pending.clear();
+  }
+  return st;
+}
+
+hg_status hg_enumerate_pattern(hg_graph* g, int32_t pattern, int32_t* triples, uint64_t capacity,
+                               int triples_on_device, uint64_t* total) {
+  if (!g || !total || pattern < 0 || pattern > 20 || (capacity > 0 && !triples) ||
+      capacity > (UINT64_MAX / 12))
+    return HG_ERR_INVALID_ARG;
+  if (!g->built) return HG_ERR_STATE;
+  if (g->nm > 0) return HG_ERR_UNSUPPORTED;
+  auto run = [&]() -> hg_status {
+    if (!g->upper_built) HG_TRY(upper_impl(g));
+    cudaStream_t s = g->stream;
+    uint8_t lut[128];
+    build_lut(lut);
+    sample_set_lut(lut, s);
+    std::vector<Block> tmp;
+    int32_t* out = triples;
+    if (!triples_on_device && capacity > 0) {
+      out = alloc_t<int32_t>(g, tmp, (int64_t)(3 * capacity));
+      if (!out) return HG_ERR_OOM;
+    }
+    unsigned long long* count = &g->small->found;
+    HG_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned long long), s));
+    t_begin(g, "enumerate");
+    launch_enumerate(dev_graph(g), g->up_ptr, g->up, g->packed, g->stats.W, pattern, out,
+                     capacity, count, s, g->nsm);
+    t_end(g);
+    unsigned long long n = 0;
+    HG_CUDA(cudaMemcpyAsync(&n, count, sizeof(n), cudaMemcpyDeviceToHost, s));
+    HG_CUDA(cudaStreamSynchronize(s));
+    if (!triples_on_device && capacity > 0 && n > 0)
+      HG_CUDA(cudaMemcpyAsync(triples, out, sizeof(int32_t) * 3 * std::min<uint64_t>(n, capacity),
+                              cudaMemcpyDeviceToHost, s));
+    Small h;
+    HG_TRY(sync_small(g, &h));
+    release(g, tmp);
+    t_collect(g);
+    *total = n;
+    return HG_OK;
+  };
+  hg_status st = run();
   if (st != HG_OK) {
     cudaStreamSynchronize(g->stream);
     cudaGetLastError();

@@ -159,6 +159,10 @@ void launch_sample_adv(const DevGraph& g, const int64_t* set_ptr, const Oriented
                        uint64_t Wx, int type, int cls, uint32_t stream, const int64_t* full_ptr,
                        const Oriented& full, int packed, uint64_t seed, uint64_t first,
                        uint64_t num, unsigned long long* raw, cudaStream_t s, int nsm);
+// single-pattern enumeration over the upper rows
+void launch_enumerate(const DevGraph& g, const int64_t* up_ptr, const Oriented& up, int packed,
+                      uint64_t W, int target, int32_t* out, unsigned long long cap,
+                      unsigned long long* count, cudaStream_t s, int nsm);
 // the sub-hypergraph G' of Algorithms 6-7 (sigma < 1)
 void launch_priority(int32_t ne, uint64_t seed, unsigned long long* pr, cudaStream_t s);
 void launch_digit_hist(const unsigned long long* pr, int32_t ne, int shift,

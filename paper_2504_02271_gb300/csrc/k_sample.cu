@@ -348,6 +348,79 @@ __global__ void __launch_bounds__(kSampleWarps * 32)
   }
 }
 
+// ------------------------------------------------------------------ single-pattern enumeration
+
+// One warp per hyperwedge (i, j) of the upper rows (m over 0 .. W-1): every k > j in both
+// upper(i) and upper(j) closes the triangle i < j < k (each found once); those of pattern
+// `target` (0 = all) are appended to out as (i, j, k), while fewer than cap were written.
+__global__ void __launch_bounds__(kSampleWarps * 32)
+    k_enumerate(DevGraph g, const int64_t* __restrict__ up_ptr, Oriented up, int packed,
+                uint64_t W, int target, int32_t* __restrict__ out, unsigned long long cap,
+                unsigned long long* __restrict__ count) {
+  __shared__ uint8_t lut[128];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int k = threadIdx.x; k < 128; k += blockDim.x) lut[k] = c_sample_lut[k];
+  __syncthreads();
+  const uint64_t warps = (uint64_t)gridDim.x * kSampleWarps;
+  for (uint64_t m = (uint64_t)blockIdx.x * kSampleWarps + w; m < W; m += warps) {
+    int32_t lo = 0, hi = g.ne - 1;
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (__ldg(up_ptr + mid) <= (int64_t)m) lo = mid; else hi = mid - 1;
+    }
+    const int32_t i = lo;
+    const int64_t ie = __ldg(up_ptr + i + 1);
+    int32_t j, wij;
+    up_entry(up, packed, (int64_t)m, j, wij);
+    const int64_t jb = __ldg(up_ptr + j), je = __ldg(up_ptr + j + 1);
+    const int64_t ei = g.e_ptr[i], ej = g.e_ptr[j];
+    const int szi = (int)(g.e_ptr[i + 1] - ei), szj = (int)(g.e_ptr[j + 1] - ej);
+    for (int64_t a0 = (int64_t)m + 1; a0 < ie; a0 += 32) {   // warp-uniform trip count
+      const int64_t a = a0 + lane;
+      bool hit = false;
+      int32_t k = 0;
+      if (a < ie) {
+        int32_t wik;
+        up_entry(up, packed, a, k, wik);
+        int64_t l = jb, h = je;
+        while (l < h) {
+          const int64_t mid = (l + h) >> 1;
+          int32_t x, om;
+          up_entry(up, packed, mid, x, om);
+          if (x < k) l = mid + 1; else h = mid;
+        }
+        if (l < je) {
+          int32_t x, wjk;
+          up_entry(up, packed, l, x, wjk);
+          if (x == k) {
+            const int64_t ek = g.e_ptr[k];
+            const int szk = (int)(g.e_ptr[k + 1] - ek);
+            const int gg = triple_common(g.e_idx + ei, szi, g.e_idx + ej, szj, g.e_idx + ek, szk);
+            const int ra = szi - wij - wik + gg, rb = szj - wij - wjk + gg,
+                      rc = szk - wik - wjk + gg;
+            const int bits = (ra > 0) | ((rb > 0) << 1) | ((rc > 0) << 2) | ((wij > gg) << 3) |
+                             ((wjk > gg) << 4) | ((wik > gg) << 5) | ((gg > 0) << 6);
+            hit = target == 0 || lut[bits] == target;
+          }
+        }
+      }
+      const unsigned bal = __ballot_sync(kFull, hit);
+      if (!bal) continue;
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(bal));
+      base = __shfl_sync(kFull, base, 0);
+      if (hit) {
+        const unsigned long long at = base + __popc(bal & ((1u << lane) - 1u));
+        if (at < cap) {
+          out[3 * at] = i;
+          out[3 * at + 1] = j;
+          out[3 * at + 2] = k;
+        }
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ the sub-hypergraph G'
 
 // Priority of hyperedge i: Philox4x32-10(counter (i, 0, 1, 0), key seed), x1 << 32 | x0.
@@ -533,6 +606,17 @@ void launch_gather_rows(const int64_t* e_ptr, const int32_t* e_idx, const int32_
   if (nk == 0) return;
   note_launch();
   k_gather_rows<<<grid_n(nk, 8), 256, 0, s>>>(e_ptr, e_idx, ids, nk, sub_ptr, sub_idx);
+}
+
+void launch_enumerate(const DevGraph& g, const int64_t* up_ptr, const Oriented& up, int packed,
+                      uint64_t W, int target, int32_t* out, unsigned long long cap,
+                      unsigned long long* count, cudaStream_t s, int nsm) {
+  if (W == 0) return;
+  uint64_t blocks = (W + kSampleWarps - 1) / kSampleWarps;
+  if (blocks > (uint64_t)nsm * 16) blocks = (uint64_t)nsm * 16;
+  note_launch();
+  k_enumerate<<<(unsigned)blocks, kSampleWarps * 32, 0, s>>>(g, up_ptr, up, packed, W, target, out,
+                                                              cap, count);
 }
 
 }  // namespace hg

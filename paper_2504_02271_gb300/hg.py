@@ -35,7 +35,7 @@ EXPORTED = ("hg_set_allocator", "hg_load_csr", "hg_build_wedges", "hg_count_patt
             "hg_batch_waves", "hg_batch_wave", "hg_batch_free", "hg_load_batch_members",
             "hg_server_create", "hg_server_add_graph", "hg_server_submit", "hg_server_wait",
             "hg_server_drain", "hg_server_stats_get", "hg_server_destroy",
-            "hg_sample_estimate_adv")
+            "hg_sample_estimate_adv", "hg_enumerate_pattern")
 
 
 class HgError(RuntimeError):
@@ -124,6 +124,7 @@ def _open():
     lib.hg_sample_estimate.argtypes = [vp, u64, u64, u64, ctypes.c_double, vp, vp]
     lib.hg_sample_estimate_adv.argtypes = [vp, u64, u64, u64, ctypes.c_double, ctypes.c_uint32,
                                            vp, vp, vp]
+    lib.hg_enumerate_pattern.argtypes = [vp, i32, vp, u64, ctypes.c_int, ctypes.POINTER(u64)]
     lib.hg_load_batch.argtypes = [i32, vp, vp, vp, vp, ctypes.c_int, i64, vp, ctypes.POINTER(vp)]
     lib.hg_batch_build_wedges.argtypes = [vp, ctypes.POINTER(_Tuning)]
     lib.hg_batch_count_patterns.argtypes = [vp, vp, vp]
@@ -302,6 +303,32 @@ def hg_sample_estimate_adv(g: Graph, seed: int, first_sample: int, num_samples: 
                                        info.ctypes.data))
     keys = ("W", "W_t", "W_c", "alpha_1", "alpha_2", "alpha_3", "alpha_4", "edges")
     return raw, est, {k: int(v) for k, v in zip(keys, info)}
+
+
+def hg_enumerate_pattern(g: Graph, pattern: int, capacity: int | None = None, out=None):
+    """(triples, total): the hyper-triangles of `pattern` (0 = all) as (i, j, k) rows.
+
+    With `out` (a contiguous int32 torch tensor of shape [capacity, 3] on the device) the
+    triples are written there; otherwise into a numpy array of `capacity` rows (default:
+    the total, found by a first call with capacity 0)."""
+    total = ctypes.c_uint64()
+    if out is not None:
+        _check("hg_enumerate_pattern",
+               _lib.hg_enumerate_pattern(ctypes.c_void_p(g.ptr), int(pattern),
+                                         ctypes.c_void_p(out.data_ptr()), out.shape[0], 1,
+                                         ctypes.byref(total)))
+        return out, int(total.value)
+    if capacity is None:
+        _check("hg_enumerate_pattern",
+               _lib.hg_enumerate_pattern(ctypes.c_void_p(g.ptr), int(pattern), None, 0, 0,
+                                         ctypes.byref(total)))
+        capacity = int(total.value)
+    arr = np.zeros((int(capacity), 3), dtype=np.int32)
+    _check("hg_enumerate_pattern",
+           _lib.hg_enumerate_pattern(ctypes.c_void_p(g.ptr), int(pattern),
+                                     arr.ctypes.data if capacity else None, int(capacity), 0,
+                                     ctypes.byref(total)))
+    return arr[:min(int(capacity), int(total.value))], int(total.value)
 
 
 def hg_clustering_coeff(g: Graph, eps) -> tuple[float, int, int]:
