@@ -435,6 +435,14 @@ hg_status hg_server_destroy(hg_server* s);
  */
 hg_status hg_pattern_table(uint8_t lut[128]);
 
+/*
+ * Reads made by the last hg_sample_estimate on this handle (its G' for sigma < 1):
+ * work[0] row-pointer reads (8 bytes each) of the row searches, work[1] upper-row entries
+ * read (4 bytes packed, 8 unpacked) by the walks and searches, work[2] vertex ids
+ * (4 bytes) read by the 3-way merges.  For roofline accounting.
+ */
+hg_status hg_sample_work_get(hg_graph* g, uint64_t work[3]);
+
 /* Static description of a status code. */
 const char* hg_status_str(hg_status s);
 

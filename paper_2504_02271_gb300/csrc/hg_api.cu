@@ -49,6 +49,7 @@ struct Small {
   unsigned long long hist[24];       // pattern histogram (bin 0 = unclassifiable)
   unsigned long long work[kCloseBuckets][3];   // closure per team shape: probes, E_y entries, out-entries
   unsigned long long found;                    // triples of hg_enumerate_pattern
+  unsigned long long sample_work[3];           // last sampler launch: pointer, entry, id reads
 };
 
 struct KTime {
@@ -106,6 +107,7 @@ struct hg_graph {
   hg_graph* sub = nullptr;
   uint64_t sub_seed = 0;
   double sub_sigma = 1.0;
+  uint64_t sample_work[3] = {0, 0, 0};   // of the last hg_sample_estimate
   // count stage
   std::vector<Block> count_blocks;
   bool counted = false;
@@ -853,15 +855,17 @@ hg_status sample_impl(hg_graph* g, uint64_t seed, uint64_t first, uint64_t num, 
   build_lut(lut);
   sample_set_lut(lut, s);
   HG_CUDA(cudaMemsetAsync(g->small->hist, 0, sizeof(g->small->hist), s));
+  HG_CUDA(cudaMemsetAsync(g->small->sample_work, 0, sizeof(g->small->sample_work), s));
   DevGraph d = dev_graph(g);
   t_begin(g, "sample");
-  launch_sample(d, g->up_ptr, g->up, g->packed, g->stats.W, seed, first, num, g->small->hist, s,
-                g->nsm);
+  launch_sample(d, g->up_ptr, g->up, g->packed, g->stats.W, seed, first, num, g->small->hist,
+                g->small->sample_work, s, g->nsm);
   t_end(g);
   Small h;
   HG_TRY(sync_small(g, &h));
   t_collect(g);
   if (h.hist[0] != 0) return HG_ERR_INTERNAL;
+  for (int k = 0; k < 3; ++k) g->sample_work[k] = h.sample_work[k];
   uint64_t total = 0;
   for (int p = 1; p <= 20; ++p) total += h.hist[p];
   raw[0] = total;
@@ -1465,6 +1469,13 @@ hg_status hg_close_stats_get(hg_graph* g, hg_close_stats* out) {
   if (!g || !out) return HG_ERR_INVALID_ARG;
   if (!g->counted) return HG_ERR_STATE;
   *out = g->cstats;
+  return HG_OK;
+}
+
+hg_status hg_sample_work_get(hg_graph* g, uint64_t work[3]) {
+  if (!g || !work) return HG_ERR_INVALID_ARG;
+  hg_graph* h = g->sub && g->sub->sample_work[1] ? g->sub : g;
+  for (int k = 0; k < 3; ++k) work[k] = h->sample_work[k];
   return HG_OK;
 }
 

@@ -146,9 +146,10 @@ int sample_sort_max_log2();
 void sample_set_lut(const uint8_t lut[128], cudaStream_t s);
 cudaError_t launch_sort_upper(const int64_t* up_ptr, int32_t ne, const Oriented& up, int packed,
                               int* err, cudaStream_t s, int nsm);
+// work (may be null): [0] row-pointer reads, [1] upper-row entries read, [2] vertex ids merged
 void launch_sample(const DevGraph& g, const int64_t* up_ptr, const Oriented& up, int packed,
                    uint64_t W, uint64_t seed, uint64_t first, uint64_t num,
-                   unsigned long long* raw, cudaStream_t s, int nsm);
+                   unsigned long long* raw, unsigned long long* work, cudaStream_t s, int nsm);
 // Appro-adv (Algorithm 7)
 void launch_type_counts(const int32_t* upc, const int32_t* wcr, int32_t ne, int32_t* cnt_t,
                         cudaStream_t s);

@@ -129,12 +129,16 @@ __device__ int triple_common(const int32_t* a, int na, const int32_t* b, int nb,
   return n;
 }
 
-// One warp per sample (grid-stride).  raw[0..23] += per-pattern counts.
+// One warp per sample (grid-stride).  raw[0..23] += per-pattern counts; work[0] +=
+// row-pointer reads of the row searches, work[1] += upper-row entries read (walks
+// and searches), work[2] += vertex ids read by the 3-way merges.
 __global__ void __launch_bounds__(kSampleWarps * 32)
     k_sample(DevGraph g, const int64_t* __restrict__ up_ptr, Oriented up, int packed, uint64_t W,
-             uint64_t seed, uint64_t first, uint64_t num, unsigned long long* __restrict__ raw) {
+             uint64_t seed, uint64_t first, uint64_t num, unsigned long long* __restrict__ raw,
+             unsigned long long* __restrict__ work) {
   __shared__ uint32_t hist[kSampleWarps][24];
   __shared__ uint8_t lut[128];
+  unsigned long long n_ptr = 0, n_ent = 0, n_vtx = 0;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int k = threadIdx.x; k < 128; k += blockDim.x) lut[k] = c_sample_lut[k];
   for (int k = lane; k < 24; k += 32) hist[w][k] = 0;
@@ -151,6 +155,7 @@ __global__ void __launch_bounds__(kSampleWarps * 32)
     while (lo < hi) {
       const int32_t mid = (lo + hi + 1) >> 1;
       if (__ldg(up_ptr + mid) <= (int64_t)m) lo = mid; else hi = mid - 1;
+      if (lane == 0) ++n_ptr;
     }
     const int32_t i = lo;
     const int64_t ib = (int64_t)m, ie = __ldg(up_ptr + i + 1);
@@ -159,29 +164,47 @@ __global__ void __launch_bounds__(kSampleWarps * 32)
     const int64_t jb = __ldg(up_ptr + j), je = __ldg(up_ptr + j + 1);
     const int64_t ei = g.e_ptr[i], ej = g.e_ptr[j];
     const int szi = (int)(g.e_ptr[i + 1] - ei), szj = (int)(g.e_ptr[j + 1] - ej);
+    if (lane == 0) {
+      n_ptr += 3;
+      n_ent += 1;
+    }
     // k > j in upper(i) (entries after m) and in upper(j): binary search each in upper(j)
     for (int64_t a = ib + 1 + lane; a < ie; a += 32) {
       int32_t k, wik;
       up_entry(up, packed, a, k, wik);
+      ++n_ent;
       int64_t l = jb, h = je;
       while (l < h) {
         const int64_t mid = (l + h) >> 1;
         int32_t x, om;
         up_entry(up, packed, mid, x, om);
+        ++n_ent;
         if (x < k) l = mid + 1; else h = mid;
       }
       if (l >= je) continue;
       int32_t x, wjk;
       up_entry(up, packed, l, x, wjk);
+      ++n_ent;
       if (x != k) continue;
       const int64_t ek = g.e_ptr[k];
       const int szk = (int)(g.e_ptr[k + 1] - ek);
       const int gg = triple_common(g.e_idx + ei, szi, g.e_idx + ej, szj, g.e_idx + ek, szk);
+      n_vtx += (unsigned long long)(szi + szj + szk);
       const int ra = szi - wij - wik + gg, rb = szj - wij - wjk + gg, rc = szk - wik - wjk + gg;
       const int bits = (ra > 0) | ((rb > 0) << 1) | ((rc > 0) << 2) | ((wij > gg) << 3) |
                        ((wjk > gg) << 4) | ((wik > gg) << 5) | ((gg > 0) << 6);
       atomicAdd(&hist[w][lut[bits]], 1u);
     }
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    n_ent += __shfl_down_sync(kFull, n_ent, d);
+    n_vtx += __shfl_down_sync(kFull, n_vtx, d);
+  }
+  if (lane == 0 && work) {
+    atomicAdd(&work[0], n_ptr);
+    atomicAdd(&work[1], n_ent);
+    atomicAdd(&work[2], n_vtx);
   }
   __syncthreads();
   for (int k = threadIdx.x; k < 24; k += blockDim.x) {
@@ -529,13 +552,13 @@ cudaError_t launch_sort_upper(const int64_t* up_ptr, int32_t ne, const Oriented&
 
 void launch_sample(const DevGraph& g, const int64_t* up_ptr, const Oriented& up, int packed,
                    uint64_t W, uint64_t seed, uint64_t first, uint64_t num,
-                   unsigned long long* raw, cudaStream_t s, int nsm) {
+                   unsigned long long* raw, unsigned long long* work, cudaStream_t s, int nsm) {
   if (num == 0 || W == 0) return;
   uint64_t blocks = (num + kSampleWarps - 1) / kSampleWarps;
   if (blocks > (uint64_t)nsm * 16) blocks = (uint64_t)nsm * 16;
   note_launch();
   k_sample<<<(unsigned)blocks, kSampleWarps * 32, 0, s>>>(g, up_ptr, up, packed, W, seed, first,
-                                                          num, raw);
+                                                          num, raw, work);
 }
 
 void launch_type_counts(const int32_t* upc, const int32_t* wcr, int32_t ne, int32_t* cnt_t,

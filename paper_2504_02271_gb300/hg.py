@@ -35,7 +35,7 @@ EXPORTED = ("hg_set_allocator", "hg_load_csr", "hg_build_wedges", "hg_count_patt
             "hg_batch_waves", "hg_batch_wave", "hg_batch_free", "hg_load_batch_members",
             "hg_server_create", "hg_server_add_graph", "hg_server_submit", "hg_server_wait",
             "hg_server_drain", "hg_server_stats_get", "hg_server_destroy",
-            "hg_sample_estimate_adv", "hg_enumerate_pattern")
+            "hg_sample_estimate_adv", "hg_enumerate_pattern", "hg_sample_work_get")
 
 
 class HgError(RuntimeError):
@@ -125,6 +125,7 @@ def _open():
     lib.hg_sample_estimate_adv.argtypes = [vp, u64, u64, u64, ctypes.c_double, ctypes.c_uint32,
                                            vp, vp, vp]
     lib.hg_enumerate_pattern.argtypes = [vp, i32, vp, u64, ctypes.c_int, ctypes.POINTER(u64)]
+    lib.hg_sample_work_get.argtypes = [vp, vp]
     lib.hg_load_batch.argtypes = [i32, vp, vp, vp, vp, ctypes.c_int, i64, vp, ctypes.POINTER(vp)]
     lib.hg_batch_build_wedges.argtypes = [vp, ctypes.POINTER(_Tuning)]
     lib.hg_batch_count_patterns.argtypes = [vp, vp, vp]
@@ -630,3 +631,10 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def hg_sample_work_get(g: Graph) -> dict:
+    """Reads of the last hg_sample_estimate: row-pointer reads, entries, vertex ids."""
+    w = np.zeros(3, dtype=np.uint64)
+    _check("hg_sample_work_get", _lib.hg_sample_work_get(ctypes.c_void_p(g.ptr), w.ctypes.data))
+    return {"ptr_reads": int(w[0]), "entry_reads": int(w[1]), "vertex_reads": int(w[2])}
