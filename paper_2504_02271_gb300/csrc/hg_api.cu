@@ -95,12 +95,15 @@ struct hg_graph {
   // sampling stage: rows of neighbours j > i sorted by j (order O of Sec. 2)
   std::vector<Block> sample_blocks;
   int64_t* up_ptr = nullptr;
+  int32_t* up_index = nullptr;   // bucket index of up_ptr
   Oriented up{};
   bool upper_built = false;
   // Algorithm 7: the upper rows split by type, and every neighbour row sorted
   bool adv_built = false;
   int64_t* t_ptr = nullptr;
   int64_t* c_ptr = nullptr;
+  int32_t* t_index = nullptr;
+  int32_t* c_index = nullptr;
   Oriented t_ent{}, c_ent{}, full{};
   uint64_t Wt = 0, Wc = 0;
   // the sub-hypergraph G' for sigma < 1 (Algorithms 6-7, line 2), kept for its seed
@@ -632,6 +635,10 @@ hg_status upper_impl(hg_graph* g) {
   t_begin(g, "upper_sort");
   HG_CUDA(launch_sort_upper(g->up_ptr, g->ne, g->up, g->packed, &g->small->err, s, g->nsm));
   t_end(g);
+  g->up_index = alloc_t<int32_t>(g, g->sample_blocks,
+                                 row_index_buckets(g->stats.W, row_index_shift(g->stats.W, g->ne)) + 1);
+  if (!g->up_index) return HG_ERR_OOM;
+  launch_row_index(g->up_ptr, g->ne, g->stats.W, g->up_index, s);
   Small h;
   HG_TRY(sync_small(g, &h));
   t_collect(g);
@@ -683,6 +690,13 @@ hg_status adv_impl(hg_graph* g) {
   t_begin(g, "adv_split");
   launch_split_types(d, g->up_ptr, g->up, g->packed, g->t_ptr, g->t_ent, g->c_ptr, g->c_ent, s);
   t_end(g);
+  g->t_index = alloc_t<int32_t>(g, g->sample_blocks,
+                                row_index_buckets(g->Wt, row_index_shift(g->Wt, g->ne)) + 1);
+  g->c_index = alloc_t<int32_t>(g, g->sample_blocks,
+                                row_index_buckets(g->Wc, row_index_shift(g->Wc, g->ne)) + 1);
+  if (!g->t_index || !g->c_index) return HG_ERR_OOM;
+  launch_row_index(g->t_ptr, g->ne, g->Wt, g->t_index, s);
+  launch_row_index(g->c_ptr, g->ne, g->Wc, g->c_index, s);
   HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
   t_begin(g, "full_emit");
   launch_wedge_pass(3, d, g->wb, g->nb, g->max_cand, g->deg, &g->small->wc, g->full, g->packed,
@@ -822,9 +836,10 @@ hg_status sample_adv_impl(hg_graph* g, uint64_t seed, uint64_t first, uint64_t n
     const uint64_t Wx = incl ? Wc : Wt;
     HG_CUDA(cudaMemsetAsync(g->small->hist, 0, sizeof(g->small->hist), s));
     t_begin(g, "sample_adv");
-    launch_sample_adv(d, incl ? g->c_ptr : g->t_ptr, incl ? g->c_ent : g->t_ent, Wx, kType[x],
-                      kClass[x], (uint32_t)(1 + x), g->ori.row_ptr, g->full, g->packed, seed,
-                      first, alpha[x], g->small->hist, s, g->nsm);
+    launch_sample_adv(d, incl ? g->c_ptr : g->t_ptr, incl ? g->c_index : g->t_index,
+                      incl ? g->c_ent : g->t_ent, Wx, kType[x], kClass[x], (uint32_t)(1 + x),
+                      g->ori.row_ptr, g->full, g->packed, seed, first, alpha[x], g->small->hist,
+                      s, g->nsm);
     t_end(g);
     Small h;
     HG_TRY(sync_small(g, &h));
@@ -858,8 +873,8 @@ hg_status sample_impl(hg_graph* g, uint64_t seed, uint64_t first, uint64_t num, 
   HG_CUDA(cudaMemsetAsync(g->small->sample_work, 0, sizeof(g->small->sample_work), s));
   DevGraph d = dev_graph(g);
   t_begin(g, "sample");
-  launch_sample(d, g->up_ptr, g->up, g->packed, g->stats.W, seed, first, num, g->small->hist,
-                g->small->sample_work, s, g->nsm);
+  launch_sample(d, g->up_ptr, g->up_index, g->up, g->packed, g->stats.W, seed, first, num,
+                g->small->hist, g->small->sample_work, s, g->nsm);
   t_end(g);
   Small h;
   HG_TRY(sync_small(g, &h));
@@ -1250,8 +1265,8 @@ hg_status hg_enumerate_pattern(hg_graph* g, int32_t pattern, int32_t* triples, u
     unsigned long long* count = &g->small->found;
     HG_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned long long), s));
     t_begin(g, "enumerate");
-    launch_enumerate(dev_graph(g), g->up_ptr, g->up, g->packed, g->stats.W, pattern, out,
-                     capacity, count, s, g->nsm);
+    launch_enumerate(dev_graph(g), g->up_ptr, g->up_index, g->up, g->packed, g->stats.W, pattern,
+                     out, capacity, count, s, g->nsm);
     t_end(g);
     unsigned long long n = 0;
     HG_CUDA(cudaMemcpyAsync(&n, count, sizeof(n), cudaMemcpyDeviceToHost, s));

@@ -146,24 +146,33 @@ int sample_sort_max_log2();
 void sample_set_lut(const uint8_t lut[128], cudaStream_t s);
 cudaError_t launch_sort_upper(const int64_t* up_ptr, int32_t ne, const Oriented& up, int packed,
                               int* err, cudaStream_t s, int nsm);
-// work (may be null): [0] row-pointer reads, [1] upper-row entries read, [2] vertex ids merged
-void launch_sample(const DevGraph& g, const int64_t* up_ptr, const Oriented& up, int packed,
-                   uint64_t W, uint64_t seed, uint64_t first, uint64_t num,
-                   unsigned long long* raw, unsigned long long* work, cudaStream_t s, int nsm);
+// Bucket index of a row-pointer array of `entries` entries over ne rows (sampler row
+// searches): row_index_buckets(entries, row_index_shift(entries, ne)) + 1 int32.
+int row_index_shift(uint64_t entries, int32_t rows);
+int64_t row_index_buckets(uint64_t entries, int shift);
+void launch_row_index(const int64_t* ptr, int32_t ne, uint64_t entries, int32_t* first,
+                      cudaStream_t s);
+// work (may be null): [0] row-pointer reads, [1] upper-row entries read, [2] vertex ids merged;
+// up_index (may be null): the bucket index of up_ptr
+void launch_sample(const DevGraph& g, const int64_t* up_ptr, const int32_t* up_index,
+                   const Oriented& up, int packed, uint64_t W, uint64_t seed, uint64_t first,
+                   uint64_t num, unsigned long long* raw, unsigned long long* work, cudaStream_t s,
+                   int nsm);
 // Appro-adv (Algorithm 7)
 void launch_type_counts(const int32_t* upc, const int32_t* wcr, int32_t ne, int32_t* cnt_t,
                         cudaStream_t s);
 void launch_split_types(const DevGraph& g, const int64_t* up_ptr, const Oriented& up, int packed,
                         const int64_t* t_ptr, const Oriented& t, const int64_t* c_ptr,
                         const Oriented& c, cudaStream_t s);
-void launch_sample_adv(const DevGraph& g, const int64_t* set_ptr, const Oriented& set_ent,
-                       uint64_t Wx, int type, int cls, uint32_t stream, const int64_t* full_ptr,
-                       const Oriented& full, int packed, uint64_t seed, uint64_t first,
-                       uint64_t num, unsigned long long* raw, cudaStream_t s, int nsm);
+void launch_sample_adv(const DevGraph& g, const int64_t* set_ptr, const int32_t* set_index,
+                       const Oriented& set_ent, uint64_t Wx, int type, int cls, uint32_t stream,
+                       const int64_t* full_ptr, const Oriented& full, int packed, uint64_t seed,
+                       uint64_t first, uint64_t num, unsigned long long* raw, cudaStream_t s,
+                       int nsm);
 // single-pattern enumeration over the upper rows
-void launch_enumerate(const DevGraph& g, const int64_t* up_ptr, const Oriented& up, int packed,
-                      uint64_t W, int target, int32_t* out, unsigned long long cap,
-                      unsigned long long* count, cudaStream_t s, int nsm);
+void launch_enumerate(const DevGraph& g, const int64_t* up_ptr, const int32_t* up_index,
+                      const Oriented& up, int packed, uint64_t W, int target, int32_t* out,
+                      unsigned long long cap, unsigned long long* count, cudaStream_t s, int nsm);
 // the sub-hypergraph G' of Algorithms 6-7 (sigma < 1)
 void launch_priority(int32_t ne, uint64_t seed, unsigned long long* pr, cudaStream_t s);
 void launch_digit_hist(const unsigned long long* pr, int32_t ne, int shift,

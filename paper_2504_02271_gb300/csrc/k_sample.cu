@@ -8,7 +8,8 @@
 // r = x1 << 32 | x0 and draws hyperwedge m = floor(r * W / 2^64).  For the drawn
 // (i, j) every k > j in both upper(i) and upper(j) closes the hyper-triangle
 // {i, j, k} whose smallest hyperwedge in O is (i, j); it is classified from its
-// seven Venn regions (g by a 3-way merge of the vertex lists) and counted.
+// seven Venn regions (g = |e_i cap e_j cap e_k| from the staged e_i cap e_j) and
+// counted.
 #include <mutex>
 
 #include "hg_internal.cuh"
@@ -129,17 +130,199 @@ __device__ int triple_common(const int32_t* a, int na, const int32_t* b, int nb,
   return n;
 }
 
-// One warp per sample (grid-stride).  raw[0..23] += per-pattern counts; work[0] +=
-// row-pointer reads of the row searches, work[1] += upper-row entries read (walks
-// and searches), work[2] += vertex ids read by the 3-way merges.
+// ------------------------------------------------------------------ warp routines
+//
+// A draw (i, j) closes its triangles by probing each candidate k in a sorted row of
+// j, and computes g = |e_i cap e_j cap e_k| for each.  Both are served from the warp's
+// shared memory when they fit: the searched row is staged once per draw (a binary
+// search then costs shared loads, not dependent global ones), and e_i cap e_j (of
+// size omega_ij, known from the entry) is staged once, so that g needs omega_ij
+// binary searches in e_k instead of a 3-way merge.
+
+constexpr int kCacheEntries = 384;   // searched rows up to this long go to shared memory
+constexpr int kCommonMax = 64;       // e_i cap e_j up to this large goes to shared memory
+
+struct WarpCache {
+  int32_t key[kCacheEntries];
+  int32_t om[kCacheEntries];
+  int32_t common[kCommonMax];
+};
+
+// Reads made by a warp, for roofline accounting: [0] row pointers, [1] row entries,
+// [2] vertex ids.  Lanes count their own; reduced at exit.
+struct ReadCount {
+  unsigned long long ptr = 0, ent = 0, vtx = 0;
+  __device__ void flush(unsigned long long* work, int lane) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      ptr += __shfl_down_sync(kFull, ptr, d);
+      ent += __shfl_down_sync(kFull, ent, d);
+      vtx += __shfl_down_sync(kFull, vtx, d);
+    }
+    if (lane == 0 && work) {
+      atomicAdd(&work[0], ptr);
+      atomicAdd(&work[1], ent);
+      atomicAdd(&work[2], vtx);
+    }
+  }
+};
+
+// Copy row [b, e) into the cache when it fits (warp-uniform; all lanes).
+__device__ __forceinline__ bool stage_row(WarpCache& c, const Oriented& rows, int packed,
+                                          int64_t b, int64_t e, int lane, ReadCount& rc) {
+  const int64_t len = e - b;
+  if (len > kCacheEntries) return false;
+  for (int64_t t = lane; t < len; t += 32) {
+    int32_t x, om;
+    up_entry(rows, packed, b + t, x, om);
+    c.key[t] = x;
+    c.om[t] = om;
+    ++rc.ent;
+  }
+  __syncwarp();
+  return true;
+}
+
+// omega of key k in row [b, e) (sorted), -1 when absent.
+__device__ __forceinline__ int find_in_row(const WarpCache& c, bool cached, const Oriented& rows,
+                                           int packed, int64_t b, int64_t e, int32_t k,
+                                           ReadCount& rc) {
+  if (cached) {
+    int l = 0, h = (int)(e - b);
+    while (l < h) {
+      const int mid = (l + h) >> 1;
+      if (c.key[mid] < k) l = mid + 1; else h = mid;
+    }
+    return (l < (int)(e - b) && c.key[l] == k) ? c.om[l] : -1;
+  }
+  int64_t l = b, h = e;
+  while (l < h) {
+    const int64_t mid = (l + h) >> 1;
+    int32_t x, om;
+    up_entry(rows, packed, mid, x, om);
+    ++rc.ent;
+    if (x < k) l = mid + 1; else h = mid;
+  }
+  if (l >= e) return -1;
+  int32_t x, om;
+  up_entry(rows, packed, l, x, om);
+  ++rc.ent;
+  return x == k ? om : -1;
+}
+
+__device__ __forceinline__ bool in_sorted(const int32_t* a, int n, int32_t y, ReadCount& rc) {
+  int l = 0, h = n;
+  while (l < h) {
+    const int mid = (l + h) >> 1;
+    const int32_t x = __ldg(a + mid);
+    ++rc.vtx;
+    if (x < y) l = mid + 1; else h = mid;
+  }
+  if (l >= n) return false;
+  ++rc.vtx;
+  return __ldg(a + l) == y;
+}
+
+// e_i cap e_j into the cache (ascending) when omega_ij fits (warp-uniform; all lanes).
+__device__ __forceinline__ bool stage_common(WarpCache& c, const int32_t* ei, int szi,
+                                             const int32_t* ej, int szj, int wij, int lane,
+                                             ReadCount& rc) {
+  if (wij > kCommonMax) return false;
+  const bool a_is_i = szi <= szj;
+  const int32_t* a = a_is_i ? ei : ej;
+  const int32_t* b = a_is_i ? ej : ei;
+  const int na = a_is_i ? szi : szj, nb = a_is_i ? szj : szi;
+  int n = 0;
+  for (int t0 = 0; t0 < na; t0 += 32) {
+    const int t = t0 + lane;
+    bool in = false;
+    int32_t y = 0;
+    if (t < na) {
+      y = __ldg(a + t);
+      ++rc.vtx;
+      in = in_sorted(b, nb, y, rc);
+    }
+    const unsigned bal = __ballot_sync(kFull, in);
+    if (in && n + __popc(bal & ((1u << lane) - 1u)) < kCommonMax)
+      c.common[n + __popc(bal & ((1u << lane) - 1u))] = y;
+    n += __popc(bal);
+  }
+  __syncwarp();
+  return n == wij;
+}
+
+// g = |e_i cap e_j cap e_k|
+__device__ __forceinline__ int common3(const WarpCache& c, bool staged, int wij,
+                                       const int32_t* ei, int szi, const int32_t* ej, int szj,
+                                       const int32_t* ek, int szk, ReadCount& rc) {
+  if (staged) {
+    int gg = 0;
+    for (int t = 0; t < wij; ++t) gg += in_sorted(ek, szk, c.common[t], rc);
+    return gg;
+  }
+  rc.vtx += (unsigned long long)(szi + szj + szk);
+  return triple_common(ei, szi, ej, szj, ek, szk);
+}
+
+__device__ __forceinline__ int region_bits7(int szi, int szj, int szk, int wij, int wik, int wjk,
+                                            int gg) {
+  const int ra = szi - wij - wik + gg, rb = szj - wij - wjk + gg, rc = szk - wik - wjk + gg;
+  return (ra > 0) | ((rb > 0) << 1) | ((rc > 0) << 2) | ((wij > gg) << 3) | ((wjk > gg) << 4) |
+         ((wik > gg) << 5) | ((gg > 0) << 6);
+}
+
+// Bucket index of a row-pointer array: bucket b covers entries [b << shift, (b+1) << shift)
+// and first[b] is the row holding entry b << shift, so the row of entry m lies in
+// [first[m >> shift], first[(m >> shift) + 1]] (first has one more, sentinel, entry).
+struct RowIndex {
+  const int32_t* first;
+  int shift;
+  int64_t buckets;
+};
+
+// Row of entry m: the last i with ptr[i] <= m (searched between the bucket bounds).
+__device__ __forceinline__ int32_t row_of(const int64_t* __restrict__ ptr, int32_t ne,
+                                          const RowIndex& ix, uint64_t m, int lane,
+                                          ReadCount& rc) {
+  int32_t lo = 0, hi = ne - 1;
+  if (ix.first) {
+    const int64_t b = (int64_t)(m >> ix.shift);
+    lo = __ldg(ix.first + b);
+    hi = __ldg(ix.first + b + 1);
+    if (lane == 0) rc.ptr += 1;   // two 4-byte reads
+  }
+  while (lo < hi) {
+    const int32_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(ptr + mid) <= (int64_t)m) lo = mid; else hi = mid - 1;
+    if (lane == 0) ++rc.ptr;
+  }
+  return lo;
+}
+
+// first[b] for every bucket: row i writes the buckets whose first entry it holds.
+__global__ void k_row_index(const int64_t* __restrict__ ptr, int32_t ne, int shift,
+                            int64_t buckets, int32_t* __restrict__ first) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b0 = (ptr[i] + ((int64_t(1) << shift) - 1)) >> shift;
+    const int64_t b1 = (ptr[i + 1] + ((int64_t(1) << shift) - 1)) >> shift;
+    for (int64_t b = b0; b < b1; ++b) first[b] = (int32_t)i;
+    if (i == ne - 1) first[buckets] = (int32_t)(ne - 1);
+  }
+}
+
+// One warp per sample (grid-stride).  raw[0..23] += per-pattern counts; work[0..2] +=
+// the reads made (ReadCount).
 __global__ void __launch_bounds__(kSampleWarps * 32)
-    k_sample(DevGraph g, const int64_t* __restrict__ up_ptr, Oriented up, int packed, uint64_t W,
-             uint64_t seed, uint64_t first, uint64_t num, unsigned long long* __restrict__ raw,
-             unsigned long long* __restrict__ work) {
+    k_sample(DevGraph g, const int64_t* __restrict__ up_ptr, RowIndex ix, Oriented up, int packed,
+             uint64_t W, uint64_t seed, uint64_t first, uint64_t num,
+             unsigned long long* __restrict__ raw, unsigned long long* __restrict__ work) {
   __shared__ uint32_t hist[kSampleWarps][24];
   __shared__ uint8_t lut[128];
-  unsigned long long n_ptr = 0, n_ent = 0, n_vtx = 0;
+  __shared__ WarpCache cache[kSampleWarps];
+  ReadCount rc;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  WarpCache& cw = cache[w];
   for (int k = threadIdx.x; k < 128; k += blockDim.x) lut[k] = c_sample_lut[k];
   for (int k = lane; k < 24; k += 32) hist[w][k] = 0;
   __syncthreads();
@@ -150,62 +333,36 @@ __global__ void __launch_bounds__(kSampleWarps * 32)
     philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
     const uint64_t r = ((uint64_t)c[1] << 32) | c[0];
     const uint64_t m = __umul64hi(r, W);
-    // row i: last i with up_ptr[i] <= m
-    int32_t lo = 0, hi = g.ne - 1;
-    while (lo < hi) {
-      const int32_t mid = (lo + hi + 1) >> 1;
-      if (__ldg(up_ptr + mid) <= (int64_t)m) lo = mid; else hi = mid - 1;
-      if (lane == 0) ++n_ptr;
-    }
-    const int32_t i = lo;
+    const int32_t i = row_of(up_ptr, g.ne, ix, m, lane, rc);
     const int64_t ib = (int64_t)m, ie = __ldg(up_ptr + i + 1);
     int32_t j, wij;
     up_entry(up, packed, ib, j, wij);
     const int64_t jb = __ldg(up_ptr + j), je = __ldg(up_ptr + j + 1);
-    const int64_t ei = g.e_ptr[i], ej = g.e_ptr[j];
-    const int szi = (int)(g.e_ptr[i + 1] - ei), szj = (int)(g.e_ptr[j + 1] - ej);
+    const int32_t* ei = g.e_idx + g.e_ptr[i];
+    const int32_t* ej = g.e_idx + g.e_ptr[j];
+    const int szi = g.esize[i], szj = g.esize[j];
     if (lane == 0) {
-      n_ptr += 3;
-      n_ent += 1;
+      rc.ptr += 3;
+      rc.ent += 1;
     }
-    // k > j in upper(i) (entries after m) and in upper(j): binary search each in upper(j)
+    __syncwarp();   // the previous draw's readers are done with the cache
+    const bool walk = ie > ib + 1;   // warp-uniform
+    const bool cached = walk && stage_row(cw, up, packed, jb, je, lane, rc);
+    const bool staged = walk && stage_common(cw, ei, szi, ej, szj, wij, lane, rc);
+    // k > j in upper(i) (the entries after m) that are in upper(j)
     for (int64_t a = ib + 1 + lane; a < ie; a += 32) {
       int32_t k, wik;
       up_entry(up, packed, a, k, wik);
-      ++n_ent;
-      int64_t l = jb, h = je;
-      while (l < h) {
-        const int64_t mid = (l + h) >> 1;
-        int32_t x, om;
-        up_entry(up, packed, mid, x, om);
-        ++n_ent;
-        if (x < k) l = mid + 1; else h = mid;
-      }
-      if (l >= je) continue;
-      int32_t x, wjk;
-      up_entry(up, packed, l, x, wjk);
-      ++n_ent;
-      if (x != k) continue;
-      const int64_t ek = g.e_ptr[k];
-      const int szk = (int)(g.e_ptr[k + 1] - ek);
-      const int gg = triple_common(g.e_idx + ei, szi, g.e_idx + ej, szj, g.e_idx + ek, szk);
-      n_vtx += (unsigned long long)(szi + szj + szk);
-      const int ra = szi - wij - wik + gg, rb = szj - wij - wjk + gg, rc = szk - wik - wjk + gg;
-      const int bits = (ra > 0) | ((rb > 0) << 1) | ((rc > 0) << 2) | ((wij > gg) << 3) |
-                       ((wjk > gg) << 4) | ((wik > gg) << 5) | ((gg > 0) << 6);
-      atomicAdd(&hist[w][lut[bits]], 1u);
+      ++rc.ent;
+      const int wjk = find_in_row(cw, cached, up, packed, jb, je, k, rc);
+      if (wjk < 0) continue;
+      const int32_t* ek = g.e_idx + g.e_ptr[k];
+      const int szk = g.esize[k];
+      const int gg = common3(cw, staged, wij, ei, szi, ej, szj, ek, szk, rc);
+      atomicAdd(&hist[w][lut[region_bits7(szi, szj, szk, wij, wik, wjk, gg)]], 1u);
     }
   }
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) {
-    n_ent += __shfl_down_sync(kFull, n_ent, d);
-    n_vtx += __shfl_down_sync(kFull, n_vtx, d);
-  }
-  if (lane == 0 && work) {
-    atomicAdd(&work[0], n_ptr);
-    atomicAdd(&work[1], n_ent);
-    atomicAdd(&work[2], n_vtx);
-  }
+  rc.flush(work, lane);
   __syncthreads();
   for (int k = threadIdx.x; k < 24; k += blockDim.x) {
     unsigned long long x = 0;
@@ -272,6 +429,7 @@ __constant__ int8_t c_class_of[24] = {-1, 0, 1, 1, 1, 1, 2, 2, 2, 3, 3, 3, 3,
 
 struct AdvSet {
   const int64_t* ptr;   // rows of the drawn type
+  RowIndex ix;          // bucket index of ptr
   Oriented ent;
   uint64_t Wx;          // hyperwedges of that type
   int type;             // 0 intersection, 1 inclusion
@@ -281,16 +439,19 @@ struct AdvSet {
 
 __device__ __forceinline__ int wedge_type(int om, int sa, int sb) { return om == min(sa, sb); }
 
-// One warp per draw of set `st`: the drawn (i, j), every k in N(i) cap N(j); the
-// triangle counts when its class is st.cls and (i, j) is its first hyperwedge of
-// type st.type in O.  raw[0..23] += per-pattern counts.
+// One warp per draw of set `st`: the drawn (i, j), every k in N(i) cap N(j) (the shorter
+// row walked, the longer searched); the triangle counts when its class is st.cls and
+// (i, j) is its first hyperwedge of type st.type in O.  raw[0..23] += per-pattern counts.
 __global__ void __launch_bounds__(kSampleWarps * 32)
     k_sample_adv(DevGraph g, AdvSet st, const int64_t* __restrict__ full_ptr, Oriented full,
                  int packed, uint64_t seed, uint64_t first, uint64_t num,
                  unsigned long long* __restrict__ raw) {
   __shared__ uint32_t hist[kSampleWarps][24];
   __shared__ uint8_t lut[128];
+  __shared__ WarpCache cache[kSampleWarps];
+  ReadCount rc;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  WarpCache& cw = cache[w];
   for (int k = threadIdx.x; k < 128; k += blockDim.x) lut[k] = c_sample_lut[k];
   for (int k = lane; k < 24; k += 32) hist[w][k] = 0;
   __syncthreads();
@@ -301,16 +462,12 @@ __global__ void __launch_bounds__(kSampleWarps * 32)
     philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
     const uint64_t r = ((uint64_t)c[1] << 32) | c[0];
     const uint64_t m = __umul64hi(r, st.Wx);
-    int32_t lo = 0, hi = g.ne - 1;   // row: last i with ptr[i] <= m
-    while (lo < hi) {
-      const int32_t mid = (lo + hi + 1) >> 1;
-      if (__ldg(st.ptr + mid) <= (int64_t)m) lo = mid; else hi = mid - 1;
-    }
-    const int32_t i = lo;
+    const int32_t i = row_of(st.ptr, g.ne, st.ix, m, lane, rc);
     int32_t j, wij;
     up_entry(st.ent, packed, (int64_t)m, j, wij);
-    const int64_t ei = g.e_ptr[i], ej = g.e_ptr[j];
-    const int szi = (int)(g.e_ptr[i + 1] - ei), szj = (int)(g.e_ptr[j + 1] - ej);
+    const int32_t* ei = g.e_idx + g.e_ptr[i];
+    const int32_t* ej = g.e_idx + g.e_ptr[j];
+    const int szi = g.esize[i], szj = g.esize[j];
     // walk the shorter neighbour row, search the longer one
     int64_t ab = __ldg(full_ptr + i), ae = __ldg(full_ptr + i + 1);
     int64_t bb = __ldg(full_ptr + j), be = __ldg(full_ptr + j + 1);
@@ -322,29 +479,21 @@ __global__ void __launch_bounds__(kSampleWarps * 32)
       bb = t0;
       be = t1;
     }
+    __syncwarp();
+    const bool cached = stage_row(cw, full, packed, bb, be, lane, rc);
+    const bool staged = stage_common(cw, ei, szi, ej, szj, wij, lane, rc);
     for (int64_t a = ab + lane; a < ae; a += 32) {
       int32_t k, wa;
       up_entry(full, packed, a, k, wa);
+      ++rc.ent;
       if (k == i || k == j) continue;
-      int64_t l = bb, h = be;
-      while (l < h) {
-        const int64_t mid = (l + h) >> 1;
-        int32_t x, om;
-        up_entry(full, packed, mid, x, om);
-        if (x < k) l = mid + 1; else h = mid;
-      }
-      if (l >= be) continue;
-      int32_t x, wb;
-      up_entry(full, packed, l, x, wb);
-      if (x != k) continue;
+      const int wb = find_in_row(cw, cached, full, packed, bb, be, k, rc);
+      if (wb < 0) continue;
       const int wik = swap ? wb : wa, wjk = swap ? wa : wb;
-      const int64_t ek = g.e_ptr[k];
-      const int szk = (int)(g.e_ptr[k + 1] - ek);
-      const int gg = triple_common(g.e_idx + ei, szi, g.e_idx + ej, szj, g.e_idx + ek, szk);
-      const int ra = szi - wij - wik + gg, rb = szj - wij - wjk + gg, rc = szk - wik - wjk + gg;
-      const int bits = (ra > 0) | ((rb > 0) << 1) | ((rc > 0) << 2) | ((wij > gg) << 3) |
-                       ((wjk > gg) << 4) | ((wik > gg) << 5) | ((gg > 0) << 6);
-      const int pat = lut[bits];
+      const int32_t* ek = g.e_idx + g.e_ptr[k];
+      const int szk = g.esize[k];
+      const int gg = common3(cw, staged, wij, ei, szi, ej, szj, ek, szk, rc);
+      const int pat = lut[region_bits7(szi, szj, szk, wij, wik, wjk, gg)];
       if (c_class_of[pat] != st.cls) continue;
       // the triangle's hyperwedges in O, (a,b) < (a,c) < (b,c) for a < b < c; the
       // first of the drawn type must be (i, j)
@@ -377,27 +526,30 @@ __global__ void __launch_bounds__(kSampleWarps * 32)
 // upper(i) and upper(j) closes the triangle i < j < k (each found once); those of pattern
 // `target` (0 = all) are appended to out as (i, j, k), while fewer than cap were written.
 __global__ void __launch_bounds__(kSampleWarps * 32)
-    k_enumerate(DevGraph g, const int64_t* __restrict__ up_ptr, Oriented up, int packed,
-                uint64_t W, int target, int32_t* __restrict__ out, unsigned long long cap,
-                unsigned long long* __restrict__ count) {
+    k_enumerate(DevGraph g, const int64_t* __restrict__ up_ptr, RowIndex ix, Oriented up,
+                int packed, uint64_t W, int target, int32_t* __restrict__ out,
+                unsigned long long cap, unsigned long long* __restrict__ count) {
   __shared__ uint8_t lut[128];
+  __shared__ WarpCache cache[kSampleWarps];
+  ReadCount rc;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  WarpCache& cw = cache[w];
   for (int k = threadIdx.x; k < 128; k += blockDim.x) lut[k] = c_sample_lut[k];
   __syncthreads();
   const uint64_t warps = (uint64_t)gridDim.x * kSampleWarps;
   for (uint64_t m = (uint64_t)blockIdx.x * kSampleWarps + w; m < W; m += warps) {
-    int32_t lo = 0, hi = g.ne - 1;
-    while (lo < hi) {
-      const int32_t mid = (lo + hi + 1) >> 1;
-      if (__ldg(up_ptr + mid) <= (int64_t)m) lo = mid; else hi = mid - 1;
-    }
-    const int32_t i = lo;
+    const int32_t i = row_of(up_ptr, g.ne, ix, m, lane, rc);
     const int64_t ie = __ldg(up_ptr + i + 1);
+    if ((int64_t)m + 1 >= ie) continue;   // nothing after (i, j) in upper(i)
     int32_t j, wij;
     up_entry(up, packed, (int64_t)m, j, wij);
     const int64_t jb = __ldg(up_ptr + j), je = __ldg(up_ptr + j + 1);
-    const int64_t ei = g.e_ptr[i], ej = g.e_ptr[j];
-    const int szi = (int)(g.e_ptr[i + 1] - ei), szj = (int)(g.e_ptr[j + 1] - ej);
+    const int32_t* ei = g.e_idx + g.e_ptr[i];
+    const int32_t* ej = g.e_idx + g.e_ptr[j];
+    const int szi = g.esize[i], szj = g.esize[j];
+    __syncwarp();
+    const bool cached = stage_row(cw, up, packed, jb, je, lane, rc);
+    const bool staged = stage_common(cw, ei, szi, ej, szj, wij, lane, rc);
     for (int64_t a0 = (int64_t)m + 1; a0 < ie; a0 += 32) {   // warp-uniform trip count
       const int64_t a = a0 + lane;
       bool hit = false;
@@ -405,26 +557,12 @@ __global__ void __launch_bounds__(kSampleWarps * 32)
       if (a < ie) {
         int32_t wik;
         up_entry(up, packed, a, k, wik);
-        int64_t l = jb, h = je;
-        while (l < h) {
-          const int64_t mid = (l + h) >> 1;
-          int32_t x, om;
-          up_entry(up, packed, mid, x, om);
-          if (x < k) l = mid + 1; else h = mid;
-        }
-        if (l < je) {
-          int32_t x, wjk;
-          up_entry(up, packed, l, x, wjk);
-          if (x == k) {
-            const int64_t ek = g.e_ptr[k];
-            const int szk = (int)(g.e_ptr[k + 1] - ek);
-            const int gg = triple_common(g.e_idx + ei, szi, g.e_idx + ej, szj, g.e_idx + ek, szk);
-            const int ra = szi - wij - wik + gg, rb = szj - wij - wjk + gg,
-                      rc = szk - wik - wjk + gg;
-            const int bits = (ra > 0) | ((rb > 0) << 1) | ((rc > 0) << 2) | ((wij > gg) << 3) |
-                             ((wjk > gg) << 4) | ((wik > gg) << 5) | ((gg > 0) << 6);
-            hit = target == 0 || lut[bits] == target;
-          }
+        const int wjk = find_in_row(cw, cached, up, packed, jb, je, k, rc);
+        if (wjk >= 0) {
+          const int32_t* ek = g.e_idx + g.e_ptr[k];
+          const int szk = g.esize[k];
+          const int gg = common3(cw, staged, wij, ei, szi, ej, szj, ek, szk, rc);
+          hit = target == 0 || lut[region_bits7(szi, szj, szk, wij, wik, wjk, gg)] == target;
         }
       }
       const unsigned bal = __ballot_sync(kFull, hit);
@@ -550,15 +688,43 @@ cudaError_t launch_sort_upper(const int64_t* up_ptr, int32_t ne, const Oriented&
   return cudaGetLastError();
 }
 
-void launch_sample(const DevGraph& g, const int64_t* up_ptr, const Oriented& up, int packed,
-                   uint64_t W, uint64_t seed, uint64_t first, uint64_t num,
-                   unsigned long long* raw, unsigned long long* work, cudaStream_t s, int nsm) {
+int row_index_shift(uint64_t entries, int32_t rows) {
+  int sh = 0;   // bucket of about entries / rows entries, at least 1
+  while (rows > 0 && (entries >> (sh + 1)) >= (uint64_t)rows) ++sh;
+  return sh;
+}
+
+int64_t row_index_buckets(uint64_t entries, int shift) {
+  return (int64_t)((entries + (uint64_t(1) << shift) - 1) >> shift);
+}
+
+void launch_row_index(const int64_t* ptr, int32_t ne, uint64_t entries, int32_t* first,
+                      cudaStream_t s) {
+  if (ne == 0) return;
+  const int sh = row_index_shift(entries, ne);
+  note_launch();
+  k_row_index<<<grid_n(ne, 256), 256, 0, s>>>(ptr, ne, sh, row_index_buckets(entries, sh), first);
+}
+
+static RowIndex make_index(const int32_t* first, uint64_t entries, int32_t ne) {
+  RowIndex ix{first, 0, 0};
+  if (first) {
+    ix.shift = row_index_shift(entries, ne);
+    ix.buckets = row_index_buckets(entries, ix.shift);
+  }
+  return ix;
+}
+
+void launch_sample(const DevGraph& g, const int64_t* up_ptr, const int32_t* up_index,
+                   const Oriented& up, int packed, uint64_t W, uint64_t seed, uint64_t first,
+                   uint64_t num, unsigned long long* raw, unsigned long long* work, cudaStream_t s,
+                   int nsm) {
   if (num == 0 || W == 0) return;
   uint64_t blocks = (num + kSampleWarps - 1) / kSampleWarps;
   if (blocks > (uint64_t)nsm * 16) blocks = (uint64_t)nsm * 16;
   note_launch();
-  k_sample<<<(unsigned)blocks, kSampleWarps * 32, 0, s>>>(g, up_ptr, up, packed, W, seed, first,
-                                                          num, raw, work);
+  k_sample<<<(unsigned)blocks, kSampleWarps * 32, 0, s>>>(
+      g, up_ptr, make_index(up_index, W, g.ne), up, packed, W, seed, first, num, raw, work);
 }
 
 void launch_type_counts(const int32_t* upc, const int32_t* wcr, int32_t ne, int32_t* cnt_t,
@@ -576,12 +742,13 @@ void launch_split_types(const DevGraph& g, const int64_t* up_ptr, const Oriented
   k_split_types<<<grid_n(g.ne, 8), 256, 0, s>>>(g, up_ptr, up, packed, t_ptr, t, c_ptr, c);
 }
 
-void launch_sample_adv(const DevGraph& g, const int64_t* set_ptr, const Oriented& set_ent,
-                       uint64_t Wx, int type, int cls, uint32_t stream, const int64_t* full_ptr,
-                       const Oriented& full, int packed, uint64_t seed, uint64_t first,
-                       uint64_t num, unsigned long long* raw, cudaStream_t s, int nsm) {
+void launch_sample_adv(const DevGraph& g, const int64_t* set_ptr, const int32_t* set_index,
+                       const Oriented& set_ent, uint64_t Wx, int type, int cls, uint32_t stream,
+                       const int64_t* full_ptr, const Oriented& full, int packed, uint64_t seed,
+                       uint64_t first, uint64_t num, unsigned long long* raw, cudaStream_t s,
+                       int nsm) {
   if (num == 0 || Wx == 0) return;
-  AdvSet st{set_ptr, set_ent, Wx, type, cls, stream};
+  AdvSet st{set_ptr, make_index(set_index, Wx, g.ne), set_ent, Wx, type, cls, stream};
   uint64_t blocks = (num + kSampleWarps - 1) / kSampleWarps;
   if (blocks > (uint64_t)nsm * 16) blocks = (uint64_t)nsm * 16;
   note_launch();
@@ -631,15 +798,15 @@ void launch_gather_rows(const int64_t* e_ptr, const int32_t* e_idx, const int32_
   k_gather_rows<<<grid_n(nk, 8), 256, 0, s>>>(e_ptr, e_idx, ids, nk, sub_ptr, sub_idx);
 }
 
-void launch_enumerate(const DevGraph& g, const int64_t* up_ptr, const Oriented& up, int packed,
-                      uint64_t W, int target, int32_t* out, unsigned long long cap,
-                      unsigned long long* count, cudaStream_t s, int nsm) {
+void launch_enumerate(const DevGraph& g, const int64_t* up_ptr, const int32_t* up_index,
+                      const Oriented& up, int packed, uint64_t W, int target, int32_t* out,
+                      unsigned long long cap, unsigned long long* count, cudaStream_t s, int nsm) {
   if (W == 0) return;
   uint64_t blocks = (W + kSampleWarps - 1) / kSampleWarps;
   if (blocks > (uint64_t)nsm * 16) blocks = (uint64_t)nsm * 16;
   note_launch();
-  k_enumerate<<<(unsigned)blocks, kSampleWarps * 32, 0, s>>>(g, up_ptr, up, packed, W, target, out,
-                                                              cap, count);
+  k_enumerate<<<(unsigned)blocks, kSampleWarps * 32, 0, s>>>(
+      g, up_ptr, make_index(up_index, W, g.ne), up, packed, W, target, out, cap, count);
 }
 
 }  // namespace hg
