@@ -88,7 +88,10 @@ typedef struct hg_tuning {
   int32_t close_mode;      /* step two team shape: 0 = by out-degree and |e_u| (warp
                               teams where they fit), 1 = block teams for every
                               hyperedge; counts do not depend on it */
-  int32_t reserved[5];
+  int32_t orient_exact;    /* 1 = oriented rows in an exact layout (W entries, one extra
+                              counting pass); 0 = room for deg(i) per row (2W entries)
+                              while that fits 8 GB.  Counts do not depend on it */
+  int32_t reserved[4];
 } hg_tuning;
 
 typedef struct hg_wedge_stats {

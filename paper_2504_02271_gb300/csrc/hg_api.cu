@@ -86,10 +86,10 @@ struct hg_graph {
   uint64_t two_w = 0;
   bool built = false;
   hg_wedge_stats stats{};
-  // what a later pass over the same hyperwedges needs (kept with build_blocks)
-  WedgeBuckets wb{};
-  int32_t nb[3] = {0, 0, 0};
-  unsigned long long* wscratch = nullptr;
+  // every row's (j, omega_ij) in the capacity layout, kept for the samplers' rows
+  int64_t* cap_ptr = nullptr;
+  Oriented cap_rows{};
+  int64_t* deg_ptr = nullptr;   // exclusive scan of deg (offsets of exact neighbour rows)
   DenseInfo dn{};
   int32_t* upc = nullptr;          // |{j > i : omega_ij > 0}| per row
   // sampling stage: rows of neighbours j > i sorted by j (order O of Sec. 2)
@@ -500,9 +500,12 @@ void release_sampling(hg_graph* g) {
   }
 }
 
+constexpr int64_t kOrientSlackBytes = int64_t(8) << 30;   // oriented rows with room for deg(i)
+
 hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   g->close_mode = opt ? opt->close_mode : 0;
   if (g->close_mode < 0 || g->close_mode > 1) return HG_ERR_INVALID_ARG;
+  if (opt && (opt->orient_exact < 0 || opt->orient_exact > 1)) return HG_ERR_INVALID_ARG;
   cudaStream_t s = g->stream;
   release(g, g->count_blocks);
   release_sampling(g);
@@ -510,18 +513,22 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   g->built = false;
   g->counted = false;
   const int64_t ne = g->ne;
+  const size_t ne1 = (size_t)std::max<int64_t>(ne, 1);
   g->packed = (ne < (int64_t(1) << 24) && g->max_size < 256) ? 1 : 0;
   Small h;
   HG_CUDA(cudaMemsetAsync(g->small, 0, sizeof(Small), s));
   g->deg = alloc_t<int32_t>(g, g->build_blocks, ne);
   int32_t* rows = alloc_t<int32_t>(g, g->build_blocks, 3 * ne);
+  int32_t* cap = alloc_t<int32_t>(g, g->build_blocks, ne);
+  g->cap_ptr = alloc_t<int64_t>(g, g->build_blocks, ne + 1);
+  g->deg_ptr = alloc_t<int64_t>(g, g->build_blocks, ne + 1);
   g->ori.row_ptr = alloc_t<int64_t>(g, g->build_blocks, ne + 1);
   g->ori.dplus = alloc_t<int32_t>(g, g->build_blocks, ne);
   g->upc = alloc_t<int32_t>(g, g->build_blocks, ne);
-  if (!g->deg || !rows || !g->ori.row_ptr || !g->ori.dplus || !g->upc) return HG_ERR_OOM;
   g->wcr = alloc_t<int32_t>(g, g->build_blocks, ne);
-  if (!g->wcr) return HG_ERR_OOM;
-  HG_CUDA(cudaMemsetAsync(g->wcr, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1), s));
+  if (!g->deg || !rows || !cap || !g->cap_ptr || !g->deg_ptr || !g->ori.row_ptr ||
+      !g->ori.dplus || !g->upc || !g->wcr)
+    return HG_ERR_OOM;
   g->mstats = nullptr;
   if (g->nm > 0) {
     g->mstats = alloc_t<unsigned long long>(g, g->build_blocks, 4 * (int64_t)g->nm);
@@ -531,6 +538,11 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   for (int k = 0; k < 3; ++k) wb.rows[k] = rows + k * ne;
   wb.count = g->small->bucket_count;
   launch_bucket_rows(g->cand, g->ne, wb, s);
+  // capacity layout of the gather pass: min(gathered incidences, |E| - 1) per row
+  launch_cap_rows(g->cand, g->ne, cap, s);
+  scan_i32_to_i64(cap, g->cap_ptr, ne, g->scan_tmp, s);
+  int64_t total_cap = 0;
+  HG_CUDA(cudaMemcpyAsync(&total_cap, g->cap_ptr + ne, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   HG_TRY(sync_small(g, &h));
   int32_t nb[3] = {h.bucket_count[0], h.bucket_count[1], h.bucket_count[2]};
   unsigned long long* scratch = nullptr;
@@ -539,39 +551,64 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
         dev_alloc(g, g->build_blocks, wedge_heavy_scratch_bytes(g->max_cand, g->nsm)));
     if (!scratch) return HG_ERR_OOM;
   }
+  g->cap_rows = Oriented{};
+  g->cap_rows.row_ptr = g->cap_ptr;
+  if (g->packed) {
+    g->cap_rows.packed = alloc_t<uint32_t>(g, g->build_blocks, total_cap);
+    if (!g->cap_rows.packed) return HG_ERR_OOM;
+  } else {
+    g->cap_rows.nbr = alloc_t<int32_t>(g, g->build_blocks, total_cap);
+    g->cap_rows.omega = alloc_t<int32_t>(g, g->build_blocks, total_cap);
+    if (!g->cap_rows.nbr || !g->cap_rows.omega) return HG_ERR_OOM;
+  }
   DevGraph d = dev_graph(g);
   DenseInfo dn{};
   HG_TRY(dense_impl(g, opt, &dn));
-  HG_CUDA(cudaMemsetAsync(g->deg, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1), s));
-  HG_CUDA(cudaMemsetAsync(g->ori.dplus, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1), s));
-  HG_CUDA(cudaMemsetAsync(g->upc, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(ne, 1), s));
+  HG_CUDA(cudaMemsetAsync(g->deg, 0, sizeof(int32_t) * ne1, s));
+  HG_CUDA(cudaMemsetAsync(g->upc, 0, sizeof(int32_t) * ne1, s));
+  HG_CUDA(cudaMemsetAsync(g->wcr, 0, sizeof(int32_t) * ne1, s));
   HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
-  t_begin(g, "wedge_count");
-  launch_wedge_pass(0, d, wb, nb, g->max_cand, g->deg, &g->small->wc, g->ori, g->packed, scratch,
-                    &g->small->err, g->small->counters, dn, RowCounts{g->upc, g->wcr}, s,
-                    g->nsm);
+  t_begin(g, "wedge_gather");
+  launch_wedge_rows(d, wb, nb, g->max_cand, g->deg, &g->small->wc, g->cap_rows, g->packed, scratch,
+                    &g->small->err, g->small->counters, dn, RowCounts{g->upc, g->wcr}, s, g->nsm);
   t_end(g);
-  t_begin(g, "wedge_scan");
-  scan_i32_to_i64(g->deg, g->ori.row_ptr, ne, g->scan_tmp, s);
+  // orientation by (deg, id).  Out-lists go to rows with room for deg(i) entries (offsets
+  // = the scan of deg, one filter pass) while 2W slots fit kOrientSlackBytes; beyond that
+  // to an exact layout (a counting pass, its scan, then the filter pass).
+  t_begin(g, "wedge_orient");
+  scan_i32_to_i64(g->deg, g->deg_ptr, ne, g->scan_tmp, s);
   reduce_deg_stats(g->deg, ne, g->small->deg_stats, s);
   t_end(g);
-  HG_TRY(sync_small(g, &h));
   int64_t two_w = 0;
-  HG_CUDA(cudaMemcpyAsync(&two_w, g->ori.row_ptr + ne, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  HG_CUDA(cudaStreamSynchronize(s));
+  HG_CUDA(cudaMemcpyAsync(&two_w, g->deg_ptr + ne, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  HG_TRY(sync_small(g, &h));
   g->two_w = (uint64_t)two_w;
+  const int64_t entry_bytes = g->packed ? 4 : 8;
+  const bool exact = (opt && opt->orient_exact) || two_w * entry_bytes > kOrientSlackBytes;
+  int64_t slots = two_w;
+  if (exact) {
+    t_begin(g, "wedge_orient");
+    launch_filter_rows(0, true, g->cap_ptr, g->deg, g->cap_rows, g->deg, g->ne, g->packed,
+                       nullptr, Oriented{}, g->ori.dplus, s);
+    scan_i32_to_i64(g->ori.dplus, g->ori.row_ptr, ne, g->scan_tmp, s);
+    t_end(g);
+    HG_CUDA(cudaMemcpyAsync(&slots, g->ori.row_ptr + ne, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    HG_CUDA(cudaStreamSynchronize(s));
+  } else {
+    HG_CUDA(cudaMemcpyAsync(g->ori.row_ptr, g->deg_ptr, sizeof(int64_t) * ((size_t)ne + 1),
+                            cudaMemcpyDeviceToDevice, s));
+  }
   if (g->packed) {
-    g->ori.packed = alloc_t<uint32_t>(g, g->build_blocks, two_w);
+    g->ori.packed = alloc_t<uint32_t>(g, g->build_blocks, slots);
     if (!g->ori.packed) return HG_ERR_OOM;
   } else {
-    g->ori.nbr = alloc_t<int32_t>(g, g->build_blocks, two_w);
-    g->ori.omega = alloc_t<int32_t>(g, g->build_blocks, two_w);
+    g->ori.nbr = alloc_t<int32_t>(g, g->build_blocks, slots);
+    g->ori.omega = alloc_t<int32_t>(g, g->build_blocks, slots);
     if (!g->ori.nbr || !g->ori.omega) return HG_ERR_OOM;
   }
-  HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
   t_begin(g, "wedge_emit");
-  launch_wedge_pass(1, d, wb, nb, g->max_cand, g->deg, &g->small->wc, g->ori, g->packed, scratch,
-                    &g->small->err, g->small->counters, dn, RowCounts{}, s, g->nsm);
+  launch_filter_rows(0, false, g->cap_ptr, g->deg, g->cap_rows, g->deg, g->ne, g->packed,
+                     g->ori.row_ptr, g->ori, exact ? nullptr : g->ori.dplus, s);
   reduce_deg_stats(g->ori.dplus, ne, g->small->out_stats, s);
   t_end(g);
   if (g->nm > 0) {
@@ -591,11 +628,9 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   st.max_deg = h.deg_stats[1];
   st.max_out_deg = h.out_stats[1];
   st.dense_edges = (uint64_t)dn.nh;
-  if (h.deg_stats[2] != (unsigned long long)two_w || h.out_stats[2] != st.W || (two_w & 1))
+  if (h.deg_stats[2] != (unsigned long long)two_w || h.out_stats[2] != st.W ||
+      (exact && (uint64_t)slots != st.W) || (two_w & 1) || two_w > total_cap)
     return HG_ERR_INTERNAL;
-  g->wb = wb;
-  for (int k = 0; k < 3; ++k) g->nb[k] = nb[k];
-  g->wscratch = scratch;
   g->dn = dn;
   g->built = true;
   if (out) *out = st;
@@ -625,12 +660,9 @@ hg_status upper_impl(hg_graph* g) {
     g->up.omega = alloc_t<int32_t>(g, g->sample_blocks, w);
     if (!g->up.nbr || !g->up.omega) return HG_ERR_OOM;
   }
-  DevGraph d = dev_graph(g);
-  HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
   t_begin(g, "upper_emit");
-  launch_wedge_pass(2, d, g->wb, g->nb, g->max_cand, g->deg, &g->small->wc, g->up, g->packed,
-                    g->wscratch, &g->small->err, g->small->counters, g->dn, RowCounts{}, s,
-                    g->nsm);
+  launch_filter_rows(1, false, g->cap_ptr, g->deg, g->cap_rows, g->deg, g->ne, g->packed,
+                     g->up_ptr, g->up, nullptr, s);
   t_end(g);
   t_begin(g, "upper_sort");
   HG_CUDA(launch_sort_upper(g->up_ptr, g->ne, g->up, g->packed, &g->small->err, s, g->nsm));
@@ -669,7 +701,7 @@ hg_status adv_impl(hg_graph* g) {
   g->t_ent = Oriented{};
   g->c_ent = Oriented{};
   g->full = Oriented{};
-  g->full.row_ptr = g->ori.row_ptr;
+  g->full.row_ptr = g->deg_ptr;
   if (g->packed) {
     g->t_ent.packed = alloc_t<uint32_t>(g, g->sample_blocks, wt);
     g->c_ent.packed = alloc_t<uint32_t>(g, g->sample_blocks, wc);
@@ -697,14 +729,12 @@ hg_status adv_impl(hg_graph* g) {
   if (!g->t_index || !g->c_index) return HG_ERR_OOM;
   launch_row_index(g->t_ptr, g->ne, g->Wt, g->t_index, s);
   launch_row_index(g->c_ptr, g->ne, g->Wc, g->c_index, s);
-  HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
   t_begin(g, "full_emit");
-  launch_wedge_pass(3, d, g->wb, g->nb, g->max_cand, g->deg, &g->small->wc, g->full, g->packed,
-                    g->wscratch, &g->small->err, g->small->counters, g->dn, RowCounts{}, s,
-                    g->nsm);
+  launch_filter_rows(2, false, g->cap_ptr, g->deg, g->cap_rows, g->deg, g->ne, g->packed,
+                     g->deg_ptr, g->full, nullptr, s);
   t_end(g);
   t_begin(g, "full_sort");
-  HG_CUDA(launch_sort_upper(g->ori.row_ptr, g->ne, g->full, g->packed, &g->small->err, s, g->nsm));
+  HG_CUDA(launch_sort_upper(g->deg_ptr, g->ne, g->full, g->packed, &g->small->err, s, g->nsm));
   t_end(g);
   Small h;
   HG_TRY(sync_small(g, &h));
@@ -838,7 +868,7 @@ hg_status sample_adv_impl(hg_graph* g, uint64_t seed, uint64_t first, uint64_t n
     t_begin(g, "sample_adv");
     launch_sample_adv(d, incl ? g->c_ptr : g->t_ptr, incl ? g->c_index : g->t_index,
                       incl ? g->c_ent : g->t_ent, Wx, kType[x], kClass[x], (uint32_t)(1 + x),
-                      g->ori.row_ptr, g->full, g->packed, seed, first, alpha[x], g->small->hist,
+                      g->deg_ptr, g->full, g->packed, seed, first, alpha[x], g->small->hist,
                       s, g->nsm);
     t_end(g);
     Small h;

@@ -119,15 +119,22 @@ struct RowCounts {
   int32_t* wcr;
 };
 
-// mode 0: count (deg, W_c, dup check, RowCounts); mode 1: emit the degree-oriented rows
-// at o.row_ptr (lengths into o.dplus); mode 2: emit the rows of neighbours j > i at
-// o.row_ptr (exact offsets from a scan of upc); mode 3: emit every neighbour at
-// o.row_ptr (exact offsets from a scan of deg)
-void launch_wedge_pass(int mode, const DevGraph& g, const WedgeBuckets& b, const int32_t* nb,
+// The gather pass of step one: deg(i), RowCounts, W_c into *wc, the duplicate check,
+// and every (j, omega_ij) of row i written from rows.row_ptr[i] (a capacity layout:
+// room for cap[i] = min(gathered incidences, |E| - 1) entries, see launch_cap_rows).
+void launch_wedge_rows(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb,
                        int64_t heavy_max_cand, int32_t* deg, unsigned long long* wc,
-                       const Oriented& o, int packed, unsigned long long* scratch,
-                       int* err, int32_t* work_counter, const DenseInfo& dense, RowCounts rc,
+                       const Oriented& rows, int packed, unsigned long long* scratch, int* err,
+                       int32_t* work_counter, const DenseInfo& dense, RowCounts rc,
                        cudaStream_t s, int nsm);
+void launch_cap_rows(const int64_t* cand, int32_t ne, int32_t* cap, cudaStream_t s);
+// Filter rows of the capacity layout (len[i] entries from src_ptr[i]) into an exact layout
+// (row i from dst_ptr[i]), order kept: keep 0 = j ranked above i in (deg, id), 1 = j > i,
+// 2 = all.  count_only: write the number kept to cnt[i] instead.
+void launch_filter_rows(int keep, bool count_only, const int64_t* src_ptr, const int32_t* len,
+                        const Oriented& src, const int32_t* deg, int32_t ne, int packed,
+                        const int64_t* dst_ptr, const Oriented& dst, int32_t* cnt,
+                        cudaStream_t s);
 
 // hg_api.cu: allocations of the calling thread skip the caller-installed hooks
 void alloc_bypass_hooks(bool on);

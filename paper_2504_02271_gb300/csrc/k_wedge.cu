@@ -4,17 +4,16 @@
 // For each hyperedge e_i the kernels gather, for every vertex v of e_i, the
 // hyperedges j != i of E_v, and accumulate omega_ij = |e_i cap e_j| (the number
 // of shared vertices, Def. 2.2) in a hash table keyed by j.  That is row i of
-// the sparse product H * H^T without its diagonal.  Two passes run over the same
-// accumulation:
-//   pass 0 (count): deg(i) = number of distinct j, the inclusion-type count
-//            W_c (omega_ij = min(|e_i|, |e_j|), Def. 2.3) and the duplicate-
-//            hyperedge check (omega_ij = |e_i| = |e_j|);
-//   pass 1 (emit):  after every deg(j) is known, keep only the j ranked above i
-//            in the order (deg, id) and write (j, omega_ij) into row i of the
-//            oriented line graph.
-// Algorithm 2 merges the sorted E_v lists one id at a time on a CPU; here the
-// accumulation is a hash table in shared memory (one warp per light row, one
-// block per medium row) or in global scratch (one block per heavy row).
+// the sparse product H * H^T without its diagonal.  One gather pass per row
+// yields deg(i) (the number of distinct j), the inclusion-type counts (omega_ij =
+// min(|e_i|, |e_j|), Def. 2.3), the duplicate-hyperedge check (omega_ij = |e_i| =
+// |e_j|), and writes every (j, omega_ij) of the row into a capacity layout (room
+// for min(gathered incidences, |E| - 1) entries per row).  Once every deg(j) is
+// known, a streaming row filter keeps the j ranked above i in the order (deg, id)
+// (the oriented line graph, exact layout), or the j > i (the sampler's rows), or
+// copies the row.  Algorithm 2 merges the sorted E_v lists one id at a time on a
+// CPU; here the accumulation is a hash table in shared memory (one warp per light
+// row, one block per medium row) or in global scratch (one block per heavy row).
 #include "hg_internal.cuh"
 
 namespace hg {
@@ -92,7 +91,7 @@ __device__ __forceinline__ void put_entry(const Oriented& o, int64_t at, uint32_
 }
 
 // One warp per row; the table lives in shared memory.
-template <int MODE, bool PACKED>
+template <bool PACKED>
 __global__ void __launch_bounds__(kLightWarps * 32)
     k_wedge_light(DevGraph g, const int32_t* __restrict__ rows, const int32_t* __restrict__ nrows_p,
                   int32_t* __restrict__ deg, unsigned long long* __restrict__ wc, Oriented o,
@@ -133,68 +132,49 @@ __global__ void __launch_bounds__(kLightWarps * 32)
     }
     __syncwarp();
     const int32_t szi = (int32_t)(e - b);
-    if (MODE == 0) {
-      int distinct = 0, up = 0, incl = 0;
-      for (int s = lane; s < CAP; s += 32) {
-        const unsigned long long x = T[s];
-        if (x == kEmpty) continue;
-        ++distinct;
-        const int32_t j = (int32_t)(x >> 32), om = (int32_t)(x & 0xffffffffu);
-        if (j > i) {
+    const int64_t base = o.row_ptr[i];
+    int written = 0, up = 0, incl = 0;
+    for (int s0 = 0; s0 < CAP; s0 += 32) {
+      const unsigned long long x = T[s0 + lane];
+      const bool valid = x != kEmpty;
+      uint32_t j = 0, om = 0;
+      if (valid) {
+        j = (uint32_t)(x >> 32);
+        om = (uint32_t)(x & 0xffffffffu);
+        if ((int32_t)j > i) {
           ++up;
           const int32_t szj = g.esize[j];
-          if (om == szi && om == szj) dev_fail(err, DE_DUPEDGE);
-          if (om == min(szi, szj)) ++incl;
+          if ((int32_t)om == szi && (int32_t)om == szj) dev_fail(err, DE_DUPEDGE);
+          if ((int32_t)om == min(szi, szj)) ++incl;
         }
       }
-      my_wc += (unsigned long long)incl;
+      const unsigned bal = __ballot_sync(kFull, valid);
+      if (valid) put_entry<PACKED>(o, base + written + __popc(bal & ((1u << lane) - 1u)), j, om);
+      written += __popc(bal);
+    }
+    my_wc += (unsigned long long)incl;
 #pragma unroll
-      for (int d = 16; d > 0; d >>= 1) {
-        distinct += __shfl_down_sync(kFull, distinct, d);
-        up += __shfl_down_sync(kFull, up, d);
-        incl += __shfl_down_sync(kFull, incl, d);
-      }
-      if (lane == 0) {
-        deg[i] = distinct;
-        if (rc.upc) rc.upc[i] = up;
-        if (rc.wcr) rc.wcr[i] = incl;
-      }
-    } else {
-      // MODE 1: the out-list of the degree orientation; MODE 2: the neighbours j > i;
-      // MODE 3: every neighbour
-      const int32_t di = MODE == 1 ? deg[i] : 0;
-      const int64_t base = o.row_ptr[i];
-      int32_t written = 0;
-      for (int s0 = 0; s0 < CAP; s0 += 32) {
-        const unsigned long long x = T[s0 + lane];
-        bool emit = false;
-        uint32_t j = 0, om = 0;
-        if (x != kEmpty) {
-          j = (uint32_t)(x >> 32);
-          om = (uint32_t)(x & 0xffffffffu);
-          emit = MODE == 1 ? ranked_above(di, i, deg[j], (int32_t)j)
-                           : (MODE == 2 ? (int32_t)j > i : true);
-        }
-        const unsigned bal = __ballot_sync(kFull, emit);
-        if (emit) put_entry<PACKED>(o, base + written + __popc(bal & ((1u << lane) - 1u)), j, om);
-        written += __popc(bal);
-      }
-      if (lane == 0 && MODE == 1) o.dplus[i] = written;
+    for (int d = 16; d > 0; d >>= 1) {
+      up += __shfl_down_sync(kFull, up, d);
+      incl += __shfl_down_sync(kFull, incl, d);
+    }
+    if (lane == 0) {
+      deg[i] = written;
+      if (rc.upc) rc.upc[i] = up;
+      if (rc.wcr) rc.wcr[i] = incl;
     }
     __syncwarp();
   }
-  if (MODE == 0) {
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) my_wc += __shfl_down_sync(kFull, my_wc, d);
-    if (lane == 0) atomicAdd(&blk_wc, my_wc);
-    __syncthreads();
-    if (threadIdx.x == 0 && blk_wc) atomicAdd(wc, blk_wc);
-  }
+  for (int d = 16; d > 0; d >>= 1) my_wc += __shfl_down_sync(kFull, my_wc, d);
+  if (lane == 0) atomicAdd(&blk_wc, my_wc);
+  __syncthreads();
+  if (threadIdx.x == 0 && blk_wc) atomicAdd(wc, blk_wc);
 }
 
 // One block per row; the table is in dynamic shared memory (SMEM) or in a
 // per-block slice of global scratch.
-template <int MODE, bool PACKED, bool SMEM>
+template <bool PACKED, bool SMEM>
 __global__ void __launch_bounds__(kBlockThreads)
     k_wedge_block(DevGraph g, const int32_t* __restrict__ rows, const int32_t* __restrict__ nrows_p,
                   int cap_log2, unsigned long long* __restrict__ gscratch,
@@ -244,63 +224,97 @@ __global__ void __launch_bounds__(kBlockThreads)
     }
     __syncthreads();
     const int32_t szi = (int32_t)(e - b);
-    if (MODE == 0) {
-      int distinct = 0, up = 0, incl = 0;
-      for (uint32_t s = threadIdx.x; s < CAP; s += kBlockThreads) {
-        const unsigned long long x = T[s];
-        if (x == kEmpty) continue;
-        ++distinct;
-        const int32_t j = (int32_t)(x >> 32), om = (int32_t)(x & 0xffffffffu);
-        if (j > i) {
-          ++up;
-          const int32_t szj = g.esize[j];
-          if (om == szi && om == szj) dev_fail(err, DE_DUPEDGE);
-          if (om == min(szi, szj)) ++incl;
-        }
+    const int64_t base = o.row_ptr[i];
+    int up = 0, incl = 0;
+    for (uint32_t s = threadIdx.x; s < CAP; s += kBlockThreads) {
+      const unsigned long long x = T[s];
+      if (x == kEmpty) continue;
+      const uint32_t j = (uint32_t)(x >> 32), om = (uint32_t)(x & 0xffffffffu);
+      if ((int32_t)j > i) {
+        ++up;
+        const int32_t szj = g.esize[j];
+        if ((int32_t)om == szi && (int32_t)om == szj) dev_fail(err, DE_DUPEDGE);
+        if ((int32_t)om == min(szi, szj)) ++incl;
       }
-      my_wc += (unsigned long long)incl;
+      put_entry<PACKED>(o, base + atomicAdd(&s_cnt, 1), j, om);
+    }
+    my_wc += (unsigned long long)incl;
 #pragma unroll
-      for (int d = 16; d > 0; d >>= 1) {
-        distinct += __shfl_down_sync(kFull, distinct, d);
-        up += __shfl_down_sync(kFull, up, d);
-        incl += __shfl_down_sync(kFull, incl, d);
-      }
-      if (lane == 0) {
-        atomicAdd(&s_cnt, distinct);
-        atomicAdd(&s_up, up);
-        atomicAdd(&s_incl, incl);
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        deg[i] = s_cnt;
-        if (rc.upc) rc.upc[i] = s_up;
-        if (rc.wcr) rc.wcr[i] = s_incl;
-      }
-    } else {
-      // MODE 1: the out-list of the degree orientation; MODE 2: the neighbours j > i;
-      // MODE 3: every neighbour
-      const int32_t di = MODE == 1 ? deg[i] : 0;
-      const int64_t base = o.row_ptr[i];
-      for (uint32_t s = threadIdx.x; s < CAP; s += kBlockThreads) {
-        const unsigned long long x = T[s];
-        if (x == kEmpty) continue;
-        const uint32_t j = (uint32_t)(x >> 32), om = (uint32_t)(x & 0xffffffffu);
-        if (MODE == 1 ? ranked_above(di, i, deg[j], (int32_t)j)
-                      : (MODE == 2 ? (int32_t)j > i : true)) {
-          const int32_t pos = atomicAdd(&s_cnt, 1);
-          put_entry<PACKED>(o, base + pos, j, om);
-        }
-      }
-      __syncthreads();
-      if (threadIdx.x == 0 && MODE == 1) o.dplus[i] = s_cnt;
+    for (int d = 16; d > 0; d >>= 1) {
+      up += __shfl_down_sync(kFull, up, d);
+      incl += __shfl_down_sync(kFull, incl, d);
+    }
+    if (lane == 0) {
+      atomicAdd(&s_up, up);
+      atomicAdd(&s_incl, incl);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      deg[i] = s_cnt;
+      if (rc.upc) rc.upc[i] = s_up;
+      if (rc.wcr) rc.wcr[i] = s_incl;
     }
   }
-  if (MODE == 0) {
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) my_wc += __shfl_down_sync(kFull, my_wc, d);
-    if (lane == 0) atomicAdd(&s_wc, my_wc);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_wc) atomicAdd(wc, s_wc);
+  for (int d = 16; d > 0; d >>= 1) my_wc += __shfl_down_sync(kFull, my_wc, d);
+  if (lane == 0) atomicAdd(&s_wc, my_wc);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_wc) atomicAdd(wc, s_wc);
+}
+
+// Row capacity of the gather pass: min(gathered incidences, |E| - 1) distinct neighbours.
+__global__ void k_cap_rows(const int64_t* __restrict__ cand, int32_t ne, int32_t* __restrict__ cap) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = cand[i];
+    cap[i] = (int32_t)(c < (int64_t)ne - 1 ? c : (int64_t)ne - 1);
+  }
+}
+
+template <bool PACKED>
+__device__ __forceinline__ void get_row_entry(const Oriented& o, int64_t at, uint32_t& j,
+                                              uint32_t& om) {
+  if (PACKED) {
+    const uint32_t x = o.packed[at];
+    j = x >> 8;
+    om = x & 0xffu;
+  } else {
+    j = (uint32_t)o.nbr[at];
+    om = (uint32_t)o.omega[at];
+  }
+}
+
+// One warp per row: row i of the capacity layout (len[i] entries from src_ptr[i]) filtered
+// into row i of an exact layout (from dst_ptr[i]), order kept.  KEEP 0: j ranked above i in
+// (deg, id) (the oriented line graph); 1: j > i; 2: every entry.  COUNT: only the number
+// kept, into cnt[i]; otherwise the rows, and the number kept into cnt[i] when cnt is set.
+template <int KEEP, bool PACKED, bool COUNT>
+__global__ void k_filter_rows(const int64_t* __restrict__ src_ptr, const int32_t* __restrict__ len,
+                              Oriented src, const int32_t* __restrict__ deg, int32_t ne,
+                              const int64_t* __restrict__ dst_ptr, Oriented dst,
+                              int32_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += warps) {
+    const int64_t b = src_ptr[i];
+    const int32_t n = len[i];
+    const int32_t di = KEEP == 0 ? deg[i] : 0;
+    const int64_t out = COUNT ? 0 : dst_ptr[i];
+    int32_t kept = 0;
+    for (int32_t t0 = 0; t0 < n; t0 += 32) {
+      const int32_t t = t0 + lane;
+      bool keep = false;
+      uint32_t j = 0, om = 0;
+      if (t < n) {
+        get_row_entry<PACKED>(src, b + t, j, om);
+        keep = KEEP == 0 ? ranked_above(di, i, deg[j], (int32_t)j)
+                         : (KEEP == 1 ? (int32_t)j > i : true);
+      }
+      const unsigned bal = __ballot_sync(kFull, keep);
+      if (!COUNT && keep) put_entry<PACKED>(dst, out + kept + __popc(bal & ((1u << lane) - 1u)), j, om);
+      kept += __popc(bal);
+    }
+    if (lane == 0 && cnt) cnt[i] = kept;
   }
 }
 
@@ -335,7 +349,7 @@ int cap_log2_for(int64_t cand) {
   return l;
 }
 
-template <int MODE, bool PACKED>
+template <bool PACKED>
 void launch_all(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb, int64_t heavy_max,
                 int32_t* deg, unsigned long long* wc, const Oriented& o,
                 unsigned long long* scratch, int* err, int32_t* counters, const DenseInfo& dn,
@@ -345,27 +359,46 @@ void launch_all(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb, int
     int blocks = (nb[0] + kLightWarps - 1) / kLightWarps;
     blocks = blocks < nsm * 4 ? blocks : nsm * 4;
     note_launch();
-    k_wedge_light<MODE, PACKED><<<blocks, kLightWarps * 32, 0, s>>>(g, b.rows[0], b.count + 0, deg,
-                                                                    wc, o, err, counters + 0, dn,
-                                                                    rc);
+    k_wedge_light<PACKED><<<blocks, kLightWarps * 32, 0, s>>>(g, b.rows[0], b.count + 0, deg, wc,
+                                                              o, err, counters + 0, dn, rc);
   }
   if (nb[1] > 0) {
     const size_t smem = sizeof(unsigned long long) << kMediumCapLog2;
-    cudaFuncSetAttribute(k_wedge_block<MODE, PACKED, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_wedge_block<PACKED, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     int blocks = nb[1] < nsm * 3 ? nb[1] : nsm * 3;
     note_launch();
-    k_wedge_block<MODE, PACKED, true><<<blocks, kBlockThreads, smem, s>>>(
+    k_wedge_block<PACKED, true><<<blocks, kBlockThreads, smem, s>>>(
         g, b.rows[1], b.count + 1, kMediumCapLog2, nullptr, deg, wc, o, err, counters + 1, dn,
         rc);
   }
   if (nb[2] > 0) {
     int blocks = nb[2] < nsm * 2 ? nb[2] : nsm * 2;
     note_launch();
-    k_wedge_block<MODE, PACKED, false><<<blocks, kBlockThreads, 0, s>>>(
+    k_wedge_block<PACKED, false><<<blocks, kBlockThreads, 0, s>>>(
         g, b.rows[2], b.count + 2, cap_log2_for(heavy_max), scratch, deg, wc, o, err,
         counters + 2, dn, rc);
   }
+}
+
+int grid_rows(int64_t rows, int per_block) {
+  int64_t b = (rows + per_block - 1) / per_block;
+  if (b > 65535) b = 65535;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+template <int KEEP, bool PACKED>
+void launch_filter_t(bool count_only, const int64_t* src_ptr, const int32_t* len,
+                     const Oriented& src, const int32_t* deg, int32_t ne, const int64_t* dst_ptr,
+                     const Oriented& dst, int32_t* cnt, cudaStream_t s) {
+  note_launch();
+  if (count_only)
+    k_filter_rows<KEEP, PACKED, true><<<grid_rows(ne, 8), 256, 0, s>>>(src_ptr, len, src, deg, ne,
+                                                                        dst_ptr, dst, cnt);
+  else
+    k_filter_rows<KEEP, PACKED, false><<<grid_rows(ne, 8), 256, 0, s>>>(src_ptr, len, src, deg,
+                                                                         ne, dst_ptr, dst, cnt);
 }
 
 }  // namespace
@@ -387,28 +420,43 @@ void launch_bucket_rows(const int64_t* cand, int32_t ne, WedgeBuckets b, cudaStr
                                                  wedge_medium_max_cand());
 }
 
-void launch_wedge_pass(int mode, const DevGraph& g, const WedgeBuckets& b, const int32_t* nb,
+void launch_wedge_rows(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb,
                        int64_t heavy_max_cand, int32_t* deg, unsigned long long* wc,
-                       const Oriented& o, int packed, unsigned long long* scratch, int* err,
+                       const Oriented& rows, int packed, unsigned long long* scratch, int* err,
                        int32_t* work_counter, const DenseInfo& dn, RowCounts rc, cudaStream_t s,
                        int nsm) {
-#define HG_WEDGE_PASS(M)                                                                        \
-  if (packed)                                                                                  \
-    launch_all<M, true>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, dn, \
-                        rc, s, nsm);                                                           \
-  else                                                                                         \
-    launch_all<M, false>(g, b, nb, heavy_max_cand, deg, wc, o, scratch, err, work_counter, dn, \
-                         rc, s, nsm);
-  if (mode == 0) {
-    HG_WEDGE_PASS(0)
-  } else if (mode == 1) {
-    HG_WEDGE_PASS(1)
-  } else if (mode == 2) {
-    HG_WEDGE_PASS(2)
+  if (packed)
+    launch_all<true>(g, b, nb, heavy_max_cand, deg, wc, rows, scratch, err, work_counter, dn, rc,
+                     s, nsm);
+  else
+    launch_all<false>(g, b, nb, heavy_max_cand, deg, wc, rows, scratch, err, work_counter, dn, rc,
+                      s, nsm);
+}
+
+void launch_cap_rows(const int64_t* cand, int32_t ne, int32_t* cap, cudaStream_t s) {
+  if (ne == 0) return;
+  note_launch();
+  k_cap_rows<<<grid_rows(ne, 256), 256, 0, s>>>(cand, ne, cap);
+}
+
+void launch_filter_rows(int keep, bool count_only, const int64_t* src_ptr, const int32_t* len,
+                        const Oriented& src, const int32_t* deg, int32_t ne, int packed,
+                        const int64_t* dst_ptr, const Oriented& dst, int32_t* cnt,
+                        cudaStream_t s) {
+  if (ne == 0) return;
+#define HG_FILTER(K)                                                                        \
+  if (packed)                                                                              \
+    launch_filter_t<K, true>(count_only, src_ptr, len, src, deg, ne, dst_ptr, dst, cnt, s); \
+  else                                                                                     \
+    launch_filter_t<K, false>(count_only, src_ptr, len, src, deg, ne, dst_ptr, dst, cnt, s);
+  if (keep == 0) {
+    HG_FILTER(0)
+  } else if (keep == 1) {
+    HG_FILTER(1)
   } else {
-    HG_WEDGE_PASS(3)
+    HG_FILTER(2)
   }
-#undef HG_WEDGE_PASS
+#undef HG_FILTER
 }
 
 }  // namespace hg

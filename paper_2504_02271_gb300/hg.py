@@ -47,7 +47,8 @@ class HgError(RuntimeError):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("dense_min_size", ctypes.c_int32), ("dense_max_count", ctypes.c_int32),
-                ("close_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("close_mode", ctypes.c_int32), ("orient_exact", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class _WedgeStats(ctypes.Structure):
@@ -263,9 +264,9 @@ def hg_load_csr(num_vertices: int, num_edges: int, edge_ptr, edge_vtx, stream: i
 
 
 def hg_build_wedges(g: Graph, dense_min_size: int = 0, dense_max_count: int = 0,
-                    close_mode: int = 0) -> dict:
+                    close_mode: int = 0, orient_exact: int = 0) -> dict:
     """Step one: hyperwedges, their types and the degree orientation; returns the stats."""
-    tun = _Tuning(int(dense_min_size), int(dense_max_count), int(close_mode))
+    tun = _Tuning(int(dense_min_size), int(dense_max_count), int(close_mode), int(orient_exact))
     st = _WedgeStats()
     _check("hg_build_wedges",
            _lib.hg_build_wedges(ctypes.c_void_p(g.ptr), ctypes.byref(tun), ctypes.byref(st)))
@@ -475,8 +476,8 @@ def hg_load_batch(num_vertices, edge_off, edge_ptr, edge_vtx, max_wave_edges: in
 
 
 def hg_batch_build_wedges(b: Batch, dense_min_size: int = 0, dense_max_count: int = 0,
-                          close_mode: int = 0) -> None:
-    tun = _Tuning(int(dense_min_size), int(dense_max_count), int(close_mode))
+                          close_mode: int = 0, orient_exact: int = 0) -> None:
+    tun = _Tuning(int(dense_min_size), int(dense_max_count), int(close_mode), int(orient_exact))
     _check("hg_batch_build_wedges", _lib.hg_batch_build_wedges(ctypes.c_void_p(b.ptr),
                                                                ctypes.byref(tun)))
 

@@ -122,6 +122,21 @@ def test_workload_golden(hglib, name):
         assert st[k] == gold[k], k
 
 
+@pytest.mark.parametrize("name", ["tiny_plain", "coauthor_prefix50k", "tag_heavy_prefix2000"])
+def test_counts_do_not_depend_on_the_oriented_layout(hglib, name):
+    # oriented rows in the exact layout (W entries) or with room for deg(i) (2W)
+    import hgen
+
+    gold = load_json("workloads.json")[name]
+    e_ptr, e_idx = hgen.generate(hgen.WORKLOADS[gold["workload"]])
+    if gold["prefix_edges"] is not None:
+        e_ptr, e_idx = hgen.prefix(e_ptr, e_idx, gold["prefix_edges"])
+    counts, st = gpu_count(hglib, gold["num_vertices"], e_ptr, e_idx, orient_exact=1)
+    assert counts.tolist() == gold["counts"]
+    assert (st["W"], st["W_c"], st["connected"], st["open"]) == \
+        (gold["W"], gold["W_c"], gold["connected"], gold["open"])
+
+
 @pytest.mark.parametrize("name", ["tiny_plain", "coauthor_prefix50k"])
 def test_counts_do_not_depend_on_team_shape(hglib, name):
     # every hyperedge through the block kernel gives the same counts as the
