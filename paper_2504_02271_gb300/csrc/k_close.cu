@@ -743,44 +743,88 @@ __global__ void __launch_bounds__(kWideThreads)
 
 constexpr int kWarpMaskBits = 32;   // warp tables keep Omega_ux in one 32-bit word
 
-__global__ void k_bucket_close(DevGraph g, Oriented o, CloseBuckets b,
-                               unsigned long long* __restrict__ wide_max, bool all_block) {
+// Team shape of u (bucket index, -1 when u closes nothing).
+__device__ __forceinline__ int close_bucket_of(int32_t d, int32_t sz, bool all_block) {
+  if (d < 2) return -1;
+  if (all_block) return kWideBucket;
+  if (sz <= kWarpMaskBits && d <= 64) return 0;
+  if (sz <= kWarpMaskBits && d <= 128) return 1;
+  if (sz <= kWarpMaskBits && d <= 256) return 2;
+  if (sz <= kWarpMaskBits && d <= 1024) return 3;
+  if (sz <= kWarpMaskBits && d <= 4096) return 4;
+  return kWideBucket;
+}
+
+// Each block takes a contiguous range of kBucketRowsPerBlock hyperedges: it counts
+// them per bucket in shared memory, reserves its slice of every list with one global
+// atomic per bucket, then writes the hyperedges into the slices.  The largest
+// out-degree and size of the wide bucket are reduced per warp before their atomics.
+constexpr int kBucketThreads = 256;
+constexpr int kBucketRowsPerThread = 8;
+constexpr int kBucketRowsPerBlock = kBucketThreads * kBucketRowsPerThread;
+
+__global__ void __launch_bounds__(kBucketThreads)
+    k_bucket_close(DevGraph g, Oriented o, CloseBuckets b,
+                   unsigned long long* __restrict__ wide_max, bool all_block) {
+  __shared__ int32_t s_cnt[kCloseBuckets], s_base[kCloseBuckets];
   const int lane = threadIdx.x & 31;
   unsigned long long my_d = 0, my_s = 0;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < g.ne;
-       base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t u = base + threadIdx.x;
-    int bucket = -1;
-    if (u < g.ne) {
-      const int32_t d = o.dplus[u];
-      const int32_t sz = g.esize[u];
-      if (d >= 2) {
-        if (all_block) bucket = kWideBucket;
-        else if (sz <= kWarpMaskBits && d <= 64) bucket = 0;
-        else if (sz <= kWarpMaskBits && d <= 128) bucket = 1;
-        else if (sz <= kWarpMaskBits && d <= 256) bucket = 2;
-        else if (sz <= kWarpMaskBits && d <= 1024) bucket = 3;
-        else if (sz <= kWarpMaskBits && d <= 4096) bucket = 4;
-        else bucket = kWideBucket;
-        if (bucket == kWideBucket) {
+  for (int64_t r0 = (int64_t)blockIdx.x * kBucketRowsPerBlock; r0 < g.ne;
+       r0 += (int64_t)gridDim.x * kBucketRowsPerBlock) {
+    if (threadIdx.x < kCloseBuckets) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int bk[kBucketRowsPerThread];
+#pragma unroll
+    for (int q = 0; q < kBucketRowsPerThread; ++q) {   // rows r0 + q * 256 + thread
+      const int64_t u = r0 + (int64_t)q * kBucketThreads + threadIdx.x;
+      bk[q] = -1;
+      if (u < g.ne) {
+        const int32_t d = o.dplus[u], sz = g.esize[u];
+        bk[q] = close_bucket_of(d, sz, all_block);
+        if (bk[q] == kWideBucket) {
           my_d = (unsigned long long)d > my_d ? (unsigned long long)d : my_d;
           my_s = (unsigned long long)sz > my_s ? (unsigned long long)sz : my_s;
         }
       }
-    }
 #pragma unroll
-    for (int k = 0; k < kCloseBuckets; ++k) {
-      const unsigned bal = __ballot_sync(kFull, bucket == k);
-      if (!bal) continue;
-      int32_t at = 0;
-      const int leader = __ffs(bal) - 1;
-      if (lane == leader) at = atomicAdd(&b.count[k], __popc(bal));
-      at = __shfl_sync(kFull, at, leader);
-      if (bucket == k) b.lists[k][at + __popc(bal & ((1u << lane) - 1u))] = (int32_t)u;
+      for (int k = 0; k < kCloseBuckets; ++k) {
+        const unsigned bal = __ballot_sync(kFull, bk[q] == k);
+        if (bal && lane == 0) atomicAdd(&s_cnt[k], __popc(bal));
+      }
     }
+    __syncthreads();
+    if (threadIdx.x < kCloseBuckets) {
+      const int32_t n = s_cnt[threadIdx.x];
+      s_base[threadIdx.x] = n ? atomicAdd(&b.count[threadIdx.x], n) : 0;
+      s_cnt[threadIdx.x] = 0;   // reused as the running offset
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kBucketRowsPerThread; ++q) {
+      const int64_t u = r0 + (int64_t)q * kBucketThreads + threadIdx.x;
+#pragma unroll
+      for (int k = 0; k < kCloseBuckets; ++k) {
+        const unsigned bal = __ballot_sync(kFull, bk[q] == k);
+        if (!bal) continue;
+        int at = 0;
+        if (lane == 0) at = atomicAdd(&s_cnt[k], __popc(bal));
+        at = __shfl_sync(kFull, at, 0);
+        if (bk[q] == k) b.lists[k][s_base[k] + at + __popc(bal & ((1u << lane) - 1u))] = (int32_t)u;
+      }
+    }
+    __syncthreads();
   }
-  atomicMax(&wide_max[0], my_d);
-  atomicMax(&wide_max[1], my_s);
+#pragma unroll
+  for (int dd = 16; dd > 0; dd >>= 1) {
+    const unsigned long long od = __shfl_down_sync(kFull, my_d, dd);
+    const unsigned long long os = __shfl_down_sync(kFull, my_s, dd);
+    my_d = od > my_d ? od : my_d;
+    my_s = os > my_s ? os : my_s;
+  }
+  if (lane == 0 && (my_d | my_s)) {
+    atomicMax(&wide_max[0], my_d);
+    atomicMax(&wide_max[1], my_s);
+  }
 }
 
 template <int D_LOG2, int WARPS, bool PACKED>
@@ -859,10 +903,10 @@ void close_set_lut(const uint8_t lut[128], cudaStream_t s) {
 void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,
                          unsigned long long* wide_max, bool all_block, cudaStream_t s) {
   if (g.ne == 0) return;
-  int64_t blocks = (g.ne + 255) / 256;
+  int64_t blocks = (g.ne + kBucketRowsPerBlock - 1) / kBucketRowsPerBlock;
   if (blocks > 4096) blocks = 4096;
   note_launch();
-  k_bucket_close<<<(unsigned)blocks, 256, 0, s>>>(g, o, b, wide_max, all_block);
+  k_bucket_close<<<(unsigned)blocks, kBucketThreads, 0, s>>>(g, o, b, wide_max, all_block);
 }
 
 size_t close_wide_scratch_bytes(int64_t cap, int64_t words, int64_t dmax, int nsm) {
