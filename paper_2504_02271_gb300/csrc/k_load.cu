@@ -66,28 +66,35 @@ __global__ void k_scatter(DevGraph g, int32_t* __restrict__ cursor, int32_t* __r
   }
 }
 
-// cand[i] = sum_{v in e_i} (|E_v| - 1): how many (j, v) incidences row i gathers.
+// cand[i] = sum_{v in e_i} (|E_v| - 1): how many (j, v) incidences row i gathers.  One
+// thread per row (rows are short); maxima reduced per warp before their atomics.
 __global__ void k_candidates(DevGraph g, int64_t* __restrict__ cand,
                              unsigned long long* __restrict__ max_cand,
                              int32_t* __restrict__ max_size) {
   const int lane = threadIdx.x & 31;
-  const int warps = (gridDim.x * blockDim.x) >> 5;
   unsigned long long my_max = 0;
   int32_t my_size = 0;
-  for (int32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < g.ne; i += warps) {
-    const int64_t b = g.e_ptr[i], e = g.e_ptr[i + 1];
-    int64_t c = 0;
-    for (int64_t p = b + lane; p < e; p += 32) {
-      const int32_t v = g.e_idx[p];
-      c += g.v_ptr[v + 1] - g.v_ptr[v] - 1;
-    }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(0xffffffffu, c, d);
-    if (lane == 0) {
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < g.ne;
+       i0 += (int64_t)gridDim.x * blockDim.x) {   // warp-uniform trip count
+    const int64_t i = i0 + threadIdx.x;
+    if (i < g.ne) {
+      const int64_t b = g.e_ptr[i], e = g.e_ptr[i + 1];
+      int64_t c = 0;
+      for (int64_t p = b; p < e; ++p) {
+        const int32_t v = g.e_idx[p];
+        c += g.v_ptr[v + 1] - g.v_ptr[v] - 1;
+      }
       cand[i] = c;
       my_max = (unsigned long long)c > my_max ? (unsigned long long)c : my_max;
       my_size = (int32_t)(e - b) > my_size ? (int32_t)(e - b) : my_size;
     }
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const unsigned long long om = __shfl_down_sync(0xffffffffu, my_max, d);
+    const int32_t os = __shfl_down_sync(0xffffffffu, my_size, d);
+    my_max = om > my_max ? om : my_max;
+    my_size = os > my_size ? os : my_size;
   }
   if (lane == 0) {
     atomicMax(max_cand, my_max);
@@ -126,7 +133,7 @@ void launch_candidates(const DevGraph& g, int64_t* cand, unsigned long long* max
                        int32_t* max_size, cudaStream_t s) {
   if (g.ne == 0) return;
   note_launch();
-  k_candidates<<<grid_for(g.ne, 8), 256, 0, s>>>(g, cand, max_cand, max_size);
+  k_candidates<<<grid_for(g.ne, 256), 256, 0, s>>>(g, cand, max_cand, max_size);
 }
 
 }  // namespace hg
