@@ -175,8 +175,11 @@ def source_sha(path):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def profiled_traffic(kernel, workload_name):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+def profiled_traffic(kernel, workload_name, units=None):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged.
+
+    Entries captured on a smaller launch store bytes per unit (`dram_bytes_per_sample`);
+    they are scaled by the `units` of the measured launch."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
@@ -189,6 +192,8 @@ def profiled_traffic(kernel, workload_name):
     src = os.path.join(ROOT, "paper_2504_02271_gb300", "csrc", e["source"])
     if not os.path.exists(src) or source_sha(src) != e["source_sha"]:
         return None
+    if "dram_bytes_per_sample" in e:
+        return None if units is None else round(float(e["dram_bytes_per_sample"]) * units)
     return float(e["dram_bytes_per_launch"])
 
 
@@ -731,7 +736,7 @@ def run_sample(args):
     roof = {"bound": "hbm", "kernel": "sample (k_sample)", "achieved": round(nbytes / s_ms / 1e6, 1),
             "peak": peak_hbm, "unit": "GB/s", "frac": round(nbytes / s_ms / 1e6 / peak_hbm, 4),
             "peak_source": peak_kind, "algorithmic_bytes_per_launch": int(nbytes),
-            "launch_ms": round(s_ms, 4), "traffic": None,
+            "launch_ms": round(s_ms, 4), "traffic": profiled_traffic("sample", "coauthor", N),
             "reads_per_sample": {"row_pointer": round(work[0] / args.steps / N, 2),
                                  "entries": round(work[1] / args.steps / N, 2),
                                  "vertex_ids": round(work[2] / args.steps / N, 2)},
