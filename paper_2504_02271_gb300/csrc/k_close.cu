@@ -58,9 +58,9 @@ __device__ __forceinline__ int region_bits(int szu, int szv, int szw, int wuv, i
 //
 // One warp owns one hyperedge u with |e_u| <= 32 and out-degree <= D.  Shared
 // memory per warp holds a hash set of out(u) (load factor <= 1/2) with the
-// Omega_ux mask and |e_x| of each member, a 16*D-bit filter that rejects most
-// absent keys with one load (only keys that pass it walk the linear-probing
-// table), and per-neighbour arrays (row start, out-degree, mask, size).  The
+// index of each member in out(u), a 16*D-bit filter that rejects most absent keys
+// with one load (only keys that pass it walk the linear-probing table), and
+// per-neighbour arrays (row start, out-degree, Omega_ux mask, |e_x|).  The
 // closure walks the concatenation of the out(v) lists as one flat range: lane l
 // takes flat entries base + l + 32 q, so each load instruction reads 32
 // consecutive entries and every slot is full.  Hits are queued and classified
@@ -70,20 +70,28 @@ __device__ __forceinline__ int region_bits(int szu, int szv, int szw, int wuv, i
 constexpr int kUnroll = 4;
 constexpr int kQueue = 32 * kUnroll + 32;
 
+// Two layouts of the slot data.  Tables for out-degree up to 128 keep the Omega mask and
+// |e_x| per hash slot as well (a hit then needs no slot -> index load: these kernels are
+// issue-bound).  Tables for out-degree 256 keep only a slot -> index byte, so that more
+// warps fit an SM (that kernel is occupancy-bound).
 template <int D_LOG2, bool PACKED>
 struct WarpTables {
   static constexpr int D = 1 << D_LOG2;      // max out-degree of u
   static constexpr int CAP = 2 * D;          // hash slots
   static constexpr int FWORDS = D / 2;       // filter words (16 * D bits)
+  static constexpr bool kIndexed = D_LOG2 >= 8;
+  static_assert(D <= 256, "neighbour indices are queued in 8 bits");
   int32_t key[CAP];
-  uint32_t mask[CAP];
-  uint16_t size[CAP];
+  uint8_t kidx[kIndexed ? CAP : 1];          // slot -> index k of the key in out(u)
+  uint32_t mask[kIndexed ? 1 : CAP];         // slot -> Omega_ux
+  uint16_t size[kIndexed ? 1 : CAP];         // slot -> |e_x|
   uint32_t filt[FWORDS];
   int64_t kbeg[D];
   int32_t kcnt[D];
-  uint32_t kmask[D];
-  uint16_t ksz[D];
-  uint32_t queue[kQueue];                    // hits: (v index << 24) | (slot of w << 8) | omega
+  uint32_t kmask[D];                         // Omega_ux of the k-th out-neighbour x
+  uint16_t ksz[D];                           // |e_x|
+  uint32_t queue[kQueue];                    // hits: (index of v << 24) | (w << 8) | omega, w the
+                                             // index of w (indexed layout) or its slot
   int32_t qom[PACKED ? 1 : kQueue];          // omega_vw when it may not fit 8 bits
 };
 
@@ -125,17 +133,21 @@ __device__ __forceinline__ void warp_flush(RunHist& rh, uint32_t* hist,
   __syncwarp();
 }
 
-// Classify queued hit number `at`: v = k-th out-neighbour, w = table slot.
+// Classify queued hit number `at`: v is out-neighbour number kv of u; w is given by its
+// index (indexed layout) or its table slot.
 template <int D_LOG2, bool PACKED>
 __device__ __forceinline__ void classify_queued(const WarpTables<D_LOG2, PACKED>& t, int at,
                                                 int szu, const uint8_t* lut, uint32_t* hist,
                                                 RunHist& rh) {
+  using TT = WarpTables<D_LOG2, PACKED>;
   const uint32_t e = t.queue[at];
-  const uint32_t k = e >> 24, sw = (e >> 8) & 0xffffu;
+  const uint32_t kv = e >> 24, w = (e >> 8) & 0xffffu;
   const int om = PACKED ? (int)(e & 0xffu) : t.qom[at];
-  const uint32_t muv = t.kmask[k], muw = t.mask[sw];
+  const uint32_t muv = t.kmask[kv];
+  const uint32_t muw = TT::kIndexed ? t.kmask[w] : t.mask[w];
+  const int szw = TT::kIndexed ? t.ksz[w] : t.size[w];
   const int gg = __popc(muv & muw);
-  const int bits = region_bits(szu, t.ksz[k], t.size[sw], __popc(muv), __popc(muw), om, gg);
+  const int bits = region_bits(szu, t.ksz[kv], szw, __popc(muv), __popc(muw), om, gg);
   rh.add(lut[bits], hist);
 }
 
@@ -200,8 +212,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
       const int32_t xs = __ldg(g.esize + x);
       uint32_t s = slot_of((uint32_t)x, CAP_LOG2);
       while (atomicCAS(&t.key[s], -1, x) != -1) s = (s + 1) & (CAP - 1);
-      t.mask[s] = 0;
-      t.size[s] = (uint16_t)xs;
+      if constexpr (TT::kIndexed) {
+        t.kidx[s] = (uint8_t)k;
+        t.kmask[k] = 0;
+        t.ksz[k] = (uint16_t)xs;
+      } else {
+        t.mask[s] = 0;
+        t.size[s] = (uint16_t)xs;
+      }
       const uint32_t fb = filt_bit((uint32_t)x, FB_LOG2);
       atomicOr(&t.filt[fb >> 5], 1u << (fb & 31));
       t.kbeg[k] = xb;
@@ -239,18 +257,22 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
         uint32_t s = slot_of((uint32_t)x, CAP_LOG2);
         int32_t kk;
         while ((kk = t.key[s]) != x && kk != -1) s = (s + 1) & (CAP - 1);
-        if (kk == x) atomicOr(&t.mask[s], 1u << p);   // lanes may be at different p
+        if (kk == x) {   // lanes may be at different p
+          if constexpr (TT::kIndexed) atomicOr(&t.kmask[t.kidx[s]], 1u << p);
+          else atomicOr(&t.mask[s], 1u << p);
+        }
       }
     }
     __syncwarp();
-    // per-neighbour copies of mask and size for the closure loop
-    for (int k = lane; k < du; k += 32) {
-      int32_t x, om;
-      get_entry<PACKED>(o, bu + k, x, om);
-      uint32_t s = slot_of((uint32_t)x, CAP_LOG2);
-      while (t.key[s] != x) s = (s + 1) & (CAP - 1);
-      t.kmask[k] = t.mask[s];
-      t.ksz[k] = t.size[s];
+    if constexpr (!TT::kIndexed) {   // per-neighbour copies of mask and size
+      for (int k = lane; k < du; k += 32) {
+        int32_t x, om;
+        get_entry<PACKED>(o, bu + k, x, om);
+        uint32_t s = slot_of((uint32_t)x, CAP_LOG2);
+        while (t.key[s] != x) s = (s + 1) & (CAP - 1);
+        t.kmask[k] = t.mask[s];
+        t.ksz[k] = t.size[s];
+      }
     }
     int32_t F = my_cnt;
 #pragma unroll
@@ -304,7 +326,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
         const unsigned bal = __ballot_sync(kFull, hit);
         if (hit) {
           const int at = qn + __popc(bal & ((1u << lane) - 1u));
-          t.queue[at] = ((uint32_t)ent_k[q] << 24) | (s << 8) |
+          t.queue[at] = ((uint32_t)ent_k[q] << 24) |
+                        ((TT::kIndexed ? (uint32_t)t.kidx[s] : s) << 8) |
                         (PACKED ? (uint32_t)ent_om[q] : 0u);
           if (!PACKED) t.qom[at] = ent_om[q];
         }
