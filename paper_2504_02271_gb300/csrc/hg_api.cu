@@ -569,7 +569,8 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   HG_CUDA(cudaMemsetAsync(g->wcr, 0, sizeof(int32_t) * ne1, s));
   HG_CUDA(cudaMemsetAsync(g->small->counters, 0, sizeof(int32_t) * 16, s));
   t_begin(g, "wedge_gather");
-  launch_wedge_rows(d, wb, nb, g->max_cand, g->deg, &g->small->wc, g->cap_rows, g->packed, scratch,
+  launch_wedge_rows(d, wb, nb, g->max_cand, g->cand, g->deg, &g->small->wc, g->cap_rows, g->packed,
+                    scratch,
                     &g->small->err, g->small->counters, dn, RowCounts{g->upc, g->wcr}, s, g->nsm);
   t_end(g);
   // orientation by (deg, id).  Out-lists go to rows with room for deg(i) entries (offsets

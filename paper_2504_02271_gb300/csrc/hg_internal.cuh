@@ -123,10 +123,10 @@ struct RowCounts {
 // and every (j, omega_ij) of row i written from rows.row_ptr[i] (a capacity layout:
 // room for cap[i] = min(gathered incidences, |E| - 1) entries, see launch_cap_rows).
 void launch_wedge_rows(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb,
-                       int64_t heavy_max_cand, int32_t* deg, unsigned long long* wc,
-                       const Oriented& rows, int packed, unsigned long long* scratch, int* err,
-                       int32_t* work_counter, const DenseInfo& dense, RowCounts rc,
-                       cudaStream_t s, int nsm);
+                       int64_t heavy_max_cand, const int64_t* cand, int32_t* deg,
+                       unsigned long long* wc, const Oriented& rows, int packed,
+                       unsigned long long* scratch, int* err, int32_t* work_counter,
+                       const DenseInfo& dense, RowCounts rc, cudaStream_t s, int nsm);
 void launch_cap_rows(const int64_t* cand, int32_t ne, int32_t* cap, cudaStream_t s);
 // Filter rows of the capacity layout (len[i] entries from src_ptr[i]) into an exact layout
 // (row i from dst_ptr[i]), order kept: keep 0 = j ranked above i in (deg, id), 1 = j > i,

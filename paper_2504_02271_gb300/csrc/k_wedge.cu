@@ -76,6 +76,14 @@ __device__ __forceinline__ bool gather_pair(const DenseInfo& dn, int32_t hi, int
   return hi < 0 || dn.heavy_idx[j] < 0;
 }
 
+// Table size of a row: the smallest power of two >= 2 * (its gathered incidences), so the
+// load factor stays <= 1/2, clamped to [2^lo, 2^hi].
+__device__ __forceinline__ int row_cap_log2(int64_t cand, int lo, int hi) {
+  int l = lo;
+  while (l < hi && (int64_t(1) << l) < 2 * cand) ++l;
+  return l;
+}
+
 __device__ __forceinline__ bool ranked_above(int32_t di, int32_t i, int32_t dj, int32_t j) {
   return di < dj || (di == dj && i < j);
 }
@@ -94,9 +102,9 @@ __device__ __forceinline__ void put_entry(const Oriented& o, int64_t at, uint32_
 template <bool PACKED>
 __global__ void __launch_bounds__(kLightWarps * 32)
     k_wedge_light(DevGraph g, const int32_t* __restrict__ rows, const int32_t* __restrict__ nrows_p,
-                  int32_t* __restrict__ deg, unsigned long long* __restrict__ wc, Oriented o,
-                  int* __restrict__ err, int32_t* __restrict__ counter, DenseInfo dn,
-                  RowCounts rc) {
+                  const int64_t* __restrict__ cand, int32_t* __restrict__ deg,
+                  unsigned long long* __restrict__ wc, Oriented o, int* __restrict__ err,
+                  int32_t* __restrict__ counter, DenseInfo dn, RowCounts rc) {
   constexpr int CAP = 1 << kLightCapLog2;
   __shared__ unsigned long long tab[kLightWarps][CAP];
   __shared__ unsigned long long blk_wc;
@@ -112,7 +120,9 @@ __global__ void __launch_bounds__(kLightWarps * 32)
     r = __shfl_sync(kFull, r, 0);
     if (r >= nrows) break;
     const int32_t i = rows[r];
-    for (int s = lane; s < CAP; s += 32) T[s] = kEmpty;
+    const int cl = row_cap_log2(cand[i], 5, kLightCapLog2);   // this row's table: 2^cl slots
+    const int cap = 1 << cl;
+    for (int s = lane; s < cap; s += 32) T[s] = kEmpty;
     __syncwarp();
     const int32_t hi = dn.heavy_idx ? dn.heavy_idx[i] : -1;
     const int64_t b = g.e_ptr[i], e = g.e_ptr[i + 1];
@@ -121,20 +131,20 @@ __global__ void __launch_bounds__(kLightWarps * 32)
       const int64_t vb = g.v_ptr[v], ve = g.v_ptr[v + 1];
       for (int64_t q = vb + lane; q < ve; q += 32) {
         const int32_t j = g.v_idx[q];
-        if (j != i && gather_pair(dn, hi, j)) ht_add(T, kLightCapLog2, (uint32_t)j);
+        if (j != i && gather_pair(dn, hi, j)) ht_add(T, cl, (uint32_t)j);
       }
     }
     if (hi >= 0) {
       for (int32_t h = lane; h < dn.nh; h += 32) {
         const uint32_t om = dn.omega[(int64_t)hi * dn.ld + h];
-        if (om && h != hi) ht_add_n(T, kLightCapLog2, (uint32_t)dn.ids[h], om);
+        if (om && h != hi) ht_add_n(T, cl, (uint32_t)dn.ids[h], om);
       }
     }
     __syncwarp();
     const int32_t szi = (int32_t)(e - b);
     const int64_t base = o.row_ptr[i];
     int written = 0, up = 0, incl = 0;
-    for (int s0 = 0; s0 < CAP; s0 += 32) {
+    for (int s0 = 0; s0 < cap; s0 += 32) {
       const unsigned long long x = T[s0 + lane];
       const bool valid = x != kEmpty;
       uint32_t j = 0, om = 0;
@@ -177,13 +187,12 @@ __global__ void __launch_bounds__(kLightWarps * 32)
 template <bool PACKED, bool SMEM>
 __global__ void __launch_bounds__(kBlockThreads)
     k_wedge_block(DevGraph g, const int32_t* __restrict__ rows, const int32_t* __restrict__ nrows_p,
-                  int cap_log2, unsigned long long* __restrict__ gscratch,
-                  int32_t* __restrict__ deg, unsigned long long* __restrict__ wc, Oriented o,
-                  int* __restrict__ err, int32_t* __restrict__ counter, DenseInfo dn,
-                  RowCounts rc) {
+                  const int64_t* __restrict__ cand, int cap_log2,
+                  unsigned long long* __restrict__ gscratch, int32_t* __restrict__ deg,
+                  unsigned long long* __restrict__ wc, Oriented o, int* __restrict__ err,
+                  int32_t* __restrict__ counter, DenseInfo dn, RowCounts rc) {
   extern __shared__ unsigned long long dyn[];
   unsigned long long* T = SMEM ? dyn : gscratch + ((size_t)blockIdx.x << cap_log2);
-  const uint32_t CAP = 1u << cap_log2;
   __shared__ int32_t s_row;
   __shared__ int32_t s_cnt, s_up, s_incl;
   __shared__ unsigned long long s_wc;
@@ -204,6 +213,8 @@ __global__ void __launch_bounds__(kBlockThreads)
     const int32_t r = s_row;
     if (r >= nrows) break;
     const int32_t i = rows[r];
+    const int cl = row_cap_log2(cand[i], 8, cap_log2);   // this row's table: 2^cl slots
+    const uint32_t CAP = 1u << cl;
     for (uint32_t s = threadIdx.x; s < CAP; s += kBlockThreads) T[s] = kEmpty;
     __syncthreads();
     const int32_t hi = dn.heavy_idx ? dn.heavy_idx[i] : -1;
@@ -213,13 +224,13 @@ __global__ void __launch_bounds__(kBlockThreads)
       const int64_t vb = g.v_ptr[v], ve = g.v_ptr[v + 1];
       for (int64_t q = vb + lane; q < ve; q += 32) {
         const int32_t j = g.v_idx[q];
-        if (j != i && gather_pair(dn, hi, j)) ht_add(T, cap_log2, (uint32_t)j);
+        if (j != i && gather_pair(dn, hi, j)) ht_add(T, cl, (uint32_t)j);
       }
     }
     if (hi >= 0) {
       for (int32_t h = threadIdx.x; h < dn.nh; h += kBlockThreads) {
         const uint32_t om = dn.omega[(int64_t)hi * dn.ld + h];
-        if (om && h != hi) ht_add_n(T, cap_log2, (uint32_t)dn.ids[h], om);
+        if (om && h != hi) ht_add_n(T, cl, (uint32_t)dn.ids[h], om);
       }
     }
     __syncthreads();
@@ -351,7 +362,7 @@ int cap_log2_for(int64_t cand) {
 
 template <bool PACKED>
 void launch_all(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb, int64_t heavy_max,
-                int32_t* deg, unsigned long long* wc, const Oriented& o,
+                const int64_t* cand, int32_t* deg, unsigned long long* wc, const Oriented& o,
                 unsigned long long* scratch, int* err, int32_t* counters, const DenseInfo& dn,
                 RowCounts rc, cudaStream_t s, int nsm) {
   // counters[0..2] are zeroed by the caller
@@ -359,8 +370,9 @@ void launch_all(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb, int
     int blocks = (nb[0] + kLightWarps - 1) / kLightWarps;
     blocks = blocks < nsm * 4 ? blocks : nsm * 4;
     note_launch();
-    k_wedge_light<PACKED><<<blocks, kLightWarps * 32, 0, s>>>(g, b.rows[0], b.count + 0, deg, wc,
-                                                              o, err, counters + 0, dn, rc);
+    k_wedge_light<PACKED><<<blocks, kLightWarps * 32, 0, s>>>(g, b.rows[0], b.count + 0, cand,
+                                                              deg, wc, o, err, counters + 0, dn,
+                                                              rc);
   }
   if (nb[1] > 0) {
     const size_t smem = sizeof(unsigned long long) << kMediumCapLog2;
@@ -369,14 +381,14 @@ void launch_all(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb, int
     int blocks = nb[1] < nsm * 3 ? nb[1] : nsm * 3;
     note_launch();
     k_wedge_block<PACKED, true><<<blocks, kBlockThreads, smem, s>>>(
-        g, b.rows[1], b.count + 1, kMediumCapLog2, nullptr, deg, wc, o, err, counters + 1, dn,
-        rc);
+        g, b.rows[1], b.count + 1, cand, kMediumCapLog2, nullptr, deg, wc, o, err, counters + 1,
+        dn, rc);
   }
   if (nb[2] > 0) {
     int blocks = nb[2] < nsm * 2 ? nb[2] : nsm * 2;
     note_launch();
     k_wedge_block<PACKED, false><<<blocks, kBlockThreads, 0, s>>>(
-        g, b.rows[2], b.count + 2, cap_log2_for(heavy_max), scratch, deg, wc, o, err,
+        g, b.rows[2], b.count + 2, cand, cap_log2_for(heavy_max), scratch, deg, wc, o, err,
         counters + 2, dn, rc);
   }
 }
@@ -421,16 +433,16 @@ void launch_bucket_rows(const int64_t* cand, int32_t ne, WedgeBuckets b, cudaStr
 }
 
 void launch_wedge_rows(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb,
-                       int64_t heavy_max_cand, int32_t* deg, unsigned long long* wc,
-                       const Oriented& rows, int packed, unsigned long long* scratch, int* err,
-                       int32_t* work_counter, const DenseInfo& dn, RowCounts rc, cudaStream_t s,
-                       int nsm) {
+                       int64_t heavy_max_cand, const int64_t* cand, int32_t* deg,
+                       unsigned long long* wc, const Oriented& rows, int packed,
+                       unsigned long long* scratch, int* err, int32_t* work_counter,
+                       const DenseInfo& dn, RowCounts rc, cudaStream_t s, int nsm) {
   if (packed)
-    launch_all<true>(g, b, nb, heavy_max_cand, deg, wc, rows, scratch, err, work_counter, dn, rc,
-                     s, nsm);
+    launch_all<true>(g, b, nb, heavy_max_cand, cand, deg, wc, rows, scratch, err, work_counter, dn,
+                     rc, s, nsm);
   else
-    launch_all<false>(g, b, nb, heavy_max_cand, deg, wc, rows, scratch, err, work_counter, dn, rc,
-                      s, nsm);
+    launch_all<false>(g, b, nb, heavy_max_cand, cand, deg, wc, rows, scratch, err, work_counter,
+                      dn, rc, s, nsm);
 }
 
 void launch_cap_rows(const int64_t* cand, int32_t ne, int32_t* cap, cudaStream_t s) {
