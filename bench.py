@@ -199,7 +199,7 @@ def profiled_traffic(kernel, workload_name, units=None):
 
 # team shape of each closure kernel group -> index of its work counters
 CLOSE_GROUPS = {"close_warp256": 0, "close_warp512": 1, "close_warp1024": 2, "close_block2048": 3,
-                "close_block8192": 4, "close_wide": 5}
+                "close_block4096": 4, "close_block8192": 5, "close_wide": 6}
 ISSUE_LANE_OPS_PER_CYCLE_PER_SM = 4 * 32   # 4 schedulers, one 32-lane instruction per cycle
 
 

@@ -218,19 +218,19 @@ hg_status hg_clustering_coeff(hg_graph* g, const double eps[20], double* cc,
  *                of hyperedges with out-degree >= 2);
  *   teams        hyperedges u that owned a closing team (out-degree >= 2);
  *   bucket_*     the same per team shape: warp teams for out-degree <= 64, <= 128,
- *                <= 256; block teams with shared-memory tables for <= 1024 and <= 4096;
- *                block teams with global-memory tables for the rest (index 5, which
- *                also takes what the other teams hand over).
+ *                <= 256; block teams with shared-memory tables for <= 1024, <= 2048 and
+ *                <= 4096; block teams with global-memory tables for the rest (index 6,
+ *                which also takes what the other teams hand over).
  */
 typedef struct hg_close_stats {
   uint64_t probes;
   uint64_t gathers;
   uint64_t out_entries;
   uint64_t teams;
-  uint64_t bucket_teams[6];
-  uint64_t bucket_probes[6];
-  uint64_t bucket_gathers[6];
-  uint64_t bucket_out_entries[6];
+  uint64_t bucket_teams[7];
+  uint64_t bucket_probes[7];
+  uint64_t bucket_gathers[7];
+  uint64_t bucket_out_entries[7];
 } hg_close_stats;
 hg_status hg_close_stats_get(hg_graph* g, hg_close_stats* out);
 

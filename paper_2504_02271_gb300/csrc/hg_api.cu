@@ -972,7 +972,8 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   if (!scratch) return HG_ERR_OOM;
   static const char* names[kCloseBuckets] = {"close_warp256",   "close_warp512",
                                              "close_warp1024",  "close_block2048",
-                                             "close_block8192", "close_wide"};
+                                             "close_block4096", "close_block8192",
+                                             "close_wide"};
   for (int k = kCloseBuckets - 1; k >= 0; --k) {
     if (n[k] <= 0) continue;
     t_begin(g, names[k]);

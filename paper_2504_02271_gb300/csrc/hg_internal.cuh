@@ -198,8 +198,8 @@ size_t wedge_heavy_scratch_bytes(int64_t heavy_max_cand, int nsm);
 // k_close.cu
 // close team shapes: warp teams (out-degree <= 64, 128, 256), block teams with shared
 // tables (<= 1024, <= 4096), block teams with global scratch (the rest)
-constexpr int kCloseBuckets = 6;
-constexpr int kWideBucket = 5;
+constexpr int kCloseBuckets = 7;
+constexpr int kWideBucket = 6;
 struct CloseBuckets {
   int32_t* lists[kCloseBuckets];
   int32_t* count;     // [kCloseBuckets]

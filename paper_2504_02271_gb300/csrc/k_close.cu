@@ -774,7 +774,8 @@ __device__ __forceinline__ int close_bucket_of(int32_t d, int32_t sz, bool all_b
   if (sz <= kWarpMaskBits && d <= 128) return 1;
   if (sz <= kWarpMaskBits && d <= 256) return 2;
   if (sz <= kWarpMaskBits && d <= 1024) return 3;
-  if (sz <= kWarpMaskBits && d <= 4096) return 4;
+  if (sz <= kWarpMaskBits && d <= 2048) return 4;
+  if (sz <= kWarpMaskBits && d <= 4096) return 5;
   return kWideBucket;
 }
 
@@ -960,6 +961,9 @@ void launch_close(int bucket, const DevGraph& g, const Oriented& o, int packed,
       launch_block<10, 16>(g, o, packed, list, n, n_p, hist, work, counter, s, nsm);
       break;
     case 4:
+      launch_block<11, 16>(g, o, packed, list, n, n_p, hist, work, counter, s, nsm);
+      break;
+    case 5:
       launch_block<12, 16>(g, o, packed, list, n, n_p, hist, work, counter, s, nsm);
       break;
     default: {

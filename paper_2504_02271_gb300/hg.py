@@ -59,9 +59,9 @@ class _WedgeStats(ctypes.Structure):
 class _CloseStats(ctypes.Structure):
     _fields_ = [("probes", ctypes.c_uint64), ("gathers", ctypes.c_uint64),
                 ("out_entries", ctypes.c_uint64), ("teams", ctypes.c_uint64),
-                ("bucket_teams", ctypes.c_uint64 * 6), ("bucket_probes", ctypes.c_uint64 * 6),
-                ("bucket_gathers", ctypes.c_uint64 * 6),
-                ("bucket_out_entries", ctypes.c_uint64 * 6)]
+                ("bucket_teams", ctypes.c_uint64 * 7), ("bucket_probes", ctypes.c_uint64 * 7),
+                ("bucket_gathers", ctypes.c_uint64 * 7),
+                ("bucket_out_entries", ctypes.c_uint64 * 7)]
 
 
 class _ServerOptions(ctypes.Structure):
