@@ -90,3 +90,25 @@ def test_stored_hub_values_follow_the_sunflower_closed_form():
     assert gold["counts"] == want
     assert (gold["W"], gold["W_c"], gold["W_t"]) == (comb(3000, 2), 0, comb(3000, 2))
     assert gold["connected"] == 3000 * comb(2999, 2) and gold["open"] == 0
+
+
+def test_generate_batch_layout_and_thread_independence():
+    # members drawn in threads land in the concatenated layout exactly as drawn alone,
+    # whatever the thread count; a member that exhausts its fresh hyperedges is redrawn
+    import hgen
+
+    specs = [hgen.batched(s) for s in (100, 101, 962, 105)]   # seed 962 needs a redraw
+    nv, eoff, eptr, evtx, used = hgen.generate_batch(specs, threads=1,
+                                                     redraw=hgen.batched_redraw)
+    nv4, eoff4, eptr4, evtx4, used4 = hgen.generate_batch(specs, threads=4,
+                                                          redraw=hgen.batched_redraw)
+    assert (eoff.tolist(), nv.tolist()) == (eoff4.tolist(), nv4.tolist())
+    assert hgen.csr_hash(eptr, evtx) == hgen.csr_hash(eptr4, evtx4)
+    assert [u.seed for u in used] == [100, 101, 962 + (1 << 32), 105] == [u.seed for u in used4]
+    for m, sp in enumerate(used):
+        p, i = hgen.generate(sp)
+        lo, hi = eoff[m], eoff[m + 1]
+        assert (eptr[lo:hi + 1] - eptr[lo]).tolist() == p.tolist()
+        assert evtx[eptr[lo]:eptr[hi]].tolist() == i.tolist()
+    with pytest.raises(hgen.DedupExhausted):
+        hgen.generate(specs[2])

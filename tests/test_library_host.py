@@ -61,3 +61,40 @@ def test_no_cpu_fallback_without_gpu(lib):
     with pytest.raises(lib.HgError) as e:
         lib.hg_load_csr(3, 1, np.array([0, 2]), np.array([0, 1]), stream=0)
     assert e.value.name == "HG_ERR_NO_DEVICE"
+
+
+def test_concat_members_layout(lib):
+    # the binding's concatenation of member CSRs for hg_load_batch: row pointers shifted
+    # by the incidences before each member, ids left member-local, empty members kept
+    import numpy as np
+
+    from conftest import csr_of
+
+    members = [(3, *csr_of([[0, 1], [1, 2]])),
+               (4, np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32)),
+               (2, *csr_of([[0, 1]]))]
+    nv, eoff, eptr, evtx = lib.concat_members(members)
+    assert nv.tolist() == [3, 4, 2] and eoff.tolist() == [0, 2, 2, 3]
+    assert eptr.tolist() == [0, 2, 4, 6] and evtx.tolist() == [0, 1, 1, 2, 0, 1]
+
+
+def test_server_and_batch_structs_match_the_header(lib):
+    # ctypes layouts of the structs the C ABI exchanges, against sizes from a C compile
+    import ctypes
+    import subprocess
+    import tempfile
+
+    src = ('#include <stdio.h>\n#include "hg.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu\\n",'
+           'sizeof(hg_result),sizeof(hg_query),sizeof(hg_server_options),sizeof(hg_server_stats),'
+           'sizeof(hg_close_stats),sizeof(hg_tuning));return 0;}\n')
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "s.c")
+        with open(c, "w") as f:
+            f.write(src)
+        exe = os.path.join(d, "s")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        want = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
+    hg = lib.hg
+    got = [ctypes.sizeof(t) for t in (hg._Result, hg._Query, hg._ServerOptions, hg._ServerStats,
+                                      hg._CloseStats, hg._Tuning)]
+    assert got == want
