@@ -338,9 +338,9 @@ def run_ours(args):
     tri_all, total_s = aggregate(float(tri), sum(step_ms) / 1000.0, dist, dev)
     value = tri_all / total_s
 
-    # end to end through the C ABI from pinned host buffers
+    # end to end through the C ABI from pinned host buffers (--e2e-steps 0 skips it)
     e2e_ms = []
-    for k in range(max(1, args.e2e_steps)):
+    for k in range(args.e2e_steps):
         do_flush(k + 99)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -350,9 +350,11 @@ def run_ours(args):
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
         assert c2.tolist() == counts.tolist()
-    e2e_units, e2e_s = aggregate(float(int(counts[0]) * len(e2e_ms)), sum(e2e_ms) / 1000.0, dist,
-                                 dev)
-    e2e_value = e2e_units / e2e_s
+    e2e_value = None
+    if e2e_ms:
+        e2e_units, e2e_s = aggregate(float(int(counts[0]) * len(e2e_ms)), sum(e2e_ms) / 1000.0,
+                                     dist, dev)
+        e2e_value = e2e_units / e2e_s
 
     if rank != 0:
         if dist is not None:
@@ -410,10 +412,11 @@ def run_ours(args):
                        parity="counts equal stored oracle values" if parity else "not checked",
                        dense_tiles={"min_size": args.dense_min_size, "max_count": args.dense_max_count,
                                     "hyperedges": st["dense_edges"]}),
-        "e2e": {"value": round(e2e_value, 1), "unit": UNIT,
-                "h2d_bytes_per_step": int(e_ptr.nbytes + e_idx.nbytes),
-                "d2h_bytes_per_step": 21 * 8 + 8 * 8,
-                "ms_per_step": round(statistics.mean(e2e_ms), 4)},
+        "e2e": None if e2e_value is None else {
+            "value": round(e2e_value, 1), "unit": UNIT,
+            "h2d_bytes_per_step": int(e_ptr.nbytes + e_idx.nbytes),
+            "d2h_bytes_per_step": 21 * 8 + 8 * 8,
+            "ms_per_step": round(statistics.mean(e2e_ms), 4)},
         "roofline": roof,
         "dense_roofline": dense,
         "kernel_ms_per_step": {n: round(v[0] / args.steps, 4) for n, v in sorted(kernel_ms.items())},
