@@ -967,7 +967,7 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   const int64_t dmax = std::max<int64_t>((int64_t)h.wide_max[0], 256);
   const int64_t words = std::max<int64_t>(((int64_t)h.wide_max[1] + 31) / 32, 1);
   int64_t cap = 16;
-  while (cap < 4 * dmax) cap *= 2;
+  while (cap < 2 * dmax) cap *= 2;
   void* scratch = dev_alloc(g, g->count_blocks, close_wide_scratch_bytes(cap, words, dmax, g->nsm));
   if (!scratch) return HG_ERR_OOM;
   static const char* names[kCloseBuckets] = {"close_warp256",   "close_warp512",

@@ -28,6 +28,9 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBins = 24;      // pattern 0 (invalid) .. 20, padded
 constexpr int kHistCopies = 4; // spread same-pattern increments of the block kernel
 constexpr int kWideThreads = 256;
+constexpr int kWideFilterLog2 = 18;   // 32 KiB shared filter per wide-team block
+constexpr int kWideUnroll = 4;        // 32-entry loads in flight per warp
+constexpr int kWideBlocksPerSm = 4;
 
 __constant__ uint8_t c_lut[128];
 
@@ -612,11 +615,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
 // ------------------------------------------------------------------ block per u (wide)
 // Any |e_u| (masks of `words` 32-bit words) and any out-degree; tables in global scratch.
 
+// Per block: the hash set of out(u) (key and the key's index k in out(u) per slot, load
+// factor <= 1/2) and per out-neighbour arrays (Omega_ux of `words` words, |e_x|, list
+// length and start).  Only the slots and the du rows of masks in use are cleared per u.
 struct WideScratch {
   int32_t* key;     // [cap]
-  int32_t* size;    // [cap]
-  uint32_t* mask;   // [cap * words]
-  int32_t* kslot;   // [dmax]
+  int32_t* kidx;    // [cap]
+  uint32_t* mask;   // [dmax * words]
+  int32_t* ksz;     // [dmax]
   int32_t* kcnt;    // [dmax]
   int64_t* kbeg;    // [dmax]
 };
@@ -624,7 +630,7 @@ struct WideScratch {
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 __host__ __device__ inline size_t wide_block_bytes(int64_t cap, int64_t words, int64_t dmax) {
-  return align256(cap * 4) * 2 + align256(cap * words * 4) + align256(dmax * 4) * 2 +
+  return align256(cap * 4) * 2 + align256(dmax * words * 4) + align256(dmax * 4) * 2 +
          align256(dmax * 8);
 }
 
@@ -632,11 +638,11 @@ __device__ WideScratch wide_carve(char* base, int64_t cap, int64_t words, int64_
   WideScratch w;
   w.key = (int32_t*)base;
   base += align256(cap * 4);
-  w.size = (int32_t*)base;
+  w.kidx = (int32_t*)base;
   base += align256(cap * 4);
   w.mask = (uint32_t*)base;
-  base += align256(cap * words * 4);
-  w.kslot = (int32_t*)base;
+  base += align256(dmax * words * 4);
+  w.ksz = (int32_t*)base;
   base += align256(dmax * 4);
   w.kcnt = (int32_t*)base;
   base += align256(dmax * 4);
@@ -645,7 +651,7 @@ __device__ WideScratch wide_carve(char* base, int64_t cap, int64_t words, int64_
 }
 
 template <bool PACKED>
-__global__ void __launch_bounds__(kWideThreads)
+__global__ void __launch_bounds__(kWideThreads, kWideBlocksPerSm)
     k_close_wide(DevGraph g, Oriented o, const int32_t* __restrict__ list,
                  const int32_t* __restrict__ n_p, int64_t cap_max, int64_t words_max,
                  int64_t dmax, char* __restrict__ scratch, unsigned long long* __restrict__ hist_out,
@@ -654,6 +660,9 @@ __global__ void __launch_bounds__(kWideThreads)
   __shared__ uint8_t lut[128];
   __shared__ int32_t s_r;
   __shared__ unsigned long long s_since;   // probes since the last flush (block-wide)
+  // out(u) membership filter: 16 bits per key up to 16,384 keys (fewer beyond), so that
+  // most absent keys are rejected without touching the table in global memory
+  __shared__ uint32_t filt[(1 << kWideFilterLog2) / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   constexpr int kW = kWideThreads / 32;
   static_assert(kHistCopies * kBins <= kWideThreads, "one thread per shared bin");
@@ -695,18 +704,23 @@ __global__ void __launch_bounds__(kWideThreads)
     const int32_t words = (szu + 31) / 32;
     if (threadIdx.x == 0) outs += (unsigned long long)du;
     int cl = 4;
-    while ((int64_t(1) << cl) < 4 * (int64_t)du) ++cl;
+    while ((int64_t(1) << cl) < 2 * (int64_t)du) ++cl;
     const uint32_t cap = 1u << cl;
+    int fl = 5;   // filter bits: 2^fl >= 16 du, at most 2^kWideFilterLog2
+    while (fl < kWideFilterLog2 && (int64_t(1) << fl) < 16 * (int64_t)du) ++fl;
     for (uint32_t s = threadIdx.x; s < cap; s += kWideThreads) t.key[s] = -1;
-    for (uint32_t s = threadIdx.x; s < cap * (uint32_t)words; s += kWideThreads) t.mask[s] = 0;
+    for (int64_t s = threadIdx.x; s < (int64_t)du * words; s += kWideThreads) t.mask[s] = 0;
+    for (int s = threadIdx.x; s < (1 << fl) / 32; s += kWideThreads) filt[s] = 0;
     __syncthreads();
     for (int k = threadIdx.x; k < du; k += kWideThreads) {
       int32_t x, om;
       get_entry<PACKED>(o, bu + k, x, om);
+      const uint32_t fb = filt_bit((uint32_t)x, fl);
+      atomicOr(&filt[fb >> 5], 1u << (fb & 31));
       uint32_t s = slot_of((uint32_t)x, cl);
       while (atomicCAS(&t.key[s], -1, x) != -1) s = (s + 1) & (cap - 1);
-      t.size[s] = __ldg(g.esize + x);
-      t.kslot[k] = (int32_t)s;
+      t.kidx[s] = k;
+      t.ksz[k] = __ldg(g.esize + x);
       t.kbeg[k] = __ldg(o.row_ptr + x);
       t.kcnt[k] = __ldg(o.dplus + x);
     }
@@ -717,17 +731,18 @@ __global__ void __launch_bounds__(kWideThreads)
       if (lane == 0) gathers += (unsigned long long)(ye - yb);
       for (int64_t q = yb + lane; q < ye; q += 32) {
         const int32_t x = __ldg(g.v_idx + q);
+        const uint32_t fb = filt_bit((uint32_t)x, fl);
+        if (!((filt[fb >> 5] >> (fb & 31)) & 1u)) continue;
         uint32_t s = slot_of((uint32_t)x, cl);
         int32_t kk;
         while ((kk = *((volatile int32_t*)&t.key[s])) != x && kk != -1) s = (s + 1) & (cap - 1);
-        if (kk == x) atomicOr(&t.mask[(size_t)s * words + (p >> 5)], 1u << (p & 31));
+        if (kk == x) atomicOr(&t.mask[(size_t)t.kidx[s] * words + (p >> 5)], 1u << (p & 31));
       }
     }
     __syncthreads();
     for (int k = w; k < du; k += kW) {
-      const int sv = t.kslot[k];
-      const uint32_t* muv = t.mask + (size_t)sv * words;
-      const int szv = t.size[sv];
+      const uint32_t* muv = t.mask + (size_t)k * words;
+      const int szv = t.ksz[k];
       int wuv = 0;
       for (int q = 0; q < words; ++q) wuv += __popc(muv[q]);
       const int64_t vb = t.kbeg[k];
@@ -736,21 +751,36 @@ __global__ void __launch_bounds__(kWideThreads)
         probes += (unsigned long long)cnt;
         atomicAdd(&s_since, (unsigned long long)cnt);
       }
-      for (int32_t j = lane; j < cnt; j += 32) {
-        int32_t wv, om;
-        get_entry<PACKED>(o, vb + j, wv, om);
-        uint32_t s = slot_of((uint32_t)wv, cl);
-        int32_t kk;
-        while ((kk = t.key[s]) != wv && kk != -1) s = (s + 1) & (cap - 1);
-        if (kk != wv) continue;
-        const uint32_t* muw = t.mask + (size_t)s * words;
-        int wuw = 0, gg = 0;
-        for (int q = 0; q < words; ++q) {
-          wuw += __popc(muw[q]);
-          gg += __popc(muw[q] & muv[q]);
+      // kWideUnroll independent 32-entry loads in flight per warp, then their probes
+      for (int32_t j0 = 0; j0 < cnt; j0 += 32 * kWideUnroll) {
+        int32_t wv[kWideUnroll], om[kWideUnroll];
+#pragma unroll
+        for (int q = 0; q < kWideUnroll; ++q) {
+          const int32_t j = j0 + q * 32 + lane;
+          wv[q] = -1;
+          om[q] = 0;
+          if (j < cnt) get_entry<PACKED>(o, vb + j, wv[q], om[q]);
         }
-        const int bits = region_bits(szu, szv, t.size[s], wuv, wuw, om, gg);
-        atomicAdd(&my_hist[lut[bits]], 1u);
+#pragma unroll
+        for (int q = 0; q < kWideUnroll; ++q) {
+          const int32_t x = wv[q];
+          if (x < 0) continue;
+          const uint32_t fb = filt_bit((uint32_t)x, fl);
+          if (!((filt[fb >> 5] >> (fb & 31)) & 1u)) continue;
+          uint32_t s = slot_of((uint32_t)x, cl);
+          int32_t kk;
+          while ((kk = t.key[s]) != x && kk != -1) s = (s + 1) & (cap - 1);
+          if (kk != x) continue;
+          const int kw = t.kidx[s];
+          const uint32_t* muw = t.mask + (size_t)kw * words;
+          int wuw = 0, gg = 0;
+          for (int qq = 0; qq < words; ++qq) {
+            wuw += __popc(muw[qq]);
+            gg += __popc(muw[qq] & muv[qq]);
+          }
+          const int bits = region_bits(szu, szv, t.ksz[kw], wuv, wuw, om[q], gg);
+          atomicAdd(&my_hist[lut[bits]], 1u);
+        }
       }
     }
   }
@@ -935,7 +965,7 @@ void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,
 
 size_t close_wide_scratch_bytes(int64_t cap, int64_t words, int64_t dmax, int nsm) {
   if (cap <= 0) return 0;
-  return wide_block_bytes(cap, words, dmax) * (size_t)(nsm * 2);
+  return wide_block_bytes(cap, words, dmax) * (size_t)(nsm * kWideBlocksPerSm);
 }
 
 void launch_close(int bucket, const DevGraph& g, const Oriented& o, int packed,
@@ -967,7 +997,7 @@ void launch_close(int bucket, const DevGraph& g, const Oriented& o, int packed,
       launch_block<12, 16>(g, o, packed, list, n, n_p, hist, work, counter, s, nsm);
       break;
     default: {
-      int blocks = n < nsm * 2 ? n : nsm * 2;
+      int blocks = n < nsm * kWideBlocksPerSm ? n : nsm * kWideBlocksPerSm;
       note_launch();
       if (packed)
         k_close_wide<true><<<blocks, kWideThreads, 0, s>>>(g, o, list, n_p, wide_cap, wide_words,
