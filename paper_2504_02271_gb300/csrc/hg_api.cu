@@ -504,7 +504,7 @@ constexpr int64_t kOrientSlackBytes = int64_t(8) << 30;   // oriented rows with 
 
 hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   g->close_mode = opt ? opt->close_mode : 0;
-  if (g->close_mode < 0 || g->close_mode > 1) return HG_ERR_INVALID_ARG;
+  if (g->close_mode < 0 || g->close_mode > 2) return HG_ERR_INVALID_ARG;
   if (opt && (opt->orient_exact < 0 || opt->orient_exact > 1)) return HG_ERR_INVALID_ARG;
   cudaStream_t s = g->stream;
   release(g, g->count_blocks);
@@ -979,7 +979,7 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
     t_begin(g, names[k]);
     launch_close(k, d, g->ori, g->packed, cb.lists[k], n[k], cb.count + k, cap, words, dmax,
                  scratch, hist, g->small->work[k], g->small->counters + k, overflow,
-                 n_overflow, s, g->nsm);
+                 n_overflow, g->close_mode == 2 ? 1 : 0, s, g->nsm);
     t_end(g);
   }
   HG_TRY(sync_small(g, &h));
@@ -988,7 +988,7 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
     t_begin(g, "close_wide");
     launch_close(kWideBucket, d, g->ori, g->packed, overflow, n_over, n_overflow, cap, words, dmax,
                  scratch, hist, g->small->work[kWideBucket], g->small->counters + 8,
-                 overflow, n_overflow, s, g->nsm);
+                 overflow, n_overflow, 0, s, g->nsm);
     t_end(g);
     HG_TRY(sync_small(g, &h));
   }

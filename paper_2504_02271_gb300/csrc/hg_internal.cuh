@@ -210,12 +210,13 @@ void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,
 void close_set_lut(const uint8_t lut[128], cudaStream_t s);
 // n: list length (host copy); n_p: the same on the device; counter: zeroed fetch counter;
 // work[0] += probes (entries of out(v) streamed), work[1] += E_y entries scanned for masks;
-// warp kernels append hyperedges their tables cannot hold to overflow[*n_overflow++]
+// warp kernels append hyperedges their tables cannot hold (every hyperedge when
+// handover is set) to overflow[*n_overflow++]
 void launch_close(int bucket, const DevGraph& g, const Oriented& o, int packed,
                   const int32_t* list, int32_t n, const int32_t* n_p, int64_t wide_cap,
                   int64_t wide_words, int64_t wide_dmax, void* scratch, unsigned long long* hist,
                   unsigned long long* work, int32_t* counter, int32_t* overflow,
-                  int32_t* n_overflow, cudaStream_t s, int nsm);
+                  int32_t* n_overflow, int handover, cudaStream_t s, int nsm);
 size_t close_wide_scratch_bytes(int64_t cap, int64_t words, int64_t dmax, int nsm);
 
 }  // namespace hg

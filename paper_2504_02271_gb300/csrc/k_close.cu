@@ -18,6 +18,7 @@
 // Their non-emptiness bits index a 128-entry table giving the pattern 1..20; a
 // block-local histogram is flushed to 64-bit global counters.
 #include <mutex>
+#include <type_traits>
 
 #include "hg_internal.cuh"
 
@@ -60,43 +61,67 @@ __device__ __forceinline__ int region_bits(int szu, int szv, int szw, int wuv, i
 // ------------------------------------------------------------------ warp per u
 //
 // One warp owns one hyperedge u with |e_u| <= 32 and out-degree <= D.  Shared
-// memory per warp holds a hash set of out(u) (load factor <= 1/2) with the
-// index of each member in out(u), a 16*D-bit filter that rejects most absent keys
-// with one load (only keys that pass it walk the linear-probing table), and
-// per-neighbour arrays (row start, out-degree, Omega_ux mask, |e_x|).  The
-// closure walks the concatenation of the out(v) lists as one flat range: lane l
-// takes flat entries base + l + 32 q, so each load instruction reads 32
+// memory per warp holds out(u) as a two-table cuckoo set: key x sits at slot
+// h1(x) of table 1 or at slot h2(x) of table 2 (2D slots each, so at most a
+// quarter of the slots are used), each slot packing x with its index k in out(u).
+// A lookup is two shared loads and two compares, the same on every lane: no
+// probing loop, no divergence.  Keys that insertion could not place within
+// kCuckooTries evictions go to a small stash that every lookup of the team also
+// scans; a team whose stash overflows is handed to the global-table teams.
+// Per-neighbour arrays hold the row start, out-degree, Omega_ux mask and |e_x|.
+// The closure walks the concatenation of the out(v) lists as one flat range:
+// lane l takes flat entries base + l + 32 q, so each load instruction reads 32
 // consecutive entries and every slot is full.  Hits are queued and classified
-// 32 at a time, so the classification runs with every lane active.  Shared-
-// memory traffic per probe is what bounds this kernel: a miss costs one load.
+// 32 at a time, so the classification runs with every lane active.
 
 constexpr int kUnroll = 4;
 constexpr int kQueue = 32 * kUnroll + 32;
+constexpr int kCuckooTries = 16;
+constexpr int kStash = 8;
 
-// Two layouts of the slot data.  Tables for out-degree up to 128 keep the Omega mask and
-// |e_x| per hash slot as well (a hit then needs no slot -> index load: these kernels are
-// issue-bound).  Tables for out-degree 256 keep only a slot -> index byte, so that more
-// warps fit an SM (that kernel is occupancy-bound).
 template <int D_LOG2, bool PACKED>
-struct WarpTables {
+struct alignas(16) WarpTables {
   static constexpr int D = 1 << D_LOG2;      // max out-degree of u
-  static constexpr int CAP = 2 * D;          // hash slots
-  static constexpr int FWORDS = D / 2;       // filter words (16 * D bits)
-  static constexpr bool kIndexed = D_LOG2 >= 8;
-  static_assert(D <= 256, "neighbour indices are queued in 8 bits");
-  int32_t key[CAP];
-  uint8_t kidx[kIndexed ? CAP : 1];          // slot -> index k of the key in out(u)
-  uint32_t mask[kIndexed ? 1 : CAP];         // slot -> Omega_ux
-  uint16_t size[kIndexed ? 1 : CAP];         // slot -> |e_x|
-  uint32_t filt[FWORDS];
+  static constexpr int T_LOG2 = D_LOG2 + 1;  // slots per cuckoo table
+  static constexpr int T = 1 << T_LOG2;
+  static_assert(D <= 256, "neighbour indices are packed in 8 bits");
+  // (x << 8) | k; all ones = empty.  Packed rows have x < 2^24.
+  using Item = typename std::conditional<PACKED, uint32_t, unsigned long long>::type;
+  Item c1[T];
+  Item c2[T];
+  Item stash[kStash];
   int64_t kbeg[D];
   int32_t kcnt[D];
   uint32_t kmask[D];                         // Omega_ux of the k-th out-neighbour x
   uint16_t ksz[D];                           // |e_x|
-  uint32_t queue[kQueue];                    // hits: (index of v << 24) | (w << 8) | omega, w the
-                                             // index of w (indexed layout) or its slot
+  uint32_t queue[kQueue];                    // hits: (k_v << 24) | (k_w << 8) | omega_vw
   int32_t qom[PACKED ? 1 : kQueue];          // omega_vw when it may not fit 8 bits
+  int32_t nstash;
 };
+
+__device__ __forceinline__ uint32_t cuckoo_h1(uint32_t key, int t_log2) {
+  return (key * 0x9E3779B1u) >> (32 - t_log2);
+}
+__device__ __forceinline__ uint32_t cuckoo_h2(uint32_t key, int t_log2) {
+  return (key * 0x85EBCA6Bu) >> (32 - t_log2);
+}
+
+// Index k in out(u) of hyperedge x, or -1.  Branch-free but for the stash scan,
+// whose length nst is the same on every lane of the warp.
+template <class TT>
+__device__ __forceinline__ int warp_find(const TT& t, int32_t x, int nst) {
+  using Item = typename TT::Item;
+  const uint32_t key = (uint32_t)x;
+  const Item a = t.c1[cuckoo_h1(key, TT::T_LOG2)];
+  const Item b = t.c2[cuckoo_h2(key, TT::T_LOG2)];
+  int k = (a >> 8) == (Item)key ? (int)(a & 0xffu) : -1;
+  k = (b >> 8) == (Item)key ? (int)(b & 0xffu) : k;
+  for (int i = 0; i < nst; ++i) {
+    const Item c = t.stash[i];
+    k = (c >> 8) == (Item)key ? (int)(c & 0xffu) : k;
+  }
+  return k;
+}
 
 __device__ __forceinline__ uint32_t filt_bit(uint32_t key, int bits_log2) {
   return (key * 0x85EBCA6Bu) >> (32 - bits_log2);
@@ -136,21 +161,17 @@ __device__ __forceinline__ void warp_flush(RunHist& rh, uint32_t* hist,
   __syncwarp();
 }
 
-// Classify queued hit number `at`: v is out-neighbour number kv of u; w is given by its
-// index (indexed layout) or its table slot.
+// Classify queued hit number `at`: v and w are out-neighbours number kv and kw of u.
 template <int D_LOG2, bool PACKED>
 __device__ __forceinline__ void classify_queued(const WarpTables<D_LOG2, PACKED>& t, int at,
                                                 int szu, const uint8_t* lut, uint32_t* hist,
                                                 RunHist& rh) {
-  using TT = WarpTables<D_LOG2, PACKED>;
   const uint32_t e = t.queue[at];
-  const uint32_t kv = e >> 24, w = (e >> 8) & 0xffffu;
+  const uint32_t kv = e >> 24, kw = (e >> 8) & 0xffu;
   const int om = PACKED ? (int)(e & 0xffu) : t.qom[at];
-  const uint32_t muv = t.kmask[kv];
-  const uint32_t muw = TT::kIndexed ? t.kmask[w] : t.mask[w];
-  const int szw = TT::kIndexed ? t.ksz[w] : t.size[w];
+  const uint32_t muv = t.kmask[kv], muw = t.kmask[kw];
   const int gg = __popc(muv & muw);
-  const int bits = region_bits(szu, t.ksz[kv], szw, __popc(muv), __popc(muw), om, gg);
+  const int bits = region_bits(szu, t.ksz[kv], t.ksz[kw], __popc(muv), __popc(muw), om, gg);
   rh.add(lut[bits], hist);
 }
 
@@ -159,11 +180,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
     k_close_warp(DevGraph g, Oriented o, const int32_t* __restrict__ list,
                  const int32_t* __restrict__ n_p, unsigned long long* __restrict__ hist_out,
                  unsigned long long* __restrict__ work, int32_t* __restrict__ counter,
-                 int32_t* __restrict__ overflow, int32_t* __restrict__ n_overflow) {
+                 int32_t* __restrict__ overflow, int32_t* __restrict__ n_overflow, int handover) {
   using TT = WarpTables<D_LOG2, PACKED>;
-  constexpr int CAP = TT::CAP, CAP_LOG2 = D_LOG2 + 1, FB_LOG2 = D_LOG2 + 4;
-  (void)overflow;
-  (void)n_overflow;   // linear probing at load <= 1/2 never overflows
+  using Item = typename TT::Item;
+  constexpr int T = TT::T, T_LOG2 = TT::T_LOG2;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   TT* tabs = reinterpret_cast<TT*>(dyn_smem);   // WARPS tables
   __shared__ uint32_t hist[WARPS][kBins];
@@ -195,8 +215,12 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
     const int64_t eb = g.e_ptr[u];
     const int32_t szu = (int32_t)(g.e_ptr[u + 1] - eb);
 
-    for (int s = lane; s < CAP; s += 32) t.key[s] = -1;
-    for (int s = lane; s < TT::FWORDS; s += 32) t.filt[s] = 0;
+    {   // both cuckoo tables to empty, 16 bytes per store
+      uint4* c = reinterpret_cast<uint4*>(t.c1);
+      constexpr int kVec = (int)(2 * T * sizeof(Item) / 16);
+      for (int s = lane; s < kVec; s += 32) c[s] = make_uint4(~0u, ~0u, ~0u, ~0u);
+    }
+    if (lane == 0) t.nstash = 0;
     // vertex y of e_u at lane p: its E_y range (one round trip for all p)
     int64_t yb = 0, ye = 0;
     if (lane < szu) {
@@ -205,7 +229,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
       ye = __ldg(g.v_ptr + y + 1);
     }
     __syncwarp();
-    // 1. out(u) into the table and the filter
+    // 1. out(u) into the cuckoo set
     int32_t my_cnt = 0;
     for (int k = lane; k < du; k += 32) {
       int32_t x, om;
@@ -213,23 +237,32 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
       const int64_t xb = __ldg(o.row_ptr + x);
       const int32_t xc = __ldg(o.dplus + x);
       const int32_t xs = __ldg(g.esize + x);
-      uint32_t s = slot_of((uint32_t)x, CAP_LOG2);
-      while (atomicCAS(&t.key[s], -1, x) != -1) s = (s + 1) & (CAP - 1);
-      if constexpr (TT::kIndexed) {
-        t.kidx[s] = (uint8_t)k;
-        t.kmask[k] = 0;
-        t.ksz[k] = (uint16_t)xs;
-      } else {
-        t.mask[s] = 0;
-        t.size[s] = (uint16_t)xs;
+      Item it = ((Item)(uint32_t)x << 8) | (Item)k;
+      bool second = false;   // the table the item in hand goes to next
+      for (int tries = 0; tries < kCuckooTries; ++tries) {
+        const uint32_t key = (uint32_t)(it >> 8);
+        Item* slot = second ? &t.c2[cuckoo_h2(key, T_LOG2)] : &t.c1[cuckoo_h1(key, T_LOG2)];
+        it = atomicExch(slot, it);
+        if (it == ~(Item)0) break;
+        second = !second;   // the evicted item sat at its own slot of this table
       }
-      const uint32_t fb = filt_bit((uint32_t)x, FB_LOG2);
-      atomicOr(&t.filt[fb >> 5], 1u << (fb & 31));
+      if (it != ~(Item)0) {
+        const int at = atomicAdd(&t.nstash, 1);
+        if (at < kStash) t.stash[at] = it;
+      }
+      t.kmask[k] = 0;
+      t.ksz[k] = (uint16_t)xs;
       t.kbeg[k] = xb;
       t.kcnt[k] = xc;
       my_cnt += xc;
     }
     __syncwarp();
+    const int nst = *((volatile int32_t*)&t.nstash);
+    if (nst > kStash || handover) {   // warp-uniform: the global-table teams take u
+      if (lane == 0) overflow[atomicAdd(n_overflow, 1)] = u;
+      __syncwarp();
+      continue;
+    }
     // 2. Omega_ux masks: flat walk over the E_y lists of the vertices of e_u
     {
       const int64_t len = ye - yb;   // lanes >= szu hold 0
@@ -255,26 +288,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
                                                           __shfl_sync(kFull, len, p));
         if (f >= total) continue;
         const int32_t x = __ldg(g.v_idx + start + f);
-        const uint32_t fb = filt_bit((uint32_t)x, FB_LOG2);
-        if (!((t.filt[fb >> 5] >> (fb & 31)) & 1u)) continue;
-        uint32_t s = slot_of((uint32_t)x, CAP_LOG2);
-        int32_t kk;
-        while ((kk = t.key[s]) != x && kk != -1) s = (s + 1) & (CAP - 1);
-        if (kk == x) {   // lanes may be at different p
-          if constexpr (TT::kIndexed) atomicOr(&t.kmask[t.kidx[s]], 1u << p);
-          else atomicOr(&t.mask[s], 1u << p);
-        }
-      }
-    }
-    __syncwarp();
-    if constexpr (!TT::kIndexed) {   // per-neighbour copies of mask and size
-      for (int k = lane; k < du; k += 32) {
-        int32_t x, om;
-        get_entry<PACKED>(o, bu + k, x, om);
-        uint32_t s = slot_of((uint32_t)x, CAP_LOG2);
-        while (t.key[s] != x) s = (s + 1) & (CAP - 1);
-        t.kmask[k] = t.mask[s];
-        t.ksz[k] = t.size[s];
+        const int kx = warp_find(t, x, nst);
+        if (kx >= 0) atomicOr(&t.kmask[kx], 1u << p);   // lanes may be at different p
       }
     }
     int32_t F = my_cnt;
@@ -311,26 +326,15 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
           }
         }
       }
-      // probe; hits go to the warp's queue as (v index, slot of w, omega_vw)
+      // probe; hits go to the warp's queue as (index of v, index of w, omega_vw)
 #pragma unroll
       for (int q = 0; q < kUnroll; ++q) {
-        const int32_t x = ent_w[q];
-        bool hit = false;
-        uint32_t s = 0;
-        if (x >= 0) {
-          const uint32_t fb = filt_bit((uint32_t)x, FB_LOG2);
-          if ((t.filt[fb >> 5] >> (fb & 31)) & 1u) {
-            s = slot_of((uint32_t)x, CAP_LOG2);
-            int32_t kk;
-            while ((kk = t.key[s]) != x && kk != -1) s = (s + 1) & (CAP - 1);
-            hit = kk == x;
-          }
-        }
+        const int kw = warp_find(t, ent_w[q], nst);   // -1 never matches a key
+        const bool hit = kw >= 0;
         const unsigned bal = __ballot_sync(kFull, hit);
         if (hit) {
           const int at = qn + __popc(bal & ((1u << lane) - 1u));
-          t.queue[at] = ((uint32_t)ent_k[q] << 24) |
-                        ((TT::kIndexed ? (uint32_t)t.kidx[s] : s) << 8) |
+          t.queue[at] = ((uint32_t)ent_k[q] << 24) | ((uint32_t)kw << 8) |
                         (PACKED ? (uint32_t)ent_om[q] : 0u);
           if (!PACKED) t.qom[at] = ent_om[q];
         }
@@ -884,8 +888,8 @@ __global__ void __launch_bounds__(kBucketThreads)
 template <int D_LOG2, int WARPS, bool PACKED>
 void launch_warp_t(const DevGraph& g, const Oriented& o, const int32_t* list, int32_t n,
                    const int32_t* n_p, unsigned long long* hist, unsigned long long* work,
-                   int32_t* counter, int32_t* overflow, int32_t* n_overflow, cudaStream_t s,
-                   int nsm) {
+                   int32_t* counter, int32_t* overflow, int32_t* n_overflow, int handover,
+                   cudaStream_t s, int nsm) {
   auto kern = k_close_warp<D_LOG2, WARPS, PACKED>;
   const int smem = (int)(WARPS * sizeof(WarpTables<D_LOG2, PACKED>));
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -896,20 +900,20 @@ void launch_warp_t(const DevGraph& g, const Oriented& o, const int32_t* list, in
   if (blocks > per_sm * nsm) blocks = per_sm * nsm;
   note_launch();
   kern<<<blocks, WARPS * 32, smem, s>>>(g, o, list, n_p, hist, work, counter, overflow,
-                                         n_overflow);
+                                         n_overflow, handover);
 }
 
 template <int D_LOG2, int WARPS>
 void launch_warp(const DevGraph& g, const Oriented& o, int packed, const int32_t* list, int32_t n,
                  const int32_t* n_p, unsigned long long* hist, unsigned long long* work,
-                 int32_t* counter, int32_t* overflow, int32_t* n_overflow, cudaStream_t s,
-                 int nsm) {
+                 int32_t* counter, int32_t* overflow, int32_t* n_overflow, int handover,
+                 cudaStream_t s, int nsm) {
   if (packed)
     launch_warp_t<D_LOG2, WARPS, true>(g, o, list, n, n_p, hist, work, counter, overflow,
-                                       n_overflow, s, nsm);
+                                       n_overflow, handover, s, nsm);
   else
     launch_warp_t<D_LOG2, WARPS, false>(g, o, list, n, n_p, hist, work, counter, overflow,
-                                        n_overflow, s, nsm);
+                                        n_overflow, handover, s, nsm);
 }
 
 template <int D_LOG2, int WARPS, bool PACKED>
@@ -972,20 +976,20 @@ void launch_close(int bucket, const DevGraph& g, const Oriented& o, int packed,
                   const int32_t* list, int32_t n, const int32_t* n_p, int64_t wide_cap,
                   int64_t wide_words, int64_t wide_dmax, void* scratch, unsigned long long* hist,
                   unsigned long long* work, int32_t* counter, int32_t* overflow,
-                  int32_t* n_overflow, cudaStream_t s, int nsm) {
+                  int32_t* n_overflow, int handover, cudaStream_t s, int nsm) {
   if (n <= 0) return;
   switch (bucket) {
     case 0:
-      launch_warp<6, 8>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow, s,
-                        nsm);
+      launch_warp<6, 8>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow,
+                        handover, s, nsm);
       break;
     case 1:
-      launch_warp<7, 6>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow, s,
-                        nsm);
+      launch_warp<7, 6>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow,
+                        handover, s, nsm);
       break;
     case 2:
-      launch_warp<8, 4>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow, s,
-                        nsm);
+      launch_warp<8, 4>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow,
+                        handover, s, nsm);
       break;
     case 3:
       launch_block<10, 16>(g, o, packed, list, n, n_p, hist, work, counter, s, nsm);

@@ -16,6 +16,7 @@ def gpu_count(hg, nv, e_ptr, e_idx, **kw):
     try:
         stats = hg.hg_build_wedges(g, **kw)
         counts = hg.hg_count_patterns(g)
+        stats["close"] = hg.hg_close_stats_get(g)
         cc1, open_, connected = hg.hg_clustering_coeff(g, [1.0] * 20)
     finally:
         hg.hg_free(g)
@@ -137,18 +138,25 @@ def test_counts_do_not_depend_on_the_oriented_layout(hglib, name):
         (gold["W"], gold["W_c"], gold["connected"], gold["open"])
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("name", ["tiny_plain", "coauthor_prefix50k"])
-def test_counts_do_not_depend_on_team_shape(hglib, name):
-    # every hyperedge through the block kernel gives the same counts as the
-    # out-degree/size buckets of warp kernels
+def test_counts_do_not_depend_on_team_shape(hglib, name, mode):
+    # every hyperedge through the global-table kernel (mode 1), or handed over to it
+    # by the warp teams after they built their cuckoo tables (mode 2, the path of a
+    # team whose stash overflows), gives the counts of the out-degree/size buckets
     import hgen
 
     gold = load_json("workloads.json")[name]
     e_ptr, e_idx = hgen.generate(hgen.WORKLOADS[gold["workload"]])
     if gold["prefix_edges"] is not None:
         e_ptr, e_idx = hgen.prefix(e_ptr, e_idx, gold["prefix_edges"])
-    counts, _ = gpu_count(hglib, gold["num_vertices"], e_ptr, e_idx, close_mode=1)
+    counts, st = gpu_count(hglib, gold["num_vertices"], e_ptr, e_idx, close_mode=mode)
     assert counts.tolist() == gold["counts"]
+    probes = st["close"]["bucket_probes"]
+    if mode == 2:   # the warp teams probed nothing; the global-table teams did it all
+        assert st["close"]["bucket_teams"][:3] != [0, 0, 0]
+        assert probes[:3] == [0, 0, 0] and probes[6] > 0
+    assert sum(probes) == st["close"]["probes"]
 
 
 def big_hyperedges(seed, ne, nv, lo, hi):
