@@ -87,10 +87,10 @@ typedef struct hg_tuning {
   int32_t dense_max_count; /* cap on the size of the dense set (0 = 1% of |E|) */
   int32_t close_mode;      /* step two team shape: 0 = by out-degree and |e_u| (warp
                               teams where they fit), 1 = global-table teams for every
-                              hyperedge, 2 = warp teams build their tables, then hand
-                              every hyperedge over to the global-table teams (the path
-                              a team whose cuckoo stash overflows takes); counts do not
-                              depend on it */
+                              hyperedge, 2 = warp and block teams build their tables,
+                              then hand every hyperedge over to the global-table teams
+                              (the path a team whose cuckoo stash overflows takes);
+                              counts do not depend on it */
   int32_t orient_exact;    /* 1 = oriented rows in an exact layout (W entries, one extra
                               counting pass); 0 = room for deg(i) per row (2W entries)
                               while that fits 8 GB.  Counts do not depend on it */

@@ -963,8 +963,12 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   int32_t n[kCloseBuckets];
   for (int k = 0; k < kCloseBuckets; ++k) n[k] = h.bucket_count[4 + k];
   // block-kernel scratch: any out-degree and |e_u| of bucket 3, and the warp
-  // buckets' limits (out-degree 256, |e_u| 32) for hyperedges they hand over
-  const int64_t dmax = std::max<int64_t>((int64_t)h.wide_max[0], 256);
+  // and block buckets' limits (the largest out-degree of a non-empty one, |e_u| 32) for
+  // hyperedges they hand over
+  int64_t team_dmax = 256;
+  for (int k = 3; k < kWideBucket; ++k)
+    if (n[k] > 0) team_dmax = int64_t(1024) << (k - 3);
+  const int64_t dmax = std::max<int64_t>((int64_t)h.wide_max[0], team_dmax);
   const int64_t words = std::max<int64_t>(((int64_t)h.wide_max[1] + 31) / 32, 1);
   int64_t cap = 16;
   while (cap < 2 * dmax) cap *= 2;

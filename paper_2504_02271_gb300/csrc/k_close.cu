@@ -361,50 +361,69 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
 
 // ------------------------------------------------------------------ block per u (shared tables)
 //
-// One block owns one hyperedge u with |e_u| <= 32 and out-degree <= D.  The hash
-// set of out(u) (load factor <= 1/2) maps a key to its index k in out(u); per-k
-// arrays hold the Omega_ux mask, |e_x| and the place and length of out(x).  The
-// flat range of all out(v) entries is cut into WARPS slices of equal length (by a
-// prefix sum over the out-degrees); each warp walks its slice like the warp
-// kernel (32 consecutive entries per load, filter, queue, 32-wide
-// classification).
+// One block owns one hyperedge u with |e_u| <= 32 and out-degree <= D.  out(u)
+// is a two-table cuckoo set with 2D slots per table.  A slot stores a key by
+// quotient: with the odd multiplier A of its table, p = x A mod 2^32 is a
+// bijection of x, the top T_LOG2 bits of p are the slot and the remaining
+// 31 - D_LOG2 bits are stored beside the index k of x in out(u), so 31 bits
+// identify (x, k) exactly and the top bit marks an empty slot.  An evicted key
+// is recovered from its slot and remainder with the inverse of A.  Keys not
+// placed within kCuckooTries evictions go to a stash; a team whose stash
+// overflows is handed to the global-table teams.  Per-k arrays hold the Omega_ux
+// mask, |e_x|, and the place and prefix-summed length of out(x).  The flat range
+// of all out(v) entries is cut into WARPS slices of equal length; each warp walks
+// its slice like the warp kernel (32 consecutive entries per load, lookup, queue,
+// 32-wide classification).
+
+constexpr uint32_t kCuckooA1 = 0x9E3779B1u, kCuckooA1Inv = 0x0E8B2F51u;
+constexpr uint32_t kCuckooA2 = 0x85EBCA6Bu, kCuckooA2Inv = 0xA5CB9243u;
+static_assert(kCuckooA1 * kCuckooA1Inv == 1u && kCuckooA2 * kCuckooA2Inv == 1u,
+              "multiplicative inverses mod 2^32");
 
 template <int D_LOG2, int WARPS, bool PACKED>
-struct BlockTables {
+struct alignas(16) BlockTables {
   static constexpr int D = 1 << D_LOG2;
-  static constexpr int CAP = 2 * D;
-  static constexpr int FWORDS = D / 2;
-  int32_t key[CAP];
-  uint16_t kidx[CAP];
-  uint32_t filt[FWORDS];
+  static constexpr int T_LOG2 = D_LOG2 + 1;
+  static constexpr int T = 1 << T_LOG2;
+  uint32_t c1[T];
+  uint32_t c2[T];
+  int32_t skey[kStash];
+  int32_t sidx[kStash];
   int64_t kbeg[D];
-  int32_t kcnt[D];
-  int32_t kpre[D + 1];       // exclusive prefix of kcnt
+  int32_t kpre[D + 1];       // exclusive prefix of the out-degrees of out(u)
   uint32_t kmask[D];
   uint16_t ksz[D];
   uint32_t queue[WARPS][kQueue];   // hits: (k_v << 16) | k_w ; omega in qom
   uint8_t qom8[PACKED ? WARPS : 1][PACKED ? kQueue : 1];
   int32_t qom[PACKED ? 1 : WARPS][PACKED ? 1 : kQueue];
   int64_t ylen[32], yincl[32], ybeg[32];
-  int32_t u, du, szu;
+  int32_t nstash;
 };
 
+// Index k in out(u) of hyperedge x, or -1 (x = -1 matches nothing: keys are < 2^31).
 template <int D_LOG2, int WARPS, bool PACKED>
-__device__ __forceinline__ int block_find(const BlockTables<D_LOG2, WARPS, PACKED>& t, int32_t x) {
-  constexpr int CAP = BlockTables<D_LOG2, WARPS, PACKED>::CAP;
-  uint32_t s = slot_of((uint32_t)x, D_LOG2 + 1);
-  int32_t kk;
-  while ((kk = t.key[s]) != x && kk != -1) s = (s + 1) & (CAP - 1);
-  return kk == x ? (int)t.kidx[s] : -1;
+__device__ __forceinline__ int block_find(const BlockTables<D_LOG2, WARPS, PACKED>& t, int32_t x,
+                                          int nst) {
+  constexpr int SH = 32 - (D_LOG2 + 1);   // remainder bits
+  constexpr uint32_t RM = (1u << SH) - 1u, KM = (1u << D_LOG2) - 1u;
+  const uint32_t p1 = (uint32_t)x * kCuckooA1, p2 = (uint32_t)x * kCuckooA2;
+  const uint32_t a = t.c1[p1 >> SH], b = t.c2[p2 >> SH];
+  int k = (a >> D_LOG2) == (p1 & RM) ? (int)(a & KM) : -1;
+  k = (b >> D_LOG2) == (p2 & RM) ? (int)(b & KM) : k;
+  for (int i = 0; i < nst; ++i) k = t.skey[i] == x ? t.sidx[i] : k;
+  return k;
 }
 
+// Tables up to out-degree 2048 leave room for two blocks per SM (at most 64 registers).
 template <int D_LOG2, int WARPS, bool PACKED>
-__global__ void __launch_bounds__(WARPS * 32, 1)
+__global__ void __launch_bounds__(WARPS * 32, D_LOG2 <= 11 ? 2 : 1)
     k_close_block(DevGraph g, Oriented o, const int32_t* __restrict__ list,
                   const int32_t* __restrict__ n_p, unsigned long long* __restrict__ hist_out,
-                  unsigned long long* __restrict__ work, int32_t* __restrict__ counter) {
+                  unsigned long long* __restrict__ work, int32_t* __restrict__ counter,
+                  int32_t* __restrict__ overflow, int32_t* __restrict__ n_overflow, int handover) {
   using TT = BlockTables<D_LOG2, WARPS, PACKED>;
-  constexpr int CAP = TT::CAP, CAP_LOG2 = D_LOG2 + 1, FB_LOG2 = D_LOG2 + 4;
+  constexpr int T = TT::T, SH = 32 - TT::T_LOG2;
+  constexpr uint32_t RM = (1u << SH) - 1u, KM = (1u << D_LOG2) - 1u;
   constexpr int NT = WARPS * 32;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   TT& t = *reinterpret_cast<TT*>(dyn_smem);
@@ -449,8 +468,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     const int64_t bu = o.row_ptr[u];
     const int64_t eb = g.e_ptr[u];
     const int32_t szu = (int32_t)(g.e_ptr[u + 1] - eb);
-    for (int s = threadIdx.x; s < CAP; s += NT) t.key[s] = -1;
-    for (int s = threadIdx.x; s < TT::FWORDS; s += NT) t.filt[s] = 0;
+    {   // both cuckoo tables to empty, 16 bytes per store
+      uint4* c = reinterpret_cast<uint4*>(t.c1);
+      for (int s = threadIdx.x; s < 2 * T / 4; s += NT) c[s] = make_uint4(~0u, ~0u, ~0u, ~0u);
+    }
+    if (threadIdx.x == 0) t.nstash = 0;
     if (w == 0) {   // E_y ranges of the vertices of e_u and their prefix sums
       int64_t yb = 0, len = 0;
       if (lane < szu) {
@@ -469,21 +491,44 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
       t.ybeg[lane] = yb;
     }
     __syncthreads();
-    // 1. out(u) into the table and the filter
+    // 1. out(u) into the cuckoo set; out-degrees into kpre[k + 1] for the prefix sum
     for (int k = threadIdx.x; k < du; k += NT) {
       int32_t x, om;
       get_entry<PACKED>(o, bu + k, x, om);
-      uint32_t s = slot_of((uint32_t)x, CAP_LOG2);
-      while (atomicCAS(&t.key[s], -1, x) != -1) s = (s + 1) & (CAP - 1);
-      t.kidx[s] = (uint16_t)k;
-      const uint32_t fb = filt_bit((uint32_t)x, FB_LOG2);
-      atomicOr(&t.filt[fb >> 5], 1u << (fb & 31));
+      uint32_t key = (uint32_t)x, kk = (uint32_t)k;
+      bool second = false, placed = false;
+      for (int tries = 0; tries < kCuckooTries; ++tries) {
+        const uint32_t pa = key * (second ? kCuckooA2 : kCuckooA1);
+        const uint32_t slot = pa >> SH;
+        uint32_t* c = second ? t.c2 : t.c1;
+        const uint32_t e = atomicExch(&c[slot], ((pa & RM) << D_LOG2) | kk);
+        if (e == ~0u) {
+          placed = true;
+          break;
+        }
+        // the evicted key sat at `slot` of this table: rebuild it from slot and remainder
+        key = ((slot << SH) | (e >> D_LOG2)) * (second ? kCuckooA2Inv : kCuckooA1Inv);
+        kk = e & KM;
+        second = !second;
+      }
+      if (!placed) {
+        const int at = atomicAdd(&t.nstash, 1);
+        if (at < kStash) {
+          t.skey[at] = (int32_t)key;
+          t.sidx[at] = (int32_t)kk;
+        }
+      }
       t.kbeg[k] = __ldg(o.row_ptr + x);
-      t.kcnt[k] = __ldg(o.dplus + x);
+      t.kpre[k + 1] = __ldg(o.dplus + x);
       t.ksz[k] = (uint16_t)__ldg(g.esize + x);
       t.kmask[k] = 0;
     }
     __syncthreads();
+    const int nst = t.nstash;   // read after a barrier: uniform
+    if (nst > kStash || handover) {   // the global-table teams take u
+      if (threadIdx.x == 0) overflow[atomicAdd(n_overflow, 1)] = u;
+      continue;
+    }
     // 2. Omega_ux masks over the flat E_y range; prefix of the out-degrees (warp 0)
     {
       const int64_t total = t.yincl[31];
@@ -496,27 +541,25 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         }
         const int p = lo;
         const int32_t x = __ldg(g.v_idx + t.ybeg[p] + (f - (t.yincl[p] - t.ylen[p])));
-        const uint32_t fb = filt_bit((uint32_t)x, FB_LOG2);
-        if (!((t.filt[fb >> 5] >> (fb & 31)) & 1u)) continue;
-        const int k = block_find(t, x);
+        const int k = block_find(t, x, nst);
         if (k >= 0) atomicOr(&t.kmask[k], 1u << p);
       }
     }
-    if (w == 0) {
+    if (w == 0) {   // in place: kpre[k + 1] holds the out-degree of out-neighbour k
       int32_t run = 0;
       for (int k0 = 0; k0 < du; k0 += 32) {
         const int k = k0 + lane;
-        const int32_t c = k < du ? t.kcnt[k] : 0;
+        const int32_t c = k < du ? t.kpre[k + 1] : 0;
         int32_t incl = c;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
           const int32_t o2 = __shfl_up_sync(kFull, incl, d);
           if (lane >= d) incl += o2;
         }
-        if (k < du) t.kpre[k] = run + incl - c;
+        if (k < du) t.kpre[k + 1] = run + incl;
         run += __shfl_sync(kFull, incl, 31);
       }
-      if (lane == 0) t.kpre[du] = run;
+      if (lane == 0) t.kpre[0] = 0;
     }
     __syncthreads();
     const int32_t F = t.kpre[du];
@@ -544,7 +587,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         ck = du;
       } else {
         cj = f0 - t.kpre[ck];
-        ccnt = t.kcnt[ck];
+        ccnt = t.kpre[ck + 1] - t.kpre[ck];
         cb = t.kbeg[ck];
       }
     }
@@ -560,19 +603,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         while (cj >= ccnt && ck < du) {
           cj -= ccnt;
           if (++ck < du) {
-            ccnt = t.kcnt[ck];
+            ccnt = t.kpre[ck + 1] - t.kpre[ck];
             cb = t.kbeg[ck];
           }
         }
       }
 #pragma unroll
       for (int q = 0; q < kUnroll; ++q) {
-        const int32_t x = ent_w[q];
-        int kw = -1;
-        if (x >= 0) {
-          const uint32_t fb = filt_bit((uint32_t)x, FB_LOG2);
-          if ((t.filt[fb >> 5] >> (fb & 31)) & 1u) kw = block_find(t, x);
-        }
+        const int kw = block_find(t, ent_w[q], nst);
         const bool hit = kw >= 0;
         const unsigned bal = __ballot_sync(kFull, hit);
         if (hit) {
@@ -919,7 +957,8 @@ void launch_warp(const DevGraph& g, const Oriented& o, int packed, const int32_t
 template <int D_LOG2, int WARPS, bool PACKED>
 void launch_block_t(const DevGraph& g, const Oriented& o, const int32_t* list, int32_t n,
                     const int32_t* n_p, unsigned long long* hist, unsigned long long* work,
-                    int32_t* counter, cudaStream_t s, int nsm) {
+                    int32_t* counter, int32_t* overflow, int32_t* n_overflow, int handover,
+                    cudaStream_t s, int nsm) {
   auto kern = k_close_block<D_LOG2, WARPS, PACKED>;
   const int smem = (int)sizeof(BlockTables<D_LOG2, WARPS, PACKED>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -928,17 +967,21 @@ void launch_block_t(const DevGraph& g, const Oriented& o, const int32_t* list, i
   if (per_sm < 1) per_sm = 1;
   int blocks = n < per_sm * nsm ? n : per_sm * nsm;
   note_launch();
-  kern<<<blocks, WARPS * 32, smem, s>>>(g, o, list, n_p, hist, work, counter);
+  kern<<<blocks, WARPS * 32, smem, s>>>(g, o, list, n_p, hist, work, counter, overflow,
+                                         n_overflow, handover);
 }
 
 template <int D_LOG2, int WARPS>
 void launch_block(const DevGraph& g, const Oriented& o, int packed, const int32_t* list, int32_t n,
                   const int32_t* n_p, unsigned long long* hist, unsigned long long* work,
-                  int32_t* counter, cudaStream_t s, int nsm) {
+                  int32_t* counter, int32_t* overflow, int32_t* n_overflow, int handover,
+                  cudaStream_t s, int nsm) {
   if (packed)
-    launch_block_t<D_LOG2, WARPS, true>(g, o, list, n, n_p, hist, work, counter, s, nsm);
+    launch_block_t<D_LOG2, WARPS, true>(g, o, list, n, n_p, hist, work, counter, overflow,
+                                        n_overflow, handover, s, nsm);
   else
-    launch_block_t<D_LOG2, WARPS, false>(g, o, list, n, n_p, hist, work, counter, s, nsm);
+    launch_block_t<D_LOG2, WARPS, false>(g, o, list, n, n_p, hist, work, counter, overflow,
+                                         n_overflow, handover, s, nsm);
 }
 
 }  // namespace
@@ -992,13 +1035,16 @@ void launch_close(int bucket, const DevGraph& g, const Oriented& o, int packed,
                         handover, s, nsm);
       break;
     case 3:
-      launch_block<10, 16>(g, o, packed, list, n, n_p, hist, work, counter, s, nsm);
+      launch_block<10, 16>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow,
+                            handover, s, nsm);
       break;
     case 4:
-      launch_block<11, 16>(g, o, packed, list, n, n_p, hist, work, counter, s, nsm);
+      launch_block<11, 16>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow,
+                            handover, s, nsm);
       break;
     case 5:
-      launch_block<12, 16>(g, o, packed, list, n, n_p, hist, work, counter, s, nsm);
+      launch_block<12, 16>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow,
+                            handover, s, nsm);
       break;
     default: {
       int blocks = n < nsm * kWideBlocksPerSm ? n : nsm * kWideBlocksPerSm;

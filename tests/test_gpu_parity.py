@@ -142,8 +142,9 @@ def test_counts_do_not_depend_on_the_oriented_layout(hglib, name):
 @pytest.mark.parametrize("name", ["tiny_plain", "coauthor_prefix50k"])
 def test_counts_do_not_depend_on_team_shape(hglib, name, mode):
     # every hyperedge through the global-table kernel (mode 1), or handed over to it
-    # by the warp teams after they built their cuckoo tables (mode 2, the path of a
-    # team whose stash overflows), gives the counts of the out-degree/size buckets
+    # by the warp and block teams after they built their cuckoo tables (mode 2, the
+    # path of a team whose stash overflows), gives the counts of the out-degree/size
+    # buckets
     import hgen
 
     gold = load_json("workloads.json")[name]
@@ -153,9 +154,9 @@ def test_counts_do_not_depend_on_team_shape(hglib, name, mode):
     counts, st = gpu_count(hglib, gold["num_vertices"], e_ptr, e_idx, close_mode=mode)
     assert counts.tolist() == gold["counts"]
     probes = st["close"]["bucket_probes"]
-    if mode == 2:   # the warp teams probed nothing; the global-table teams did it all
+    if mode == 2:   # the warp and block teams probed nothing; the global-table teams did it all
         assert st["close"]["bucket_teams"][:3] != [0, 0, 0]
-        assert probes[:3] == [0, 0, 0] and probes[6] > 0
+        assert probes[:6] == [0] * 6 and probes[6] > 0
     assert sum(probes) == st["close"]["probes"]
 
 
@@ -218,5 +219,7 @@ def test_block_teams_with_shared_tables(hglib):
     e_ptr, e_idx = hgen.generate(spec)
     shared, st = gpu_count(hglib, spec.num_vertices, e_ptr, e_idx)
     glob, _ = gpu_count(hglib, spec.num_vertices, e_ptr, e_idx, close_mode=1)
+    handed, st2 = gpu_count(hglib, spec.num_vertices, e_ptr, e_idx, close_mode=2)
     assert st["max_out_deg"] > 1024
-    assert shared.tolist() == glob.tolist()
+    assert shared.tolist() == glob.tolist() == handed.tolist()
+    assert sum(st["close"]["bucket_teams"][3:6]) > 0 and st2["close"]["bucket_probes"][:6] == [0] * 6
