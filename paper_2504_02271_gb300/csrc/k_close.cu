@@ -35,10 +35,6 @@ constexpr int kWideBlocksPerSm = 4;
 
 __constant__ uint8_t c_lut[128];
 
-__device__ __forceinline__ uint32_t slot_of(uint32_t key, int cap_log2) {
-  return (key * 0x9E3779B1u) >> (32 - cap_log2);
-}
-
 template <bool PACKED>
 __device__ __forceinline__ void get_entry(const Oriented& o, int64_t at, int32_t& nbr, int32_t& om) {
   if (PACKED) {
@@ -414,9 +410,8 @@ __device__ __forceinline__ int block_find(const BlockTables<D_LOG2, WARPS, PACKE
   return k;
 }
 
-// Tables up to out-degree 2048 leave room for two blocks per SM (at most 64 registers).
 template <int D_LOG2, int WARPS, bool PACKED>
-__global__ void __launch_bounds__(WARPS * 32, D_LOG2 <= 11 ? 2 : 1)
+__global__ void __launch_bounds__(WARPS * 32, 1)
     k_close_block(DevGraph g, Oriented o, const int32_t* __restrict__ list,
                   const int32_t* __restrict__ n_p, unsigned long long* __restrict__ hist_out,
                   unsigned long long* __restrict__ work, int32_t* __restrict__ counter,
@@ -657,30 +652,34 @@ __global__ void __launch_bounds__(WARPS * 32, D_LOG2 <= 11 ? 2 : 1)
 // ------------------------------------------------------------------ block per u (wide)
 // Any |e_u| (masks of `words` 32-bit words) and any out-degree; tables in global scratch.
 
-// Per block: the hash set of out(u) (key and the key's index k in out(u) per slot, load
-// factor <= 1/2) and per out-neighbour arrays (Omega_ux of `words` words, |e_x|, list
-// length and start).  Only the slots and the du rows of masks in use are cleared per u.
+// Per block: out(u) as a two-table cuckoo set coded by quotient like the block teams'
+// (2^(dl+1) slots per table for du <= 2^dl), a stash with room for every key (these
+// teams hand nothing over), and per out-neighbour arrays (Omega_ux of `words` words,
+// |e_x|, list length and start).  Only the slots and the du rows of masks in use are
+// cleared per u.
 struct WideScratch {
-  int32_t* key;     // [cap]
-  int32_t* kidx;    // [cap]
+  uint32_t* c1;     // [cap]
+  uint32_t* c2;     // [cap]
   uint32_t* mask;   // [dmax * words]
   int32_t* ksz;     // [dmax]
   int32_t* kcnt;    // [dmax]
   int64_t* kbeg;    // [dmax]
+  int32_t* skey;    // [dmax]
+  int32_t* sidx;    // [dmax]
 };
 
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 __host__ __device__ inline size_t wide_block_bytes(int64_t cap, int64_t words, int64_t dmax) {
-  return align256(cap * 4) * 2 + align256(dmax * words * 4) + align256(dmax * 4) * 2 +
+  return align256(cap * 4) * 2 + align256(dmax * words * 4) + align256(dmax * 4) * 4 +
          align256(dmax * 8);
 }
 
 __device__ WideScratch wide_carve(char* base, int64_t cap, int64_t words, int64_t dmax) {
   WideScratch w;
-  w.key = (int32_t*)base;
+  w.c1 = (uint32_t*)base;
   base += align256(cap * 4);
-  w.kidx = (int32_t*)base;
+  w.c2 = (uint32_t*)base;
   base += align256(cap * 4);
   w.mask = (uint32_t*)base;
   base += align256(dmax * words * 4);
@@ -689,7 +688,23 @@ __device__ WideScratch wide_carve(char* base, int64_t cap, int64_t words, int64_
   w.kcnt = (int32_t*)base;
   base += align256(dmax * 4);
   w.kbeg = (int64_t*)base;
+  base += align256(dmax * 8);
+  w.skey = (int32_t*)base;
+  base += align256(dmax * 4);
+  w.sidx = (int32_t*)base;
   return w;
+}
+
+// Index k in out(u) of hyperedge x in the tables of a team with du <= 2^dl, or -1.
+__device__ __forceinline__ int wide_find(const WideScratch& t, int32_t x, int dl, int nst) {
+  const int sh = 31 - dl;
+  const uint32_t rm = (1u << sh) - 1u, km = (1u << dl) - 1u;
+  const uint32_t p1 = (uint32_t)x * kCuckooA1, p2 = (uint32_t)x * kCuckooA2;
+  const uint32_t a = t.c1[p1 >> sh], b = t.c2[p2 >> sh];
+  int k = (a >> dl) == (p1 & rm) ? (int)(a & km) : -1;
+  k = (b >> dl) == (p2 & rm) ? (int)(b & km) : k;
+  for (int i = 0; i < nst; ++i) k = t.skey[i] == x ? t.sidx[i] : k;
+  return k;
 }
 
 template <bool PACKED>
@@ -702,6 +717,7 @@ __global__ void __launch_bounds__(kWideThreads, kWideBlocksPerSm)
   __shared__ uint8_t lut[128];
   __shared__ int32_t s_r;
   __shared__ unsigned long long s_since;   // probes since the last flush (block-wide)
+  __shared__ int32_t s_nstash;
   // out(u) membership filter: 16 bits per key up to 16,384 keys (fewer beyond), so that
   // most absent keys are rejected without touching the table in global memory
   __shared__ uint32_t filt[(1 << kWideFilterLog2) / 32];
@@ -745,28 +761,51 @@ __global__ void __launch_bounds__(kWideThreads, kWideBlocksPerSm)
     const int32_t szu = (int32_t)(g.e_ptr[u + 1] - eb);
     const int32_t words = (szu + 31) / 32;
     if (threadIdx.x == 0) outs += (unsigned long long)du;
-    int cl = 4;
-    while ((int64_t(1) << cl) < 2 * (int64_t)du) ++cl;
-    const uint32_t cap = 1u << cl;
+    int dl = 4;   // du <= 2^dl; 2^(dl+1) slots per cuckoo table
+    while ((int64_t(1) << dl) < (int64_t)du) ++dl;
+    const uint32_t tslots = 2u << dl;
+    const int sh = 31 - dl;
+    const uint32_t rm = (1u << sh) - 1u, km = (1u << dl) - 1u;
     int fl = 5;   // filter bits: 2^fl >= 16 du, at most 2^kWideFilterLog2
     while (fl < kWideFilterLog2 && (int64_t(1) << fl) < 16 * (int64_t)du) ++fl;
-    for (uint32_t s = threadIdx.x; s < cap; s += kWideThreads) t.key[s] = -1;
+    for (uint32_t s = threadIdx.x; s < tslots; s += kWideThreads) {
+      t.c1[s] = ~0u;
+      t.c2[s] = ~0u;
+    }
     for (int64_t s = threadIdx.x; s < (int64_t)du * words; s += kWideThreads) t.mask[s] = 0;
     for (int s = threadIdx.x; s < (1 << fl) / 32; s += kWideThreads) filt[s] = 0;
+    if (threadIdx.x == 0) s_nstash = 0;
     __syncthreads();
     for (int k = threadIdx.x; k < du; k += kWideThreads) {
       int32_t x, om;
       get_entry<PACKED>(o, bu + k, x, om);
       const uint32_t fb = filt_bit((uint32_t)x, fl);
       atomicOr(&filt[fb >> 5], 1u << (fb & 31));
-      uint32_t s = slot_of((uint32_t)x, cl);
-      while (atomicCAS(&t.key[s], -1, x) != -1) s = (s + 1) & (cap - 1);
-      t.kidx[s] = k;
+      uint32_t key = (uint32_t)x, kk = (uint32_t)k;
+      bool second = false, placed = false;
+      for (int tries = 0; tries < kCuckooTries; ++tries) {
+        const uint32_t pa = key * (second ? kCuckooA2 : kCuckooA1);
+        const uint32_t slot = pa >> sh;
+        const uint32_t e = atomicExch(second ? &t.c2[slot] : &t.c1[slot], ((pa & rm) << dl) | kk);
+        if (e == ~0u) {
+          placed = true;
+          break;
+        }
+        key = ((slot << sh) | (e >> dl)) * (second ? kCuckooA2Inv : kCuckooA1Inv);
+        kk = e & km;
+        second = !second;
+      }
+      if (!placed) {   // room for every key: du <= dmax
+        const int at = atomicAdd(&s_nstash, 1);
+        t.skey[at] = (int32_t)key;
+        t.sidx[at] = (int32_t)kk;
+      }
       t.ksz[k] = __ldg(g.esize + x);
       t.kbeg[k] = __ldg(o.row_ptr + x);
       t.kcnt[k] = __ldg(o.dplus + x);
     }
     __syncthreads();
+    const int nst = s_nstash;   // read after a barrier: uniform
     for (int p = w; p < szu; p += kW) {
       const int32_t y = __ldg(g.e_idx + eb + p);
       const int64_t yb = __ldg(g.v_ptr + y), ye = __ldg(g.v_ptr + y + 1);
@@ -775,10 +814,8 @@ __global__ void __launch_bounds__(kWideThreads, kWideBlocksPerSm)
         const int32_t x = __ldg(g.v_idx + q);
         const uint32_t fb = filt_bit((uint32_t)x, fl);
         if (!((filt[fb >> 5] >> (fb & 31)) & 1u)) continue;
-        uint32_t s = slot_of((uint32_t)x, cl);
-        int32_t kk;
-        while ((kk = *((volatile int32_t*)&t.key[s])) != x && kk != -1) s = (s + 1) & (cap - 1);
-        if (kk == x) atomicOr(&t.mask[(size_t)t.kidx[s] * words + (p >> 5)], 1u << (p & 31));
+        const int kx = wide_find(t, x, dl, nst);
+        if (kx >= 0) atomicOr(&t.mask[(size_t)kx * words + (p >> 5)], 1u << (p & 31));
       }
     }
     __syncthreads();
@@ -809,11 +846,8 @@ __global__ void __launch_bounds__(kWideThreads, kWideBlocksPerSm)
           if (x < 0) continue;
           const uint32_t fb = filt_bit((uint32_t)x, fl);
           if (!((filt[fb >> 5] >> (fb & 31)) & 1u)) continue;
-          uint32_t s = slot_of((uint32_t)x, cl);
-          int32_t kk;
-          while ((kk = t.key[s]) != x && kk != -1) s = (s + 1) & (cap - 1);
-          if (kk != x) continue;
-          const int kw = t.kidx[s];
+          const int kw = wide_find(t, x, dl, nst);
+          if (kw < 0) continue;
           const uint32_t* muw = t.mask + (size_t)kw * words;
           int wuw = 0, gg = 0;
           for (int qq = 0; qq < words; ++qq) {
