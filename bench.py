@@ -207,11 +207,11 @@ def close_algorithmic(cs, b, T):
     """Algorithmic work of the closure kernels of team shape b in one launch.
 
     Per probe (an entry of out(v) looked up in u's table): 4 bytes read, 8 integer
-    operations (decode 2, hash 2, filter 4).  Per out-entry of u: 20 bytes (entry,
-    row start, out-degree, |e_x|) and 10 operations (table insert).  Per E_y entry
-    read for the vertex masks: 4 bytes and 8 operations.  Per hyper-triangle: 27
-    operations (table probe 5, seven region tests 20, histogram 2); the triangles of
-    shape b are taken in proportion to its probes.
+    operations (decode 2, two hashes 2, two slot compares 4).  Per out-entry of u:
+    20 bytes (entry, row start, out-degree, |e_x|) and 10 operations (table insert).
+    Per E_y entry read for the vertex masks: 4 bytes and 8 operations.  Per
+    hyper-triangle: 27 operations (index and mask loads 5, seven region tests 20,
+    histogram 2); the triangles of shape b are taken in proportion to its probes.
     """
     probes, gathers, outs = cs["bucket_probes"][b], cs["bucket_gathers"][b], cs["bucket_out_entries"][b]
     hits = T * probes / max(cs["probes"], 1)
