@@ -113,6 +113,10 @@ typedef struct hg_wedge_stats {
  * its type (Def. 2.3), then the degree-ordered orientation used by step two.
  * opt may be NULL.  out may be NULL.  Rejects equal hyperedges with
  * HG_ERR_DUPLICATE_HYPEREDGE.  May be called again; it rebuilds.  Synchronises.
+ * A tuning field out of its range (close_mode not 0-2, orient_exact not 0-1) is
+ * rejected with HG_ERR_INVALID_ARG before anything changes: a built handle stays
+ * built.  Any other error leaves the handle unbuilt (counting then answers
+ * HG_ERR_STATE until a build succeeds).
  */
 hg_status hg_build_wedges(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out);
 
@@ -320,7 +324,8 @@ hg_status hg_load_batch_members(int32_t num_graphs, const int32_t* num_vertices,
                                 const int32_t* const* edge_vtxs, int inputs_on_device,
                                 int64_t max_wave_edges, void* cuda_stream, hg_batch** out);
 
-/* Step one (as hg_build_wedges) on every wave.  opt may be NULL.  Synchronises. */
+/* Step one (as hg_build_wedges) on every wave.  opt may be NULL; an out-of-range
+ * tuning is rejected with HG_ERR_INVALID_ARG before anything changes.  Synchronises. */
 hg_status hg_batch_build_wedges(hg_batch* b, const hg_tuning* opt);
 
 /*

@@ -502,10 +502,15 @@ void release_sampling(hg_graph* g) {
 
 constexpr int64_t kOrientSlackBytes = int64_t(8) << 30;   // oriented rows with room for deg(i)
 
+// The tuning fields that have a closed range (checked before a build changes anything).
+bool tuning_ok(const hg_tuning* opt) {
+  if (!opt) return true;
+  return opt->close_mode >= 0 && opt->close_mode <= 2 && opt->orient_exact >= 0 &&
+         opt->orient_exact <= 1;
+}
+
 hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   g->close_mode = opt ? opt->close_mode : 0;
-  if (g->close_mode < 0 || g->close_mode > 2) return HG_ERR_INVALID_ARG;
-  if (opt && (opt->orient_exact < 0 || opt->orient_exact > 1)) return HG_ERR_INVALID_ARG;
   cudaStream_t s = g->stream;
   release(g, g->count_blocks);
   release_sampling(g);
@@ -1210,7 +1215,7 @@ hg_status hg_load_csr(int32_t num_vertices, int32_t num_edges, const int64_t* ed
 }
 
 hg_status hg_build_wedges(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
-  if (!g) return HG_ERR_INVALID_ARG;
+  if (!g || !tuning_ok(opt)) return HG_ERR_INVALID_ARG;   // the handle stays as it was
   hg_status st = build_impl(g, opt, out);
   if (st != HG_OK) {
     cudaStreamSynchronize(g->stream);
@@ -1425,7 +1430,7 @@ hg_status hg_load_batch_members(int32_t num_graphs, const int32_t* num_vertices,
 }
 
 hg_status hg_batch_build_wedges(hg_batch* b, const hg_tuning* opt) {
-  if (!b) return HG_ERR_INVALID_ARG;
+  if (!b || !tuning_ok(opt)) return HG_ERR_INVALID_ARG;   // the batch stays as it was
   b->built = b->counted = false;
   for (hg_graph* g : b->waves) {
     hg_status st = hg_build_wedges(g, opt, nullptr);

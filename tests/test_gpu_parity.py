@@ -160,6 +160,53 @@ def test_counts_do_not_depend_on_team_shape(hglib, name, mode):
     assert sum(probes) == st["close"]["probes"]
 
 
+def test_cuckoo_stash_and_handover(hglib):
+    # Hyperedge ids that land on the same slot of both cuckoo tables of an
+    # out-degree-64 warp team (the top 7 bits of x*A1 and of x*A2 mod 2^32 agree).
+    # Thirteen hyperedges through one hub vertex, u = id 1 and twelve such ids, make a
+    # clique ranked by id: the team of the k-th colliding id holds 11 - k of them, so
+    # teams with 3..10 colliding keys scan the stash and teams with 11 or 12 overflow
+    # it and are handed to the global-table teams.  Counts must equal the oracle's.
+    M, A1, A2 = 0xFFFFFFFF, 0x9E3779B1, 0x85EBCA6B
+    ids = [55818, 79684, 103550, 126573, 127416, 128259, 150439, 151282, 152125, 174305,
+           175148, 175991]
+    slots = {(((x * A1) & M) >> 25, ((x * A2) & M) >> 25) for x in ids}
+    assert len(slots) == 1
+    ne = 180_000
+    edges = [[1000 + i] for i in range(ne)]   # singletons on private vertices
+    edges[1] = [0, 1, 2, 400]
+    for i, x in enumerate(ids):
+        edges[x] = [0, 500 + i, 1 + i % 3]
+    e_ptr, e_idx = csr_of(edges)
+    counts, st = check_against_oracle(hglib, 1000 + ne, e_ptr, e_idx)
+    assert int(counts[0]) == 286   # C(13, 3): every triple shares the hub
+    probes = st["close"]["bucket_probes"]
+    assert probes[0] > 0 and probes[6] > 0   # some teams closed in place, some handed over
+    # exactly the teams with 12 and 11 colliding keys overflow (2 slots + 8 stashed)
+    assert st["close"]["bucket_teams"][6] == 2
+
+
+def test_rejected_tuning_leaves_the_handle_usable(hglib):
+    import torch
+
+    e_ptr, e_idx = csr_of([[0, 1], [1, 2], [0, 2], [2, 3]])
+    stream = torch.cuda.Stream()
+    g = hglib.hg_load_csr(4, len(e_ptr) - 1, e_ptr, e_idx, stream=stream.cuda_stream)
+    try:
+        hglib.hg_build_wedges(g)
+        before = hglib.hg_count_patterns(g)
+        for bad in ({"close_mode": 3}, {"close_mode": -1}, {"orient_exact": 2}):
+            with pytest.raises(hglib.HgError) as ei:
+                hglib.hg_build_wedges(g, **bad)
+            assert ei.value.name == "HG_ERR_INVALID_ARG"
+        assert hglib.hg_count_patterns(g).tolist() == before.tolist()
+    finally:
+        hglib.hg_free(g)
+    import oracle
+
+    assert before.tolist() == [int(x) for x in oracle.count(e_ptr, e_idx, 4).counts]
+
+
 def big_hyperedges(seed, ne, nv, lo, hi):
     import hgen
 
