@@ -4,10 +4,10 @@
 // Every hyper-triangle {e_u, e_v, e_w} (Def. 2.4) is found exactly once, from
 // its lowest-ranked hyperedge u in the degree order: v and w are both
 // out-neighbours of u, and w is an out-neighbour of v.  The team that owns u
-//   1. inserts out(u) into a hash table (key w -> slot),
+//   1. inserts out(u) into a two-table cuckoo set (key x -> its index k in out(u)),
 //   2. records for every out-neighbour x the set Omega_ux = e_u cap e_x as a bit
 //      mask over the positions of e_u (scanning E_y for each vertex y of e_u),
-//   3. streams out(v) for every v in out(u) and probes each w in the table.
+//   3. streams out(v) for every v in out(u) and looks each w up in the set.
 // A hit is a hyper-triangle.  With m_uv, m_uw the masks,
 //   g = |e_u cap e_v cap e_w| = popc(m_uv & m_uw),  omega_uv = popc(m_uv),
 //   omega_uw = popc(m_uw),  omega_vw from the entry of out(v),
