@@ -160,6 +160,29 @@ def test_counts_do_not_depend_on_team_shape(hglib, name, mode):
     assert sum(probes) == st["close"]["probes"]
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_unpacked_rows_every_team_shape(hglib, mode):
+    # three hyperedges of 300 vertices make omega exceed 8 bits, so rows are two int32
+    # arrays and the warp and block teams keep 64-bit cuckoo items; the small hyperedges
+    # still close in warp teams (out-degree <= 64, <= 128, <= 256) and 1024-teams
+    import hgen
+    import oracle
+
+    e_ptr, e_idx = hgen.prefix(*hgen.generate(hgen.TINY_PLAIN), 600)
+    edges = [e_idx[e_ptr[i]:e_ptr[i + 1]].tolist() for i in range(len(e_ptr) - 1)]
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        edges.append(rng.choice(1000, 300, replace=False).tolist())
+    e_ptr, e_idx = csr_of(edges)
+    counts, st = gpu_count(hglib, 1000, e_ptr, e_idx, close_mode=mode)
+    ref = oracle.count(e_ptr, e_idx, 1000)
+    assert counts.tolist() == [int(x) for x in ref.counts]
+    assert (st["W"], st["W_c"], st["connected"]) == (ref.W, ref.W_c, ref.connected)
+    if mode == 0:
+        teams = st["close"]["bucket_teams"]
+        assert all(teams[k] > 0 for k in (0, 1, 2, 3, 6)), teams
+
+
 def test_cuckoo_stash_and_handover(hglib):
     # Hyperedge ids that land on the same slot of both cuckoo tables of an
     # out-degree-64 warp team (the top 7 bits of x*A1 and of x*A2 mod 2^32 agree).
