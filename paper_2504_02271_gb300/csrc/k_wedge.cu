@@ -126,11 +126,34 @@ __global__ void __launch_bounds__(kLightWarps * 32)
     __syncwarp();
     const int32_t hi = dn.heavy_idx ? dn.heavy_idx[i] : -1;
     const int64_t b = g.e_ptr[i], e = g.e_ptr[i + 1];
-    for (int64_t p = b; p < e; ++p) {
-      const int32_t v = g.e_idx[p];
-      const int64_t vb = g.v_ptr[v], ve = g.v_ptr[v + 1];
-      for (int64_t q = vb + lane; q < ve; q += 32) {
-        const int32_t j = g.v_idx[q];
+    // 32 vertices of e_i at a time: their E_v ranges in one round trip (lane l holds
+    // vertex p0 + l), then the concatenated lists as one flat range, 32 entries per step
+    for (int64_t p0 = b; p0 < e; p0 += 32) {
+      int64_t yb = 0, len = 0;
+      if (p0 + lane < e) {
+        const int32_t v = g.e_idx[p0 + lane];
+        yb = g.v_ptr[v];
+        len = g.v_ptr[v + 1] - yb;
+      }
+      int64_t incl = len;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int64_t o2 = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += o2;
+      }
+      const int64_t total = __shfl_sync(kFull, incl, 31);
+      for (int64_t f0 = 0; f0 < total; f0 += 32) {   // warp-uniform: all lanes shuffle
+        const int64_t f = f0 + lane;
+        int lo = 0, hi2 = 31;   // owner: first lane whose inclusive prefix exceeds f
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {
+          const int mid = (lo + hi2) >> 1;
+          if (__shfl_sync(kFull, incl, mid) > f) hi2 = mid; else lo = mid + 1;
+        }
+        const int64_t start = __shfl_sync(kFull, yb, lo) - (__shfl_sync(kFull, incl, lo) -
+                                                           __shfl_sync(kFull, len, lo));
+        if (f >= total) continue;
+        const int32_t j = g.v_idx[start + f];
         if (j != i && gather_pair(dn, hi, j)) ht_add(T, cl, (uint32_t)j);
       }
     }
@@ -196,8 +219,8 @@ __global__ void __launch_bounds__(kBlockThreads)
   __shared__ int32_t s_row;
   __shared__ int32_t s_cnt, s_up, s_incl;
   __shared__ unsigned long long s_wc;
+  __shared__ int64_t s_ybeg[32], s_yincl[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  constexpr int kWarps = kBlockThreads / 32;
   const int32_t nrows = *nrows_p;
   if (threadIdx.x == 0) s_wc = 0;
   unsigned long long my_wc = 0;
@@ -219,13 +242,38 @@ __global__ void __launch_bounds__(kBlockThreads)
     __syncthreads();
     const int32_t hi = dn.heavy_idx ? dn.heavy_idx[i] : -1;
     const int64_t b = g.e_ptr[i], e = g.e_ptr[i + 1];
-    for (int64_t p = b + w; p < e; p += kWarps) {
-      const int32_t v = g.e_idx[p];
-      const int64_t vb = g.v_ptr[v], ve = g.v_ptr[v + 1];
-      for (int64_t q = vb + lane; q < ve; q += 32) {
-        const int32_t j = g.v_idx[q];
+    // 32 vertices of e_i at a time: warp 0 puts their E_v ranges and prefix sums in
+    // shared memory, then every thread takes flat positions of the concatenated lists
+    for (int64_t p0 = b; p0 < e; p0 += 32) {   // block-uniform
+      if (w == 0) {
+        int64_t yb = 0, len = 0;
+        if (p0 + lane < e) {
+          const int32_t v = g.e_idx[p0 + lane];
+          yb = g.v_ptr[v];
+          len = g.v_ptr[v + 1] - yb;
+        }
+        int64_t incl = len;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int64_t o2 = __shfl_up_sync(kFull, incl, d);
+          if (lane >= d) incl += o2;
+        }
+        s_ybeg[lane] = yb - (incl - len);   // flat position f of this list maps to s_ybeg + f
+        s_yincl[lane] = incl;
+      }
+      __syncthreads();
+      const int64_t total = s_yincl[31];
+      for (int64_t f = threadIdx.x; f < total; f += kBlockThreads) {
+        int lo = 0, hi2 = 31;   // owner: first vertex whose inclusive prefix exceeds f
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {
+          const int mid = (lo + hi2) >> 1;
+          if (s_yincl[mid] > f) hi2 = mid; else lo = mid + 1;
+        }
+        const int32_t j = g.v_idx[s_ybeg[lo] + f];
         if (j != i && gather_pair(dn, hi, j)) ht_add(T, cl, (uint32_t)j);
       }
+      __syncthreads();   // the next chunk rewrites the ranges
     }
     if (hi >= 0) {
       for (int32_t h = threadIdx.x; h < dn.nh; h += kBlockThreads) {
