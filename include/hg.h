@@ -146,7 +146,7 @@ hg_status hg_count_patterns(hg_graph* g, uint64_t counts[21]);
  * Disjoint sample ranges with the same seed are independent draws, so split runs
  * sum to one run over the union (raw exactly).  Builds the sorted neighbour rows
  * on the first call after hg_build_wedges (W extra entries of device memory).
- * sigma in (0, 1] (line 2 of Algorithm 6): with sigma < 1 everything above runs on
+ * sigma in (0, 1] (the sigma|E| draw of Algorithm 6): with sigma < 1 everything above runs on
  * the sub-hypergraph G' of the ceil(sigma |E|) hyperedges with the smallest
  * priorities r_i = x1 * 2^32 + x0 of Philox4x32-10(counter (i, 0, 1, 0), key as
  * above) (ties by id), renumbered in id order; W is then G''s, and est[p] =
@@ -164,7 +164,7 @@ hg_status hg_sample_estimate(hg_graph* g, uint64_t seed, uint64_t first_sample,
  * Class-targeted sampling estimate (Sec. 4.2, Algorithm 7, "Appro-adv").  On G (or on
  * G' for sigma < 1, as above) the hyperwedges split into W^t (intersection type) and
  * W^c (inclusion type) (Def. 2.3), each numbered in the order O.  The num_samples = alpha
- * draws are shared out as in line 4, as exact integer floors:
+ * draws are shared out as Algorithm 7 states, as exact integer floors:
  *   set 1: alpha_1 = |W^t|^2 alpha / |W|^2 draws from W^t, counting the TTT class (9-20)
  *   set 2: alpha_2 = |W^c|^2 alpha / |W|^2 draws from W^c, counting CCC (1)
  *   set 3: alpha_3 = |W^t||W^c| alpha / |W|^2 draws from W^t, counting TTC (6-8)

@@ -233,7 +233,7 @@ def enumerate_pattern(e_ptr, e_idx, num_vertices: int, pattern: int, mode: str =
 
 def subgraph(num_edges: int, seed: int, sigma: float) -> np.ndarray:
     """Ids (ascending) of the hyperedges kept in G' for sampling proportion sigma
-    (Algorithms 6-7, line 2): the ceil(sigma |E|) smallest Philox priorities."""
+    (Algorithms 6-7, the sigma|E| draw): the ceil(sigma |E|) smallest Philox priorities."""
     kept = np.zeros(max(num_edges, 1), dtype=np.int32)
     n = _load().oracle_subgraph(int(num_edges), seed & (2**64 - 1), float(sigma), kept.ctypes.data)
     if n < 0:

@@ -367,7 +367,7 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
   out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-// The sub-hypergraph G' of Algorithms 6 and 7 (line 2: sigma|E| hyperedges drawn
+// The sub-hypergraph G' of Algorithms 6 and 7 (their first step: sigma|E| hyperedges drawn
 // uniformly at random).  Reading: hyperedge i gets the priority
 // r_i = x1 << 32 | x0 of Philox4x32-10(counter = (i, 0, 1, 0), key = (seed lo, seed hi));
 // G' keeps the ceil(sigma * |E|) hyperedges with the smallest (r_i, i), renumbered
@@ -524,7 +524,7 @@ int oracle_sample_estimate(int32_t nv, int32_t ne, const int64_t* e_ptr, const i
 
 // Appro-adv (Algorithm 7).  On G' (oracle_subgraph), the hyperwedges split into
 // W^t (intersection type) and W^c (inclusion type) (Def. 2.3), each in the order O.
-// The alpha samples are shared out as in line 4, floors of exact integer quotients:
+// The alpha samples are shared out as Algorithm 7 states, floors of exact integer quotients:
 //   alpha_1 = |W^t|^2 alpha / |W|^2     TTT class, drawn from W^t
 //   alpha_2 = |W^c|^2 alpha / |W|^2     CCC class, drawn from W^c
 //   alpha_3 = |W^t||W^c| alpha / |W|^2  TTC class, drawn from W^t

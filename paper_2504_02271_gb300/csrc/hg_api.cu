@@ -106,7 +106,7 @@ struct hg_graph {
   int32_t* c_index = nullptr;
   Oriented t_ent{}, c_ent{}, full{};
   uint64_t Wt = 0, Wc = 0;
-  // the sub-hypergraph G' for sigma < 1 (Algorithms 6-7, line 2), kept for its seed
+  // the sub-hypergraph G' for sigma < 1 (Algorithms 6-7, the sigma|E| draw), kept for its seed
   hg_graph* sub = nullptr;
   uint64_t sub_seed = 0;
   double sub_sigma = 1.0;
@@ -749,7 +749,7 @@ hg_status adv_impl(hg_graph* g) {
   return HG_OK;
 }
 
-// G' (Algorithms 6-7, line 2): the ceil(sigma |E|) hyperedges with the smallest Philox
+// G' (Algorithms 6-7, the sigma|E| draw): the ceil(sigma |E|) hyperedges with the smallest Philox
 // priorities (ties by id), renumbered in id order, as a handle of its own with step one
 // built.  The k-th smallest priority is found by a 4-pass radix select (16-bit digits).
 hg_status subgraph_impl(hg_graph* g, uint64_t seed, double sigma) {
@@ -843,7 +843,7 @@ hg_status sample_adv_impl(hg_graph* g, uint64_t seed, uint64_t first, uint64_t n
   sample_set_lut(lut, s);
   const uint64_t Wt = g->Wt, Wc = g->Wc, W = Wt + Wc;
   uint64_t alpha[4] = {0, 0, 0, 0};
-  if (W > 0) {   // Algorithm 7, line 4: exact floors
+  if (W > 0) {   // Algorithm 7's sample split: exact floors
     const unsigned __int128 den = (unsigned __int128)W * W;
     alpha[0] = (uint64_t)((unsigned __int128)Wt * Wt * num / den);
     alpha[1] = (uint64_t)((unsigned __int128)Wc * Wc * num / den);

@@ -141,7 +141,7 @@ def test_adv_estimate_is_unbiased(small):
         assert abs(mean - float(exact.counts[p])) < 4 * se + 1e-9, p
 
 
-# ------------------------------------------------------------------ sigma < 1 (line 2)
+# ------------------------------------------------------------------ sigma < 1 (the sigma|E| draw)
 
 def test_subgraph_selection(small):
     import math
@@ -165,7 +165,7 @@ def test_subgraph_selection(small):
 
 def test_sigma_estimates_run_on_the_sub_hypergraph(small):
     # every hyperwedge of G' once: raw = the exact counts of the explicitly built G',
-    # est = raw / sigma^3 (Algorithms 6 and 7, line 2 and the final scaling)
+    # est = raw / sigma^3 (Algorithms 6 and 7: the sigma|E| draw and the final scaling)
     import oracle
 
     e_ptr, e_idx, nv = small
