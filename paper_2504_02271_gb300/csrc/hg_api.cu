@@ -428,7 +428,7 @@ hg_status load_impl(hg_graph* g, const int64_t* edge_ptr, const int32_t* edge_vt
   return HG_OK;
 }
 
-// Heavy x heavy hyperwedges on the tensor cores: choose the heavy set,
+// Heavy x heavy hyperwedges on the tensor cores (dense tiles): choose the heavy set,
 // fill its 0/1 e4m3 matrix, multiply.  Leaves dn->heavy_idx null when not used.
 constexpr int64_t kDenseMinRows = 256;                  // below this a tile pass does not pay
 constexpr int64_t kDenseMaxBytes = int64_t(8) << 30;    // matrix + omega budget
