@@ -19,8 +19,8 @@ Parity status of each function:
     that is not available); class membership of every pattern is pinned;
   * the samplers (Algorithms 6 and 7): pinned by their every-hyperwedge-once
     special cases (equal to the exact counts), split ranges, uniformity and
-    unbiasedness; Philox4x32-10's identity with other implementations is parity
-    unpinned (no published known-answer vectors are stored).
+    unbiasedness; the Philox4x32-10 block function by the generator's published
+    known-answer vectors (tests/golden/philox_kat.json).
 """
 from __future__ import annotations
 

@@ -7,6 +7,8 @@ seeds the estimate is unbiased (Lemma 4.1)."""
 import numpy as np
 import pytest
 
+from conftest import load_json
+
 
 @pytest.fixture(scope="module")
 def small(native_cpu):
@@ -37,6 +39,16 @@ def test_counter_based_draws_split_over_ranges(small):
     assert (a.raw + b.raw).tolist() == whole.raw.tolist()
     other = oracle.sample_estimate(e_ptr, e_idx, nv, seed=100, first=1000, num=3000)
     assert other.raw.tolist() != whole.raw.tolist()
+
+
+def test_philox_known_answers():
+    # the block function against the generator's published known-answer vectors
+    import oracle
+
+    for v in load_json("philox_kat.json")["vectors"]:
+        got = oracle.philox4x32_10([int(x, 16) for x in v["counter"]],
+                                   [int(x, 16) for x in v["key"]])
+        assert [int(x) for x in got] == [int(x, 16) for x in v["out"]]
 
 
 def test_draws_are_uniform_over_wedges():
