@@ -1052,7 +1052,7 @@ def run_reference(args):
     wall = time.perf_counter() - t0
     value = tri / secs
     line = {
-        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 0,
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * wall / args.steps, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic", "impl": "reference", "config": cfg,
