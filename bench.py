@@ -203,6 +203,16 @@ CLOSE_GROUPS = {"close_warp256": 0, "close_warp512": 1, "close_warp1024": 2, "cl
 ISSUE_LANE_OPS_PER_CYCLE_PER_SM = 4 * 32   # 4 schedulers, one 32-lane instruction per cycle
 
 
+def dram_rate(traffic, launch_ms, peak_gbs):
+    """DRAM GB/s of a launch from captured traffic (bytes per launch) and its live duration."""
+    if not traffic or not launch_ms or launch_ms <= 0:
+        return {}
+    gbs = float(traffic) / (launch_ms / 1000.0) / 1e9
+    return {"dram_achieved": round(gbs, 1), "dram_frac": round(gbs / peak_gbs, 4),
+            "dram_source": "ncu dram__bytes_read + dram__bytes_write of the committed capture"
+                           " / live launch time"}
+
+
 def close_algorithmic(cs, b, T):
     """Algorithmic work of the closure kernels of team shape b in one launch.
 
@@ -380,6 +390,7 @@ def run_ours(args):
             "launch_ms": round(dom_ms, 4), "traffic": traffic,
             "hbm": {"achieved": round(achieved_gbs, 1), "peak": peak_hbm, "unit": "GB/s",
                     "frac": round(achieved_gbs / peak_hbm, 4), "peak_source": peak_kind}}
+    roof["hbm"].update(dram_rate(traffic, dom_ms, peak_hbm))
 
     dense = None
     if "dense_omega" in kernel_ms and st["dense_edges"]:

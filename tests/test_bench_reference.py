@@ -41,3 +41,13 @@ def test_reference_arm_other_ranks_exit_quietly(native_cpu):
                          cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
     assert out.returncode == 0, out.stderr[-2000:]
     assert not [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_dram_rate():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    r = bench.dram_rate(5.0e9, 10.0, 6791.0)   # 5 GB in 10 ms
+    assert r["dram_achieved"] == 500.0 and r["dram_frac"] == round(500.0 / 6791.0, 4)
+    assert bench.dram_rate(None, 10.0, 6791.0) == {}
+    assert bench.dram_rate(5.0e9, 0.0, 6791.0) == {}
