@@ -39,6 +39,8 @@ EXPORTED = ("hg_set_allocator", "hg_load_csr", "hg_build_wedges", "hg_count_patt
 
 
 class HgError(RuntimeError):
+    """A call of the C ABI returned a status other than HG_OK; .name is the status name."""
+
     def __init__(self, fn: str, status: int, text: str):
         super().__init__(f"{fn}: {STATUS.get(status, status)} ({text})")
         self.status = status
@@ -160,6 +162,7 @@ def _check(fn: str, status: int) -> None:
 
 
 def hg_status_str(status: int) -> str:
+    """The library's one-line description of a status code."""
     return _lib.hg_status_str(int(status)).decode()
 
 
@@ -392,12 +395,14 @@ def hg_pattern_table() -> np.ndarray:
 
 
 def hg_free(g: Graph) -> None:
+    """Release the handle and its device memory; calling it again does nothing."""
     if g.ptr:
         p, g.ptr = g.ptr, 0
         _check("hg_free", _lib.hg_free(ctypes.c_void_p(p)))
 
 
 def hg_set_timing(g: Graph, enable: bool) -> None:
+    """Turn per-kernel-group event timing of the handle on or off (read by hg_kernel_times)."""
     _check("hg_set_timing", _lib.hg_set_timing(ctypes.c_void_p(g.ptr), 1 if enable else 0))
 
 
@@ -477,6 +482,7 @@ def hg_load_batch(num_vertices, edge_off, edge_ptr, edge_vtx, max_wave_edges: in
 
 def hg_batch_build_wedges(b: Batch, dense_min_size: int = 0, dense_max_count: int = 0,
                           close_mode: int = 0, orient_exact: int = 0) -> None:
+    """Step one on every wave of the batch; the tuning is that of hg_build_wedges."""
     tun = _Tuning(int(dense_min_size), int(dense_max_count), int(close_mode), int(orient_exact))
     _check("hg_batch_build_wedges", _lib.hg_batch_build_wedges(ctypes.c_void_p(b.ptr),
                                                                ctypes.byref(tun)))
@@ -525,6 +531,7 @@ def hg_batch_waves(b: Batch) -> list[tuple[Graph, int, int]]:
 
 
 def hg_batch_free(b: Batch) -> None:
+    """Release the batch and every wave's handle; calling it again does nothing."""
     if b.ptr:
         p, b.ptr = b.ptr, 0
         _check("hg_batch_free", _lib.hg_batch_free(ctypes.c_void_p(p)))
@@ -576,6 +583,7 @@ class Server:
         self.ptr = int(out.value)
 
     def add_graph(self, num_vertices: int, edge_ptr, edge_vtx) -> int:
+        """Register a hypergraph (host or device CSR, validated and copied); returns its id."""
         p_ptr, p_dev, k1 = _as_ptr(edge_ptr, np.int64)
         v_ptr, v_dev, k2 = _as_ptr(edge_vtx, np.int32)
         if p_dev != v_dev:
@@ -591,6 +599,8 @@ class Server:
 
     def submit(self, kind: int, graph: int, seed: int = 0, first_sample: int = 0,
                num_samples: int = 0, eps=None) -> int:
+        """Queue a query (HG_Q_COUNTS, HG_Q_CLUSTERING with eps[20], HG_Q_ESTIMATE with seed
+        and sample range) on a registered hypergraph; returns its ticket."""
         q = _Query(int(kind), int(graph), int(seed) & (2**64 - 1), int(first_sample),
                    int(num_samples))
         if eps is not None:
@@ -602,6 +612,7 @@ class Server:
         return int(t.value)
 
     def wait(self, ticket: int) -> dict:
+        """Block until the ticket's query is answered and return the answer (once per ticket)."""
         r = _Result()
         _check("hg_server_wait", _lib.hg_server_wait(ctypes.c_void_p(self.ptr), int(ticket),
                                                      ctypes.byref(r)))
@@ -613,9 +624,11 @@ class Server:
                 "batch_graphs": int(r.batch_graphs), "worker": int(r.worker)}
 
     def drain(self) -> None:
+        """Block until every queued query has been answered."""
         _check("hg_server_drain", _lib.hg_server_drain(ctypes.c_void_p(self.ptr)))
 
     def stats(self) -> dict:
+        """Counters of the server: queries, batches, concurrency and memory in flight."""
         st = _ServerStats()
         _check("hg_server_stats_get", _lib.hg_server_stats_get(ctypes.c_void_p(self.ptr),
                                                                ctypes.byref(st)))
@@ -623,6 +636,7 @@ class Server:
                 for n, _ in _ServerStats._fields_}
 
     def close(self) -> None:
+        """Answer what is queued, stop the workers and free the resident hypergraphs."""
         if self.ptr:
             p, self.ptr = self.ptr, 0
             _check("hg_server_destroy", _lib.hg_server_destroy(ctypes.c_void_p(p)))
