@@ -245,6 +245,17 @@ hg_status hg_close_stats_get(hg_graph* g, hg_close_stats* out);
 hg_status hg_kernel_launches(uint64_t* n);
 
 /*
+ * A bounded device wait, the discipline every wait in libhg's kernels follows (no
+ * counterpart in the paper): one thread polls the int32 at device address flag, with
+ * back-off, until it is non-zero (HG_OK) or limit_us microseconds of the GPU's global
+ * timer have passed (HG_ERR_TIMEOUT; the context stays usable).  Runs on cuda_stream
+ * and synchronises it.  Nothing in libhg sets the flag: whatever should set it must have
+ * done so before the call (no kernel of libhg ever waits on another launch).
+ * HG_ERR_INVALID_ARG for a NULL flag or a negative limit.
+ */
+hg_status hg_wait_flag(const int32_t* flag, int32_t limit_us, void* cuda_stream);
+
+/*
  * Line-graph degrees without allocating.  The paper has no counterpart: this is
  * for callers that cannot allocate device memory while they run - code in a
  * host function enqueued on a stream (which may not make allocating CUDA

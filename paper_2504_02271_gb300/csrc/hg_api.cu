@@ -194,6 +194,7 @@ hg_status dev_err_status(int e) {
     case DE_DUPEDGE: return HG_ERR_DUPLICATE_HYPEREDGE;
     case DE_PTR: return HG_ERR_INVALID_ARG;
     case DE_LIMIT: return HG_ERR_UNSUPPORTED;
+    case DE_TIMEOUT: return HG_ERR_TIMEOUT;
     default: return HG_ERR_INTERNAL;
   }
 }
@@ -1175,6 +1176,26 @@ hg_status hg_set_allocator(hg_alloc_fn alloc, hg_free_fn free_fn, void* ctx) {
   g_hooks.free_fn = free_fn;
   g_hooks.ctx = ctx;
   return HG_OK;
+}
+
+hg_status hg_wait_flag(const int32_t* flag, int32_t limit_us, void* cuda_stream) {
+  if (!flag || limit_us < 0) return HG_ERR_INVALID_ARG;
+  int dev = 0, nsm = 0;
+  HG_TRY(check_device(&dev, &nsm));
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int* err = nullptr;
+  HG_CUDA(cudaMallocAsync(&err, sizeof(int), s));
+  int h = 0;
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    launch_wait_flag(flag, (int64_t)limit_us * 1000, err, s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(err, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return HG_ERR_CUDA;
+  return dev_err_status(h);
 }
 
 hg_status hg_load_csr(int32_t num_vertices, int32_t num_edges, const int64_t* edge_ptr,

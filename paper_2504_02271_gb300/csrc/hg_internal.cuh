@@ -24,6 +24,7 @@ enum DevErr : int {
   DE_PTR = 6,       // edge_ptr not monotone / out of [0, nnz]
   DE_INTERNAL = 7,  // a kernel-side consistency check failed
   DE_LIMIT = 8,     // an input row beyond a kernel's fixed capacity
+  DE_TIMEOUT = 9,   // a bounded device wait gave up
 };
 
 __device__ __forceinline__ void dev_fail(int* err, int code) { atomicCAS(err, 0, code); }
@@ -76,6 +77,9 @@ void scan_i64_to_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp, cuda
 void reduce_deg_stats(const int32_t* a, int64_t n, unsigned long long* acc, cudaStream_t s);
 
 // k_load.cu
+// One thread waits until *flag != 0, at most limit_ns of the global timer (and a bounded
+// number of polls), else records DE_TIMEOUT in *err.
+void launch_wait_flag(const int32_t* flag, int64_t limit_ns, int* err, cudaStream_t s);
 void launch_check_ptr(const int64_t* e_ptr, int32_t ne, int64_t nnz, int* err, cudaStream_t s);
 void launch_validate_rows(const DevGraph& g, int32_t* esize, int32_t* vdeg, int* err,
                           cudaStream_t s);

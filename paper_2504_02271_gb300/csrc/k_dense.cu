@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (threadIdx.x == 0 && abort_flag) atomicCAS(err, 0, DE_INTERNAL);
+  if (threadIdx.x == 0 && abort_flag) atomicCAS(err, 0, DE_TIMEOUT);
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d),

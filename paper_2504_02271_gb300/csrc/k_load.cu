@@ -24,6 +24,26 @@ __global__ void k_check_ptr(const int64_t* __restrict__ e_ptr, int32_t ne, int64
   }
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// A bounded wait on a flag in device memory: poll with back-off until it is set, give up
+// after limit_ns of the global timer or after a poll count that bounds the loop even if
+// the timer stalls.
+__global__ void k_wait_flag(const int32_t* flag, int64_t limit_ns, int* __restrict__ err) {
+  const uint64_t t0 = global_ns();
+  const uint64_t max_polls = (uint64_t)(limit_ns / 256) + 1024;
+  for (uint64_t it = 0; it < max_polls; ++it) {
+    if (*(volatile const int32_t*)flag != 0) return;
+    if ((int64_t)(global_ns() - t0) > limit_ns) break;
+    __nanosleep(256);
+  }
+  dev_fail(err, DE_TIMEOUT);
+}
+
 // Row checks (ascending, distinct, in range), |e_i| and vertex degrees |E_v|.
 // Runs only after k_check_ptr passed, so every row range lies inside [0, nnz).
 __global__ void k_validate_rows(DevGraph g, int32_t* __restrict__ esize,
@@ -114,6 +134,11 @@ int grid_for(int64_t work_items, int per_block) {
 void launch_check_ptr(const int64_t* e_ptr, int32_t ne, int64_t nnz, int* err, cudaStream_t s) {
   note_launch();
   k_check_ptr<<<grid_for((int64_t)ne + 1, 256), 256, 0, s>>>(e_ptr, ne, nnz, err);
+}
+
+void launch_wait_flag(const int32_t* flag, int64_t limit_ns, int* err, cudaStream_t s) {
+  note_launch();
+  k_wait_flag<<<1, 1, 0, s>>>(flag, limit_ns, err);
 }
 
 void launch_validate_rows(const DevGraph& g, int32_t* esize, int32_t* vdeg, int* err,

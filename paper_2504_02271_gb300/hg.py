@@ -29,7 +29,7 @@ HG_OK = 0
 # every entry point declared in include/hg.h
 EXPORTED = ("hg_set_allocator", "hg_load_csr", "hg_build_wedges", "hg_count_patterns",
             "hg_clustering_coeff", "hg_free", "hg_status_str", "hg_set_timing", "hg_kernel_times",
-            "hg_pattern_table", "hg_close_stats_get", "hg_kernel_launches",
+            "hg_pattern_table", "hg_close_stats_get", "hg_kernel_launches", "hg_wait_flag",
             "hg_wedge_degrees_noalloc", "hg_sample_estimate", "hg_load_batch",
             "hg_batch_build_wedges", "hg_batch_count_patterns", "hg_batch_clustering_coeff",
             "hg_batch_waves", "hg_batch_wave", "hg_batch_free", "hg_load_batch_members",
@@ -106,6 +106,7 @@ def _open():
     lib = ctypes.CDLL(LIB_PATH)
     vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     lib.hg_set_allocator.argtypes = [_ALLOC_FN, _FREE_FN, vp]
+    lib.hg_wait_flag.argtypes = [vp, ctypes.c_int32, vp]
     lib.hg_load_csr.argtypes = [i32, i32, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)]
     lib.hg_build_wedges.argtypes = [vp, ctypes.POINTER(_Tuning), ctypes.POINTER(_WedgeStats)]
     lib.hg_count_patterns.argtypes = [vp, vp]
@@ -159,6 +160,23 @@ _lib = _open()
 def _check(fn: str, status: int) -> None:
     if status != HG_OK:
         raise HgError(fn, status, hg_status_str(status))
+
+
+def hg_wait_flag(flag, limit_us: int, stream: int | None = None) -> None:
+    """Bounded device wait on an int32 device flag (a one-element CUDA tensor or a device
+    address); raises HgError HG_ERR_TIMEOUT when it is still zero after limit_us."""
+    try:
+        import torch
+        if isinstance(flag, torch.Tensor):
+            if not flag.is_cuda or flag.dtype != torch.int32:
+                raise ValueError("flag must be an int32 CUDA tensor")
+            flag = flag.data_ptr()
+    except ImportError:
+        pass
+    if stream is None:
+        stream = _default_stream()
+    _check("hg_wait_flag", _lib.hg_wait_flag(ctypes.c_void_p(int(flag)), int(limit_us),
+                                             ctypes.c_void_p(stream)))
 
 
 def hg_status_str(status: int) -> str:

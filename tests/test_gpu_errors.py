@@ -103,3 +103,25 @@ def test_empty_hypergraph(hglib):
         assert raw.tolist() == [0] * 21 and est.tolist() == [0.0] * 21
     finally:
         hglib.hg_free(g)
+
+
+def test_bounded_wait_gives_up_and_the_context_survives(hglib):
+    # a flag that nothing sets: the wait returns HG_ERR_TIMEOUT after its limit
+    import time
+
+    import torch
+
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with pytest.raises(hglib.HgError) as ei:
+        hglib.hg_wait_flag(flag, 20_000)   # 20 ms
+    assert ei.value.name == "HG_ERR_TIMEOUT"
+    assert 0.015 < time.perf_counter() - t0 < 5.0
+    flag.fill_(1)
+    torch.cuda.synchronize()
+    hglib.hg_wait_flag(flag, 20_000)        # already set: returns at once
+    with pytest.raises(hglib.HgError) as ei:
+        hglib.hg_wait_flag(flag, -1)
+    assert ei.value.name == "HG_ERR_INVALID_ARG"
+    still_works(hglib)
