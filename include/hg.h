@@ -47,7 +47,8 @@ typedef enum hg_status {
   HG_ERR_STATE = 10,               /* call out of order (e.g. counting before hg_build_wedges) */
   HG_ERR_UNSUPPORTED = 11,         /* input beyond this build's limits */
   HG_ERR_NO_DEVICE = 12,           /* no usable sm_103 device */
-  HG_ERR_INTERNAL = 13             /* a consistency check of the library failed */
+  HG_ERR_INTERNAL = 13,            /* a consistency check of the library failed */
+  HG_ERR_CANCELLED = 14            /* a served query was cancelled before it ran */
 } hg_status;
 
 /*
@@ -444,6 +445,12 @@ hg_status hg_server_wait(hg_server* s, uint64_t ticket, hg_result* out);
 
 /* Block until nothing is queued or running. */
 hg_status hg_server_drain(hg_server* s);
+
+/* Cancel a query that no worker has taken yet: it leaves the queue and its result
+ * (collected by hg_server_wait as usual) has status HG_ERR_CANCELLED.  HG_ERR_STATE when
+ * the query is already running or answered (its answer stands); HG_ERR_INVALID_ARG for
+ * an unknown or collected ticket. */
+hg_status hg_server_cancel(hg_server* s, uint64_t ticket);
 
 hg_status hg_server_stats_get(hg_server* s, hg_server_stats* out);
 

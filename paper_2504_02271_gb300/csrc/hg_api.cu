@@ -1584,6 +1584,7 @@ const char* hg_status_str(hg_status s) {
     case HG_ERR_UNSUPPORTED: return "input beyond supported limits";
     case HG_ERR_NO_DEVICE: return "no sm_103 CUDA device";
     case HG_ERR_INTERNAL: return "internal consistency check failed";
+    case HG_ERR_CANCELLED: return "query cancelled before it ran";
   }
   return "unknown status";
 }

@@ -389,6 +389,29 @@ hg_status hg_server_wait(hg_server* S, uint64_t ticket, hg_result* out) {
   return HG_OK;
 }
 
+hg_status hg_server_cancel(hg_server* S, uint64_t ticket) {
+  if (!S) return HG_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (!S->outstanding.count(ticket)) return HG_ERR_INVALID_ARG;
+    auto it = std::find_if(S->queue.begin(), S->queue.end(),
+                           [&](const Pending& p) { return p.ticket == ticket; });
+    if (it == S->queue.end()) return HG_ERR_STATE;   // taken by a worker, or answered
+    hg_result r;
+    std::memset(&r, 0, sizeof(r));
+    r.status = HG_ERR_CANCELLED;
+    r.kind = it->q.kind;
+    r.graph = it->q.graph;
+    r.t_submit = it->t_submit;
+    r.t_start = r.t_done = now(S);
+    r.worker = -1;
+    S->queue.erase(it);
+    S->done[ticket] = r;
+  }
+  S->cv_done.notify_all();   // its waiter, and a drain the emptier queue may end
+  return HG_OK;
+}
+
 hg_status hg_server_drain(hg_server* S) {
   if (!S) return HG_ERR_INVALID_ARG;
   std::unique_lock<std::mutex> lk(S->mu);

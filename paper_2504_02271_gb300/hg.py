@@ -23,6 +23,7 @@ STATUS = {
     4: "HG_ERR_VERTEX_RANGE", 5: "HG_ERR_UNSORTED", 6: "HG_ERR_DUPLICATE_HYPEREDGE",
     7: "HG_ERR_OOM", 8: "HG_ERR_CUDA", 9: "HG_ERR_TIMEOUT", 10: "HG_ERR_STATE",
     11: "HG_ERR_UNSUPPORTED", 12: "HG_ERR_NO_DEVICE", 13: "HG_ERR_INTERNAL",
+    14: "HG_ERR_CANCELLED",
 }
 HG_OK = 0
 
@@ -34,7 +35,7 @@ EXPORTED = ("hg_set_allocator", "hg_load_csr", "hg_build_wedges", "hg_count_patt
             "hg_batch_build_wedges", "hg_batch_count_patterns", "hg_batch_clustering_coeff",
             "hg_batch_waves", "hg_batch_wave", "hg_batch_free", "hg_load_batch_members",
             "hg_server_create", "hg_server_add_graph", "hg_server_submit", "hg_server_wait",
-            "hg_server_drain", "hg_server_stats_get", "hg_server_destroy",
+            "hg_server_drain", "hg_server_cancel", "hg_server_stats_get", "hg_server_destroy",
             "hg_sample_estimate_adv", "hg_enumerate_pattern", "hg_sample_work_get")
 
 
@@ -145,6 +146,7 @@ def _open():
     lib.hg_server_submit.argtypes = [vp, ctypes.POINTER(_Query), ctypes.POINTER(u64)]
     lib.hg_server_wait.argtypes = [vp, u64, ctypes.POINTER(_Result)]
     lib.hg_server_drain.argtypes = [vp]
+    lib.hg_server_cancel.argtypes = [vp, ctypes.c_uint64]
     lib.hg_server_stats_get.argtypes = [vp, ctypes.POINTER(_ServerStats)]
     lib.hg_server_destroy.argtypes = [vp]
     for name in EXPORTED:
@@ -640,6 +642,11 @@ class Server:
                 "open": int(r.open), "connected": int(r.connected), "t_submit": r.t_submit,
                 "t_start": r.t_start, "t_done": r.t_done, "batch_queries": int(r.batch_queries),
                 "batch_graphs": int(r.batch_graphs), "worker": int(r.worker)}
+
+    def cancel(self, ticket: int) -> None:
+        """Cancel a query no worker has taken yet; its wait() then has status HG_ERR_CANCELLED.
+        Raises HgError HG_ERR_STATE when it is already running or answered."""
+        _check("hg_server_cancel", _lib.hg_server_cancel(ctypes.c_void_p(self.ptr), int(ticket)))
 
     def drain(self) -> None:
         """Block until every queued query has been answered."""

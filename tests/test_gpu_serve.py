@@ -171,3 +171,40 @@ def test_server_argument_errors(hglib):
         srv.drain()
     finally:
         srv.close()
+
+
+def test_cancel_queued_queries(hglib):
+    # one worker, one query per batch: of 40 queued counts, the last ones are still queued
+    # when they are cancelled; a cancelled query waits out as HG_ERR_CANCELLED, the others
+    # are answered as usual
+    gs = graphs()
+    srv = hglib.Server(workers=1, max_batch_queries=1)
+    try:
+        gid = srv.add_graph(*gs[5])
+        tickets = [srv.submit(hglib.HG_Q_COUNTS, gid) for _ in range(40)]
+        cancelled = []
+        for t in tickets[20:]:
+            try:
+                srv.cancel(t)
+                cancelled.append(t)
+            except hglib.HgError as e:
+                assert e.name == "HG_ERR_STATE"   # a worker had taken it already
+        assert cancelled
+        with pytest.raises(hglib.HgError) as ei:
+            srv.cancel(10**9)
+        assert ei.value.name == "HG_ERR_INVALID_ARG"
+        answered = None
+        for t in tickets:
+            r = srv.wait(t)
+            if t in cancelled:
+                assert r["status"] == 14 and r["worker"] == -1   # HG_ERR_CANCELLED
+            else:
+                assert r["status"] == 0
+                answered = answered or r["counts"].tolist()
+                assert r["counts"].tolist() == answered
+        with pytest.raises(hglib.HgError) as ei:
+            srv.cancel(tickets[0])   # already collected
+        assert ei.value.name == "HG_ERR_INVALID_ARG"
+        srv.drain()
+    finally:
+        srv.close()
