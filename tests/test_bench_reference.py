@@ -51,3 +51,10 @@ def test_dram_rate():
     assert r["dram_achieved"] == 500.0 and r["dram_frac"] == round(500.0 / 6791.0, 4)
     assert bench.dram_rate(None, 10.0, 6791.0) == {}
     assert bench.dram_rate(5.0e9, 0.0, 6791.0) == {}
+
+
+def test_reference_arm_batched(native_cpu):
+    d = run_bench("--impl", "reference", "--workload", "batched", "--batch-members", "2",
+                  "--steps", "2", "--warmup", "0")
+    assert d["impl"] == "reference" and d["config"]["workload"] == "batched_2"
+    assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
