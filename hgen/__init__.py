@@ -15,6 +15,7 @@ tags, email ...).  Their recipe, one per named workload, is:
 * ``tag_heavy``   |V|=2e4    |E|=2e6    sizes log-normal(1.5,1.0) [2,200] Zipf(1.2) seed 2, degree cap 1000
 * ``batched(s)``  |E| log-uniform [100, 2e5], |V|=|E|/4, power law 2.2 [2,50], Zipf(1.0), seed s, cap 100
 * ``served(m)``   |E| log-uniform [1e3, 1e6], |V|=|E|/5, otherwise as ``coauthor``, seed 5000+m
+* ``dense_core``  |V|=24     |E|=2,600  sizes U{3..6}         uniform popularity, seed 7
 
 The degree cap withdraws a vertex from later draws once it is in that many
 hyperedges; without it the Zipf head puts a single vertex in ~8% of all
@@ -238,7 +239,12 @@ def served(member: int) -> HypergraphSpec:
                    name=f"served_{member}")
 
 
-WORKLOADS = {"tiny_plain": TINY_PLAIN, "coauthor": COAUTHOR, "tag_heavy": TAG_HEAVY}
+# a dense core: every hyperedge meets most others, so hyperedges close with out-degrees
+# up to ~1,200 after degree ordering (test input for the block-sized closure teams)
+DENSE_CORE = HypergraphSpec(24, 2600, 7, SIZE_UNIFORM, 3, 6, zipf_s=0.0, name="dense_core")
+
+WORKLOADS = {"tiny_plain": TINY_PLAIN, "coauthor": COAUTHOR, "tag_heavy": TAG_HEAVY,
+             "dense_core": DENSE_CORE}
 
 
 def hub(num_spokes: int, num_extra: int, seed: int) -> tuple[int, np.ndarray, np.ndarray]:

@@ -14,6 +14,10 @@ Def. 5.1, evaluated in IEEE double on the host.
 Parity status of each function:
   * counts, totals, wedge statistics, open triples: pinned by the paper's worked
     examples (Sec. 6.2), Algorithm 5's O(1) rules, closed forms and brute force;
+  * the canonical region-mask histogram (128 bins; the pattern of each
+    hyper-triangle before any numbering): pinned by closed forms (sunflowers,
+    chains, ordinary graphs), a pure-Python brute force written from the region
+    definitions of Sec. 2, brute force vs Exact-bs, and relabelling invariance;
   * the numbering of patterns 9, 11 and 13-20 inside the TTT class: parity
     unpinned (the paper prints that part of the numbering only in a figure
     that is not available); class membership of every pattern is pinned;
@@ -70,8 +74,13 @@ def _load():
         lib.oracle_count.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int32,
                                      ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
-                                     ctypes.POINTER(ctypes.c_double)]
+                                     ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
         lib.oracle_count.restype = ctypes.c_int
+        lib.oracle_degrees.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_degrees.restype = ctypes.c_int
+        lib.oracle_canonical_mask.argtypes = [ctypes.c_int]
+        lib.oracle_canonical_mask.restype = ctypes.c_int
         for f in (lib.oracle_classify, lib.oracle_region_mask):
             f.argtypes = [i32p, ctypes.c_int, i32p, ctypes.c_int, i32p, ctypes.c_int]
             f.restype = ctypes.c_int
@@ -114,6 +123,9 @@ class OracleResult:
     max_deg: int                # max |N(e_i)|
     seconds: float
     threads: int
+    # uint64[128]: masks[m] = hyper-triangles whose region mask in canonical form
+    # (canonical_mask) is m (Sec. 2; independent of the pattern numbering)
+    masks: np.ndarray = None
 
     @property
     def T(self) -> int:
@@ -138,16 +150,29 @@ def count(e_ptr, e_idx, num_vertices: int, mode: str = "exact_bs", threads: int 
     lo, hi = (0, ne) if i_range is None else i_range
     counts = np.zeros(21, dtype=np.uint64)
     stats = np.zeros(8, dtype=np.uint64)
+    masks = np.zeros(128, dtype=np.uint64)
     secs = ctypes.c_double(0.0)
     m = {"exact_bs": 0, "brute": 1}[mode]
     rc = lib.oracle_count(int(num_vertices), int(ne), e_ptr.ctypes.data, e_idx.ctypes.data, m,
                           int(threads), int(lo), int(hi), counts.ctypes.data, stats.ctypes.data,
-                          ctypes.byref(secs))
+                          masks.ctypes.data, ctypes.byref(secs))
     if rc != 0:
         raise ValueError(f"oracle: {_ERR.get(rc, rc)}")
     return OracleResult(counts, int(stats[0]), int(stats[1]), int(stats[2]), int(stats[3]),
                         int(stats[4]), int(stats[5]), float(secs.value),
-                        int(threads) if threads > 0 else int(lib.oracle_max_threads()))
+                        int(threads) if threads > 0 else int(lib.oracle_max_threads()), masks)
+
+
+def degrees(e_ptr, e_idx, num_vertices: int) -> np.ndarray:
+    """int32[|E|]: |N(e_i)|, the number of other hyperedges sharing a vertex with e_i."""
+    e_ptr = np.ascontiguousarray(e_ptr, dtype=np.int64)
+    e_idx = np.ascontiguousarray(e_idx, dtype=np.int32)
+    out = np.zeros(max(len(e_ptr) - 1, 1), dtype=np.int32)
+    rc = _load().oracle_degrees(int(num_vertices), len(e_ptr) - 1, e_ptr.ctypes.data,
+                                e_idx.ctypes.data, out.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle: {_ERR.get(rc, rc)}")
+    return out[:len(e_ptr) - 1]
 
 
 def _arr(x):
@@ -169,6 +194,11 @@ def region_mask(a, b, c) -> int:
 
 def pattern_of_mask(mask: int) -> int:
     return int(_load().oracle_pattern_of_mask(int(mask)))
+
+
+def canonical_mask(mask: int) -> int:
+    """Smallest of the six relabellings of a labelled region mask (Sec. 2)."""
+    return int(_load().oracle_canonical_mask(int(mask)))
 
 
 def table_ok() -> bool:

@@ -117,6 +117,27 @@ const PatternMap& pattern_map() {
   return pm;
 }
 
+// Canonical form of a labelled region mask: the smallest mask value over the six
+// relabellings of the three hyperedges.  Two hyper-triangles get the same canonical
+// mask exactly when their sets of non-empty regions agree up to relabelling, which is
+// what a pattern is (Sec. 2); the histogram over canonical masks therefore does not
+// depend on how the twenty patterns are numbered.
+struct CanonMap {
+  int of_mask[128];
+  CanonMap() {
+    const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    for (int m = 0; m < 128; ++m) {
+      int best = m;
+      for (const auto& pr : perms) best = std::min(best, relabel(m, pr));
+      of_mask[m] = best;
+    }
+  }
+};
+const CanonMap& canon_map() {
+  static CanonMap cm;
+  return cm;
+}
+
 using VSet = std::set<int32_t>;
 
 // Seven-region non-emptiness mask of (A, B, C), written from the definitions.
@@ -200,6 +221,25 @@ int oracle_region_mask(const int32_t* a, int na, const int32_t* b, int nb, const
   return region_mask(A, B, C);
 }
 
+// Line-graph degrees |N(e_i)| (Sec. 2: the hyperedges sharing a vertex with e_i) into
+// deg[ne].  Returns 0 or a negative input error as oracle_count.
+int oracle_degrees(int32_t nv, int32_t ne, const int64_t* e_ptr, const int32_t* e_idx,
+                   int32_t* deg) {
+  if (!deg || nv < 0 || ne < 0) return -6;
+  Graph g;
+  int rc = load(g, nv, ne, e_ptr, e_idx);
+  if (rc) return rc;
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int32_t i = 0; i < ne; ++i) deg[i] = (int32_t)neighbours(g, i).size();
+  return 0;
+}
+
+// Canonical form (smallest over the six relabellings) of a labelled region mask.
+int oracle_canonical_mask(int mask) {
+  if (mask < 0 || mask > 127) return -1;
+  return canon_map().of_mask[mask];
+}
+
 // Pattern of three explicit vertex lists: 1..20; 0 if not a hyper-triangle;
 // -1 if two of the sets are equal (the paper assumes distinct hyperedges).
 int oracle_classify(const int32_t* a, int na, const int32_t* b, int nb, const int32_t* c,
@@ -214,17 +254,21 @@ int oracle_classify(const int32_t* a, int na, const int32_t* b, int nb, const in
 // Only triangles whose smallest hyperedge id lies in [i_lo, i_hi) are counted
 // (pass 0, ne for the whole graph); wedge statistics always cover the needed part.
 // counts[21]: [0] = T, [p] = H[p].  stats[ST_N] as in the enum above.
+// masks[128] (may be NULL): masks[m] = hyper-triangles whose region mask, in its
+// canonical form (oracle_canonical_mask), is m; zero at non-canonical m.
 // Returns 0, or a negative input error (-2 empty hyperedge, -3 vertex out of
 // range, -4 repeated vertex, -5 duplicate hyperedge, -6 bad argument,
 // -7 pattern table inconsistent, -8 unclassifiable triple).
 int oracle_count(int32_t nv, int32_t ne, const int64_t* e_ptr, const int32_t* e_idx, int mode,
                  int nthreads, int32_t i_lo, int32_t i_hi, uint64_t* counts, uint64_t* stats,
-                 double* seconds) {
+                 uint64_t* masks, double* seconds) {
   auto t0 = std::chrono::steady_clock::now();
   if (!counts || !stats || nv < 0 || ne < 0 || i_lo < 0 || i_hi > ne || i_lo > i_hi) return -6;
   if (!oracle_pattern_table_ok()) return -7;
   std::memset(counts, 0, sizeof(uint64_t) * 21);
   std::memset(stats, 0, sizeof(uint64_t) * ST_N);
+  if (masks) std::memset(masks, 0, sizeof(uint64_t) * 128);
+  const auto& cm = canon_map();
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
@@ -237,6 +281,7 @@ int oracle_count(int32_t nv, int32_t ne, const int64_t* e_ptr, const int32_t* e_
   if (mode == 1) {
     // brute force: every unordered triple of distinct hyperedges
     uint64_t H[21] = {0};
+    uint64_t M[128] = {0};
     uint64_t open = 0, connected = 0, W = 0, Wc = 0;
     uint64_t maxdeg = 0;
     for (int32_t i = 0; i < ne; ++i) {
@@ -262,11 +307,14 @@ int oracle_count(int32_t nv, int32_t ne, const int64_t* e_ptr, const int32_t* e_
           int n = ij + jk + ik;
           if (n == 2) ++open;
           if (n != 3) continue;
-          int p = pm.of_mask[region_mask(g.e[i], g.e[j], g.e[k])];
+          const int m = region_mask(g.e[i], g.e[j], g.e[k]);
+          int p = pm.of_mask[m];
           if (p == 0) { bad = 1; continue; }
           ++H[p];
+          ++M[cm.of_mask[m]];
         }
     for (int p = 1; p <= 20; ++p) { counts[p] = H[p]; counts[0] += H[p]; }
+    if (masks) std::memcpy(masks, M, sizeof(M));
     stats[ST_W] = W; stats[ST_WC] = Wc; stats[ST_WT] = W - Wc;
     stats[ST_CONNECTED] = connected; stats[ST_OPEN] = open; stats[ST_MAXDEG] = maxdeg;
     stats[ST_T] = counts[0];
@@ -314,7 +362,7 @@ int oracle_count(int32_t nv, int32_t ne, const int64_t* e_ptr, const int32_t* e_
 #ifdef _OPENMP
   nth = omp_get_max_threads();
 #endif
-  std::vector<uint64_t> Hs((size_t)nth * 21, 0);
+  std::vector<uint64_t> Hs((size_t)nth * 21, 0), Ms((size_t)nth * 128, 0);
 #pragma omp parallel
   {
     int tid = 0;
@@ -322,6 +370,7 @@ int oracle_count(int32_t nv, int32_t ne, const int64_t* e_ptr, const int32_t* e_
     tid = omp_get_thread_num();
 #endif
     uint64_t* H = &Hs[(size_t)tid * 21];
+    uint64_t* M = &Ms[(size_t)tid * 128];
 #pragma omp for schedule(dynamic, 64) reduction(| : bad)
     for (int32_t i = i_lo; i < i_hi; ++i) {
       const auto& Ni = N[i];
@@ -331,15 +380,20 @@ int oracle_count(int32_t nv, int32_t ne, const int64_t* e_ptr, const int32_t* e_
         for (size_t b = a + 1; b < Ni.size(); ++b) {
           int32_t k = Ni[b];                                     // i < j < k
           if (!adjacent(N, j, k)) continue;                      // e_j cap e_k empty
-          int p = pm.of_mask[region_mask(g.e[i], g.e[j], g.e[k])];
+          const int m = region_mask(g.e[i], g.e[j], g.e[k]);
+          int p = pm.of_mask[m];
           if (p == 0) { bad = 1; continue; }
           ++H[p];
+          ++M[cm.of_mask[m]];
         }
       }
     }
   }
-  for (int t = 0; t < nth; ++t)
+  for (int t = 0; t < nth; ++t) {
     for (int p = 1; p <= 20; ++p) counts[p] += Hs[(size_t)t * 21 + p];
+    if (masks)
+      for (int m = 0; m < 128; ++m) masks[m] += Ms[(size_t)t * 128 + m];
+  }
   for (int p = 1; p <= 20; ++p) counts[0] += counts[p];
   stats[ST_W] = W; stats[ST_WC] = Wc; stats[ST_WT] = W - Wc;
   stats[ST_CONNECTED] = connected; stats[ST_MAXDEG] = maxdeg; stats[ST_T] = counts[0];

@@ -3,7 +3,9 @@
 Every number written here comes from the oracle (``oracle/``) run on the
 seeded generator's output (``hgen/``); nothing comes from the CUDA path.  The
 CSR content hash is stored with each entry so a test can check that the
-generator reproduced the same hypergraph before comparing counts.
+generator reproduced the same hypergraph before comparing counts.  ``masks``
+maps each canonical region mask (the smallest of its six relabellings) to the
+number of hyper-triangles that have it; absent masks have none.
 
 Usage:  python tests/golden/make_golden.py [name ...]   (default: all)
 """
@@ -30,6 +32,7 @@ CASES = {
     "coauthor_prefix50k": (hgen.COAUTHOR, 50_000),
     "tag_heavy_prefix1000": (hgen.TAG_HEAVY, 1_000),
     "tag_heavy_prefix2000": (hgen.TAG_HEAVY, 2_000),
+    "dense_core": (hgen.DENSE_CORE, None),
 }
 # hub hypergraphs (hgen.hub): name -> (spokes, extra pairs, seed)
 HUBS = {
@@ -54,7 +57,9 @@ def run(name: str) -> dict:
         "workload": workload, "prefix_edges": pre, "num_vertices": nv,
         "num_edges": len(e_ptr) - 1, "nnz": int(e_ptr[-1]),
         "csr_hash": hgen.csr_hash(e_ptr, e_idx),
-        "counts": [int(x) for x in r.counts], "W": r.W, "W_t": r.W_t, "W_c": r.W_c,
+        "counts": [int(x) for x in r.counts],
+        "masks": {str(m): int(r.masks[m]) for m in range(128) if r.masks[m]},
+        "W": r.W, "W_t": r.W_t, "W_c": r.W_c,
         "connected": r.connected, "open": r.open, "max_deg": r.max_deg,
         "oracle_seconds": round(r.seconds, 2), "oracle_threads": r.threads,
     }
@@ -63,6 +68,7 @@ def run(name: str) -> dict:
     if pre is not None and pre <= 300:
         b = oracle.count(e_ptr, e_idx, nv, mode="brute")
         assert [int(x) for x in b.counts] == entry["counts"] and b.open == r.open
+        assert b.masks.tolist() == r.masks.tolist()
         entry["brute_force_agrees"] = True
     print(f"{name}: T={r.T} W={r.W} {time.time() - t0:.1f}s", flush=True)
     return entry

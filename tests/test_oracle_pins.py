@@ -406,3 +406,122 @@ def test_enumeration_closed_form_sunflower():
     got = oracle.enumerate_pattern(e_ptr, e_idx, n + 1, 9).tolist()
     assert got == [list(t) for t in combinations(range(n), 3)]
     assert oracle.enumerate_pattern(e_ptr, e_idx, n + 1, 17).tolist() == []
+
+
+# ---------------------------------------------------------------- canonical region-mask histogram
+
+REGIONS = {"a": (1, 0, 0), "b": (0, 1, 0), "c": (0, 0, 1), "d": (1, 1, 0), "e": (0, 1, 1),
+           "f": (1, 0, 1), "g": (1, 1, 1)}
+
+
+def mask_of_sets(s0, s1, s2):
+    """Region bit r set iff region r (a..g of Sec. 2) of (s0, s1, s2) is non-empty,
+    written from the definitions: a vertex's region is the set of hyperedges holding it."""
+    m = 0
+    for x in s0 | s1 | s2:
+        inn = (int(x in s0), int(x in s1), int(x in s2))
+        m |= 1 << list(REGIONS.values()).index(inn)
+    return m
+
+
+def canonical_py(sets):
+    """Smallest region mask over the six orders of the three sets."""
+    return min(mask_of_sets(*(sets[i] for i in p)) for p in itertools.permutations(range(3)))
+
+
+def masks_brute_py(edges):
+    E = [set(e) for e in edges]
+    hist = [0] * 128
+    for i, j, k in itertools.combinations(range(len(E)), 3):
+        if pairwise_connected(E[i], E[j], E[k]):
+            hist[canonical_py((E[i], E[j], E[k]))] += 1
+    return hist
+
+
+def test_canonical_mask_is_the_smallest_relabelling(orc):
+    # the oracle's canonical form against one computed here from explicit region sets
+    for m in range(128):
+        sets = [set(), set(), set()]
+        for r, (name, inn) in enumerate(REGIONS.items()):
+            if m >> r & 1:
+                for s in range(3):
+                    if inn[s]:
+                        sets[s].add(name)
+        assert orc.canonical_mask(m) == canonical_py(sets), m
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_mask_histogram_matches_python_brute_force(orc, seed):
+    import hgen
+
+    for attempt in range(20):
+        rnd = random.Random(50 + seed + 1000 * attempt)
+        spec = hgen.HypergraphSpec(rnd.randint(6, 30), rnd.randint(10, 70), seed + 1000 * attempt,
+                                   hgen.SIZE_UNIFORM, 1, rnd.randint(2, 7),
+                                   zipf_s=rnd.uniform(0.3, 1.5), name="t")
+        try:
+            e_ptr, e_idx = hgen.generate(spec)
+            break
+        except RuntimeError:
+            continue
+    else:
+        raise AssertionError("no drawable case among 20 derived seeds")
+    edges = [e_idx[e_ptr[i]:e_ptr[i + 1]].tolist() for i in range(len(e_ptr) - 1)]
+    r = orc.count(e_ptr, e_idx, spec.num_vertices)
+    b = orc.count(e_ptr, e_idx, spec.num_vertices, mode="brute")
+    want = masks_brute_py(edges)
+    assert r.masks.tolist() == want == b.masks.tolist()
+    assert sum(want) == r.T
+
+
+def test_mask_histogram_sums_to_the_pattern_counts(orc):
+    import hgen
+
+    e_ptr, e_idx = hgen.prefix(*hgen.generate(hgen.TINY_PLAIN), 500)
+    r = orc.count(e_ptr, e_idx, 1000)
+    per_pattern = [0] * 21
+    for m in range(128):
+        if r.masks[m]:
+            assert orc.canonical_mask(m) == m   # only canonical bins are filled
+            per_pattern[orc.pattern_of_mask(m)] += int(r.masks[m])
+    assert per_pattern[0] == 0
+    assert per_pattern[1:] == [int(x) for x in r.counts[1:]]
+
+
+def test_mask_histogram_closed_forms(orc):
+    # sunflower: regions a, b, c, g; ordinary graph triangle: d, e, f; nested chain:
+    # the smallest relabelling of a, d, g
+    bit = {c: 1 << i for i, c in enumerate("abcdefg")}
+    n = 9
+    e_ptr, e_idx = csr_of([[0, 1 + 2 * k, 2 + 2 * k] for k in range(n)])
+    r = orc.count(e_ptr, e_idx, 1 + 2 * n)
+    sun = bit["a"] | bit["b"] | bit["c"] | bit["g"]
+    assert r.masks[sun] == math.comb(n, 3) and int(r.masks.sum()) == math.comb(n, 3)
+    e_ptr, e_idx = csr_of([[0, 1], [1, 2], [0, 2]])
+    r = orc.count(e_ptr, e_idx, 3)
+    assert r.masks[bit["d"] | bit["e"] | bit["f"]] == 1 and int(r.masks.sum()) == 1
+    e_ptr, e_idx = csr_of([list(range(k + 1)) for k in range(6)])
+    r = orc.count(e_ptr, e_idx, 6)
+    chain = canonical_py(({0, 1, 2}, {0, 1}, {0}))
+    assert r.masks[chain] == math.comb(6, 3) and int(r.masks.sum()) == math.comb(6, 3)
+
+
+def test_mask_histogram_relabelling_invariance(orc):
+    import hgen
+
+    e_ptr, e_idx = hgen.prefix(*hgen.generate(hgen.TINY_PLAIN), 400)
+    r = orc.count(e_ptr, e_idx, 1000)
+    rng = np.random.default_rng(3)
+    vperm = rng.permutation(1000)
+    eorder = rng.permutation(len(e_ptr) - 1)
+    p2, i2 = csr_of([sorted(vperm[e_idx[e_ptr[i]:e_ptr[i + 1]]].tolist()) for i in eorder])
+    assert orc.count(p2, i2, 1000).masks.tolist() == r.masks.tolist()
+
+
+def test_degrees_are_line_graph_row_sums(orc):
+    # |N(e_i)| against the row sums of the line graph's adjacency (H H^T > 0, no diagonal)
+    import hgen
+
+    e_ptr, e_idx = hgen.prefix(*hgen.generate(hgen.TINY_PLAIN), 400)
+    A = line_graph_adjacency(e_ptr, e_idx, 1000)
+    assert orc.degrees(e_ptr, e_idx, 1000).tolist() == A.sum(1).tolist()
