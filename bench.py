@@ -48,7 +48,9 @@ def parse_args():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-edges", type=int, default=8000,
                     help="hyperedges whose owned triangles the CPU baseline counts")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=-1,
+                    help="end-to-end steps from host buffers (-1: as many as --steps on the "
+                         "default workload, 3 on the others)")
     ap.add_argument("--dense-min-size", type=int, default=0,
                     help="hyperedges at least this large use the tensor-core tiles (0 auto, -1 off)")
     ap.add_argument("--dense-max-count", type=int, default=0,
@@ -319,7 +321,9 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    # timed region: device-resident inputs
+    # timed region: device-resident inputs, K steps with no per-kernel events (value),
+    # then K more steps with CUDA events around every launch (per-kernel durations for
+    # the roofline), both under the clock sampler
     clocks = ClockSampler(dev)
     barrier()
     torch.cuda.synchronize()
@@ -331,26 +335,31 @@ def run_ours(args):
         do_flush(k + 17)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        counts, st, cc, kt, cs = one_step(d_ptr, d_idx, timing=True)
+        counts, st, cc, kt, cs = one_step(d_ptr, d_idx)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         tri += int(counts[0])
+    torch.cuda.synchronize()
+    launches = hg.hg_kernel_launches() - launches0
+    barrier()
+    for k in range(args.steps):
+        do_flush(k + 57)
+        c3, _, _, kt, _ = one_step(d_ptr, d_idx, timing=True)
+        assert c3.tolist() == counts.tolist()
         for name, (ms, n) in kt.items():
             a = kernel_ms.setdefault(name, [0.0, 0])
             a[0] += ms
             a[1] += n
     torch.cuda.synchronize()
-    launches = hg.hg_kernel_launches() - launches0
     clk = clocks.stop()
-    barrier()
 
     tri_all, total_s = aggregate(float(tri), sum(step_ms) / 1000.0, dist, dev)
     value = tri_all / total_s
 
     # end to end through the C ABI from pinned host buffers (--e2e-steps 0 skips it)
     e2e_ms = []
-    for k in range(args.e2e_steps):
+    for k in range(args.steps if args.e2e_steps < 0 else args.e2e_steps):
         do_flush(k + 99)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -419,6 +428,8 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": dict(cfg, triangles_per_step=int(counts[0]), wedges=st["W"],
                        l2="256 MiB buffer written between steps, outside the per-step events",
+                       kernel_timing="per-launch CUDA events in K further steps after the K "
+                                     "steps that give value (those run without them)",
                        inputs="int64/int32 CSR resident in HBM", parallelism=f"replicas x{world}",
                        parity="counts equal stored oracle values" if parity else "not checked",
                        dense_tiles={"min_size": args.dense_min_size, "max_count": args.dense_max_count,
@@ -592,7 +603,7 @@ def run_batched(args):
 
     # end to end from pinned host buffers (upload inside the timed region)
     e2e_ms = []
-    for k in range(max(1, args.e2e_steps)):
+    for k in range(max(1, args.e2e_steps if args.e2e_steps >= 0 else 3)):
         (c3, _, _, _, _, _), ms = timed(lambda: batch_step(h_ptr, h_idx), 99 + k)
         assert np.array_equal(c3, counts)
         e2e_ms.append(ms)
@@ -740,7 +751,8 @@ def run_sample(args):
             return hg.hg_sample_estimate(h, seed, 0, N)
         finally:
             hg.hg_free(h)
-    e2e_ms = [timed(e2e_step, 90 + k)[1] for k in range(max(1, args.e2e_steps))]
+    e2e_ms = [timed(e2e_step, 90 + k)[1]
+              for k in range(max(1, args.e2e_steps if args.e2e_steps >= 0 else 3))]
 
     # HBM view of the sampling kernel: the reads it made (row pointers 8 B, packed
     # entries 4 B, vertex ids 4 B) over its event-timed duration

@@ -132,6 +132,18 @@ hg_status hg_build_wedges(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out
 hg_status hg_count_patterns(hg_graph* g, uint64_t counts[21]);
 
 /*
+ * The pattern of every hyper-triangle before any numbering (Sec. 2: a pattern is the
+ * set of non-empty Venn regions up to relabelling the three hyperedges).  masks[m] =
+ * hyper-triangles counted by the last hg_count_patterns whose region mask (bit r =
+ * region r of (a)..(g) non-empty), in canonical form (the smallest of its six
+ * relabellings, see hg_canonical_masks), is m; 0 at every non-canonical m.  H[p] is the
+ * sum of masks[m] over the canonical m of pattern p (hg_pattern_table).
+ *   masks[128]  out.
+ * Requires hg_count_patterns (HG_ERR_STATE before).  No device work.
+ */
+hg_status hg_mask_histogram(hg_graph* g, uint64_t masks[128]);
+
+/*
  * Hyperwedge-sampling estimate of the per-pattern counts (Sec. 4.1, Algorithm 6,
  * "Appro-bs"), with vertex-sampling rate sigma = 1.
  * The W hyperwedges (i, j), i < j, are numbered in the order O of Sec. 2 (by i,
@@ -258,11 +270,13 @@ hg_status hg_wait_flag(const int32_t* flag, int32_t limit_us, void* cuda_stream)
 
 /*
  * Line-graph degrees without allocating.  The paper has no counterpart: this is
- * for callers that cannot allocate device memory while they run - code in a
- * host function enqueued on a stream (which may not make allocating CUDA
- * calls), or a service whose device memory is a fixed arena owned by someone
- * else.  It computes what the count pass of hg_build_wedges computes, from
- * buffers the caller owns:
+ * for callers that cannot allocate device memory while they run - a service whose
+ * device memory is a fixed arena owned by someone else (reserved up front, or the
+ * pool of another framework), where a cudaMalloc would fail or stall the other
+ * streams on the device.  The call makes ordinary CUDA runtime calls (a memset, a
+ * launch, copies, a stream synchronisation), so it is made from plain host code,
+ * never from inside a host function enqueued on a stream.  It computes what the
+ * count pass of hg_build_wedges computes, from buffers the caller owns:
  *   num_edges            |E| >= 0
  *   edge_ptr, edge_vtx   device hyperedge->vertex CSR (as for hg_load_csr; rows
  *                        ascending, already valid - this call does not validate)
@@ -278,8 +292,10 @@ hg_status hg_wait_flag(const int32_t* flag, int32_t limit_us, void* cuda_stream)
  * hyperedge whose vertices lie in more than 16,384 other (hyperedge, vertex)
  * incidences does not fit a table: the call returns HG_ERR_UNSUPPORTED (and
  * degrees are then incomplete).  Equal hyperedges give HG_ERR_DUPLICATE_HYPEREDGE.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Calls share
+ * The array is placed on a device when the library's device code is loaded there
+ * (under lazy module loading: at the first call on that device).  The first call on
+ * a device also looks up the array's device address (with that device current);
+ * make that first call before any stream capture.  Calls share
  * the array and its previous contents: the call clears what must start at zero,
  * and two calls whose work overlaps on the same GPU (for example on two streams)
  * race on the array and corrupt each other.  No cudaMalloc, cudaFree or
@@ -348,6 +364,10 @@ hg_status hg_batch_build_wedges(hg_batch* b, const hg_tuning* opt);
  * Requires hg_batch_build_wedges.  Synchronises.
  */
 hg_status hg_batch_count_patterns(hg_batch* b, uint64_t* counts, hg_wedge_stats* stats);
+
+/* Per member, as hg_mask_histogram: masks [G][128] out.  Requires
+ * hg_batch_count_patterns.  No device work. */
+hg_status hg_batch_mask_histogram(hg_batch* b, uint64_t* masks);
 
 /* Def. 5.1 per member, as hg_clustering_coeff: cc, open, connected are [G] (each may
  * be NULL).  Requires hg_batch_count_patterns.  No device work. */
@@ -463,6 +483,13 @@ hg_status hg_server_destroy(hg_server* s);
  * hyper-triangle of three distinct hyperedges.  Host only; no device needed.
  */
 hg_status hg_pattern_table(uint8_t lut[128]);
+
+/*
+ * The library's canonical forms: canon[m] = the smallest region mask among the six
+ * relabellings of the three hyperedges of labelled mask m (Sec. 2: hyper-triangles of
+ * the same pattern, and only those, share a canonical mask).  Host only.
+ */
+hg_status hg_canonical_masks(uint8_t canon[128]);
 
 /*
  * Reads made by the last hg_sample_estimate on this handle (its G' for sigma < 1):

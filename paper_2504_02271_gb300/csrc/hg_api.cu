@@ -46,7 +46,7 @@ struct Small {
   unsigned long long deg_stats[3];   // sum C(deg,2), max deg, sum deg
   unsigned long long out_stats[3];   // sum C(d+,2), max d+, sum d+
   unsigned long long wide_max[2];    // close bucket 3: max d+, max |e_u|
-  unsigned long long hist[24];       // pattern histogram (bin 0 = unclassifiable)
+  unsigned long long hist[128];      // closure: labelled region masks; samplers: bins 0..20
   unsigned long long work[kCloseBuckets][3];   // closure per team shape: probes, E_y entries, out-entries
   unsigned long long found;                    // triples of hg_enumerate_pattern
   unsigned long long sample_work[3];           // last sampler launch: pointer, entry, id reads
@@ -115,6 +115,7 @@ struct hg_graph {
   std::vector<Block> count_blocks;
   bool counted = false;
   uint64_t counts[21] = {0};
+  uint64_t masks[128] = {0};   // canonical region-mask histogram of the last count
   hg_close_stats cstats{};
   // a wave of a batch: nm members, member m owning hyperedges [m_eoff[m], m_eoff[m+1])
   // and union vertices [m_voff[m], m_voff[m+1])
@@ -123,8 +124,9 @@ struct hg_graph {
   int32_t* m_voff = nullptr;
   int32_t* wcr = nullptr;                 // per-row inclusion wedges (build)
   unsigned long long* mstats = nullptr;   // [nm][4]: sum deg, sum C(deg,2), W_c, max deg
-  unsigned long long* mhist = nullptr;    // [nm][24] pattern bins (count)
-  std::vector<unsigned long long> h_mstats, h_mhist;
+  unsigned long long* mhist = nullptr;    // [nm][128] labelled region-mask bins (count)
+  std::vector<unsigned long long> h_mstats;
+  std::vector<uint64_t> h_mmasks;         // [nm][128] canonical region-mask histograms
   // timing
   bool timing = false;
   std::vector<KTime> pending;
@@ -323,6 +325,47 @@ void build_lut(uint8_t lut[128]) {
   for (int m = 0; m < 128; ++m) lut[m] = (uint8_t)pattern_of(m);
 }
 
+// Canonical form of a labelled region mask: the smallest mask among the six orders of
+// the three hyperedges.  Region r is coded by the hyperedges holding it (bit 0 = first,
+// bit 1 = second, bit 2 = third: a 1, b 2, c 4, d 3, e 6, f 5, g 7); reordering the
+// hyperedges permutes those three bits.
+int canonical_of(int m) {
+  static const int kCode[7] = {1, 2, 4, 3, 6, 5, 7};
+  static const int kOrders[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2},
+                                    {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  int best = 127;
+  for (const auto& o : kOrders) {
+    int out = 0;
+    for (int r = 0; r < 7; ++r) {
+      if (!(m >> r & 1)) continue;
+      int code = 0;   // new position q holds old hyperedge o[q]
+      for (int q = 0; q < 3; ++q) code |= (kCode[r] >> o[q] & 1) << q;
+      for (int r2 = 0; r2 < 7; ++r2)
+        if (kCode[r2] == code) out |= 1 << r2;
+    }
+    best = std::min(best, out);
+  }
+  return best;
+}
+
+// Fold 128 labelled-mask bins into canonical-mask bins and the 21 counts.  False when a
+// bin that is not a hyper-triangle of three distinct hyperedges holds anything.
+bool fold_masks(const unsigned long long labelled[128], uint64_t canon[128],
+                uint64_t counts[21]) {
+  uint8_t lut[128];
+  build_lut(lut);
+  std::memset(canon, 0, sizeof(uint64_t) * 128);
+  std::memset(counts, 0, sizeof(uint64_t) * 21);
+  for (int m = 0; m < 128; ++m) {
+    if (!labelled[m]) continue;
+    if (lut[m] == 0) return false;
+    canon[canonical_of(m)] += labelled[m];
+    counts[lut[m]] += labelled[m];
+    counts[0] += labelled[m];
+  }
+  return true;
+}
+
 hg_status check_device(int* dev, int* nsm) {
   int n = 0;
   if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
@@ -443,9 +486,11 @@ hg_status dense_impl(hg_graph* g, const hg_tuning* opt, DenseInfo* dn) {
   const int32_t min_size = forced ? want : 32;
   const int64_t cap = (opt && opt->dense_max_count > 0) ? opt->dense_max_count
                                                         : std::max<int64_t>(g->ne / 100, 1);
-  if (g->max_size < min_size) return HG_OK;
-  // size histogram -> smallest threshold >= min_size keeping at most `cap` hyperedges
-  const int32_t max_bin = std::min<int32_t>(g->max_size, 1 << 20);
+  if (g->max_size < min_size || min_size > kDenseMaxOmega) return HG_OK;
+  // size histogram -> smallest threshold >= min_size keeping at most `cap` hyperedges of at
+  // most kDenseMaxOmega vertices (the tile output holds omega in 16 bits); larger
+  // hyperedges stay on the hash path
+  const int32_t max_bin = std::min<int32_t>(g->max_size, kDenseMaxOmega + 1);
   unsigned long long* hist = alloc_t<unsigned long long>(g, g->build_blocks, (int64_t)max_bin + 1);
   if (!hist) return HG_ERR_OOM;
   HG_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * ((size_t)max_bin + 1), s));
@@ -455,24 +500,24 @@ hg_status dense_impl(hg_graph* g, const hg_tuning* opt, DenseInfo* dn) {
                           cudaMemcpyDeviceToHost, s));
   HG_CUDA(cudaStreamSynchronize(s));
   int64_t above = 0;
-  int32_t t = max_bin + 1;
-  for (int32_t k = max_bin; k >= min_size; --k) {
+  int32_t t = kDenseMaxOmega + 1;
+  for (int32_t k = std::min<int32_t>(max_bin, kDenseMaxOmega); k >= min_size; --k) {
     if (above + (int64_t)h[k] > cap) break;
     above += (int64_t)h[k];
     t = k;
   }
   if (above == 0 || (!forced && above < kDenseMinRows)) return HG_OK;
   const int64_t rows_pad = dense_round_rows(above), k_pad = dense_round_k(g->nv);
-  if (rows_pad * (k_pad + rows_pad) > kDenseMaxBytes) return HG_OK;   // stays on the hash path
+  if (rows_pad * (k_pad + 2 * rows_pad) > kDenseMaxBytes) return HG_OK;   // stays on the hash path
   int32_t* heavy_idx = alloc_t<int32_t>(g, g->build_blocks, g->ne);
   int32_t* ids = alloc_t<int32_t>(g, g->build_blocks, above);
   uint8_t* a = alloc_t<uint8_t>(g, g->build_blocks, rows_pad * k_pad);
-  uint8_t* omega = alloc_t<uint8_t>(g, g->build_blocks, rows_pad * rows_pad);
+  uint16_t* omega = alloc_t<uint16_t>(g, g->build_blocks, rows_pad * rows_pad);
   if (!heavy_idx || !ids || !a || !omega) return HG_ERR_OOM;
   int32_t* count = g->small->counters + 8;
   HG_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t), s));
   HG_CUDA(cudaMemsetAsync(a, 0, (size_t)(rows_pad * k_pad), s));
-  launch_pick_heavy(g->esize, g->ne, t, (int32_t)above, heavy_idx, ids, count, s);
+  launch_pick_heavy(g->esize, g->ne, t, kDenseMaxOmega, (int32_t)above, heavy_idx, ids, count, s);
   launch_fill_dense(g->e_ptr, g->e_idx, ids, (int32_t)above, a, k_pad, s);
   t_begin(g, "dense_omega");
   HG_CUDA(launch_dense_omega(a, above, rows_pad, k_pad, omega, &g->small->err, s));
@@ -946,14 +991,11 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   // pattern bins: one set per member of a batch wave, else the handle's own
   unsigned long long* hist = g->small->hist;
   if (g->nm > 0) {
-    g->mhist = alloc_t<unsigned long long>(g, g->count_blocks, (int64_t)g->nm * 24);
+    g->mhist = alloc_t<unsigned long long>(g, g->count_blocks, (int64_t)g->nm * 128);
     if (!g->mhist) return HG_ERR_OOM;
-    HG_CUDA(cudaMemsetAsync(g->mhist, 0, sizeof(unsigned long long) * 24 * (size_t)g->nm, s));
+    HG_CUDA(cudaMemsetAsync(g->mhist, 0, sizeof(unsigned long long) * 128 * (size_t)g->nm, s));
     hist = g->mhist;
   }
-  uint8_t lut[128];
-  build_lut(lut);
-  close_set_lut(lut, s);
   CloseBuckets cb;
   for (int k = 0; k < kCloseBuckets; ++k) cb.lists[k] = lists + k * ne;
   cb.count = g->small->bucket_count + 4;
@@ -1003,26 +1045,21 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
     HG_TRY(sync_small(g, &h));
   }
   t_collect(g);
-  if (g->nm > 0) {   // the wave's bins are the sums of its members'
-    g->h_mhist.assign(24 * (size_t)g->nm, 0);
-    HG_CUDA(cudaMemcpyAsync(g->h_mhist.data(), g->mhist, sizeof(unsigned long long) * g->h_mhist.size(),
+  if (g->nm > 0) {   // per member, and the wave's bins as the sums of its members'
+    std::vector<unsigned long long> lab(128 * (size_t)g->nm);
+    HG_CUDA(cudaMemcpyAsync(lab.data(), g->mhist, sizeof(unsigned long long) * lab.size(),
                             cudaMemcpyDeviceToHost, s));
     HG_CUDA(cudaStreamSynchronize(s));
-    for (int k = 0; k < 24; ++k) {
-      unsigned long long x = 0;
-      for (int32_t m = 0; m < g->nm; ++m) x += g->h_mhist[24 * (size_t)m + k];
-      h.hist[k] = x;
+    g->h_mmasks.assign(128 * (size_t)g->nm, 0);
+    for (int k = 0; k < 128; ++k) h.hist[k] = 0;
+    uint64_t unused[21];
+    for (int32_t m = 0; m < g->nm; ++m) {
+      if (!fold_masks(lab.data() + 128 * (size_t)m, g->h_mmasks.data() + 128 * (size_t)m, unused))
+        return HG_ERR_INTERNAL;
+      for (int k = 0; k < 128; ++k) h.hist[k] += lab[128 * (size_t)m + k];
     }
   }
-  if (h.hist[0] != 0) return HG_ERR_INTERNAL;
-  for (int k = 21; k < 24; ++k)
-    if (h.hist[k] != 0) return HG_ERR_INTERNAL;
-  uint64_t total = 0;
-  for (int p = 1; p <= 20; ++p) {
-    g->counts[p] = h.hist[p];
-    total += h.hist[p];
-  }
-  g->counts[0] = total;
+  if (!fold_masks(h.hist, g->masks, g->counts)) return HG_ERR_INTERNAL;
   std::memset(&g->cstats, 0, sizeof(g->cstats));
   for (int k = 0; k < kCloseBuckets; ++k) {
     g->cstats.bucket_probes[k] = h.work[k][0];
@@ -1461,6 +1498,18 @@ hg_status hg_batch_build_wedges(hg_batch* b, const hg_tuning* opt) {
   return HG_OK;
 }
 
+// The 21 counts of member q of a wave, from its canonical mask histogram.
+static void member_counts(const hg_graph* g, int32_t q, uint64_t counts[21]) {
+  uint8_t lut[128];
+  build_lut(lut);
+  std::memset(counts, 0, sizeof(uint64_t) * 21);
+  const uint64_t* mk = g->h_mmasks.data() + 128 * (size_t)q;
+  for (int m = 0; m < 128; ++m) {
+    counts[lut[m]] += mk[m];
+    counts[0] += mk[m];
+  }
+}
+
 hg_status hg_batch_count_patterns(hg_batch* b, uint64_t* counts, hg_wedge_stats* stats) {
   if (!b) return HG_ERR_INVALID_ARG;
   if (!b->built) return HG_ERR_STATE;
@@ -1473,14 +1522,11 @@ hg_status hg_batch_count_patterns(hg_batch* b, uint64_t* counts, hg_wedge_stats*
     const hg_graph* g = b->waves[k];
     for (int32_t q = 0; q < g->nm; ++q) {
       const size_t m = (size_t)(b->first[k] + q);
-      const unsigned long long* h = g->h_mhist.data() + 24 * (size_t)q;
+      uint64_t h[21];
+      member_counts(g, q, h);
       const unsigned long long* st = g->h_mstats.data() + 4 * (size_t)q;
-      uint64_t total = 0;
-      for (int p = 1; p <= 20; ++p) total += h[p];
-      if (counts) {
-        counts[21 * m] = total;
-        for (int p = 1; p <= 20; ++p) counts[21 * m + (size_t)p] = h[p];
-      }
+      if (counts)
+        for (int p = 0; p <= 20; ++p) counts[21 * m + (size_t)p] = h[p];
       if (st[0] & 1) return HG_ERR_INTERNAL;
       if (stats) {
         hg_wedge_stats& w = stats[m];
@@ -1505,9 +1551,9 @@ hg_status hg_batch_clustering_coeff(hg_batch* b, const double eps[20], double* c
     const hg_graph* g = b->waves[k];
     for (int32_t q = 0; q < g->nm; ++q) {
       const size_t m = (size_t)(b->first[k] + q);
-      const unsigned long long* h = g->h_mhist.data() + 24 * (size_t)q;
-      uint64_t total = 0;
-      for (int p = 1; p <= 20; ++p) total += h[p];
+      uint64_t h[21];
+      member_counts(g, q, h);
+      const uint64_t total = h[0];
       const uint64_t connected = g->h_mstats[4 * (size_t)q + 1];
       const uint64_t open = connected - 3 * total;
       // Def. 5.1, summed in order p = 1..20 in IEEE double, as hg_clustering_coeff
@@ -1565,6 +1611,30 @@ hg_status hg_kernel_launches(uint64_t* n) {
 hg_status hg_pattern_table(uint8_t lut[128]) {
   if (!lut) return HG_ERR_INVALID_ARG;
   build_lut(lut);
+  return HG_OK;
+}
+
+hg_status hg_canonical_masks(uint8_t canon[128]) {
+  if (!canon) return HG_ERR_INVALID_ARG;
+  for (int m = 0; m < 128; ++m) canon[m] = (uint8_t)canonical_of(m);
+  return HG_OK;
+}
+
+hg_status hg_mask_histogram(hg_graph* g, uint64_t masks[128]) {
+  if (!g || !masks) return HG_ERR_INVALID_ARG;
+  if (!g->counted) return HG_ERR_STATE;
+  std::memcpy(masks, g->masks, sizeof(g->masks));
+  return HG_OK;
+}
+
+hg_status hg_batch_mask_histogram(hg_batch* b, uint64_t* masks) {
+  if (!b || !masks) return HG_ERR_INVALID_ARG;
+  if (!b->counted) return HG_ERR_STATE;
+  for (size_t k = 0; k < b->waves.size(); ++k) {
+    const hg_graph* g = b->waves[k];
+    std::memcpy(masks + 128 * (size_t)b->first[k], g->h_mmasks.data(),
+                sizeof(uint64_t) * 128 * (size_t)g->nm);
+  }
   return HG_OK;
 }
 

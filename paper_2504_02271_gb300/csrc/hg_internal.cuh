@@ -92,7 +92,7 @@ void launch_candidates(const DevGraph& g, int64_t* cand, unsigned long long* max
 struct DenseInfo {
   const int32_t* heavy_idx;   // [ne] position in the heavy list or -1; nullptr = no dense path
   const int32_t* ids;         // [nh] hyperedge id of each heavy position
-  const uint8_t* omega;       // [rows_pad x rows_pad] omega of heavy pairs
+  const uint16_t* omega;      // [rows_pad x rows_pad] omega of heavy pairs
   int64_t ld;                 // row stride of omega
   int32_t nh;
 };
@@ -101,12 +101,16 @@ int64_t dense_round_rows(int64_t n);
 int64_t dense_round_k(int64_t k);
 void launch_size_hist(const int32_t* esize, int32_t ne, int32_t max_bin, unsigned long long* hist,
                       cudaStream_t s);
-void launch_pick_heavy(const int32_t* esize, int32_t ne, int32_t min_size, int32_t cap,
-                       int32_t* heavy_idx, int32_t* ids, int32_t* count, cudaStream_t s);
+// heavy: min_size <= |e_i| <= max_size, at most cap of them
+void launch_pick_heavy(const int32_t* esize, int32_t ne, int32_t min_size, int32_t max_size,
+                       int32_t cap, int32_t* heavy_idx, int32_t* ids, int32_t* count,
+                       cudaStream_t s);
+// omega values the tile kernel writes exactly (uint16 output)
+constexpr int32_t kDenseMaxOmega = 65535;
 void launch_fill_dense(const int64_t* e_ptr, const int32_t* e_idx, const int32_t* ids, int32_t nh,
                        uint8_t* a, int64_t lda, cudaStream_t s);
 cudaError_t launch_dense_omega(const uint8_t* a, int64_t rows, int64_t rows_pad, int64_t k_pad,
-                               uint8_t* omega, int* err, cudaStream_t s);
+                               uint16_t* omega, int* err, cudaStream_t s);
 
 // k_wedge.cu
 struct WedgeBuckets {
@@ -208,10 +212,9 @@ struct CloseBuckets {
   int32_t* lists[kCloseBuckets];
   int32_t* count;     // [kCloseBuckets]
 };
-// all_block: send every hyperedge to the block kernel (bucket 3)
+// all_block: send every hyperedge to the global-table kernel (bucket 6)
 void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,
                          unsigned long long* wide_max, bool all_block, cudaStream_t s);
-void close_set_lut(const uint8_t lut[128], cudaStream_t s);
 // n: list length (host copy); n_p: the same on the device; counter: zeroed fetch counter;
 // work[0] += probes (entries of out(v) streamed), work[1] += E_y entries scanned for masks;
 // warp kernels append hyperedges their tables cannot hold (every hyperedge when

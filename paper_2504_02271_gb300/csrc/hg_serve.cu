@@ -409,6 +409,9 @@ hg_status hg_server_cancel(hg_server* S, uint64_t ticket) {
     S->done[ticket] = r;
   }
   S->cv_done.notify_all();   // its waiter, and a drain the emptier queue may end
+  // a cancelled head of the queue may have been what kept the next query out of the
+  // memory budget: let idle workers look at the queue again
+  S->cv_work.notify_all();
   return HG_OK;
 }
 

@@ -8,15 +8,16 @@
 //   2. records for every out-neighbour x the set Omega_ux = e_u cap e_x as a bit
 //      mask over the positions of e_u (scanning E_y for each vertex y of e_u),
 //   3. streams out(v) for every v in out(u) and looks each w up in the set.
-// A hit is a hyper-triangle.  With m_uv, m_uw the masks,
-//   g = |e_u cap e_v cap e_w| = popc(m_uv & m_uw),  omega_uv = popc(m_uv),
-//   omega_uw = popc(m_uw),  omega_vw from the entry of out(v),
-// and the seven Venn regions of Sec. 2 follow by inclusion-exclusion:
-//   a = |e_u| - omega_uv - omega_uw + g, b = |e_v| - omega_uv - omega_vw + g,
-//   c = |e_w| - omega_uw - omega_vw + g, d = omega_uv - g, e = omega_vw - g,
-//   f = omega_uw - g, and g itself.
-// Their non-emptiness bits index a 128-entry table giving the pattern 1..20; a
-// block-local histogram is flushed to 64-bit global counters.
+// A hit is a hyper-triangle.  With m_uv, m_uw the masks, F the mask of all of e_u,
+// omega_vw from the entry of out(v), r_x = |e_x| - omega_ux (the part of e_x outside
+// e_u) and t = omega_vw - popc(m_uv & m_uw) (the part of e_v cap e_w outside e_u), the
+// seven Venn regions of Sec. 2 are non-empty exactly when
+//   (a) F & ~(m_uv | m_uw) != 0   (b) r_v > t   (c) r_w > t   (d) m_uv & ~m_uw != 0
+//   (e) t > 0   (f) m_uw & ~m_uv != 0   (g) m_uv & m_uw != 0
+// (inclusion-exclusion: b = |e_v| - omega_uv - omega_vw + g = r_v - t, and so on).
+// The seven bits, labelled (u, v, w), index a block-local 128-bin histogram that is
+// flushed to 64-bit global counters; the host folds the labelled masks into canonical
+// masks and patterns.
 #include <mutex>
 #include <type_traits>
 
@@ -26,14 +27,12 @@ namespace hg {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kBins = 24;      // pattern 0 (invalid) .. 20, padded
+constexpr int kBins = 128;     // labelled region masks (bit r = region r non-empty)
 constexpr int kHistCopies = 4; // spread same-pattern increments of the block kernel
 constexpr int kWideThreads = 256;
 constexpr int kWideFilterLog2 = 18;   // 32 KiB shared filter per wide-team block
 constexpr int kWideUnroll = 4;        // 32-entry loads in flight per warp
 constexpr int kWideBlocksPerSm = 4;
-
-__constant__ uint8_t c_lut[128];
 
 template <bool PACKED>
 __device__ __forceinline__ void get_entry(const Oriented& o, int64_t at, int32_t& nbr, int32_t& om) {
@@ -47,12 +46,20 @@ __device__ __forceinline__ void get_entry(const Oriented& o, int64_t at, int32_t
   }
 }
 
-__device__ __forceinline__ int region_bits(int szu, int szv, int szw, int wuv, int wuw, int wvw,
-                                           int g) {
-  const int a = szu - wuv - wuw + g, b = szv - wuv - wvw + g, c = szw - wuw - wvw + g;
-  return (a > 0) | ((b > 0) << 1) | ((c > 0) << 2) | ((wuv > g) << 3) | ((wvw > g) << 4) |
-         ((wuw > g) << 5) | ((g > 0) << 6);
+// Labelled region mask of the hyper-triangle (u, v, w) from one-word vertex masks (see
+// the header): fu = all of e_u, muv/muw = Omega_uv/Omega_uw, rv/rw = |e_x| - omega_ux,
+// om = omega_vw.
+__device__ __forceinline__ uint32_t region_bits(uint32_t fu, uint32_t muv, uint32_t muw, int rv,
+                                                int rw, int om) {
+  const uint32_t i = muv & muw;
+  const int t = om - __popc(i);
+  return (uint32_t)((fu & ~(muv | muw)) != 0u) | ((uint32_t)(rv > t) << 1) |
+         ((uint32_t)(rw > t) << 2) | ((uint32_t)((muv & ~muw) != 0u) << 3) |
+         ((uint32_t)(t > 0) << 4) | ((uint32_t)((muw & ~muv) != 0u) << 5) |
+         ((uint32_t)(i != 0u) << 6);
 }
+
+__device__ __forceinline__ uint32_t full_mask(int sz) { return sz >= 32 ? ~0u : (1u << sz) - 1u; }
 
 // ------------------------------------------------------------------ warp per u
 //
@@ -70,8 +77,15 @@ __device__ __forceinline__ int region_bits(int szu, int szv, int szw, int wuv, i
 // consecutive entries and every slot is full.  Hits are queued and classified
 // 32 at a time, so the classification runs with every lane active.
 
+// Entries of out(v) loaded per lane before their probes (loads in flight per warp):
+// kWarpUnroll in the warp teams, kUnroll in the block teams.
+#ifndef HG_CLOSE_WARP_UNROLL
+#define HG_CLOSE_WARP_UNROLL 8
+#endif
+constexpr int kWarpUnroll = HG_CLOSE_WARP_UNROLL;
 constexpr int kUnroll = 4;
 constexpr int kQueue = 32 * kUnroll + 32;
+constexpr int kWarpQueue = 32 * kWarpUnroll + 32;
 constexpr int kCuckooTries = 16;
 constexpr int kStash = 8;
 
@@ -89,9 +103,9 @@ struct alignas(16) WarpTables {
   int64_t kbeg[D];
   int32_t kcnt[D];
   uint32_t kmask[D];                         // Omega_ux of the k-th out-neighbour x
-  uint16_t ksz[D];                           // |e_x|
-  uint32_t queue[kQueue];                    // hits: (k_v << 24) | (k_w << 8) | omega_vw
-  int32_t qom[PACKED ? 1 : kQueue];          // omega_vw when it may not fit 8 bits
+  uint16_t ksz[D];                           // |e_x|, then |e_x| - omega_ux once masks are built
+  uint32_t queue[kWarpQueue];                // hits: (k_v << 24) | (k_w << 8) | omega_vw
+  int32_t qom[PACKED ? 1 : kWarpQueue];      // omega_vw when it may not fit 8 bits
   int32_t nstash;
 };
 
@@ -103,21 +117,55 @@ __device__ __forceinline__ uint32_t cuckoo_h2(uint32_t key, int t_log2) {
 }
 
 // Index k in out(u) of hyperedge x, or -1.  Branch-free but for the stash scan,
-// whose length nst is the same on every lane of the warp.
+// whose length nst is the same on every lane of the warp.  An item (x << 8) | k
+// xor-ed with x << 8 leaves exactly k (< 256) when the keys agree, and a value of
+// at least 256 otherwise.  The empty item (all ones) would answer 255 to a key whose
+// low 24 bits are all ones; no hyperedge id of a packed layout (< 2^24 - 1) has
+// them, and lanes without an entry look up u itself, which is never in out(u).
 template <class TT>
 __device__ __forceinline__ int warp_find(const TT& t, int32_t x, int nst) {
   using Item = typename TT::Item;
   const uint32_t key = (uint32_t)x;
-  const Item a = t.c1[cuckoo_h1(key, TT::T_LOG2)];
-  const Item b = t.c2[cuckoo_h2(key, TT::T_LOG2)];
-  int k = (a >> 8) == (Item)key ? (int)(a & 0xffu) : -1;
-  k = (b >> 8) == (Item)key ? (int)(b & 0xffu) : k;
+  const Item k8 = (Item)key << 8;
+  const Item a = t.c1[cuckoo_h1(key, TT::T_LOG2)] ^ k8;
+  const Item b = t.c2[cuckoo_h2(key, TT::T_LOG2)] ^ k8;
+  int k = a < 256 ? (int)a : -1;
+  k = b < 256 ? (int)b : k;
   for (int i = 0; i < nst; ++i) {
-    const Item c = t.stash[i];
-    k = (c >> 8) == (Item)key ? (int)(c & 0xffu) : k;
+    const Item c = t.stash[i] ^ k8;
+    k = c < 256 ? (int)c : k;
   }
   return k;
 }
+
+// Start of out(x)'s entries in the oriented rows: a pointer per layout, so that a probe
+// addresses entry j of the current row with one 32-bit index.
+template <bool PACKED>
+struct RowPtr {
+  const uint32_t* p;   // packed entries
+  const int32_t* n;    // unpacked: neighbour ids
+  const int32_t* w;    // unpacked: omega
+  __device__ __forceinline__ void at(const Oriented& o, int64_t off) {
+    if (PACKED) {
+      p = o.packed + off;
+    } else {
+      n = o.nbr + off;
+      w = o.omega + off;
+    }
+  }
+  __device__ __forceinline__ void load(int32_t j, int32_t& nbr, int32_t& om) const {
+    if (PACKED) {
+      const uint32_t x = __ldg(p + j);
+      nbr = (int32_t)(x >> 8);
+      om = (int32_t)(x & 0xffu);
+    } else {
+      nbr = __ldg(n + j);
+      om = __ldg(w + j);
+    }
+  }
+  // packed layout only: the entry as stored, (nbr << 8) | omega
+  __device__ __forceinline__ uint32_t raw(int32_t j) const { return __ldg(p + j); }
+};
 
 __device__ __forceinline__ uint32_t filt_bit(uint32_t key, int bits_log2) {
   return (key * 0x85EBCA6Bu) >> (32 - bits_log2);
@@ -160,15 +208,11 @@ __device__ __forceinline__ void warp_flush(RunHist& rh, uint32_t* hist,
 // Classify queued hit number `at`: v and w are out-neighbours number kv and kw of u.
 template <int D_LOG2, bool PACKED>
 __device__ __forceinline__ void classify_queued(const WarpTables<D_LOG2, PACKED>& t, int at,
-                                                int szu, const uint8_t* lut, uint32_t* hist,
-                                                RunHist& rh) {
+                                                uint32_t fu, uint32_t* hist, RunHist& rh) {
   const uint32_t e = t.queue[at];
   const uint32_t kv = e >> 24, kw = (e >> 8) & 0xffu;
   const int om = PACKED ? (int)(e & 0xffu) : t.qom[at];
-  const uint32_t muv = t.kmask[kv], muw = t.kmask[kw];
-  const int gg = __popc(muv & muw);
-  const int bits = region_bits(szu, t.ksz[kv], t.ksz[kw], __popc(muv), __popc(muw), om, gg);
-  rh.add(lut[bits], hist);
+  rh.add(region_bits(fu, t.kmask[kv], t.kmask[kw], t.ksz[kv], t.ksz[kw], om), hist);
 }
 
 template <int D_LOG2, int WARPS, bool PACKED>
@@ -183,10 +227,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   TT* tabs = reinterpret_cast<TT*>(dyn_smem);   // WARPS tables
   __shared__ uint32_t hist[WARPS][kBins];
-  __shared__ uint8_t lut[128];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   TT& t = tabs[w];
-  for (int k = threadIdx.x; k < 128; k += blockDim.x) lut[k] = c_lut[k];
   for (int k = lane; k < kBins; k += 32) hist[w][k] = 0;
   __syncthreads();
   const int32_t n = *n_p;
@@ -295,6 +337,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
     since_flush += (unsigned long long)F;
     outs += (unsigned long long)du;
     __syncwarp();
+    // |e_x| -> |e_x| - omega_ux, the part of e_x outside e_u
+    for (int k = lane; k < du; k += 32) t.ksz[k] = (uint16_t)(t.ksz[k] - __popc(t.kmask[k]));
+    const uint32_t fu = full_mask(szu);
+    __syncwarp();
 
     // 3. closure over the flat range of all out(v), v in out(u)
     int qn = 0;   // queued hits (the same on every lane)
@@ -304,35 +350,44 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
       cj -= ccnt;
       if (++ck < du) ccnt = t.kcnt[ck];
     }
-    int64_t cb = ck < du ? t.kbeg[ck] : 0;
-    for (int base = 0; base < F; base += 32 * kUnroll) {
-      int32_t ent_w[kUnroll], ent_om[kUnroll], ent_k[kUnroll];
+    RowPtr<PACKED> rp;
+    rp.at(o, ck < du ? t.kbeg[ck] : 0);
+    for (int base = 0; base < F; base += 32 * kWarpUnroll) {
+      // packed: the raw entry (w << 8) | omega_vw in one register; no entry: u << 8
+      // (u is never in out(u)).  Unpacked: w and omega_vw apart.
+      int32_t ent_w[kWarpUnroll], ent_om[PACKED ? 1 : kWarpUnroll], ent_k[kWarpUnroll];
 #pragma unroll
-      for (int q = 0; q < kUnroll; ++q) {
+      for (int q = 0; q < kWarpUnroll; ++q) {
         ent_k[q] = ck;
-        ent_w[q] = -1;
-        ent_om[q] = 0;
-        if (ck < du) get_entry<PACKED>(o, cb + cj, ent_w[q], ent_om[q]);
+        if (PACKED) {
+          ent_w[q] = (int32_t)((uint32_t)u << 8);
+          if (ck < du) ent_w[q] = (int32_t)rp.raw(cj);
+        } else {
+          ent_w[q] = u;
+          ent_om[q] = 0;
+          if (ck < du) rp.load(cj, ent_w[q], ent_om[q]);
+        }
         cj += 32;
         while (cj >= ccnt && ck < du) {
           cj -= ccnt;
           if (++ck < du) {
             ccnt = t.kcnt[ck];
-            cb = t.kbeg[ck];
+            rp.at(o, t.kbeg[ck]);
           }
         }
       }
       // probe; hits go to the warp's queue as (index of v, index of w, omega_vw)
 #pragma unroll
-      for (int q = 0; q < kUnroll; ++q) {
-        const int kw = warp_find(t, ent_w[q], nst);   // -1 never matches a key
+      for (int q = 0; q < kWarpUnroll; ++q) {
+        const int32_t x = PACKED ? (int32_t)((uint32_t)ent_w[q] >> 8) : ent_w[q];
+        const int kw = warp_find(t, x, nst);
         const bool hit = kw >= 0;
         const unsigned bal = __ballot_sync(kFull, hit);
         if (hit) {
           const int at = qn + __popc(bal & ((1u << lane) - 1u));
           t.queue[at] = ((uint32_t)ent_k[q] << 24) | ((uint32_t)kw << 8) |
-                        (PACKED ? (uint32_t)ent_om[q] : 0u);
-          if (!PACKED) t.qom[at] = ent_om[q];
+                        (PACKED ? ((uint32_t)ent_w[q] & 0xffu) : 0u);
+          if (!PACKED) t.qom[at] = ent_om[PACKED ? 0 : q];
         }
         qn += __popc(bal);
       }
@@ -340,11 +395,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
       // classify full rounds of 32 hits with every lane busy
       while (qn >= 32) {
         qn -= 32;
-        classify_queued<D_LOG2, PACKED>(t, qn + lane, szu, lut, hist[w], rh);
+        classify_queued<D_LOG2, PACKED>(t, qn + lane, fu, hist[w], rh);
         __syncwarp();
       }
     }
-    if (lane < qn) classify_queued<D_LOG2, PACKED>(t, lane, szu, lut, hist[w], rh);
+    if (lane < qn) classify_queued<D_LOG2, PACKED>(t, lane, fu, hist[w], rh);
     __syncwarp();
   }
   warp_flush(rh, hist[w], hist_out + (size_t)cur * kBins, lane);
@@ -388,7 +443,7 @@ struct alignas(16) BlockTables {
   int64_t kbeg[D];
   int32_t kpre[D + 1];       // exclusive prefix of the out-degrees of out(u)
   uint32_t kmask[D];
-  uint16_t ksz[D];
+  uint16_t ksz[D];           // |e_x|, then |e_x| - omega_ux once masks are built
   uint32_t queue[WARPS][kQueue];   // hits: (k_v << 16) | k_w ; omega in qom
   uint8_t qom8[PACKED ? WARPS : 1][PACKED ? kQueue : 1];
   int32_t qom[PACKED ? 1 : WARPS][PACKED ? 1 : kQueue];
@@ -423,10 +478,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   TT& t = *reinterpret_cast<TT*>(dyn_smem);
   __shared__ uint32_t hist[WARPS][kBins];
-  __shared__ uint8_t lut[128];
   __shared__ int32_t s_r;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int k = threadIdx.x; k < 128; k += NT) lut[k] = c_lut[k];
   for (int k = threadIdx.x; k < WARPS * kBins; k += NT) (&hist[0][0])[k] = 0;
   const int32_t n = *n_p;
   RunHist rh;
@@ -557,6 +610,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
       if (lane == 0) t.kpre[0] = 0;
     }
     __syncthreads();
+    // |e_x| -> |e_x| - omega_ux, the part of e_x outside e_u
+    for (int k = threadIdx.x; k < du; k += NT) t.ksz[k] = (uint16_t)(t.ksz[k] - __popc(t.kmask[k]));
+    __syncthreads();
+    const uint32_t fu = full_mask(szu);
     const int32_t F = t.kpre[du];
     since_flush += (unsigned long long)F;   // the same on every thread
     if (threadIdx.x == 0) {
@@ -623,10 +680,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
         const uint32_t e = queue[at];
         const uint32_t kv = e >> 16, kw = e & 0xffffu;
         const int om = PACKED ? (int)t.qom8[w][at] : t.qom[w][at];
-        const uint32_t muv = t.kmask[kv], muw = t.kmask[kw];
-        const int gg = __popc(muv & muw);
-        rh.add(lut[region_bits(szu, t.ksz[kv], t.ksz[kw], __popc(muv), __popc(muw), om, gg)],
-               hist[w]);
+        rh.add(region_bits(fu, t.kmask[kv], t.kmask[kw], t.ksz[kv], t.ksz[kw], om), hist[w]);
         __syncwarp();
       }
     }
@@ -634,10 +688,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
       const uint32_t e = queue[lane];
       const uint32_t kv = e >> 16, kw = e & 0xffffu;
       const int om = PACKED ? (int)t.qom8[w][lane] : t.qom[w][lane];
-      const uint32_t muv = t.kmask[kv], muw = t.kmask[kw];
-      const int gg = __popc(muv & muw);
-      rh.add(lut[region_bits(szu, t.ksz[kv], t.ksz[kw], __popc(muv), __popc(muw), om, gg)],
-             hist[w]);
+      rh.add(region_bits(fu, t.kmask[kv], t.kmask[kw], t.ksz[kv], t.ksz[kw], om), hist[w]);
     }
     __syncwarp();
   }
@@ -661,7 +712,7 @@ struct WideScratch {
   uint32_t* c1;     // [cap]
   uint32_t* c2;     // [cap]
   uint32_t* mask;   // [dmax * words]
-  int32_t* ksz;     // [dmax]
+  int32_t* ksz;     // [dmax] |e_x|, then |e_x| - omega_ux once masks are built
   int32_t* kcnt;    // [dmax]
   int64_t* kbeg;    // [dmax]
   int32_t* skey;    // [dmax]
@@ -714,7 +765,6 @@ __global__ void __launch_bounds__(kWideThreads, kWideBlocksPerSm)
                  int64_t dmax, char* __restrict__ scratch, unsigned long long* __restrict__ hist_out,
                  unsigned long long* __restrict__ work, int32_t* __restrict__ counter) {
   __shared__ uint32_t hist[kHistCopies][kBins];
-  __shared__ uint8_t lut[128];
   __shared__ int32_t s_r;
   __shared__ unsigned long long s_since;   // probes since the last flush (block-wide)
   __shared__ int32_t s_nstash;
@@ -723,10 +773,8 @@ __global__ void __launch_bounds__(kWideThreads, kWideBlocksPerSm)
   __shared__ uint32_t filt[(1 << kWideFilterLog2) / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   constexpr int kW = kWideThreads / 32;
-  static_assert(kHistCopies * kBins <= kWideThreads, "one thread per shared bin");
   WideScratch t = wide_carve(scratch + wide_block_bytes(cap_max, words_max, dmax) * blockIdx.x,
                              cap_max, words_max, dmax);
-  for (int k = threadIdx.x; k < 128; k += blockDim.x) lut[k] = c_lut[k];
   for (int k = threadIdx.x; k < kHistCopies * kBins; k += blockDim.x) (&hist[0][0])[k] = 0;
   const int32_t n = *n_p;
   uint32_t* my_hist = hist[lane & (kHistCopies - 1)];
@@ -735,10 +783,13 @@ __global__ void __launch_bounds__(kWideThreads, kWideBlocksPerSm)
   if (threadIdx.x == 0) s_since = 0;
   auto block_flush = [&]() {
     __syncthreads();
-    if (threadIdx.x < kHistCopies * kBins) {
-      const uint32_t x = (&hist[0][0])[threadIdx.x];
-      if (x) atomicAdd(&hist_out[(size_t)cur * kBins + threadIdx.x % kBins], (unsigned long long)x);
-      (&hist[0][0])[threadIdx.x] = 0;
+    for (int k = threadIdx.x; k < kBins; k += kWideThreads) {
+      unsigned long long x = 0;
+      for (int c = 0; c < kHistCopies; ++c) {
+        x += hist[c][k];
+        hist[c][k] = 0;
+      }
+      if (x) atomicAdd(&hist_out[(size_t)cur * kBins + k], x);
     }
     if (threadIdx.x == 0) s_since = 0;
     __syncthreads();
@@ -819,11 +870,16 @@ __global__ void __launch_bounds__(kWideThreads, kWideBlocksPerSm)
       }
     }
     __syncthreads();
+    // |e_x| -> |e_x| - omega_ux, the part of e_x outside e_u
+    for (int k = threadIdx.x; k < du; k += kWideThreads) {
+      int om = 0;
+      for (int q = 0; q < words; ++q) om += __popc(t.mask[(size_t)k * words + q]);
+      t.ksz[k] -= om;
+    }
+    __syncthreads();
     for (int k = w; k < du; k += kW) {
       const uint32_t* muv = t.mask + (size_t)k * words;
-      const int szv = t.ksz[k];
-      int wuv = 0;
-      for (int q = 0; q < words; ++q) wuv += __popc(muv[q]);
+      const int rv = t.ksz[k];
       const int64_t vb = t.kbeg[k];
       const int32_t cnt = t.kcnt[k];
       if (lane == 0) {
@@ -848,14 +904,25 @@ __global__ void __launch_bounds__(kWideThreads, kWideBlocksPerSm)
           if (!((filt[fb >> 5] >> (fb & 31)) & 1u)) continue;
           const int kw = wide_find(t, x, dl, nst);
           if (kw < 0) continue;
+          // the one-word rule of region_bits, word by word over e_u
           const uint32_t* muw = t.mask + (size_t)kw * words;
-          int wuw = 0, gg = 0;
+          uint32_t any_a = 0, any_d = 0, any_f = 0, any_g = 0;
+          int gg = 0;
           for (int qq = 0; qq < words; ++qq) {
-            wuw += __popc(muw[qq]);
-            gg += __popc(muw[qq] & muv[qq]);
+            const uint32_t a = muv[qq], b = muw[qq];
+            const uint32_t fq = full_mask(szu - 32 * qq);
+            any_a |= fq & ~(a | b);
+            any_d |= a & ~b;
+            any_f |= b & ~a;
+            any_g |= a & b;
+            gg += __popc(a & b);
           }
-          const int bits = region_bits(szu, szv, t.ksz[kw], wuv, wuw, om[q], gg);
-          atomicAdd(&my_hist[lut[bits]], 1u);
+          const int tt = om[q] - gg, rw = t.ksz[kw];
+          const uint32_t bits = (uint32_t)(any_a != 0u) | ((uint32_t)(rv > tt) << 1) |
+                                ((uint32_t)(rw > tt) << 2) | ((uint32_t)(any_d != 0u) << 3) |
+                                ((uint32_t)(tt > 0) << 4) | ((uint32_t)(any_f != 0u) << 5) |
+                                ((uint32_t)(any_g != 0u) << 6);
+          atomicAdd(&my_hist[bits], 1u);
         }
       }
     }
@@ -1019,21 +1086,6 @@ void launch_block(const DevGraph& g, const Oriented& o, int packed, const int32_
 }
 
 }  // namespace
-
-// The table never changes, so it is written once per device (synchronously, before the
-// first kernel that reads it); concurrent host threads never rewrite constant memory
-// that a running kernel reads.
-void close_set_lut(const uint8_t lut[128], cudaStream_t s) {
-  (void)s;
-  static std::mutex mu;
-  static uint64_t done = 0;   // bit d: device d holds the table
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
-  std::lock_guard<std::mutex> lk(mu);
-  if (done >> dev & 1) return;
-  if (cudaMemcpyToSymbol(c_lut, lut, 128, 0, cudaMemcpyHostToDevice) == cudaSuccess)
-    done |= uint64_t(1) << dev;
-}
 
 void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,
                          unsigned long long* wide_max, bool all_block, cudaStream_t s) {

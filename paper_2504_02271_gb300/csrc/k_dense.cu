@@ -6,16 +6,20 @@
 // (Def. 2.2; it is the heavy-heavy block of H * H^T, Sec. 3.1).  sm_103a has no
 // tcgen05 8-bit integer MMA, so the 0/1 entries are e4m3 values (1.0 = 0x38) and
 // the products accumulate in FP32 in tensor memory; every dot product is an
-// integer no larger than the smaller hyperedge (<= 65,535 here), which FP32
-// represents exactly, so omega is exact.
+// integer no larger than the smaller hyperedge.  The heavy set only takes
+// hyperedges of at most 65,535 vertices, so every omega fits the uint16 output and
+// is far below 2^24, where FP32 stops representing integers exactly: omega is exact.
 //
 // Kernel shape: one CTA per 128 x 256 output tile; K runs over the vertices in
-// steps of 128 bytes.  Warp 0 issues TMA loads (128-byte swizzle) of the A tile
+// steps of 128 bytes.  CTAs take tiles in a grouped raster: consecutive CTA ids walk
+// down a group of kGroupM tile rows before moving one tile column right, so the CTAs
+// resident at one time share a few A panels (128 rows) and B panels (256 rows) in L2
+// instead of each tile row streaming every B panel again.  Warp 0 issues TMA loads (128-byte swizzle) of the A tile
 // (128 rows) and the B tile (256 rows, two boxes) into a 4-stage ring; warp 1
 // allocates 256 TMEM columns and one thread issues tcgen05.mma (M=128, N=256,
 // K=32 per instruction, 4 per stage) and commits each stage back to its ring
 // slot; warps 2-5 read the accumulator rows they own with tcgen05.ld and write
-// omega as bytes.  Every mbarrier wait is bounded: on time-out the kernel raises
+// omega as uint16.  Every mbarrier wait is bounded: on time-out the kernel raises
 // an error word, stops issuing, waits for its own copies and frees its TMEM.
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -32,6 +36,7 @@ constexpr int kThreads = 192;
 constexpr uint32_t kStageBytes = (kBM + kBN) * kBK;
 constexpr uint32_t kTmemCols = 256;
 constexpr uint32_t kSpinLimit = 1u << 22;          // bounded waits (~ 1 s with backoff)
+constexpr int kGroupM = 16;                        // tile rows per raster group
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -90,7 +95,8 @@ constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kBN >> 3) << 17) | ((uint32_
 
 __global__ void __launch_bounds__(kThreads, 1)
     k_dense_omega(const __grid_constant__ CUtensorMap amap, int32_t rows, int32_t kblocks,
-                  uint8_t* __restrict__ omega, int64_t ld, int* __restrict__ err) {
+                  int32_t tiles_m, int32_t tiles_n, uint16_t* __restrict__ omega, int64_t ld,
+                  int* __restrict__ err) {
   extern __shared__ unsigned char dyn_raw[];
   // 1024-byte alignment for the swizzled tiles
   unsigned char* base = (unsigned char*)(((uintptr_t)dyn_raw + 1023) & ~(uintptr_t)1023);
@@ -101,7 +107,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile_m = blockIdx.y, tile_n = blockIdx.x;
+  // grouped raster: CTA id -> (tile_m, tile_n), kGroupM tile rows per group
+  const int per_group = kGroupM * tiles_n;
+  const int first_m = (int)(blockIdx.x / per_group) * kGroupM;
+  const int gm = min(tiles_m - first_m, kGroupM);
+  const int in_group = (int)(blockIdx.x % per_group);
+  const int tile_m = first_m + in_group % gm, tile_n = in_group / gm;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
@@ -200,21 +211,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (row < rows) {
-          uint32_t packed[8];
+          // every accumulator is an integer <= 65,535 (heavy hyperedges are capped there)
+          uint32_t packed[16];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            uint32_t v = 0;
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              const float f = __uint_as_float(r[4 * j + b]);
-              const uint32_t x = f >= 255.f ? 255u : (uint32_t)__float2uint_rn(f);
-              v |= x << (8 * b);
-            }
-            packed[j] = v;
+          for (int j = 0; j < 16; ++j) {
+            const uint32_t lo = (uint32_t)__float2uint_rn(__uint_as_float(r[2 * j]));
+            const uint32_t hi = (uint32_t)__float2uint_rn(__uint_as_float(r[2 * j + 1]));
+            packed[j] = lo | (hi << 16);
           }
           uint4* dst = reinterpret_cast<uint4*>(omega + (int64_t)row * ld + tile_n * kBN + c0);
-          dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-          dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            dst[j] = make_uint4(packed[4 * j], packed[4 * j + 1], packed[4 * j + 2], packed[4 * j + 3]);
         }
       }
     }
@@ -234,11 +242,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // heavy_idx[i] = position of i in the heavy list, or -1; ids[pos] = i
 __global__ void k_pick_heavy(const int32_t* __restrict__ esize, int32_t ne, int32_t min_size,
-                             int32_t cap, int32_t* __restrict__ heavy_idx,
+                             int32_t max_size, int32_t cap, int32_t* __restrict__ heavy_idx,
                              int32_t* __restrict__ ids, int32_t* __restrict__ count) {
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += gridDim.x * blockDim.x) {
     int32_t pos = -1;
-    if (esize[i] >= min_size) {
+    if (esize[i] >= min_size && esize[i] <= max_size) {
       pos = atomicAdd(count, 1);
       if (pos >= cap) pos = -1;   // beyond the cap: stays on the hash path
       else ids[pos] = i;
@@ -281,11 +289,12 @@ void launch_size_hist(const int32_t* esize, int32_t ne, int32_t max_bin, unsigne
   k_size_hist<<<1024, 256, 0, s>>>(esize, ne, max_bin, hist);
 }
 
-void launch_pick_heavy(const int32_t* esize, int32_t ne, int32_t min_size, int32_t cap,
-                       int32_t* heavy_idx, int32_t* ids, int32_t* count, cudaStream_t s) {
+void launch_pick_heavy(const int32_t* esize, int32_t ne, int32_t min_size, int32_t max_size,
+                       int32_t cap, int32_t* heavy_idx, int32_t* ids, int32_t* count,
+                       cudaStream_t s) {
   if (ne == 0) return;
   note_launch();
-  k_pick_heavy<<<1024, 256, 0, s>>>(esize, ne, min_size, cap, heavy_idx, ids, count);
+  k_pick_heavy<<<1024, 256, 0, s>>>(esize, ne, min_size, max_size, cap, heavy_idx, ids, count);
 }
 
 void launch_fill_dense(const int64_t* e_ptr, const int32_t* e_idx, const int32_t* ids, int32_t nh,
@@ -295,10 +304,10 @@ void launch_fill_dense(const int64_t* e_ptr, const int32_t* e_idx, const int32_t
   k_fill_dense<<<(nh + 7) / 8, 256, 0, s>>>(e_ptr, e_idx, ids, nh, a, lda);
 }
 
-// omega[rows_pad x rows_pad] (row stride ld = rows_pad) = A A^T for A[rows_pad x k_pad] e4m3.
-// Returns a CUDA error from the tensor-map encoding or the launch.
+// omega[rows_pad x rows_pad] (uint16, row stride ld = rows_pad) = A A^T for
+// A[rows_pad x k_pad] e4m3.  Returns a CUDA error from the tensor-map encoding or the launch.
 cudaError_t launch_dense_omega(const uint8_t* a, int64_t rows, int64_t rows_pad, int64_t k_pad,
-                               uint8_t* omega, int* err, cudaStream_t s) {
+                               uint16_t* omega, int* err, cudaStream_t s) {
   // looked up once (thread-safe static initialisation)
   static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() {
     cudaDriverEntryPointQueryResult q;
@@ -324,10 +333,11 @@ cudaError_t launch_dense_omega(const uint8_t* a, int64_t rows, int64_t rows_pad,
   cudaError_t e = cudaFuncSetAttribute(k_dense_omega, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)(rows_pad / kBN), (unsigned)(rows_pad / kBM));
+  const int64_t tiles_m = rows_pad / kBM, tiles_n = rows_pad / kBN;
   note_launch();
-  k_dense_omega<<<grid, kThreads, smem, s>>>(map, (int32_t)rows, (int32_t)(k_pad / kBK), omega,
-                                             rows_pad, err);
+  k_dense_omega<<<(unsigned)(tiles_m * tiles_n), kThreads, smem, s>>>(
+      map, (int32_t)rows, (int32_t)(k_pad / kBK), (int32_t)tiles_m, (int32_t)tiles_n, omega,
+      rows_pad, err);
   return cudaGetLastError();
 }
 

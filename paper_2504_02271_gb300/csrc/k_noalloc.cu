@@ -4,12 +4,19 @@
 // omega_ij over the E_v lists of its vertices in a hash table, but the tables
 // live in one file-scope device array instead of memory from an allocator.
 //
-// Who needs this: code that must not call cudaMalloc or any allocating routine
-// while it runs - for example a host function enqueued on a stream (such
-// functions may not make CUDA calls that allocate), or a service whose device
-// memory is a fixed arena owned by someone else, where an extra allocation
-// would either fail or stall every other stream on the device.  It can pass
-// device buffers for inputs and outputs, and this entry point brings the rest.
+// Who needs this: a service whose device memory is a fixed arena owned by someone
+// else (a serving process that reserved the GPU's memory up front, a plug-in living
+// inside another framework's memory pool), where an extra cudaMalloc would either
+// fail or stall every other stream on the device while the driver reclaims memory.
+// Such a caller can pass device buffers for inputs and outputs, and this entry
+// point brings the rest.  It makes ordinary CUDA runtime calls (a memset, a launch,
+// copies and a stream synchronisation), so it is called from plain host code -
+// never from inside a host function enqueued on a stream, where CUDA calls are not
+// allowed at all.
+//
+// Each row hashes into the first 2^k slots of its block's table, 2^k the smallest
+// power of two holding twice the row's gathered incidences (at least 256), so a
+// small row clears and scans a small region instead of the whole table.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -33,9 +40,9 @@ struct NoallocScratch {
 };
 static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
 
-__device__ __forceinline__ void add_neighbour(unsigned long long* T, uint32_t j) {
-  const uint32_t mask = (1u << kTableLog2) - 1u;
-  uint32_t s = (j * 0x9E3779B1u) >> (32 - kTableLog2);
+__device__ __forceinline__ void add_neighbour(unsigned long long* T, int cap_log2, uint32_t j) {
+  const uint32_t mask = (1u << cap_log2) - 1u;
+  uint32_t s = (j * 0x9E3779B1u) >> (32 - cap_log2);
   const unsigned long long key = (unsigned long long)j << 32;
   while (true) {
     unsigned long long cur = *((volatile unsigned long long*)&T[s]);
@@ -86,24 +93,29 @@ __global__ void __launch_bounds__(kThreads)
       c += (unsigned long long)(v_ptr[v + 1] - v_ptr[v] - 1);
     }
     atomicAdd(&s_cand, c);
-    for (uint32_t s = threadIdx.x; s < CAP; s += kThreads) T[s] = kEmptySlot;
     __syncthreads();
-    if (s_cand > (unsigned long long)(CAP / 2)) {
+    const unsigned long long cand = s_cand;   // read after a barrier: the same on every thread
+    if (cand > (unsigned long long)(CAP / 2)) {
       if (threadIdx.x == 0) atomicCAS(&sc->err, 0, hg::DE_LIMIT);
       continue;
     }
+    int cl = 8;   // this row's region: 2^cl >= 2 * cand slots (load factor <= 1/2)
+    while (cl < kTableLog2 && (1ull << cl) < 2 * cand) ++cl;
+    const uint32_t rcap = 1u << cl;
+    for (uint32_t s = threadIdx.x; s < rcap; s += kThreads) T[s] = kEmptySlot;
+    __syncthreads();
     for (int64_t p = b + w; p < e; p += kWarps) {
       const int32_t v = e_idx[p];
       for (int64_t q = v_ptr[v] + lane; q < v_ptr[v + 1]; q += 32) {
         const int32_t j = v_idx[q];
-        if (j != i) add_neighbour(T, (uint32_t)j);
+        if (j != i) add_neighbour(T, cl, (uint32_t)j);
       }
     }
     __syncthreads();
     const int32_t szi = (int32_t)(e - b);
     int distinct = 0;
     unsigned long long wc = 0;
-    for (uint32_t s = threadIdx.x; s < CAP; s += kThreads) {
+    for (uint32_t s = threadIdx.x; s < rcap; s += kThreads) {
       const unsigned long long x = T[s];
       if (x == kEmptySlot) continue;
       ++distinct;
@@ -163,6 +175,7 @@ extern "C" hg_status hg_wedge_degrees_noalloc(int32_t num_edges, const int64_t* 
     hg::note_launch();
     k_wedge_degrees_noalloc<<<kTables, kThreads, 0, s>>>(sc, num_edges, edge_ptr, edge_vtx,
                                                          vertex_ptr, vertex_edge, degrees);
+    if (cudaGetLastError() != cudaSuccess) return HG_ERR_CUDA;   // the launch was refused
   }
   if (cudaMemcpyAsync(inclusion_wedges, &sc->wc, sizeof(unsigned long long),
                       cudaMemcpyDeviceToDevice, s) != cudaSuccess)

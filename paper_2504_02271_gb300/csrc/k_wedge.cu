@@ -14,56 +14,58 @@
 // copies the row.  Algorithm 2 merges the sorted E_v lists one id at a time on a
 // CPU; here the accumulation is a hash table in shared memory (one warp per light
 // row, one block per medium row) or in global scratch (one block per heavy row).
+// In the packed layout (|E| < 2^24, every |e| < 256, so omega < 256) a slot is one
+// 32-bit word (j << 8) | count; otherwise a 64-bit word (j << 32) | count.  A slot
+// is claimed with one compare-and-swap that also seeds the count, so a new key costs
+// one shared atomic and a repeated key two.
+#include <type_traits>
+
 #include "hg_internal.cuh"
 
 namespace hg {
 namespace {
 
-constexpr unsigned long long kEmpty = ~0ull;
 constexpr unsigned kFull = 0xffffffffu;
+
+// Hash-table slot of the gather pass: 32-bit (j << 8) | count in the packed layout,
+// 64-bit (j << 32) | count otherwise; all ones = empty.
+template <bool PACKED>
+struct GatherSlot {
+  using T = typename std::conditional<PACKED, uint32_t, unsigned long long>::type;
+  static constexpr int kShift = PACKED ? 8 : 32;
+  static constexpr T kEmpty = ~(T)0;
+  __device__ static uint32_t key(T x) { return (uint32_t)(x >> kShift); }
+  __device__ static uint32_t count(T x) {
+    return PACKED ? (uint32_t)(x & 0xffu) : (uint32_t)(x & 0xffffffffu);
+  }
+};
 
 constexpr int kLightCapLog2 = 9;     // 512 slots, rows with cand <= 256
 constexpr int kLightWarps = 8;
-constexpr int kMediumCapLog2 = 13;   // 8192 slots (64 KiB), rows with cand <= 4096
+constexpr int kMediumCapLog2 = 13;   // 8192 slots (32 KiB packed, 64 KiB wide), rows with cand <= 4096
 constexpr int kBlockThreads = 256;
 
 __device__ __forceinline__ uint32_t slot_of(uint32_t key, int cap_log2) {
   return (key * 0x9E3779B1u) >> (32 - cap_log2);
 }
 
-// omega accumulation: slot = (j << 32) | count
-__device__ __forceinline__ void ht_add(unsigned long long* T, int cap_log2, uint32_t j) {
+// omega accumulation: add n to the count of key j (linear probing).  The claiming
+// compare-and-swap writes the key with its first count; a slot that already holds j
+// takes an atomic add.  Counts never exceed the smaller hyperedge, which fits the
+// count field (8 bits packed, 32 bits otherwise).
+template <bool PACKED>
+__device__ __forceinline__ void ht_add(typename GatherSlot<PACKED>::T* T, int cap_log2, uint32_t j,
+                                       uint32_t n = 1) {
+  using S = GatherSlot<PACKED>;
+  using W = typename S::T;
   const uint32_t mask = (1u << cap_log2) - 1u;
   uint32_t s = slot_of(j, cap_log2);
-  const unsigned long long key = (unsigned long long)j << 32;
+  const W item = ((W)j << S::kShift) | (W)n;
   while (true) {
-    unsigned long long cur = *((volatile unsigned long long*)&T[s]);
-    if (cur == kEmpty) {
-      cur = atomicCAS(&T[s], kEmpty, key | 1ull);
-      if (cur == kEmpty) return;
-    }
-    if ((uint32_t)(cur >> 32) == j) {
-      atomicAdd(&T[s], 1ull);
-      return;
-    }
-    s = (s + 1u) & mask;
-  }
-}
-
-// add omega pairs known in advance (heavy x heavy, from the tensor-core tiles)
-__device__ __forceinline__ void ht_add_n(unsigned long long* T, int cap_log2, uint32_t j,
-                                         uint32_t n) {
-  const uint32_t mask = (1u << cap_log2) - 1u;
-  uint32_t s = slot_of(j, cap_log2);
-  const unsigned long long key = (unsigned long long)j << 32;
-  while (true) {
-    unsigned long long cur = *((volatile unsigned long long*)&T[s]);
-    if (cur == kEmpty) {
-      cur = atomicCAS(&T[s], kEmpty, key | n);
-      if (cur == kEmpty) return;
-    }
-    if ((uint32_t)(cur >> 32) == j) {
-      atomicAdd(&T[s], (unsigned long long)n);
+    const W cur = atomicCAS(&T[s], S::kEmpty, item);
+    if (cur == S::kEmpty) return;
+    if (S::key(cur) == j) {
+      atomicAdd(&T[s], (W)n);
       return;
     }
     s = (s + 1u) & mask;
@@ -105,11 +107,13 @@ __global__ void __launch_bounds__(kLightWarps * 32)
                   const int64_t* __restrict__ cand, int32_t* __restrict__ deg,
                   unsigned long long* __restrict__ wc, Oriented o, int* __restrict__ err,
                   int32_t* __restrict__ counter, DenseInfo dn, RowCounts rc) {
+  using S = GatherSlot<PACKED>;
+  using W = typename S::T;
   constexpr int CAP = 1 << kLightCapLog2;
-  __shared__ unsigned long long tab[kLightWarps][CAP];
+  __shared__ W tab[kLightWarps][CAP];
   __shared__ unsigned long long blk_wc;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned long long* T = tab[w];
+  W* T = tab[w];
   const int32_t nrows = *nrows_p;
   if (threadIdx.x == 0) blk_wc = 0;
   __syncthreads();
@@ -122,7 +126,7 @@ __global__ void __launch_bounds__(kLightWarps * 32)
     const int32_t i = rows[r];
     const int cl = row_cap_log2(cand[i], 5, kLightCapLog2);   // this row's table: 2^cl slots
     const int cap = 1 << cl;
-    for (int s = lane; s < cap; s += 32) T[s] = kEmpty;
+    for (int s = lane; s < cap; s += 32) T[s] = S::kEmpty;
     __syncwarp();
     const int32_t hi = dn.heavy_idx ? dn.heavy_idx[i] : -1;
     const int64_t b = g.e_ptr[i], e = g.e_ptr[i + 1];
@@ -154,13 +158,13 @@ __global__ void __launch_bounds__(kLightWarps * 32)
                                                            __shfl_sync(kFull, len, lo));
         if (f >= total) continue;
         const int32_t j = g.v_idx[start + f];
-        if (j != i && gather_pair(dn, hi, j)) ht_add(T, cl, (uint32_t)j);
+        if (j != i && gather_pair(dn, hi, j)) ht_add<PACKED>(T, cl, (uint32_t)j);
       }
     }
     if (hi >= 0) {
       for (int32_t h = lane; h < dn.nh; h += 32) {
         const uint32_t om = dn.omega[(int64_t)hi * dn.ld + h];
-        if (om && h != hi) ht_add_n(T, cl, (uint32_t)dn.ids[h], om);
+        if (om && h != hi) ht_add<PACKED>(T, cl, (uint32_t)dn.ids[h], om);
       }
     }
     __syncwarp();
@@ -168,12 +172,12 @@ __global__ void __launch_bounds__(kLightWarps * 32)
     const int64_t base = o.row_ptr[i];
     int written = 0, up = 0, incl = 0;
     for (int s0 = 0; s0 < cap; s0 += 32) {
-      const unsigned long long x = T[s0 + lane];
-      const bool valid = x != kEmpty;
+      const W x = T[s0 + lane];
+      const bool valid = x != S::kEmpty;
       uint32_t j = 0, om = 0;
       if (valid) {
-        j = (uint32_t)(x >> 32);
-        om = (uint32_t)(x & 0xffffffffu);
+        j = S::key(x);
+        om = S::count(x);
         if ((int32_t)j > i) {
           ++up;
           const int32_t szj = g.esize[j];
@@ -214,8 +218,11 @@ __global__ void __launch_bounds__(kBlockThreads)
                   unsigned long long* __restrict__ gscratch, int32_t* __restrict__ deg,
                   unsigned long long* __restrict__ wc, Oriented o, int* __restrict__ err,
                   int32_t* __restrict__ counter, DenseInfo dn, RowCounts rc) {
+  using S = GatherSlot<PACKED>;
+  using W = typename S::T;
   extern __shared__ unsigned long long dyn[];
-  unsigned long long* T = SMEM ? dyn : gscratch + ((size_t)blockIdx.x << cap_log2);
+  W* T = SMEM ? reinterpret_cast<W*>(dyn)
+              : reinterpret_cast<W*>(gscratch) + ((size_t)blockIdx.x << cap_log2);
   __shared__ int32_t s_row;
   __shared__ int32_t s_cnt, s_up, s_incl;
   __shared__ unsigned long long s_wc;
@@ -238,7 +245,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     const int32_t i = rows[r];
     const int cl = row_cap_log2(cand[i], 8, cap_log2);   // this row's table: 2^cl slots
     const uint32_t CAP = 1u << cl;
-    for (uint32_t s = threadIdx.x; s < CAP; s += kBlockThreads) T[s] = kEmpty;
+    for (uint32_t s = threadIdx.x; s < CAP; s += kBlockThreads) T[s] = S::kEmpty;
     __syncthreads();
     const int32_t hi = dn.heavy_idx ? dn.heavy_idx[i] : -1;
     const int64_t b = g.e_ptr[i], e = g.e_ptr[i + 1];
@@ -271,14 +278,14 @@ __global__ void __launch_bounds__(kBlockThreads)
           if (s_yincl[mid] > f) hi2 = mid; else lo = mid + 1;
         }
         const int32_t j = g.v_idx[s_ybeg[lo] + f];
-        if (j != i && gather_pair(dn, hi, j)) ht_add(T, cl, (uint32_t)j);
+        if (j != i && gather_pair(dn, hi, j)) ht_add<PACKED>(T, cl, (uint32_t)j);
       }
       __syncthreads();   // the next chunk rewrites the ranges
     }
     if (hi >= 0) {
       for (int32_t h = threadIdx.x; h < dn.nh; h += kBlockThreads) {
         const uint32_t om = dn.omega[(int64_t)hi * dn.ld + h];
-        if (om && h != hi) ht_add_n(T, cl, (uint32_t)dn.ids[h], om);
+        if (om && h != hi) ht_add<PACKED>(T, cl, (uint32_t)dn.ids[h], om);
       }
     }
     __syncthreads();
@@ -286,9 +293,9 @@ __global__ void __launch_bounds__(kBlockThreads)
     const int64_t base = o.row_ptr[i];
     int up = 0, incl = 0;
     for (uint32_t s = threadIdx.x; s < CAP; s += kBlockThreads) {
-      const unsigned long long x = T[s];
-      if (x == kEmpty) continue;
-      const uint32_t j = (uint32_t)(x >> 32), om = (uint32_t)(x & 0xffffffffu);
+      const W x = T[s];
+      if (x == S::kEmpty) continue;
+      const uint32_t j = S::key(x), om = S::count(x);
       if ((int32_t)j > i) {
         ++up;
         const int32_t szj = g.esize[j];
@@ -415,18 +422,26 @@ void launch_all(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb, int
                 RowCounts rc, cudaStream_t s, int nsm) {
   // counters[0..2] are zeroed by the caller
   if (nb[0] > 0) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wedge_light<PACKED>,
+                                                  kLightWarps * 32, 0);
+    if (per_sm < 1) per_sm = 1;
     int blocks = (nb[0] + kLightWarps - 1) / kLightWarps;
-    blocks = blocks < nsm * 4 ? blocks : nsm * 4;
+    blocks = blocks < nsm * per_sm ? blocks : nsm * per_sm;
     note_launch();
     k_wedge_light<PACKED><<<blocks, kLightWarps * 32, 0, s>>>(g, b.rows[0], b.count + 0, cand,
                                                               deg, wc, o, err, counters + 0, dn,
                                                               rc);
   }
   if (nb[1] > 0) {
-    const size_t smem = sizeof(unsigned long long) << kMediumCapLog2;
+    const size_t smem = sizeof(typename GatherSlot<PACKED>::T) << kMediumCapLog2;
     cudaFuncSetAttribute(k_wedge_block<PACKED, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    int blocks = nb[1] < nsm * 3 ? nb[1] : nsm * 3;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wedge_block<PACKED, true>,
+                                                  kBlockThreads, smem);
+    if (per_sm < 1) per_sm = 1;
+    int blocks = nb[1] < nsm * per_sm ? nb[1] : nsm * per_sm;
     note_launch();
     k_wedge_block<PACKED, true><<<blocks, kBlockThreads, smem, s>>>(
         g, b.rows[1], b.count + 1, cand, kMediumCapLog2, nullptr, deg, wc, o, err, counters + 1,

@@ -36,7 +36,8 @@ EXPORTED = ("hg_set_allocator", "hg_load_csr", "hg_build_wedges", "hg_count_patt
             "hg_batch_waves", "hg_batch_wave", "hg_batch_free", "hg_load_batch_members",
             "hg_server_create", "hg_server_add_graph", "hg_server_submit", "hg_server_wait",
             "hg_server_drain", "hg_server_cancel", "hg_server_stats_get", "hg_server_destroy",
-            "hg_sample_estimate_adv", "hg_enumerate_pattern", "hg_sample_work_get")
+            "hg_sample_estimate_adv", "hg_enumerate_pattern", "hg_sample_work_get",
+            "hg_canonical_masks", "hg_mask_histogram", "hg_batch_mask_histogram")
 
 
 class HgError(RuntimeError):
@@ -122,6 +123,9 @@ def _open():
                                     ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32),
                                     ctypes.POINTER(i32)]
     lib.hg_pattern_table.argtypes = [vp]
+    lib.hg_canonical_masks.argtypes = [vp]
+    lib.hg_mask_histogram.argtypes = [vp, vp]
+    lib.hg_batch_mask_histogram.argtypes = [vp, vp]
     lib.hg_close_stats_get.argtypes = [vp, ctypes.POINTER(_CloseStats)]
     lib.hg_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
     lib.hg_wedge_degrees_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp]
@@ -303,6 +307,13 @@ def hg_count_patterns(g: Graph) -> np.ndarray:
     return out
 
 
+def hg_mask_histogram(g: Graph) -> np.ndarray:
+    """uint64[128]: hyper-triangles of the last count per canonical region mask."""
+    out = np.zeros(128, dtype=np.uint64)
+    _check("hg_mask_histogram", _lib.hg_mask_histogram(ctypes.c_void_p(g.ptr), out.ctypes.data))
+    return out
+
+
 def hg_sample_estimate(g: Graph, seed: int, first_sample: int, num_samples: int,
                        sigma: float = 1.0) -> tuple[np.ndarray, np.ndarray]:
     """Hyperwedge-sampling estimate (Algorithm 6): (raw uint64[21], est float64[21])."""
@@ -414,6 +425,13 @@ def hg_pattern_table() -> np.ndarray:
     return out
 
 
+def hg_canonical_masks() -> np.ndarray:
+    """uint8[128]: canonical form (smallest relabelling) of each labelled region mask."""
+    out = np.zeros(128, dtype=np.uint8)
+    _check("hg_canonical_masks", _lib.hg_canonical_masks(out.ctypes.data))
+    return out
+
+
 def hg_free(g: Graph) -> None:
     """Release the handle and its device memory; calling it again does nothing."""
     if g.ptr:
@@ -519,6 +537,14 @@ def hg_batch_count_patterns(b: Batch) -> tuple[np.ndarray, dict]:
                                 shape=(b.num_graphs, 8)).copy()
     names = [n for n, _ in _WedgeStats._fields_]
     return counts, {n: arr[:, k] for k, n in enumerate(names) if n != "reserved"}
+
+
+def hg_batch_mask_histogram(b: Batch) -> np.ndarray:
+    """uint64[G, 128]: each member's hyper-triangles per canonical region mask."""
+    out = np.zeros((b.num_graphs, 128), dtype=np.uint64)
+    _check("hg_batch_mask_histogram",
+           _lib.hg_batch_mask_histogram(ctypes.c_void_p(b.ptr), out.ctypes.data))
+    return out
 
 
 def hg_batch_clustering_coeff(b: Batch, eps) -> tuple[np.ndarray, np.ndarray, np.ndarray]:

@@ -45,23 +45,36 @@ def run_batch(hg, members, max_wave_edges=0, device=False, **build):
         counts, stats = hg.hg_batch_count_patterns(b)
         cc, open_, conn = hg.hg_batch_clustering_coeff(b, [1.0] * 20)
         waves = hg.hg_batch_waves(b)
+        masks = hg.hg_batch_mask_histogram(b)
     finally:
         hg.hg_batch_free(b)
-    return counts, stats, cc, open_, conn, waves
+    return counts, stats, cc, open_, conn, waves, masks
 
 
-def check_members(members, counts, stats, open_, stored=None):
-    # stored: member index -> stored oracle entry (tests/golden/workloads.json)
+def stored_masks(entry):
+    out = [0] * 128
+    for m, n in entry["masks"].items():
+        out[int(m)] = n
+    return out
+
+
+def check_members(members, counts, stats, open_, stored=None, masks=None):
+    # stored: member index -> stored oracle entry (tests/golden/workloads.json); masks:
+    # the batch's canonical region-mask histograms, compared before the counts
     import oracle
 
     for m, (nv, e_ptr, e_idx) in enumerate(members):
         if stored and m in stored:
             ref = stored[m]
+            want_masks = stored_masks(ref)
             want = (ref["counts"], ref["W"], ref["W_c"], ref["W_t"], ref["max_deg"],
                     ref["connected"], ref["open"])
         else:
             r = oracle.count(e_ptr, e_idx, nv)
+            want_masks = r.masks.tolist()
             want = ([int(x) for x in r.counts], r.W, r.W_c, r.W_t, r.max_deg, r.connected, r.open)
+        if masks is not None:
+            assert masks[m].tolist() == want_masks, m
         got = (counts[m].tolist(), int(stats["W"][m]), int(stats["W_c"][m]), int(stats["W_t"][m]),
                int(stats["max_deg"][m]), int(stats["connected"][m]), int(open_[m]))
         assert got == want, m
@@ -70,9 +83,9 @@ def check_members(members, counts, stats, open_, stored=None):
 @pytest.mark.parametrize("seed", [1, 2])
 def test_random_members_match_oracle(hglib, seed):
     members = random_members(seed, 60)
-    counts, stats, cc, open_, conn, waves = run_batch(hglib, members)
+    counts, stats, cc, open_, conn, waves, masks = run_batch(hglib, members)
     assert len(waves) == 1 and waves[0][2] == len(members)
-    check_members(members, counts, stats, open_)
+    check_members(members, counts, stats, open_, masks=masks)
 
 
 def test_waves_and_device_inputs_give_the_same_results(hglib):
@@ -87,6 +100,7 @@ def test_waves_and_device_inputs_give_the_same_results(hglib):
         for k in one[1]:
             assert other[1][k].tolist() == one[1][k].tolist(), k
         assert other[3].tolist() == one[3].tolist()
+        assert other[6].tolist() == one[6].tolist()
         np.testing.assert_array_equal(other[2], one[2])
 
 
@@ -99,23 +113,25 @@ def test_batched_workload_members_match_single_handles(hglib):
     for seed in range(100, 164):
         spec = hgen.batched(seed)
         members.append((spec.num_vertices, *hgen.generate(spec)))
-    counts, stats, cc, open_, conn, waves = run_batch(hglib, members)
+    counts, stats, cc, open_, conn, waves, masks = run_batch(hglib, members)
     stream = torch.cuda.Stream()
     for m, (nv, e_ptr, e_idx) in enumerate(members):
         g = hglib.hg_load_csr(nv, len(e_ptr) - 1, e_ptr, e_idx, stream=stream.cuda_stream)
         try:
             st = hglib.hg_build_wedges(g)
             alone = hglib.hg_count_patterns(g)
+            alone_masks = hglib.hg_mask_histogram(g)
             cc1, op1, co1 = hglib.hg_clustering_coeff(g, [1.0] * 20)
         finally:
             hglib.hg_free(g)
+        assert masks[m].tolist() == alone_masks.tolist(), m
         assert counts[m].tolist() == alone.tolist(), m
         assert int(stats["W"][m]) == st["W"] and int(stats["W_c"][m]) == st["W_c"], m
         assert int(open_[m]) == op1 and int(conn[m]) == co1, m
         assert (np.isnan(cc[m]) and np.isnan(cc1)) or cc[m] == cc1, m
     small = [k for k, m in enumerate(members) if len(m[1]) - 1 <= 3000][:12]
     check_members([members[k] for k in small], counts[small], {k: v[small] for k, v in stats.items()},
-                  open_[small])
+                  open_[small], masks=masks[small])
 
 
 def test_every_team_shape_flushes_per_member(hglib):
@@ -133,8 +149,9 @@ def test_every_team_shape_flushes_per_member(hglib):
     members.insert(15, (400, *hgen.generate(
         hgen.HypergraphSpec(400, 300, 7, hgen.SIZE_UNIFORM, 20, 90, zipf_s=0.3, name="wide"))))
     base = run_batch(hglib, members)
-    check_members(members, base[0], base[1], base[3], stored={12: gold})
+    check_members(members, base[0], base[1], base[3], stored={12: gold}, masks=base[6])
     wide = run_batch(hglib, members, close_mode=1)
+    assert wide[6].tolist() == base[6].tolist()
     assert wide[0].tolist() == base[0].tolist()
 
 

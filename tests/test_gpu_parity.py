@@ -1,5 +1,7 @@
-"""CUDA path vs the oracle, element by element (every pattern count, the total and
-the wedge statistics), through the C ABI.  Integers: bit-exact."""
+"""CUDA path vs the oracle, element by element, through the C ABI.  Integers:
+bit-exact.  The canonical region-mask histogram (the pattern of every hyper-triangle
+before the twenty patterns are numbered) is compared first, then the counts and the
+wedge statistics."""
 import numpy as np
 import pytest
 
@@ -16,6 +18,7 @@ def gpu_count(hg, nv, e_ptr, e_idx, **kw):
     try:
         stats = hg.hg_build_wedges(g, **kw)
         counts = hg.hg_count_patterns(g)
+        stats["masks"] = hg.hg_mask_histogram(g).tolist()
         stats["close"] = hg.hg_close_stats_get(g)
         cc1, open_, connected = hg.hg_clustering_coeff(g, [1.0] * 20)
     finally:
@@ -32,6 +35,7 @@ def check_against_oracle(hg, nv, e_ptr, e_idx, ref=None):
     counts, st = gpu_count(hg, nv, e_ptr, e_idx)
     if ref is None:
         ref = oracle.count(e_ptr, e_idx, nv)
+    assert st["masks"] == ref.masks.tolist()
     assert counts.tolist() == [int(x) for x in ref.counts]
     assert st["W"] == ref.W and st["W_c"] == ref.W_c and st["W_t"] == ref.W_t
     assert st["connected"] == ref.connected and st["max_deg"] == ref.max_deg
@@ -76,6 +80,13 @@ def test_random_small(hglib, seed):
     check_against_oracle(hglib, spec.num_vertices, e_ptr, e_idx)
 
 
+def stored_masks(entry):
+    out = [0] * 128
+    for m, n in entry["masks"].items():
+        out[int(m)] = n
+    return out
+
+
 def test_wide_hyperedges(hglib):
     # lowest-ranked hyperedges with more than 32 vertices take the block kernel
     import hgen
@@ -85,18 +96,27 @@ def test_wide_hyperedges(hglib):
     check_against_oracle(hglib, spec.num_vertices, e_ptr, e_idx)
 
 
-def test_heavy_wedge_rows(hglib):
-    # a hub vertex in 6000 hyperedges: rows gather > 4096 candidates (global-scratch
-    # block); about 4e10 hyper-triangles, so the oracle's counts are stored
+def test_heavy_rows_and_every_team_shape_repeated(hglib):
+    # A hub vertex in 6000 hyperedges: rows gather > 4096 candidates (global-scratch
+    # gather blocks), and the out-degrees after degree ordering run from 0 to ~6000, so
+    # every closure team shape runs - warp teams, block teams with shared tables for
+    # out-degree <= 1024, <= 2048 and <= 4096, and global-table teams beyond.  About
+    # 3.6e10 hyper-triangles, so the oracle's values are stored.  Five runs must agree
+    # with the oracle every time (a schedule-dependent miscount would show as a run
+    # that differs).
     import hgen
 
     gold = load_json("workloads.json")["hub6000"]
     nv, e_ptr, e_idx = hgen.hub(*gold["hub"])
     assert hgen.csr_hash(e_ptr, e_idx) == gold["csr_hash"]
-    counts, st = gpu_count(hglib, nv, e_ptr, e_idx)
-    assert counts.tolist() == gold["counts"]
-    for k in ("W", "W_c", "W_t", "connected", "open", "max_deg"):
-        assert st[k] == gold[k], k
+    for run in range(5):
+        counts, st = gpu_count(hglib, nv, e_ptr, e_idx)
+        teams = st["close"]["bucket_teams"]
+        assert all(teams[k] > 0 for k in range(7)), teams
+        assert st["masks"] == stored_masks(gold), run
+        assert counts.tolist() == gold["counts"], run
+        for k in ("W", "W_c", "W_t", "connected", "open", "max_deg"):
+            assert st[k] == gold[k], (run, k)
 
 
 def test_tiny_plain_full(hglib):
@@ -106,12 +126,13 @@ def test_tiny_plain_full(hglib):
     e_ptr, e_idx = hgen.generate(hgen.TINY_PLAIN)
     assert hgen.csr_hash(e_ptr, e_idx) == gold["csr_hash"]
     counts, st = gpu_count(hglib, gold["num_vertices"], e_ptr, e_idx)
+    assert st["masks"] == stored_masks(gold)
     assert counts.tolist() == gold["counts"]
     assert st["W"] == gold["W"] and st["W_c"] == gold["W_c"] and st["open"] == gold["open"]
 
 
 @pytest.mark.parametrize("name", ["coauthor_prefix50k", "tag_heavy_prefix1000",
-                                  "tag_heavy_prefix2000", "coauthor"])
+                                  "tag_heavy_prefix2000", "coauthor", "dense_core"])
 def test_workload_golden(hglib, name):
     import hgen
 
@@ -125,6 +146,7 @@ def test_workload_golden(hglib, name):
         e_ptr, e_idx = hgen.prefix(e_ptr, e_idx, gold["prefix_edges"])
     assert hgen.csr_hash(e_ptr, e_idx) == gold["csr_hash"]
     counts, st = gpu_count(hglib, gold["num_vertices"], e_ptr, e_idx)
+    assert st["masks"] == stored_masks(gold)
     assert counts.tolist() == gold["counts"]
     for k in ("W", "W_c", "W_t", "connected", "open", "max_deg"):
         assert st[k] == gold[k], k
@@ -140,6 +162,7 @@ def test_counts_do_not_depend_on_the_oriented_layout(hglib, name):
     if gold["prefix_edges"] is not None:
         e_ptr, e_idx = hgen.prefix(e_ptr, e_idx, gold["prefix_edges"])
     counts, st = gpu_count(hglib, gold["num_vertices"], e_ptr, e_idx, orient_exact=1)
+    assert st["masks"] == stored_masks(gold)
     assert counts.tolist() == gold["counts"]
     assert (st["W"], st["W_c"], st["connected"], st["open"]) == \
         (gold["W"], gold["W_c"], gold["connected"], gold["open"])
@@ -159,6 +182,7 @@ def test_counts_do_not_depend_on_team_shape(hglib, name, mode):
     if gold["prefix_edges"] is not None:
         e_ptr, e_idx = hgen.prefix(e_ptr, e_idx, gold["prefix_edges"])
     counts, st = gpu_count(hglib, gold["num_vertices"], e_ptr, e_idx, close_mode=mode)
+    assert st["masks"] == stored_masks(gold)
     assert counts.tolist() == gold["counts"]
     probes = st["close"]["bucket_probes"]
     if mode == 2:   # the warp and block teams probed nothing; the global-table teams did it all
@@ -183,6 +207,7 @@ def test_unpacked_rows_every_team_shape(hglib, mode):
     e_ptr, e_idx = csr_of(edges)
     counts, st = gpu_count(hglib, 1000, e_ptr, e_idx, close_mode=mode)
     ref = oracle.count(e_ptr, e_idx, 1000)
+    assert st["masks"] == ref.masks.tolist()
     assert counts.tolist() == [int(x) for x in ref.counts]
     assert (st["W"], st["W_c"], st["connected"]) == (ref.W, ref.W_c, ref.connected)
     if mode == 0:
@@ -254,6 +279,7 @@ def test_dense_tiles_match_oracle(hglib, seed):
                            dense_max_count=1000)
     assert st["dense_edges"] == 400
     ref = oracle.count(e_ptr, e_idx, spec.num_vertices)
+    assert st["masks"] == ref.masks.tolist()
     assert counts.tolist() == [int(x) for x in ref.counts]
     assert (st["W"], st["W_c"], st["connected"]) == (ref.W, ref.W_c, ref.connected)
 
@@ -283,20 +309,69 @@ def test_dense_tiles_tag_heavy_prefix(hglib):
     counts, st = gpu_count(hglib, gold["num_vertices"], e_ptr, e_idx, dense_min_size=20,
                            dense_max_count=1200)
     assert st["dense_edges"] > 0
+    assert st["masks"] == stored_masks(gold)
     assert counts.tolist() == gold["counts"]
     assert (st["W"], st["W_c"], st["connected"]) == (gold["W"], gold["W_c"], gold["connected"])
 
 
-def test_block_teams_with_shared_tables(hglib):
-    # out-degrees of several hundred to a few thousand: block teams with shared tables
-    # (<= 1024 and <= 4096) against block teams with global tables (close_mode=1)
+def test_dense_tiles_omega_above_255(hglib):
+    # 96 heavy hyperedges of 350-450 vertices drawn from 600 share 190-330 vertices
+    # pairwise, beyond one byte; light hyperedges on a partly overlapping range.  Every
+    # heavy pair's omega comes from the tensor-core tiles (Def. 2.2), so a truncated or
+    # saturated tile output would change omega, the hyperwedge types and the patterns.
+    import oracle
+
+    rng = np.random.default_rng(17)
+    heavy = [sorted(rng.choice(600, int(rng.integers(350, 451)), replace=False).tolist())
+             for _ in range(96)]
+    light = [sorted(rng.choice(np.arange(560, 2560), int(rng.integers(2, 6)), replace=False).tolist())
+             for _ in range(1500)]
+    edges = heavy + light
+    e_ptr, e_idx = csr_of(edges)
+    assert len({tuple(e) for e in edges}) == len(edges)
+    counts, st = gpu_count(hglib, 2560, e_ptr, e_idx, dense_min_size=300, dense_max_count=400)
+    assert st["dense_edges"] == 96
+    sets = [set(e) for e in heavy]
+    assert max(len(sets[0] & sets[j]) for j in range(1, 96)) > 255
+    ref = oracle.count(e_ptr, e_idx, 2560)
+    assert st["masks"] == ref.masks.tolist()
+    assert counts.tolist() == [int(x) for x in ref.counts]
+    assert (st["W"], st["W_c"], st["connected"], st["open"]) == (ref.W, ref.W_c, ref.connected,
+                                                                ref.open)
+
+
+def test_block_teams_out_degree_257_to_1024_repeated(hglib):
+    # 348 hyperedges of 5-10 vertices over 28: 34 hyperedges close with out-degree
+    # 257-267 (block teams with shared tables); ten runs, each equal to the oracle
+    import hgen
+    import oracle
+
+    spec = hgen.HypergraphSpec(28, 348, 1, hgen.SIZE_UNIFORM, 5, 10, zipf_s=0.0, name="dense28")
+    e_ptr, e_idx = hgen.generate(spec)
+    ref = oracle.count(e_ptr, e_idx, 28)
+    for run in range(10):
+        counts, st = gpu_count(hglib, 28, e_ptr, e_idx)
+        assert st["close"]["bucket_teams"][3] > 0
+        assert st["masks"] == ref.masks.tolist(), run
+        assert counts.tolist() == [int(x) for x in ref.counts], run
+
+
+def test_dense_core_block_teams_repeated(hglib):
+    # 2,600 hyperedges of 3-6 vertices over 24: out-degrees up to ~1,200, so block
+    # teams for out-degree <= 1024 and <= 2048 carry most of the work; every team shape
+    # (0 = by out-degree, 1 = all global tables, 2 = built then handed over) and ten
+    # default runs equal the stored oracle values
     import hgen
 
-    spec = hgen.HypergraphSpec(40, 6000, 21, hgen.SIZE_UNIFORM, 3, 5, zipf_s=0.4, name="dense_small")
-    e_ptr, e_idx = hgen.generate(spec)
-    shared, st = gpu_count(hglib, spec.num_vertices, e_ptr, e_idx)
-    glob, _ = gpu_count(hglib, spec.num_vertices, e_ptr, e_idx, close_mode=1)
-    handed, st2 = gpu_count(hglib, spec.num_vertices, e_ptr, e_idx, close_mode=2)
-    assert st["max_out_deg"] > 1024
-    assert shared.tolist() == glob.tolist() == handed.tolist()
-    assert sum(st["close"]["bucket_teams"][3:6]) > 0 and st2["close"]["bucket_probes"][:6] == [0] * 6
+    gold = load_json("workloads.json")["dense_core"]
+    e_ptr, e_idx = hgen.generate(hgen.DENSE_CORE)
+    assert hgen.csr_hash(e_ptr, e_idx) == gold["csr_hash"]
+    want = stored_masks(gold)
+    for run in range(10):
+        counts, st = gpu_count(hglib, gold["num_vertices"], e_ptr, e_idx)
+        assert st["close"]["bucket_teams"][3] > 0 and st["close"]["bucket_teams"][4] > 0
+        assert st["masks"] == want, run
+        assert counts.tolist() == gold["counts"], run
+    for mode in (1, 2):
+        counts, st = gpu_count(hglib, gold["num_vertices"], e_ptr, e_idx, close_mode=mode)
+        assert st["masks"] == want and counts.tolist() == gold["counts"], mode

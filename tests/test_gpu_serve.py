@@ -208,3 +208,45 @@ def test_cancel_queued_queries(hglib):
         srv.drain()
     finally:
         srv.close()
+
+
+def test_cancelling_a_head_that_does_not_fit_admits_the_next(hglib):
+    # Two workers and a memory budget that holds a long estimate A plus a small count C,
+    # but not A plus the big count B.  Queued behind A: B (head, does not fit), then C.
+    # Cancelling B must let the idle worker take C while A still runs (C starts before A
+    # ends), not only once A completes.
+    gs = graphs()
+    a_graph, b_graph, c_graph = gs[3], gs[5], gs[0]
+
+    def alone_bytes(kind, g, **q):
+        srv = hglib.Server(workers=1)
+        try:
+            gid = srv.add_graph(*g)
+            srv.wait(srv.submit(kind, gid, **q))
+            return srv.stats()["max_in_flight_bytes"]
+        finally:
+            srv.close()
+
+    long_q = {"seed": 5, "first_sample": 0, "num_samples": 150_000_000}
+    ma = alone_bytes(hglib.HG_Q_ESTIMATE, a_graph, **long_q)
+    mb = alone_bytes(hglib.HG_Q_COUNTS, b_graph)
+    mc = alone_bytes(hglib.HG_Q_COUNTS, c_graph)
+    assert mb > mc > 0 and ma > 0
+    srv = hglib.Server(workers=2, memory_budget=ma + mc)
+    try:
+        ga, gb, gc = (srv.add_graph(*g) for g in (a_graph, b_graph, c_graph))
+        ta = srv.submit(hglib.HG_Q_ESTIMATE, ga, **long_q)
+        deadline = time.perf_counter() + 10.0
+        while srv.stats()["batches"] < 1 and time.perf_counter() < deadline:
+            time.sleep(0.001)
+        tb = srv.submit(hglib.HG_Q_COUNTS, gb)
+        tc = srv.submit(hglib.HG_Q_COUNTS, gc)
+        time.sleep(0.02)
+        srv.cancel(tb)   # A still runs, so B cannot have been taken
+        rc = srv.wait(tc)
+        ra = srv.wait(ta)
+        assert srv.wait(tb)["status"] == 14   # HG_ERR_CANCELLED
+        assert ra["status"] == 0 and rc["status"] == 0
+        assert rc["t_start"] < ra["t_done"], (rc["t_start"], ra["t_done"])
+    finally:
+        srv.close()

@@ -46,6 +46,20 @@ def test_pattern_table_matches_oracle(lib):
     assert [int(x) for x in lut] == [oracle.pattern_of_mask(m) for m in range(128)]
 
 
+def test_canonical_masks_match_oracle(lib):
+    # both sides fold labelled masks into the same canonical forms, written apart
+    import oracle
+
+    canon = lib.hg_canonical_masks()
+    assert [int(x) for x in canon] == [oracle.canonical_mask(m) for m in range(128)]
+    lut = lib.hg_pattern_table()
+    # a pattern is one orbit: masks share a pattern iff they share a canonical form
+    for a in range(128):
+        for b in range(128):
+            if lut[a] and lut[b]:
+                assert (lut[a] == lut[b]) == (canon[a] == canon[b]), (a, b)
+
+
 def test_status_strings(lib):
     for s in range(14):
         assert lib.hg_status_str(s) not in ("", "unknown status")

@@ -1,11 +1,12 @@
 """The allocation-free entry point against the regular one, through the C ABI.
 
 hg_wedge_degrees_noalloc serves callers that cannot allocate device memory while
-they run (code in a host function on a stream, services with a fixed device
-arena): it takes only caller-owned device buffers and a fixed library array.
-Its degrees must reproduce the wedge statistics hg_build_wedges reports for the
-same hypergraph, on consecutive calls (the fixed array keeps old contents).
-This file is collected last so a stopping run has already run every other test.
+they run (services whose device memory is a fixed arena owned by someone else):
+it takes only caller-owned device buffers and a fixed library array.  Each
+hyperedge's degree must equal the oracle's |N(e_i)|, and the degrees must
+reproduce the wedge statistics hg_build_wedges reports for the same hypergraph,
+on consecutive calls (the fixed array keeps old contents).  This file is
+collected last so a stopping run has already run every other test.
 """
 import numpy as np
 import pytest
@@ -37,6 +38,7 @@ def test_noalloc_degrees_match_build_wedges(hglib, name):
     import torch
 
     import hgen
+    import oracle
     from conftest import load_json
 
     gold = load_json("workloads.json")[name]
@@ -46,6 +48,7 @@ def test_noalloc_degrees_match_build_wedges(hglib, name):
     nv, ne = gold["num_vertices"], len(e_ptr) - 1
     v_ptr, v_idx = transpose(e_ptr, e_idx, nv)
     want = regular_stats(hglib, nv, e_ptr, e_idx)
+    want_deg = oracle.degrees(e_ptr, e_idx, nv)
     dev = torch.device("cuda")
     t = [torch.from_numpy(a).to(dev) for a in (e_ptr, e_idx, v_ptr, v_idx)]
     stream = torch.cuda.Stream()
@@ -54,6 +57,7 @@ def test_noalloc_degrees_match_build_wedges(hglib, name):
         wc = torch.full((1,), 7, dtype=torch.int64, device=dev)
         hglib.hg.hg_wedge_degrees_noalloc(ne, *t, deg, wc, stream=stream.cuda_stream)
         d = deg.cpu().numpy().astype(np.int64)
+        assert d.tolist() == want_deg.tolist()   # every |N(e_i)|, element by element
         assert int(d.sum()) == 2 * want["W"]
         assert int(d.max()) == want["max_deg"]
         assert int((d * (d - 1) // 2).sum()) == want["connected"]
