@@ -46,6 +46,10 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="coauthor")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--close-mode", type=int, default=0,
+                    help="hg_tuning.close_mode (1: every closing team on the global-table kernel)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="build with the default tuning instead of hg_autotune's choice")
     ap.add_argument("--cpu-sample-edges", type=int, default=8000,
                     help="hyperedges whose owned triangles the CPU baseline counts")
     ap.add_argument("--e2e-steps", type=int, default=-1,
@@ -60,6 +64,8 @@ def parse_args():
     ap.add_argument("--per-graph-steps", type=int, default=2,
                     help="--workload batched: timed steps of the one-handle-per-hypergraph form")
     ap.add_argument("--queries", type=int, default=10_000, help="--workload served: stream length")
+    ap.add_argument("--rate", type=float, default=2000.0,
+                    help="--workload served: Poisson arrival rate (queries/s)")
     ap.add_argument("--plain-queries", type=int, default=1000,
                     help="--workload served: queries replayed with batching off")
     ap.add_argument("--serve-workers", type=int, default=4)
@@ -201,7 +207,7 @@ def profiled_traffic(kernel, workload_name, units=None):
 
 # team shape of each closure kernel group -> index of its work counters
 CLOSE_GROUPS = {"close_warp256": 0, "close_warp512": 1, "close_warp1024": 2, "close_block2048": 3,
-                "close_block4096": 4, "close_block8192": 5, "close_wide": 6}
+                "close_block4096": 4, "close_block8192": 5, "close_wide": 6, "close_cluster": 7}
 ISSUE_LANE_OPS_PER_CYCLE_PER_SM = 4 * 32   # 4 schedulers, one 32-lane instruction per cycle
 
 
@@ -287,13 +293,15 @@ def run_ours(args):
     ones = [1.0] * 20
     torch.cuda.synchronize()
 
+    tuning = {"dense_min_size": args.dense_min_size, "dense_max_count": args.dense_max_count,
+              "close_mode": args.close_mode}
+
     def one_step(p, i, timing=False):
         g = hg.hg_load_csr(nv, ne, p, i, stream=stream.cuda_stream)
         try:
             if timing:
                 hg.hg_set_timing(g, True)
-            st = hg.hg_build_wedges(g, dense_min_size=args.dense_min_size,
-                                    dense_max_count=args.dense_max_count)
+            st = hg.hg_build_wedges(g, **tuning)
             counts = hg.hg_count_patterns(g)
             cc = hg.hg_clustering_coeff(g, ones)
             kt = hg.hg_kernel_times(g) if timing else {}
@@ -316,6 +324,16 @@ def run_ours(args):
         parity = counts.tolist() == gold["counts"] and st["W"] == gold["W"]
         if not parity:
             raise SystemExit(f"bench: counts differ from the stored oracle values: {counts.tolist()}")
+    # autotune once (warm-up): the timed steps build with its choice
+    tune = None
+    if not args.no_autotune and not (args.dense_min_size or args.dense_max_count or args.close_mode):
+        g = hg.hg_load_csr(nv, ne, d_ptr, d_idx, stream=stream.cuda_stream)
+        try:
+            tune = hg.hg_autotune(g)
+        finally:
+            hg.hg_free(g)
+        tuning = tune["best"]
+        one_step(d_ptr, d_idx)
 
     def barrier():
         if dist is not None:
@@ -391,7 +409,7 @@ def run_ours(args):
     achieved_ops = ops / (dom_ms / 1000.0) / 1e12
     achieved_gbs = nbytes / (dom_ms / 1000.0) / 1e9
     traffic = profiled_traffic(dom, cfg["workload"])
-    roof = {"bound": "alu", "kernel": f"{dom} (k_close_warp / k_close_block / k_close_wide)",
+    roof = {"bound": "alu", "kernel": f"{dom} (k_close_warp / k_close_block / k_close_wide / k_close_cluster)",
             "achieved": round(achieved_ops, 3), "peak": round(peak_ops, 2), "unit": "Tops/s",
             "frac": round(achieved_ops / peak_ops, 4),
             "peak_source": f"derived: 152 SMs x 128 lane-ops/cycle x {sm_mhz:.0f} MHz (median SM clock under load)",
@@ -432,8 +450,17 @@ def run_ours(args):
                                      "steps that give value (those run without them)",
                        inputs="int64/int32 CSR resident in HBM", parallelism=f"replicas x{world}",
                        parity="counts equal stored oracle values" if parity else "not checked",
-                       dense_tiles={"min_size": args.dense_min_size, "max_count": args.dense_max_count,
-                                    "hyperedges": st["dense_edges"]}),
+                       dense_tiles={"min_size": tuning["dense_min_size"],
+                                    "max_count": tuning["dense_max_count"],
+                                    "hyperedges": st["dense_edges"]},
+                       tuning=tuning,
+                       autotune=None if tune is None else {
+                           "candidates": len(tune["tried"]),
+                           "ms": [round(x, 3) for x in tune["ms"]],
+                           "default_ms": round(tune["ms"][0], 3),
+                           "chosen_ms": round(tune["best_ms"], 3),
+                           "all_candidates_equal_counts": bool(all(
+                               c.tolist() == tune["counts"][0].tolist() for c in tune["counts"]))}),
         "e2e": None if e2e_value is None else {
             "value": round(e2e_value, 1), "unit": UNIT,
             "h2d_bytes_per_step": int(e_ptr.nbytes + e_idx.nbytes),
@@ -518,6 +545,8 @@ def run_batched(args):
         with torch.cuda.stream(stream):
             flush.fill_(k & 0xFF)
 
+    tuning = {}
+
     def batch_step(p, i, timing=False):
         b = hg.hg_load_batch(nv, eoff, p, i, stream=stream.cuda_stream)
         try:
@@ -525,7 +554,7 @@ def run_batched(args):
             if timing:
                 for w in waves:
                     hg.hg_set_timing(w[0], True)
-            hg.hg_batch_build_wedges(b)
+            hg.hg_batch_build_wedges(b, **tuning)
             counts, stats = hg.hg_batch_count_patterns(b)
             cc = hg.hg_batch_clustering_coeff(b, ones)
             kt, cs = {}, None
@@ -551,7 +580,7 @@ def run_batched(args):
             g = hg.hg_load_csr(int(nv[m]), int(eoff[m + 1] - eoff[m]), m_ptr[m], m_idx[m],
                                stream=stream.cuda_stream)
             try:
-                hg.hg_build_wedges(g)
+                hg.hg_build_wedges(g, **tuning)
                 out[m] = hg.hg_count_patterns(g)
                 hg.hg_clustering_coeff(g, ones)
             finally:
@@ -569,26 +598,39 @@ def run_batched(args):
         return r, e0.elapsed_time(e1)
 
     counts = None
+    tune = None
     for k in range(args.warmup):
         do_flush(k)
         counts, stats, _, _, _, nwaves = batch_step(d_ptr, d_idx)
+        if k == 0 and not args.no_autotune:   # autotune on the largest wave, then use it
+            b = hg.hg_load_batch(nv, eoff, d_ptr, d_idx, stream=stream.cuda_stream)
+            try:
+                tune = hg.hg_batch_autotune(b)
+            finally:
+                hg.hg_batch_free(b)
+            tuning = tune["best"]
     T = int(counts[:, 0].sum())
 
+    # timed region: K steps without per-kernel events (value), then K with them (roofline)
     clocks = ClockSampler(dev)
     torch.cuda.synchronize()
     clocks.start()
     launches0 = hg.hg_kernel_launches()
     step_ms, kernel_ms, cs = [], {}, None
     for k in range(args.steps):
-        (c2, _, _, kt, cs, _), ms = timed(lambda: batch_step(d_ptr, d_idx, timing=True), k + 17)
+        (c2, _, _, _, cs, _), ms = timed(lambda: batch_step(d_ptr, d_idx), k + 17)
         assert np.array_equal(c2, counts)
         step_ms.append(ms)
+    torch.cuda.synchronize()
+    launches = hg.hg_kernel_launches() - launches0
+    for k in range(args.steps):
+        (c2, _, _, kt, _, _), _ = timed(lambda: batch_step(d_ptr, d_idx, timing=True), k + 47)
+        assert np.array_equal(c2, counts)
         for n, (t, c) in kt.items():
             a = kernel_ms.setdefault(n, [0.0, 0])
             a[0] += t
             a[1] += c
     torch.cuda.synchronize()
-    launches = hg.hg_kernel_launches() - launches0
     clk = clocks.stop()
     value = T * len(step_ms) / (sum(step_ms) / 1000.0)
 
@@ -644,7 +686,14 @@ def run_batched(args):
                          % ((eptr.nbytes + evtx.nbytes) / 1e9),
                    "inputs": "concatenated int64/int32 CSRs resident in HBM",
                    "parallelism": "replicas x1",
-                   "parity": "per-member counts equal one-handle-per-hypergraph counts"},
+                   "parity": "per-member counts equal one-handle-per-hypergraph counts",
+                   "tuning": tuning or "defaults",
+                   "autotune": None if tune is None else {
+                       "wave": "the wave with the most hyperedges",
+                       "candidates": len(tune["tried"]), "ms": [round(x, 2) for x in tune["ms"]],
+                       "chosen": tune["best"],
+                       "all_candidates_equal_counts": bool(all(
+                           c.tolist() == tune["counts"][0].tolist() for c in tune["counts"]))}},
         "per_graph": {"value": round(pg_value, 1), "unit": UNIT, "ms_per_step": round(statistics.mean(pg_ms), 3),
                       "steps": len(pg_ms), "gpu_launches_per_step": int(launches_pg),
                       "form": "hg_load_csr / hg_build_wedges / hg_count_patterns / hg_clustering_coeff per member"},
@@ -862,7 +911,7 @@ def run_served(args):
     dev = torch.cuda.current_device()
     import paper_2504_02271_gb300 as hg
 
-    n_graphs, n_queries, rate = 64, args.queries, 2000.0
+    n_graphs, n_queries, rate = 64, args.queries, float(args.rate)
     specs = [hgen.served(m) for m in range(n_graphs)]
     nv, eoff, eptr, evtx, _ = hgen.generate_batch(specs)
     gs = []

@@ -95,7 +95,11 @@ typedef struct hg_tuning {
   int32_t orient_exact;    /* 1 = oriented rows in an exact layout (W entries, one extra
                               counting pass); 0 = room for deg(i) per row (2W entries)
                               while that fits 8 GB.  Counts do not depend on it */
-  int32_t reserved[4];
+  int32_t gather_light_max; /* step one: rows gathering at most this many incidences take
+                               one warp, larger ones a block (0 = 256; 32..256) */
+  int32_t warp_team_max;   /* step two: largest out-degree closed by a one-warp team; larger
+                              ones take 16-warp block teams (0 = 256; 64, 128 or 256) */
+  int32_t reserved[2];
 } hg_tuning;
 
 typedef struct hg_wedge_stats {
@@ -120,6 +124,33 @@ typedef struct hg_wedge_stats {
  * HG_ERR_STATE until a build succeeds).
  */
 hg_status hg_build_wedges(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out);
+
+/*
+ * Autotuner (no counterpart in the paper: the paper's parameters are its algorithms'
+ * class split, not kernel shapes).  Picks, for this hypergraph, the hg_tuning fields
+ * whose best value depends on the input - warp_team_max (64/128/256), gather_light_max
+ * (64/128/256), orient_exact (0/1) and, for hyperedges of 32+ vertices, dense_min_size
+ * (automatic / off / 64) - by coordinate descent: from the defaults, each field in turn
+ * tries its other values with the rest at the best so far and keeps one that lowers the
+ * device time of hg_build_wedges + hg_count_patterns (CUDA events on the handle's
+ * stream).  Every candidate's counts, canonical mask histogram and wedge statistics must
+ * agree (HG_ERR_INTERNAL otherwise).  The choice is kept on the handle and used by later
+ * hg_build_wedges calls given opt = NULL; the handle is left built and counted with it.
+ *   out  may be NULL; else the choice, and every candidate tried with its time and counts.
+ * HG_ERR_UNSUPPORTED for a wave handle of a batch (see hg_batch_autotune).  Synchronises.
+ */
+#define HG_AUTOTUNE_MAX 16
+typedef struct hg_autotune_result {
+  hg_tuning best;                         /* the chosen tuning */
+  float best_ms;                          /* its step one + step two time, ms */
+  int32_t best_index;                     /* its position in tried[] */
+  int32_t num_tried;                      /* candidates timed */
+  int32_t reserved;
+  hg_tuning tried[HG_AUTOTUNE_MAX];       /* in the order they ran; tried[0] = defaults */
+  float ms[HG_AUTOTUNE_MAX];
+  uint64_t counts[HG_AUTOTUNE_MAX][21];   /* each candidate's hg_count_patterns result */
+} hg_autotune_result;
+hg_status hg_autotune(hg_graph* g, hg_autotune_result* out);
 
 /*
  * Step two (Sec. 3.2-3.3; Algorithms 3-5 compute the same counts per class):
@@ -238,19 +269,21 @@ hg_status hg_clustering_coeff(hg_graph* g, const double eps[20], double* cc,
  *                of hyperedges with out-degree >= 2);
  *   teams        hyperedges u that owned a closing team (out-degree >= 2);
  *   bucket_*     the same per team shape: warp teams for out-degree <= 64, <= 128,
- *                <= 256; block teams with shared-memory tables for <= 1024, <= 2048 and
- *                <= 4096; block teams with global-memory tables for the rest (index 6,
- *                which also takes what the other teams hand over).
+ *                <= 256 (indices 0-2); block teams with shared-memory tables for <= 1024,
+ *                <= 2048 and <= 4096 (3-5); block teams with global-memory tables for
+ *                hyperedges of more than 32 vertices with out-degree <= 4096 and for
+ *                what the other teams hand over (6); thread-block clusters sharing
+ *                global-memory tables for out-degree above 4096 (7).
  */
 typedef struct hg_close_stats {
   uint64_t probes;
   uint64_t gathers;
   uint64_t out_entries;
   uint64_t teams;
-  uint64_t bucket_teams[7];
-  uint64_t bucket_probes[7];
-  uint64_t bucket_gathers[7];
-  uint64_t bucket_out_entries[7];
+  uint64_t bucket_teams[8];
+  uint64_t bucket_probes[8];
+  uint64_t bucket_gathers[8];
+  uint64_t bucket_out_entries[8];
 } hg_close_stats;
 hg_status hg_close_stats_get(hg_graph* g, hg_close_stats* out);
 
@@ -351,6 +384,11 @@ hg_status hg_load_batch_members(int32_t num_graphs, const int32_t* num_vertices,
                                 const int32_t* num_edges, const int64_t* const* edge_ptrs,
                                 const int32_t* const* edge_vtxs, int inputs_on_device,
                                 int64_t max_wave_edges, void* cuda_stream, hg_batch** out);
+
+/* The autotuner of hg_autotune run on one wave of the batch (wave = -1: the wave with the
+ * most hyperedges); its choice is kept by every wave and used by hg_batch_build_wedges
+ * given opt = NULL.  The batch must be built again afterwards.  Synchronises. */
+hg_status hg_batch_autotune(hg_batch* b, int32_t wave, hg_autotune_result* out);
 
 /* Step one (as hg_build_wedges) on every wave.  opt may be NULL; an out-of-range
  * tuning is rejected with HG_ERR_INVALID_ARG before anything changes.  Synchronises. */

@@ -83,6 +83,9 @@ struct hg_graph {
   Oriented ori{};
   int packed = 0;
   int close_mode = 0;
+  int warp_team_max = 256;   // of the last build (step two routes teams by it)
+  hg_tuning tuned{};         // hg_autotune's choice, used by builds given no tuning
+  bool has_tuned = false;
   uint64_t two_w = 0;
   bool built = false;
   hg_wedge_stats stats{};
@@ -551,12 +554,18 @@ constexpr int64_t kOrientSlackBytes = int64_t(8) << 30;   // oriented rows with 
 // The tuning fields that have a closed range (checked before a build changes anything).
 bool tuning_ok(const hg_tuning* opt) {
   if (!opt) return true;
+  const int32_t lm = opt->gather_light_max, wm = opt->warp_team_max;
   return opt->close_mode >= 0 && opt->close_mode <= 2 && opt->orient_exact >= 0 &&
-         opt->orient_exact <= 1;
+         opt->orient_exact <= 1 && (lm == 0 || (lm >= 32 && lm <= wedge_light_max_cand())) &&
+         (wm == 0 || wm == 64 || wm == 128 || wm == 256);
 }
 
 hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
+  if (!opt && g->has_tuned) opt = &g->tuned;
   g->close_mode = opt ? opt->close_mode : 0;
+  g->warp_team_max = (opt && opt->warp_team_max) ? opt->warp_team_max : 256;
+  const int light_max = (opt && opt->gather_light_max) ? opt->gather_light_max
+                                                         : wedge_light_max_cand();
   cudaStream_t s = g->stream;
   release(g, g->count_blocks);
   release_sampling(g);
@@ -588,7 +597,7 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   WedgeBuckets wb;
   for (int k = 0; k < 3; ++k) wb.rows[k] = rows + k * ne;
   wb.count = g->small->bucket_count;
-  launch_bucket_rows(g->cand, g->ne, wb, s);
+  launch_bucket_rows(g->cand, g->ne, wb, light_max, s);
   // capacity layout of the gather pass: min(gathered incidences, |E| - 1) per row
   launch_cap_rows(g->cand, g->ne, cap, s);
   scan_i32_to_i64(cap, g->cap_ptr, ne, g->scan_tmp, s);
@@ -1005,7 +1014,7 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   t_begin(g, "close_bucket");
   // warp tables keep |e_x| in 16 bits: larger hyperedges send everything to block teams
   launch_bucket_close(d, g->ori, cb, g->small->wide_max,
-                      g->close_mode == 1 || g->max_size >= 65536, s);
+                      g->close_mode == 1 || g->max_size >= 65536, g->warp_team_max, s);
   t_end(g);
   HG_TRY(sync_small(g, &h));
   int32_t n[kCloseBuckets];
@@ -1025,7 +1034,7 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   static const char* names[kCloseBuckets] = {"close_warp256",   "close_warp512",
                                              "close_warp1024",  "close_block2048",
                                              "close_block4096", "close_block8192",
-                                             "close_wide"};
+                                             "close_wide",      "close_cluster"};
   for (int k = kCloseBuckets - 1; k >= 0; --k) {
     if (n[k] <= 0) continue;
     t_begin(g, names[k]);
@@ -1076,6 +1085,106 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   g->cstats.bucket_teams[kWideBucket] += (uint64_t)n_over;   // handed from the warp kernels
   g->counted = true;
   if (counts) std::memcpy(counts, g->counts, sizeof(g->counts));
+  return HG_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+//
+// Coordinate descent over the tuning fields whose best value depends on the input:
+// starting from the defaults, each field in turn takes each of its other values with
+// the others at the best so far, and keeps a value that lowers the measured time of
+// step one plus step two (CUDA events on the handle's stream around hg_build_wedges and
+// hg_count_patterns).  Every candidate must give the same counts, canonical mask
+// histogram and wedge statistics; the handle ends built and counted with the choice.
+
+struct TuneRun {
+  hg_tuning t;
+  float ms;
+  uint64_t counts[21];
+  uint64_t masks[128];
+  hg_wedge_stats st;
+};
+
+hg_status time_candidate(hg_graph* g, const hg_tuning& t, TuneRun* r) {
+  r->t = t;
+  cudaEvent_t a = nullptr, b = nullptr;
+  HG_CUDA(cudaEventCreate(&a));
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return HG_ERR_CUDA;
+  }
+  hg_status st = cuda_status(cudaEventRecord(a, g->stream));
+  if (st == HG_OK) st = build_impl(g, &t, &r->st);
+  if (st == HG_OK) st = count_impl(g, r->counts);
+  if (st == HG_OK) st = cuda_status(cudaEventRecord(b, g->stream));
+  if (st == HG_OK) st = cuda_status(cudaEventSynchronize(b));
+  if (st == HG_OK) st = cuda_status(cudaEventElapsedTime(&r->ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  std::memcpy(r->masks, g->masks, sizeof(g->masks));
+  return st;
+}
+
+bool same_result(const TuneRun& x, const TuneRun& y) {
+  return std::memcmp(x.counts, y.counts, sizeof(x.counts)) == 0 &&
+         std::memcmp(x.masks, y.masks, sizeof(x.masks)) == 0 && x.st.W == y.st.W &&
+         x.st.W_c == y.st.W_c && x.st.connected == y.st.connected && x.st.max_deg == y.st.max_deg;
+}
+
+hg_status autotune_impl(hg_graph* g, hg_autotune_result* out) {
+  std::vector<TuneRun> runs;
+  auto run = [&](const hg_tuning& t) -> hg_status {
+    if ((int)runs.size() >= HG_AUTOTUNE_MAX) return HG_OK;
+    runs.emplace_back();
+    HG_TRY(time_candidate(g, t, &runs.back()));
+    if (!same_result(runs.front(), runs.back())) return HG_ERR_INTERNAL;
+    return HG_OK;
+  };
+  hg_tuning best{};
+  HG_TRY(run(best));
+  size_t best_i = 0;
+  // the fields, each with the values it may take besides the default (0)
+  struct Knob {
+    int32_t hg_tuning::*field;
+    std::vector<int32_t> alts;
+  };
+  std::vector<Knob> knobs = {
+      {&hg_tuning::warp_team_max, {128, 64}},
+      {&hg_tuning::gather_light_max, {128, 64}},
+      {&hg_tuning::orient_exact, {1}},
+  };
+  if (g->max_size >= 32) knobs.push_back({&hg_tuning::dense_min_size, {-1, 64}});
+  for (const Knob& k : knobs) {
+    const hg_tuning base = best;
+    for (int32_t v : k.alts) {
+      hg_tuning t = base;
+      t.*(k.field) = v;
+      const size_t before = runs.size();
+      HG_TRY(run(t));
+      if (runs.size() > before && runs.back().ms < runs[best_i].ms) {
+        best = t;
+        best_i = runs.size() - 1;
+      }
+    }
+  }
+  // leave the handle built and counted with the choice
+  TuneRun last;
+  HG_TRY(time_candidate(g, best, &last));
+  if (!same_result(runs.front(), last)) return HG_ERR_INTERNAL;
+  g->tuned = best;
+  g->has_tuned = true;
+  if (out) {
+    std::memset(out, 0, sizeof(*out));
+    out->best = best;
+    out->best_ms = runs[best_i].ms;
+    out->best_index = (int32_t)best_i;
+    out->num_tried = (int32_t)runs.size();
+    for (size_t k = 0; k < runs.size(); ++k) {
+      out->tried[k] = runs[k].t;
+      out->ms[k] = runs[k].ms;
+      std::memcpy(out->counts[k], runs[k].counts, sizeof(runs[k].counts));
+    }
+  }
   return HG_OK;
 }
 
@@ -1284,6 +1393,19 @@ hg_status hg_build_wedges(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out
   return st;
 }
 
+hg_status hg_autotune(hg_graph* g, hg_autotune_result* out) {
+  if (!g) return HG_ERR_INVALID_ARG;
+  if (g->nm > 0) return HG_ERR_UNSUPPORTED;   // a wave: hg_batch_autotune
+  hg_status st = autotune_impl(g, out);
+  if (st != HG_OK) {
+    cudaStreamSynchronize(g->stream);
+    cudaGetLastError();
+    g->pending.clear();
+    g->built = g->counted = false;
+  }
+  return st;
+}
+
 hg_status hg_count_patterns(hg_graph* g, uint64_t counts[21]) {
   if (!g) return HG_ERR_INVALID_ARG;
   if (!g->built) return HG_ERR_STATE;
@@ -1484,6 +1606,30 @@ hg_status hg_load_batch_members(int32_t num_graphs, const int32_t* num_vertices,
     return st;
   }
   *out = b;
+  return HG_OK;
+}
+
+hg_status hg_batch_autotune(hg_batch* b, int32_t wave, hg_autotune_result* out) {
+  if (!b || wave < -1 || wave >= (int32_t)b->waves.size()) return HG_ERR_INVALID_ARG;
+  if (wave < 0) {   // the wave with the most hyperedges
+    wave = 0;
+    for (size_t k = 1; k < b->waves.size(); ++k)
+      if (b->waves[k]->ne > b->waves[(size_t)wave]->ne) wave = (int32_t)k;
+  }
+  b->built = b->counted = false;
+  hg_graph* g = b->waves[(size_t)wave];
+  hg_status st = autotune_impl(g, out);
+  if (st != HG_OK) {
+    cudaStreamSynchronize(g->stream);
+    cudaGetLastError();
+    g->pending.clear();
+    g->built = g->counted = false;
+    return st;
+  }
+  for (hg_graph* w : b->waves) {
+    w->tuned = g->tuned;
+    w->has_tuned = true;
+  }
   return HG_OK;
 }
 

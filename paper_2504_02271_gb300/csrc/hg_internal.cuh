@@ -117,7 +117,9 @@ struct WedgeBuckets {
   int32_t* rows[3];  // light (warp), medium (block, smem), heavy (block, global scratch)
   int32_t* count;    // [3] device counters
 };
-void launch_bucket_rows(const int64_t* cand, int32_t ne, WedgeBuckets b, cudaStream_t s);
+// rows gathering at most light_max incidences take one warp (light_max <= wedge_light_max_cand)
+void launch_bucket_rows(const int64_t* cand, int32_t ne, WedgeBuckets b, int light_max,
+                        cudaStream_t s);
 int wedge_light_max_cand();
 int wedge_medium_max_cand();
 // Per-row outputs of the count pass (each may be null): upc[i] = |{j > i}|,
@@ -205,16 +207,23 @@ size_t wedge_heavy_scratch_bytes(int64_t heavy_max_cand, int nsm);
 
 // k_close.cu
 // close team shapes: warp teams (out-degree <= 64, 128, 256), block teams with shared
-// tables (<= 1024, <= 4096), block teams with global scratch (the rest)
-constexpr int kCloseBuckets = 7;
+// tables (<= 1024, <= 2048, <= 4096), block teams with global scratch (|e_u| > 32 with
+// out-degree <= 4096, and teams handed over), cluster teams with global scratch
+// (out-degree above kWideLargeMin)
+constexpr int kCloseBuckets = 8;
 constexpr int kWideBucket = 6;
+constexpr int kClusterBucket = 7;
+constexpr int kWideLargeMin = 4096;
 struct CloseBuckets {
   int32_t* lists[kCloseBuckets];
   int32_t* count;     // [kCloseBuckets]
 };
 // all_block: send every hyperedge to the global-table kernel (bucket 6)
+// warp_max: the largest out-degree a warp team takes (64, 128 or 256); larger out-degrees
+// (and |e_u| > 32) go to block teams
 void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,
-                         unsigned long long* wide_max, bool all_block, cudaStream_t s);
+                         unsigned long long* wide_max, bool all_block, int warp_max,
+                         cudaStream_t s);
 // n: list length (host copy); n_p: the same on the device; counter: zeroed fetch counter;
 // work[0] += probes (entries of out(v) streamed), work[1] += E_y entries scanned for masks;
 // warp kernels append hyperedges their tables cannot hold (every hyperedge when

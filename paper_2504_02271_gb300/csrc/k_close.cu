@@ -18,7 +18,10 @@
 // The seven bits, labelled (u, v, w), index a block-local 128-bin histogram that is
 // flushed to 64-bit global counters; the host folds the labelled masks into canonical
 // masks and patterns.
+#include <climits>
 #include <mutex>
+
+#include <cooperative_groups.h>
 #include <type_traits>
 
 #include "hg_internal.cuh"
@@ -29,10 +32,16 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBins = 128;     // labelled region masks (bit r = region r non-empty)
 constexpr int kHistCopies = 4; // spread same-pattern increments of the block kernel
-constexpr int kWideThreads = 256;
+// Global-table teams: one block of kWideThreads per hyperedge, kWideBlocksPerSm blocks
+// per SM; fewer, wider blocks keep fewer teams' tables in flight (they live in global
+// memory, so the resident set decides the L2 hit rate).
+#ifndef HG_WIDE_THREADS
+#define HG_WIDE_THREADS 256
+#endif
+constexpr int kWideThreads = HG_WIDE_THREADS;
 constexpr int kWideFilterLog2 = 18;   // 32 KiB shared filter per wide-team block
 constexpr int kWideUnroll = 4;        // 32-entry loads in flight per warp
-constexpr int kWideBlocksPerSm = 4;
+constexpr int kWideBlocksPerSm = 1024 / kWideThreads;
 
 template <bool PACKED>
 __device__ __forceinline__ void get_entry(const Oriented& o, int64_t at, int32_t& nbr, int32_t& om) {
@@ -78,13 +87,13 @@ __device__ __forceinline__ uint32_t full_mask(int sz) { return sz >= 32 ? ~0u : 
 // 32 at a time, so the classification runs with every lane active.
 
 // Entries of out(v) loaded per lane before their probes (loads in flight per warp):
-// kWarpUnroll in the warp teams, kUnroll in the block teams.
+// kWarpUnroll in the warp teams, kBlockUnroll in the block teams.
 #ifndef HG_CLOSE_WARP_UNROLL
 #define HG_CLOSE_WARP_UNROLL 8
 #endif
 constexpr int kWarpUnroll = HG_CLOSE_WARP_UNROLL;
-constexpr int kUnroll = 4;
-constexpr int kQueue = 32 * kUnroll + 32;
+constexpr int kBlockUnroll = 8;
+constexpr int kQueue = 32 * kBlockUnroll + 32;
 constexpr int kWarpQueue = 32 * kWarpUnroll + 32;
 constexpr int kCuckooTries = 16;
 constexpr int kStash = 8;
@@ -122,7 +131,7 @@ __device__ __forceinline__ uint32_t cuckoo_h2(uint32_t key, int t_log2) {
 // at least 256 otherwise.  The empty item (all ones) would answer 255 to a key whose
 // low 24 bits are all ones; no hyperedge id of a packed layout (< 2^24 - 1) has
 // them, and lanes without an entry look up u itself, which is never in out(u).
-template <class TT>
+template <class TT, bool STASH = true>
 __device__ __forceinline__ int warp_find(const TT& t, int32_t x, int nst) {
   using Item = typename TT::Item;
   const uint32_t key = (uint32_t)x;
@@ -131,9 +140,11 @@ __device__ __forceinline__ int warp_find(const TT& t, int32_t x, int nst) {
   const Item b = t.c2[cuckoo_h2(key, TT::T_LOG2)] ^ k8;
   int k = a < 256 ? (int)a : -1;
   k = b < 256 ? (int)b : k;
-  for (int i = 0; i < nst; ++i) {
-    const Item c = t.stash[i] ^ k8;
-    k = c < 256 ? (int)c : k;
+  if (STASH) {
+    for (int i = 0; i < nst; ++i) {
+      const Item c = t.stash[i] ^ k8;
+      k = c < 256 ? (int)c : k;
+    }
   }
   return k;
 }
@@ -213,6 +224,77 @@ __device__ __forceinline__ void classify_queued(const WarpTables<D_LOG2, PACKED>
   const uint32_t kv = e >> 24, kw = (e >> 8) & 0xffu;
   const int om = PACKED ? (int)(e & 0xffu) : t.qom[at];
   rh.add(region_bits(fu, t.kmask[kv], t.kmask[kw], t.ksz[kv], t.ksz[kw], om), hist);
+}
+
+// Step 3 of a warp team: the flat range of all out(v), v in out(u) (F entries), each
+// lane walking entries lane, lane + 32, ... with its own cursor (row ck of out(u),
+// entry cj of out(v_ck)); kWarpUnroll loads in flight, then their probes; hits are
+// queued and classified 32 at a time.  STASH = false when the team's stash is empty
+// (the usual case): the probes then skip the stash scan altogether.
+template <int D_LOG2, bool PACKED, bool STASH>
+__device__ __forceinline__ void warp_walk(WarpTables<D_LOG2, PACKED>& t, const Oriented& o,
+                                          int32_t u, int32_t du, int32_t F, int nst,
+                                          uint32_t fu, uint32_t* hist, RunHist& rh, int lane) {
+  int qn = 0;   // queued hits (the same on every lane)
+  int ck = 0, cj = lane;
+  int ccnt = t.kcnt[0];   // du >= 2; past the last row ccnt stays INT32_MAX
+  while (cj >= ccnt) {
+    cj -= ccnt;
+    ++ck;
+    ccnt = ck < du ? t.kcnt[ck] : INT32_MAX;
+  }
+  RowPtr<PACKED> rp;
+  rp.at(o, ck < du ? t.kbeg[ck] : 0);
+  for (int base = 0; base < F; base += 32 * kWarpUnroll) {
+    // packed: the raw entry (w << 8) | omega_vw in one register; no entry: u << 8
+    // (u is never in out(u)).  Unpacked: w and omega_vw apart.
+    int32_t ent_w[kWarpUnroll], ent_om[PACKED ? 1 : kWarpUnroll], ent_k[kWarpUnroll];
+#pragma unroll
+    for (int q = 0; q < kWarpUnroll; ++q) {
+      ent_k[q] = ck;
+      if (PACKED) {
+        ent_w[q] = (int32_t)((uint32_t)u << 8);
+        if (ck < du) ent_w[q] = (int32_t)rp.raw(cj);
+      } else {
+        ent_w[q] = u;
+        ent_om[q] = 0;
+        if (ck < du) rp.load(cj, ent_w[q], ent_om[q]);
+      }
+      cj += 32;
+      if (cj >= ccnt) {   // next row(s): the row pointer is set once, at the row reached
+        do {
+          cj -= ccnt;
+          ++ck;
+          ccnt = ck < du ? t.kcnt[ck] : INT32_MAX;
+        } while (cj >= ccnt);
+        if (ck < du) rp.at(o, t.kbeg[ck]);
+      }
+    }
+    // probe; hits go to the warp's queue as (index of v, index of w, omega_vw)
+#pragma unroll
+    for (int q = 0; q < kWarpUnroll; ++q) {
+      const int32_t x = PACKED ? (int32_t)((uint32_t)ent_w[q] >> 8) : ent_w[q];
+      const int kw = warp_find<WarpTables<D_LOG2, PACKED>, STASH>(t, x, nst);
+      const bool hit = kw >= 0;
+      const unsigned bal = __ballot_sync(kFull, hit);
+      if (hit) {
+        const int at = qn + __popc(bal & ((1u << lane) - 1u));
+        t.queue[at] = ((uint32_t)ent_k[q] << 24) | ((uint32_t)kw << 8) |
+                      (PACKED ? ((uint32_t)ent_w[q] & 0xffu) : 0u);
+        if (!PACKED) t.qom[at] = ent_om[PACKED ? 0 : q];
+      }
+      qn += __popc(bal);
+    }
+    __syncwarp();
+    // classify full rounds of 32 hits with every lane busy
+    while (qn >= 32) {
+      qn -= 32;
+      classify_queued<D_LOG2, PACKED>(t, qn + lane, fu, hist, rh);
+      __syncwarp();
+    }
+  }
+  if (lane < qn) classify_queued<D_LOG2, PACKED>(t, lane, fu, hist, rh);
+  __syncwarp();
 }
 
 template <int D_LOG2, int WARPS, bool PACKED>
@@ -343,64 +425,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
     __syncwarp();
 
     // 3. closure over the flat range of all out(v), v in out(u)
-    int qn = 0;   // queued hits (the same on every lane)
-    int ck = 0, cj = lane;             // this lane's cursor: entry cj of out(v_ck)
-    int ccnt = du > 0 ? t.kcnt[0] : 0;
-    while (cj >= ccnt && ck < du) {
-      cj -= ccnt;
-      if (++ck < du) ccnt = t.kcnt[ck];
-    }
-    RowPtr<PACKED> rp;
-    rp.at(o, ck < du ? t.kbeg[ck] : 0);
-    for (int base = 0; base < F; base += 32 * kWarpUnroll) {
-      // packed: the raw entry (w << 8) | omega_vw in one register; no entry: u << 8
-      // (u is never in out(u)).  Unpacked: w and omega_vw apart.
-      int32_t ent_w[kWarpUnroll], ent_om[PACKED ? 1 : kWarpUnroll], ent_k[kWarpUnroll];
-#pragma unroll
-      for (int q = 0; q < kWarpUnroll; ++q) {
-        ent_k[q] = ck;
-        if (PACKED) {
-          ent_w[q] = (int32_t)((uint32_t)u << 8);
-          if (ck < du) ent_w[q] = (int32_t)rp.raw(cj);
-        } else {
-          ent_w[q] = u;
-          ent_om[q] = 0;
-          if (ck < du) rp.load(cj, ent_w[q], ent_om[q]);
-        }
-        cj += 32;
-        while (cj >= ccnt && ck < du) {
-          cj -= ccnt;
-          if (++ck < du) {
-            ccnt = t.kcnt[ck];
-            rp.at(o, t.kbeg[ck]);
-          }
-        }
-      }
-      // probe; hits go to the warp's queue as (index of v, index of w, omega_vw)
-#pragma unroll
-      for (int q = 0; q < kWarpUnroll; ++q) {
-        const int32_t x = PACKED ? (int32_t)((uint32_t)ent_w[q] >> 8) : ent_w[q];
-        const int kw = warp_find(t, x, nst);
-        const bool hit = kw >= 0;
-        const unsigned bal = __ballot_sync(kFull, hit);
-        if (hit) {
-          const int at = qn + __popc(bal & ((1u << lane) - 1u));
-          t.queue[at] = ((uint32_t)ent_k[q] << 24) | ((uint32_t)kw << 8) |
-                        (PACKED ? ((uint32_t)ent_w[q] & 0xffu) : 0u);
-          if (!PACKED) t.qom[at] = ent_om[PACKED ? 0 : q];
-        }
-        qn += __popc(bal);
-      }
-      __syncwarp();
-      // classify full rounds of 32 hits with every lane busy
-      while (qn >= 32) {
-        qn -= 32;
-        classify_queued<D_LOG2, PACKED>(t, qn + lane, fu, hist[w], rh);
-        __syncwarp();
-      }
-    }
-    if (lane < qn) classify_queued<D_LOG2, PACKED>(t, lane, fu, hist[w], rh);
-    __syncwarp();
+    if (nst == 0) warp_walk<D_LOG2, PACKED, false>(t, o, u, du, F, nst, fu, hist[w], rh, lane);
+    else warp_walk<D_LOG2, PACKED, true>(t, o, u, du, F, nst, fu, hist[w], rh, lane);
   }
   warp_flush(rh, hist[w], hist_out + (size_t)cur * kBins, lane);
   if (lane == 0) {
@@ -452,7 +478,7 @@ struct alignas(16) BlockTables {
 };
 
 // Index k in out(u) of hyperedge x, or -1 (x = -1 matches nothing: keys are < 2^31).
-template <int D_LOG2, int WARPS, bool PACKED>
+template <int D_LOG2, int WARPS, bool PACKED, bool STASH = true>
 __device__ __forceinline__ int block_find(const BlockTables<D_LOG2, WARPS, PACKED>& t, int32_t x,
                                           int nst) {
   constexpr int SH = 32 - (D_LOG2 + 1);   // remainder bits
@@ -461,8 +487,96 @@ __device__ __forceinline__ int block_find(const BlockTables<D_LOG2, WARPS, PACKE
   const uint32_t a = t.c1[p1 >> SH], b = t.c2[p2 >> SH];
   int k = (a >> D_LOG2) == (p1 & RM) ? (int)(a & KM) : -1;
   k = (b >> D_LOG2) == (p2 & RM) ? (int)(b & KM) : k;
-  for (int i = 0; i < nst; ++i) k = t.skey[i] == x ? t.sidx[i] : k;
+  if (STASH)
+    for (int i = 0; i < nst; ++i) k = t.skey[i] == x ? t.sidx[i] : k;
   return k;
+}
+
+// Step 3 of a block team, for warp w: the slice [f_lo, f_hi) of the flat range of all
+// out(v), v in out(u), walked like the warp teams' (kBlockUnroll loads in flight, a
+// cursor per lane, queued 32-wide classification); the slice start is found by a
+// binary search over the prefix sums kpre of the out-degrees.
+template <int D_LOG2, int WARPS, bool PACKED, bool STASH>
+__device__ __forceinline__ void block_walk(BlockTables<D_LOG2, WARPS, PACKED>& t,
+                                           const Oriented& o, int32_t u, int32_t du,
+                                           int32_t f_lo, int32_t f_hi, int nst, uint32_t fu,
+                                           uint32_t* hist, RunHist& rh, int lane, int w) {
+  int qn = 0;
+  uint32_t* queue = t.queue[w];
+  // cursor of this lane: first entry f_lo + lane -> (ck, cj); past the slice: ck = du
+  int ck = du, cj = 0, ccnt = INT32_MAX;
+  RowPtr<PACKED> rp;
+  rp.at(o, 0);
+  {
+    const int32_t f0 = f_lo + lane;
+    int lo = 0, hi = du;   // last k with kpre[k] <= f0
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (t.kpre[mid] <= f0) lo = mid; else hi = mid - 1;
+    }
+    if (f0 < f_hi && lo < du) {
+      ck = lo;
+      cj = f0 - t.kpre[ck];
+      ccnt = t.kpre[ck + 1] - t.kpre[ck];
+      rp.at(o, t.kbeg[ck]);
+    }
+  }
+  for (int32_t base = f_lo; base < f_hi; base += 32 * kBlockUnroll) {
+    int32_t ent_w[kBlockUnroll], ent_om[PACKED ? 1 : kBlockUnroll], ent_k[kBlockUnroll];
+#pragma unroll
+    for (int q = 0; q < kBlockUnroll; ++q) {
+      ent_k[q] = ck;
+      const bool in = ck < du && base + q * 32 + lane < f_hi;
+      if (PACKED) {
+        ent_w[q] = (int32_t)((uint32_t)u << 8);   // no entry: u, never in out(u)
+        if (in) ent_w[q] = (int32_t)rp.raw(cj);
+      } else {
+        ent_w[q] = u;
+        ent_om[q] = 0;
+        if (in) rp.load(cj, ent_w[q], ent_om[q]);
+      }
+      cj += 32;
+      if (cj >= ccnt) {
+        do {
+          cj -= ccnt;
+          ++ck;
+          ccnt = ck < du ? t.kpre[ck + 1] - t.kpre[ck] : INT32_MAX;
+        } while (cj >= ccnt);
+        if (ck < du) rp.at(o, t.kbeg[ck]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kBlockUnroll; ++q) {
+      const int32_t x = PACKED ? (int32_t)((uint32_t)ent_w[q] >> 8) : ent_w[q];
+      const int kw = block_find<D_LOG2, WARPS, PACKED, STASH>(t, x, nst);
+      const bool hit = kw >= 0;
+      const unsigned bal = __ballot_sync(kFull, hit);
+      if (hit) {
+        const int at = qn + __popc(bal & ((1u << lane) - 1u));
+        queue[at] = ((uint32_t)ent_k[q] << 16) | (uint32_t)kw;
+        if (PACKED) t.qom8[w][at] = (uint8_t)((uint32_t)ent_w[q] & 0xffu);
+        else t.qom[w][at] = ent_om[PACKED ? 0 : q];
+      }
+      qn += __popc(bal);
+    }
+    __syncwarp();
+    while (qn >= 32) {
+      qn -= 32;
+      const int at = qn + lane;
+      const uint32_t e = queue[at];
+      const uint32_t kv = e >> 16, kw = e & 0xffffu;
+      const int om = PACKED ? (int)t.qom8[w][at] : t.qom[w][at];
+      rh.add(region_bits(fu, t.kmask[kv], t.kmask[kw], t.ksz[kv], t.ksz[kw], om), hist);
+      __syncwarp();
+    }
+  }
+  if (lane < qn) {
+    const uint32_t e = queue[lane];
+    const uint32_t kv = e >> 16, kw = e & 0xffffu;
+    const int om = PACKED ? (int)t.qom8[w][lane] : t.qom[w][lane];
+    rh.add(region_bits(fu, t.kmask[kv], t.kmask[kw], t.ksz[kv], t.ksz[kw], om), hist);
+  }
+  __syncwarp();
 }
 
 template <int D_LOG2, int WARPS, bool PACKED>
@@ -622,75 +736,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     }
     // 3. closure: warp w walks the flat slice [F*w/WARPS, F*(w+1)/WARPS)
     const int32_t f_lo = (int32_t)((int64_t)F * w / WARPS), f_hi = (int32_t)((int64_t)F * (w + 1) / WARPS);
-    int qn = 0;
-    uint32_t* queue = t.queue[w];
-    // cursor of this lane: first entry f_lo + lane -> (ck, cj)
-    int ck = 0, cj = 0, ccnt = 0;
-    int64_t cb = 0;
-    {
-      const int32_t f0 = f_lo + lane;
-      int lo = 0, hi = du;   // last k with kpre[k] <= f0
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (t.kpre[mid] <= f0) lo = mid; else hi = mid - 1;
-      }
-      ck = lo;
-      if (f0 >= f_hi || ck >= du) {
-        ck = du;
-      } else {
-        cj = f0 - t.kpre[ck];
-        ccnt = t.kpre[ck + 1] - t.kpre[ck];
-        cb = t.kbeg[ck];
-      }
-    }
-    for (int32_t base = f_lo; base < f_hi; base += 32 * kUnroll) {
-      int32_t ent_w[kUnroll], ent_om[kUnroll], ent_k[kUnroll];
-#pragma unroll
-      for (int q = 0; q < kUnroll; ++q) {
-        ent_k[q] = ck;
-        ent_w[q] = -1;
-        ent_om[q] = 0;
-        if (ck < du && base + q * 32 + lane < f_hi) get_entry<PACKED>(o, cb + cj, ent_w[q], ent_om[q]);
-        cj += 32;
-        while (cj >= ccnt && ck < du) {
-          cj -= ccnt;
-          if (++ck < du) {
-            ccnt = t.kpre[ck + 1] - t.kpre[ck];
-            cb = t.kbeg[ck];
-          }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < kUnroll; ++q) {
-        const int kw = block_find(t, ent_w[q], nst);
-        const bool hit = kw >= 0;
-        const unsigned bal = __ballot_sync(kFull, hit);
-        if (hit) {
-          const int at = qn + __popc(bal & ((1u << lane) - 1u));
-          queue[at] = ((uint32_t)ent_k[q] << 16) | (uint32_t)kw;
-          if (PACKED) t.qom8[w][at] = (uint8_t)ent_om[q];
-          else t.qom[w][at] = ent_om[q];
-        }
-        qn += __popc(bal);
-      }
-      __syncwarp();
-      while (qn >= 32) {
-        qn -= 32;
-        const int at = qn + lane;
-        const uint32_t e = queue[at];
-        const uint32_t kv = e >> 16, kw = e & 0xffffu;
-        const int om = PACKED ? (int)t.qom8[w][at] : t.qom[w][at];
-        rh.add(region_bits(fu, t.kmask[kv], t.kmask[kw], t.ksz[kv], t.ksz[kw], om), hist[w]);
-        __syncwarp();
-      }
-    }
-    if (lane < qn) {
-      const uint32_t e = queue[lane];
-      const uint32_t kv = e >> 16, kw = e & 0xffffu;
-      const int om = PACKED ? (int)t.qom8[w][lane] : t.qom[w][lane];
-      rh.add(region_bits(fu, t.kmask[kv], t.kmask[kw], t.ksz[kv], t.ksz[kw], om), hist[w]);
-    }
-    __syncwarp();
+    if (nst == 0)
+      block_walk<D_LOG2, WARPS, PACKED, false>(t, o, u, du, f_lo, f_hi, nst, fu, hist[w], rh, lane, w);
+    else
+      block_walk<D_LOG2, WARPS, PACKED, true>(t, o, u, du, f_lo, f_hi, nst, fu, hist[w], rh, lane, w);
   }
   block_flush();
   if (threadIdx.x == 0) {
@@ -717,13 +766,14 @@ struct WideScratch {
   int64_t* kbeg;    // [dmax]
   int32_t* skey;    // [dmax]
   int32_t* sidx;    // [dmax]
+  int32_t* nstash;  // [1] stash length (cluster teams: shared by the cluster's blocks)
 };
 
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 __host__ __device__ inline size_t wide_block_bytes(int64_t cap, int64_t words, int64_t dmax) {
   return align256(cap * 4) * 2 + align256(dmax * words * 4) + align256(dmax * 4) * 4 +
-         align256(dmax * 8);
+         align256(dmax * 8) + 256;
 }
 
 __device__ WideScratch wide_carve(char* base, int64_t cap, int64_t words, int64_t dmax) {
@@ -743,6 +793,8 @@ __device__ WideScratch wide_carve(char* base, int64_t cap, int64_t words, int64_
   w.skey = (int32_t*)base;
   base += align256(dmax * 4);
   w.sidx = (int32_t*)base;
+  base += align256(dmax * 4);
+  w.nstash = (int32_t*)base;
   return w;
 }
 
@@ -935,21 +987,269 @@ __global__ void __launch_bounds__(kWideThreads, kWideBlocksPerSm)
   }
 }
 
+// ------------------------------------------------------------------ cluster per u (large)
+//
+// Teams of out-degree above kWideLargeMin: a thread-block cluster of C blocks of
+// kClusterThreads threads shares one hyperedge u and one set of global-memory tables.
+// Every phase of the team (clearing, cuckoo insertion, Omega_ux masks, |e_x| -
+// omega_ux, closure) is cut across all C * kClusterThreads threads, with a cluster
+// barrier between phases, so only (blocks on the GPU) / C teams' tables are in use at
+// any time.  Rank 0 takes the next hyperedge from the counter and the others read it
+// from rank 0's shared memory.  Reads of the team's tables, masks and per-out-neighbour
+// arrays go through L2 (ld.global.cg): other blocks of the cluster wrote them.  Each
+// block keeps its own membership filter of out(u) (every key) in shared memory, and its
+// own histogram.  The closure gives each warp one v at a time; hits (w's index and
+// omega_vw) are queued per warp and classified 32 at a time.  C = 1 by default: on the
+// tag-shaped workload at full size C = 2, 4 and 8 were 2%, 9% and 39% slower (the
+// tables of fewer teams at a time did not pay for the cluster barriers).
+
+constexpr int kClusterThreads = 1024;
+#ifndef HG_WIDE_CLUSTER
+#define HG_WIDE_CLUSTER 1
+#endif
+constexpr int kWideCluster = HG_WIDE_CLUSTER;   // blocks per cluster team
+
+__device__ __forceinline__ int wide_find_l2(const WideScratch& t, int32_t x, int dl, int nst) {
+  const int sh = 31 - dl;
+  const uint32_t rm = (1u << sh) - 1u, km = (1u << dl) - 1u;
+  const uint32_t p1 = (uint32_t)x * kCuckooA1, p2 = (uint32_t)x * kCuckooA2;
+  const uint32_t a = __ldcg(t.c1 + (p1 >> sh)), b = __ldcg(t.c2 + (p2 >> sh));
+  int k = (a >> dl) == (p1 & rm) ? (int)(a & km) : -1;
+  k = (b >> dl) == (p2 & rm) ? (int)(b & km) : k;
+  for (int i = 0; i < nst; ++i) k = __ldcg(t.skey + i) == x ? __ldcg(t.sidx + i) : k;
+  return k;
+}
+
+template <bool PACKED>
+__global__ void __launch_bounds__(kClusterThreads, 1)
+    k_close_cluster(DevGraph g, Oriented o, const int32_t* __restrict__ list,
+                    const int32_t* __restrict__ n_p, int64_t cap_max, int64_t words_max,
+                    int64_t dmax, char* __restrict__ scratch,
+                    unsigned long long* __restrict__ hist_out, unsigned long long* __restrict__ work,
+                    int32_t* __restrict__ counter) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank(), csize = (int)cluster.num_blocks();
+  constexpr int kCQ = 32 * kWideUnroll + 32;   // hit queue per warp
+  __shared__ uint32_t hist[kHistCopies][kBins];
+  __shared__ int32_t s_r;
+  __shared__ unsigned long long s_since;
+  __shared__ uint32_t filt[(1 << kWideFilterLog2) / 32];
+  __shared__ int32_t qk[kClusterThreads / 32][kCQ];   // index of w in out(u)
+  __shared__ int32_t qo[kClusterThreads / 32][kCQ];   // omega_vw
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int gt = rank * kClusterThreads + (int)threadIdx.x, GT = csize * kClusterThreads;
+  const int gw = gt >> 5, GW = GT >> 5;
+  WideScratch t = wide_carve(scratch + wide_block_bytes(cap_max, words_max, dmax) *
+                                           (size_t)(blockIdx.x / csize),
+                             cap_max, words_max, dmax);
+  for (int k = threadIdx.x; k < kHistCopies * kBins; k += kClusterThreads) (&hist[0][0])[k] = 0;
+  const int32_t n = *n_p;
+  uint32_t* my_hist = hist[lane & (kHistCopies - 1)];
+  RunHist rh;
+  unsigned long long probes = 0, gathers = 0, outs = 0;
+  int32_t cur = 0;
+  if (threadIdx.x == 0) s_since = 0;
+  __syncthreads();
+  auto block_flush = [&]() {
+    rh.flush(my_hist);
+    __syncthreads();
+    for (int k = threadIdx.x; k < kBins; k += kClusterThreads) {
+      unsigned long long x = 0;
+      for (int c = 0; c < kHistCopies; ++c) {
+        x += hist[c][k];
+        hist[c][k] = 0;
+      }
+      if (x) atomicAdd(&hist_out[(size_t)cur * kBins + k], x);
+    }
+    if (threadIdx.x == 0) s_since = 0;
+    __syncthreads();
+  };
+  while (true) {
+    if (rank == 0 && threadIdx.x == 0) s_r = atomicAdd(counter, 1);
+    cluster.sync();
+    const int32_t r = *cluster.map_shared_rank(&s_r, 0);
+    if (r >= n) {
+      cluster.sync();   // rank 0's shared memory stays until every block has read it
+      break;
+    }
+    const int32_t u = list[r];
+    const int32_t m = member_of(g, u);
+    if (m != cur || s_since > (1ull << 28)) {   // read after a barrier: uniform in the block
+      block_flush();
+      cur = m;
+    }
+    const int32_t du = o.dplus[u];
+    const int64_t bu = o.row_ptr[u];
+    const int64_t eb = g.e_ptr[u];
+    const int32_t szu = (int32_t)(g.e_ptr[u + 1] - eb);
+    const int32_t words = (szu + 31) / 32;
+    if (gt == 0) outs += (unsigned long long)du;
+    int dl = 4;
+    while ((int64_t(1) << dl) < (int64_t)du) ++dl;
+    const uint32_t tslots = 2u << dl;
+    const int sh = 31 - dl;
+    const uint32_t rm = (1u << sh) - 1u, km = (1u << dl) - 1u;
+    int fl = 5;
+    while (fl < kWideFilterLog2 && (int64_t(1) << fl) < 16 * (int64_t)du) ++fl;
+    // 1. clear the team's tables and masks (cluster-wide), and this block's filter
+    for (uint32_t s = (uint32_t)gt; s < tslots; s += (uint32_t)GT) {
+      t.c1[s] = ~0u;
+      t.c2[s] = ~0u;
+    }
+    for (int64_t s = gt; s < (int64_t)du * words; s += GT) t.mask[s] = 0;
+    if (gt == 0) *t.nstash = 0;
+    for (int s = threadIdx.x; s < (1 << fl) / 32; s += kClusterThreads) filt[s] = 0;
+    cluster.sync();
+    // 2. out(u) into the cuckoo set (cluster-wide share of the keys); every key into
+    //    this block's filter
+    for (int k = gt; k < du; k += GT) {
+      int32_t x, om;
+      get_entry<PACKED>(o, bu + k, x, om);
+      uint32_t key = (uint32_t)x, kk = (uint32_t)k;
+      bool second = false, placed = false;
+      for (int tries = 0; tries < kCuckooTries; ++tries) {
+        const uint32_t pa = key * (second ? kCuckooA2 : kCuckooA1);
+        const uint32_t slot = pa >> sh;
+        const uint32_t e = atomicExch(second ? &t.c2[slot] : &t.c1[slot], ((pa & rm) << dl) | kk);
+        if (e == ~0u) {
+          placed = true;
+          break;
+        }
+        key = ((slot << sh) | (e >> dl)) * (second ? kCuckooA2Inv : kCuckooA1Inv);
+        kk = e & km;
+        second = !second;
+      }
+      if (!placed) {   // room for every key: du <= dmax
+        const int at = atomicAdd(t.nstash, 1);
+        t.skey[at] = (int32_t)key;
+        t.sidx[at] = (int32_t)kk;
+      }
+      t.ksz[k] = __ldg(g.esize + x);
+      t.kbeg[k] = __ldg(o.row_ptr + x);
+      t.kcnt[k] = __ldg(o.dplus + x);
+    }
+    for (int k = threadIdx.x; k < du; k += kClusterThreads) {
+      int32_t x, om;
+      get_entry<PACKED>(o, bu + k, x, om);
+      const uint32_t fb = filt_bit((uint32_t)x, fl);
+      atomicOr(&filt[fb >> 5], 1u << (fb & 31));
+    }
+    cluster.sync();
+    const int nst = __ldcg(t.nstash);
+    // 3. Omega_ux masks: vertex p of e_u per warp of the cluster
+    for (int p = gw; p < szu; p += GW) {
+      const int32_t y = __ldg(g.e_idx + eb + p);
+      const int64_t yb = __ldg(g.v_ptr + y), ye = __ldg(g.v_ptr + y + 1);
+      if (lane == 0) gathers += (unsigned long long)(ye - yb);
+      for (int64_t q = yb + lane; q < ye; q += 32) {
+        const int32_t x = __ldg(g.v_idx + q);
+        const uint32_t fb = filt_bit((uint32_t)x, fl);
+        if (!((filt[fb >> 5] >> (fb & 31)) & 1u)) continue;
+        const int kx = wide_find_l2(t, x, dl, nst);
+        if (kx >= 0) atomicOr(&t.mask[(size_t)kx * words + (p >> 5)], 1u << (p & 31));
+      }
+    }
+    cluster.sync();
+    // |e_x| -> |e_x| - omega_ux, the part of e_x outside e_u
+    for (int k = gt; k < du; k += GT) {
+      int om = 0;
+      for (int q = 0; q < words; ++q) om += __popc(__ldcg(t.mask + (size_t)k * words + q));
+      t.ksz[k] = __ldcg(t.ksz + k) - om;
+    }
+    cluster.sync();
+    // 4. closure: out-neighbour k (= v) per warp of the cluster; hits (w's index and
+    //    omega_vw) are queued and classified 32 at a time with every lane busy
+    for (int k = gw; k < du; k += GW) {
+      const uint32_t* muv = t.mask + (size_t)k * words;
+      const int rv = __ldcg(t.ksz + k);
+      const int64_t vb = __ldcg(t.kbeg + k);
+      const int32_t cnt = __ldcg(t.kcnt + k);
+      if (lane == 0) {
+        probes += (unsigned long long)cnt;
+        atomicAdd(&s_since, (unsigned long long)cnt);
+      }
+      auto classify = [&](int at) {
+        const int kw = qk[wl][at];
+        const uint32_t* muw = t.mask + (size_t)kw * words;
+        uint32_t any_a = 0, any_d = 0, any_f = 0, any_g = 0;
+        int gg = 0;
+        for (int qq = 0; qq < words; ++qq) {
+          const uint32_t a = __ldcg(muv + qq), b = __ldcg(muw + qq);
+          const uint32_t fq = full_mask(szu - 32 * qq);
+          any_a |= fq & ~(a | b);
+          any_d |= a & ~b;
+          any_f |= b & ~a;
+          any_g |= a & b;
+          gg += __popc(a & b);
+        }
+        const int tt = qo[wl][at] - gg, rw = __ldcg(t.ksz + kw);
+        rh.add((uint32_t)(any_a != 0u) | ((uint32_t)(rv > tt) << 1) | ((uint32_t)(rw > tt) << 2) |
+                   ((uint32_t)(any_d != 0u) << 3) | ((uint32_t)(tt > 0) << 4) |
+                   ((uint32_t)(any_f != 0u) << 5) | ((uint32_t)(any_g != 0u) << 6),
+               my_hist);
+      };
+      int qn = 0;   // queued hits (the same on every lane)
+      for (int32_t j0 = 0; j0 < cnt; j0 += 32 * kWideUnroll) {
+        int32_t wv[kWideUnroll], om[kWideUnroll];
+#pragma unroll
+        for (int q = 0; q < kWideUnroll; ++q) {
+          const int32_t j = j0 + q * 32 + lane;
+          wv[q] = -1;
+          om[q] = 0;
+          if (j < cnt) get_entry<PACKED>(o, vb + j, wv[q], om[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < kWideUnroll; ++q) {
+          const int32_t x = wv[q];
+          int kw = -1;
+          if (x >= 0) {
+            const uint32_t fb = filt_bit((uint32_t)x, fl);
+            if ((filt[fb >> 5] >> (fb & 31)) & 1u) kw = wide_find_l2(t, x, dl, nst);
+          }
+          const bool hit = kw >= 0;
+          const unsigned bal = __ballot_sync(kFull, hit);
+          if (hit) {
+            const int at = qn + __popc(bal & ((1u << lane) - 1u));
+            qk[wl][at] = kw;
+            qo[wl][at] = om[q];
+          }
+          qn += __popc(bal);
+        }
+        __syncwarp();
+        while (qn >= 32) {
+          qn -= 32;
+          classify(qn + lane);
+          __syncwarp();
+        }
+      }
+      if (lane < qn) classify(lane);
+      __syncwarp();
+    }
+    cluster.sync();   // the next team clears these tables
+  }
+  block_flush();
+  if (lane == 0) {
+    atomicAdd(&work[0], probes);
+    atomicAdd(&work[1], gathers);
+    atomicAdd(&work[2], outs);
+  }
+}
+
 // ------------------------------------------------------------------ bucketing
 
 constexpr int kWarpMaskBits = 32;   // warp tables keep Omega_ux in one 32-bit word
 
 // Team shape of u (bucket index, -1 when u closes nothing).
-__device__ __forceinline__ int close_bucket_of(int32_t d, int32_t sz, bool all_block) {
+__device__ __forceinline__ int close_bucket_of(int32_t d, int32_t sz, bool all_block,
+                                               int warp_max) {
   if (d < 2) return -1;
   if (all_block) return kWideBucket;
-  if (sz <= kWarpMaskBits && d <= 64) return 0;
-  if (sz <= kWarpMaskBits && d <= 128) return 1;
-  if (sz <= kWarpMaskBits && d <= 256) return 2;
+  if (sz <= kWarpMaskBits && d <= warp_max) return d <= 64 ? 0 : (d <= 128 ? 1 : 2);
   if (sz <= kWarpMaskBits && d <= 1024) return 3;
   if (sz <= kWarpMaskBits && d <= 2048) return 4;
   if (sz <= kWarpMaskBits && d <= 4096) return 5;
-  return kWideBucket;
+  return d > kWideLargeMin ? kClusterBucket : kWideBucket;
 }
 
 // Each block takes a contiguous range of kBucketRowsPerBlock hyperedges: it counts
@@ -962,7 +1262,7 @@ constexpr int kBucketRowsPerBlock = kBucketThreads * kBucketRowsPerThread;
 
 __global__ void __launch_bounds__(kBucketThreads)
     k_bucket_close(DevGraph g, Oriented o, CloseBuckets b,
-                   unsigned long long* __restrict__ wide_max, bool all_block) {
+                   unsigned long long* __restrict__ wide_max, bool all_block, int warp_max) {
   __shared__ int32_t s_cnt[kCloseBuckets], s_base[kCloseBuckets];
   const int lane = threadIdx.x & 31;
   unsigned long long my_d = 0, my_s = 0;
@@ -977,8 +1277,8 @@ __global__ void __launch_bounds__(kBucketThreads)
       bk[q] = -1;
       if (u < g.ne) {
         const int32_t d = o.dplus[u], sz = g.esize[u];
-        bk[q] = close_bucket_of(d, sz, all_block);
-        if (bk[q] == kWideBucket) {
+        bk[q] = close_bucket_of(d, sz, all_block, warp_max);
+        if (bk[q] >= kWideBucket) {
           my_d = (unsigned long long)d > my_d ? (unsigned long long)d : my_d;
           my_s = (unsigned long long)sz > my_s ? (unsigned long long)sz : my_s;
         }
@@ -1088,12 +1388,14 @@ void launch_block(const DevGraph& g, const Oriented& o, int packed, const int32_
 }  // namespace
 
 void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,
-                         unsigned long long* wide_max, bool all_block, cudaStream_t s) {
+                         unsigned long long* wide_max, bool all_block, int warp_max,
+                         cudaStream_t s) {
   if (g.ne == 0) return;
   int64_t blocks = (g.ne + kBucketRowsPerBlock - 1) / kBucketRowsPerBlock;
   if (blocks > 4096) blocks = 4096;
   note_launch();
-  k_bucket_close<<<(unsigned)blocks, kBucketThreads, 0, s>>>(g, o, b, wide_max, all_block);
+  k_bucket_close<<<(unsigned)blocks, kBucketThreads, 0, s>>>(g, o, b, wide_max, all_block,
+                                                             warp_max);
 }
 
 size_t close_wide_scratch_bytes(int64_t cap, int64_t words, int64_t dmax, int nsm) {
@@ -1132,6 +1434,34 @@ void launch_close(int bucket, const DevGraph& g, const Oriented& o, int packed,
       launch_block<12, 16>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow,
                             handover, s, nsm);
       break;
+    case kClusterBucket: {
+      // clusters of kWideCluster blocks, as many as can be resident at once
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = kWideCluster;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.blockDim = dim3(kClusterThreads);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = s;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      auto kern = packed ? k_close_cluster<true> : k_close_cluster<false>;
+      int clusters = 0;
+      cfg.gridDim = dim3((unsigned)(nsm / kWideCluster * kWideCluster));
+      if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess || clusters < 1) {
+        cudaGetLastError();
+        clusters = nsm / kWideCluster;
+      }
+      if (clusters > n) clusters = n;
+      if (clusters < 1) clusters = 1;
+      cfg.gridDim = dim3((unsigned)(clusters * kWideCluster));
+      note_launch();
+      cudaLaunchKernelEx(&cfg, kern, g, o, list, n_p, wide_cap, wide_words, wide_dmax,
+                         (char*)scratch, hist, work, counter);
+      break;
+    }
     default: {
       int blocks = n < nsm * kWideBlocksPerSm ? n : nsm * kWideBlocksPerSm;
       note_launch();

@@ -486,13 +486,13 @@ size_t wedge_heavy_scratch_bytes(int64_t heavy_max_cand, int nsm) {
   return (sizeof(unsigned long long) << cap_log2_for(heavy_max_cand)) * (size_t)(nsm * 2);
 }
 
-void launch_bucket_rows(const int64_t* cand, int32_t ne, WedgeBuckets b, cudaStream_t s) {
+void launch_bucket_rows(const int64_t* cand, int32_t ne, WedgeBuckets b, int light_max,
+                        cudaStream_t s) {
   if (ne == 0) return;
   int64_t blocks = (ne + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   note_launch();
-  k_bucket_rows<<<(unsigned)blocks, 256, 0, s>>>(cand, ne, b, wedge_light_max_cand(),
-                                                 wedge_medium_max_cand());
+  k_bucket_rows<<<(unsigned)blocks, 256, 0, s>>>(cand, ne, b, light_max, wedge_medium_max_cand());
 }
 
 void launch_wedge_rows(const DevGraph& g, const WedgeBuckets& b, const int32_t* nb,

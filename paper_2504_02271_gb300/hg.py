@@ -37,7 +37,8 @@ EXPORTED = ("hg_set_allocator", "hg_load_csr", "hg_build_wedges", "hg_count_patt
             "hg_server_create", "hg_server_add_graph", "hg_server_submit", "hg_server_wait",
             "hg_server_drain", "hg_server_cancel", "hg_server_stats_get", "hg_server_destroy",
             "hg_sample_estimate_adv", "hg_enumerate_pattern", "hg_sample_work_get",
-            "hg_canonical_masks", "hg_mask_histogram", "hg_batch_mask_histogram")
+            "hg_canonical_masks", "hg_mask_histogram", "hg_batch_mask_histogram",
+            "hg_autotune", "hg_batch_autotune")
 
 
 class HgError(RuntimeError):
@@ -52,7 +53,45 @@ class HgError(RuntimeError):
 class _Tuning(ctypes.Structure):
     _fields_ = [("dense_min_size", ctypes.c_int32), ("dense_max_count", ctypes.c_int32),
                 ("close_mode", ctypes.c_int32), ("orient_exact", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("gather_light_max", ctypes.c_int32), ("warp_team_max", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+
+TUNING_FIELDS = ("dense_min_size", "dense_max_count", "close_mode", "orient_exact",
+                 "gather_light_max", "warp_team_max")
+
+
+def _tuning(fields: dict):
+    """A _Tuning from keyword fields, or None (NULL: the handle's own choice) when all are 0."""
+    bad = set(fields) - set(TUNING_FIELDS)
+    if bad:
+        raise TypeError(f"unknown tuning fields {sorted(bad)}")
+    if not any(int(v) for v in fields.values()):
+        return None
+    return _Tuning(*(int(fields.get(n, 0)) for n in TUNING_FIELDS))
+
+
+def _tuning_dict(t) -> dict:
+    return {n: int(getattr(t, n)) for n in TUNING_FIELDS}
+
+
+_AUTOTUNE_MAX = 16
+
+
+class _AutotuneResult(ctypes.Structure):
+    _fields_ = [("best", _Tuning), ("best_ms", ctypes.c_float), ("best_index", ctypes.c_int32),
+                ("num_tried", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tried", _Tuning * _AUTOTUNE_MAX), ("ms", ctypes.c_float * _AUTOTUNE_MAX),
+                ("counts", (ctypes.c_uint64 * 21) * _AUTOTUNE_MAX)]
+
+
+def _autotune_dict(r) -> dict:
+    n = int(r.num_tried)
+    return {"best": _tuning_dict(r.best), "best_ms": float(r.best_ms),
+            "best_index": int(r.best_index),
+            "tried": [_tuning_dict(r.tried[k]) for k in range(n)],
+            "ms": [float(r.ms[k]) for k in range(n)],
+            "counts": np.array([list(r.counts[k]) for k in range(n)], dtype=np.uint64)}
 
 
 class _WedgeStats(ctypes.Structure):
@@ -63,9 +102,9 @@ class _WedgeStats(ctypes.Structure):
 class _CloseStats(ctypes.Structure):
     _fields_ = [("probes", ctypes.c_uint64), ("gathers", ctypes.c_uint64),
                 ("out_entries", ctypes.c_uint64), ("teams", ctypes.c_uint64),
-                ("bucket_teams", ctypes.c_uint64 * 7), ("bucket_probes", ctypes.c_uint64 * 7),
-                ("bucket_gathers", ctypes.c_uint64 * 7),
-                ("bucket_out_entries", ctypes.c_uint64 * 7)]
+                ("bucket_teams", ctypes.c_uint64 * 8), ("bucket_probes", ctypes.c_uint64 * 8),
+                ("bucket_gathers", ctypes.c_uint64 * 8),
+                ("bucket_out_entries", ctypes.c_uint64 * 8)]
 
 
 class _ServerOptions(ctypes.Structure):
@@ -126,6 +165,8 @@ def _open():
     lib.hg_canonical_masks.argtypes = [vp]
     lib.hg_mask_histogram.argtypes = [vp, vp]
     lib.hg_batch_mask_histogram.argtypes = [vp, vp]
+    lib.hg_autotune.argtypes = [vp, vp]
+    lib.hg_batch_autotune.argtypes = [vp, i32, vp]
     lib.hg_close_stats_get.argtypes = [vp, ctypes.POINTER(_CloseStats)]
     lib.hg_kernel_launches.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
     lib.hg_wedge_degrees_noalloc.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp]
@@ -290,14 +331,25 @@ def hg_load_csr(num_vertices: int, num_edges: int, edge_ptr, edge_vtx, stream: i
     return Graph(int(out.value), int(stream), int(num_vertices), int(num_edges), nnz)
 
 
-def hg_build_wedges(g: Graph, dense_min_size: int = 0, dense_max_count: int = 0,
-                    close_mode: int = 0, orient_exact: int = 0) -> dict:
-    """Step one: hyperwedges, their types and the degree orientation; returns the stats."""
-    tun = _Tuning(int(dense_min_size), int(dense_max_count), int(close_mode), int(orient_exact))
+def hg_build_wedges(g: Graph, **tuning) -> dict:
+    """Step one: hyperwedges, their types and the degree orientation; returns the stats.
+    Keyword fields of hg_tuning (dense_min_size, dense_max_count, close_mode, orient_exact,
+    gather_light_max, warp_team_max); none (or all 0) = the handle's autotuned choice if
+    hg_autotune ran, else the defaults."""
+    tun = _tuning(tuning)
     st = _WedgeStats()
     _check("hg_build_wedges",
-           _lib.hg_build_wedges(ctypes.c_void_p(g.ptr), ctypes.byref(tun), ctypes.byref(st)))
+           _lib.hg_build_wedges(ctypes.c_void_p(g.ptr),
+                                ctypes.byref(tun) if tun is not None else None, ctypes.byref(st)))
     return {n: int(getattr(st, n)) for n, _ in _WedgeStats._fields_ if n != "reserved"}
+
+
+def hg_autotune(g: Graph) -> dict:
+    """Autotune the tuning of step one and two on this hypergraph (see include/hg.h); returns
+    the choice and every candidate tried with its time (ms) and counts."""
+    r = _AutotuneResult()
+    _check("hg_autotune", _lib.hg_autotune(ctypes.c_void_p(g.ptr), ctypes.byref(r)))
+    return _autotune_dict(r)
 
 
 def hg_count_patterns(g: Graph) -> np.ndarray:
@@ -518,12 +570,21 @@ def hg_load_batch(num_vertices, edge_off, edge_ptr, edge_vtx, max_wave_edges: in
     return Batch(int(out.value), int(stream), len(nv))
 
 
-def hg_batch_build_wedges(b: Batch, dense_min_size: int = 0, dense_max_count: int = 0,
-                          close_mode: int = 0, orient_exact: int = 0) -> None:
-    """Step one on every wave of the batch; the tuning is that of hg_build_wedges."""
-    tun = _Tuning(int(dense_min_size), int(dense_max_count), int(close_mode), int(orient_exact))
-    _check("hg_batch_build_wedges", _lib.hg_batch_build_wedges(ctypes.c_void_p(b.ptr),
-                                                               ctypes.byref(tun)))
+def hg_batch_build_wedges(b: Batch, **tuning) -> None:
+    """Step one on every wave of the batch; the tuning fields are those of hg_build_wedges."""
+    tun = _tuning(tuning)
+    _check("hg_batch_build_wedges",
+           _lib.hg_batch_build_wedges(ctypes.c_void_p(b.ptr),
+                                      ctypes.byref(tun) if tun is not None else None))
+
+
+def hg_batch_autotune(b: Batch, wave: int = -1) -> dict:
+    """hg_autotune on one wave (-1: the one with the most hyperedges); every wave keeps the
+    choice for hg_batch_build_wedges without tuning fields."""
+    r = _AutotuneResult()
+    _check("hg_batch_autotune",
+           _lib.hg_batch_autotune(ctypes.c_void_p(b.ptr), int(wave), ctypes.byref(r)))
+    return _autotune_dict(r)
 
 
 def hg_batch_count_patterns(b: Batch) -> tuple[np.ndarray, dict]:

@@ -100,7 +100,7 @@ def test_heavy_rows_and_every_team_shape_repeated(hglib):
     # A hub vertex in 6000 hyperedges: rows gather > 4096 candidates (global-scratch
     # gather blocks), and the out-degrees after degree ordering run from 0 to ~6000, so
     # every closure team shape runs - warp teams, block teams with shared tables for
-    # out-degree <= 1024, <= 2048 and <= 4096, and global-table teams beyond.  About
+    # out-degree <= 1024, <= 2048 and <= 4096, and cluster teams beyond.  About
     # 3.6e10 hyper-triangles, so the oracle's values are stored.  Five runs must agree
     # with the oracle every time (a schedule-dependent miscount would show as a run
     # that differs).
@@ -112,7 +112,8 @@ def test_heavy_rows_and_every_team_shape_repeated(hglib):
     for run in range(5):
         counts, st = gpu_count(hglib, nv, e_ptr, e_idx)
         teams = st["close"]["bucket_teams"]
-        assert all(teams[k] > 0 for k in range(7)), teams
+        # every shape but 6 (|e_u| > 32 or handed over): the hub's hyperedges have <= 3 vertices
+        assert all(teams[k] > 0 for k in (0, 1, 2, 3, 4, 5, 7)), teams
         assert st["masks"] == stored_masks(gold), run
         assert counts.tolist() == gold["counts"], run
         for k in ("W", "W_c", "W_t", "connected", "open", "max_deg"):
@@ -250,7 +251,8 @@ def test_rejected_tuning_leaves_the_handle_usable(hglib):
     try:
         hglib.hg_build_wedges(g)
         before = hglib.hg_count_patterns(g)
-        for bad in ({"close_mode": 3}, {"close_mode": -1}, {"orient_exact": 2}):
+        for bad in ({"close_mode": 3}, {"close_mode": -1}, {"orient_exact": 2},
+                    {"gather_light_max": 16}, {"gather_light_max": 300}, {"warp_team_max": 100}):
             with pytest.raises(hglib.HgError) as ei:
                 hglib.hg_build_wedges(g, **bad)
             assert ei.value.name == "HG_ERR_INVALID_ARG"

@@ -98,9 +98,9 @@ def test_server_and_batch_structs_match_the_header(lib):
     import subprocess
     import tempfile
 
-    src = ('#include <stdio.h>\n#include "hg.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu\\n",'
+    src = ('#include <stdio.h>\n#include "hg.h"\nint main(void){printf("%zu %zu %zu %zu %zu %zu %zu\\n",'
            'sizeof(hg_result),sizeof(hg_query),sizeof(hg_server_options),sizeof(hg_server_stats),'
-           'sizeof(hg_close_stats),sizeof(hg_tuning));return 0;}\n')
+           'sizeof(hg_close_stats),sizeof(hg_tuning),sizeof(hg_autotune_result));return 0;}\n')
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "s.c")
         with open(c, "w") as f:
@@ -110,5 +110,5 @@ def test_server_and_batch_structs_match_the_header(lib):
         want = [int(x) for x in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     hg = lib.hg
     got = [ctypes.sizeof(t) for t in (hg._Result, hg._Query, hg._ServerOptions, hg._ServerStats,
-                                      hg._CloseStats, hg._Tuning)]
+                                      hg._CloseStats, hg._Tuning, hg._AutotuneResult)]
     assert got == want
