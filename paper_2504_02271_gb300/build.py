@@ -4,6 +4,11 @@ Each .cu file is compiled by its own nvcc process (in parallel) and the objects
 are linked into ``paper_2504_02271_gb300/libhg.so``.  No GPU is needed: nvcc
 cross-compiles.  Host code is compiled with ``-ffp-contract=off`` so the
 clustering coefficient's double arithmetic is not fused into FMAs.
+
+The environment variable ``HG_DEFINES`` (comma-separated ``NAME=VALUE`` items) adds
+preprocessor definitions, for the compile-time kernel shapes the sources leave open
+(``HG_CLOSE_WARP_UNROLL``, ``HG_WIDE_THREADS``, ``HG_WIDE_CLUSTER``); a change of them
+rebuilds everything.
 """
 from __future__ import annotations
 
@@ -44,6 +49,13 @@ def _stale(target: str, deps: list[str]) -> bool:
 
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    defines = [f"-D{d.strip()}" for d in os.environ.get("HG_DEFINES", "").split(",") if d.strip()]
+    stamp = os.path.join(BUILD, "defines.txt")
+    old = open(stamp).read() if os.path.exists(stamp) else ""
+    if old != " ".join(defines):
+        force = True
+        with open(stamp, "w") as f:
+            f.write(" ".join(defines))
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     objs, procs = [], []
@@ -51,7 +63,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
-            cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+            cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *defines, "-c", src, "-o", obj]
             if verbose:
                 print(" ".join(cmd), file=sys.stderr)
             procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE,
