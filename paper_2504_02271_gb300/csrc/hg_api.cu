@@ -659,6 +659,7 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
     HG_CUDA(cudaMemcpyAsync(g->ori.row_ptr, g->deg_ptr, sizeof(int64_t) * ((size_t)ne + 1),
                             cudaMemcpyDeviceToDevice, s));
   }
+  g->ori.slots = slots;
   if (g->packed) {
     g->ori.packed = alloc_t<uint32_t>(g, g->build_blocks, slots);
     if (!g->ori.packed) return HG_ERR_OOM;

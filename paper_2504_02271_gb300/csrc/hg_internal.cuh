@@ -37,6 +37,7 @@ struct Oriented {
   uint32_t* packed;   // [2W] packed entries, or nullptr
   int32_t* nbr;       // [2W] wide entries, or nullptr
   int32_t* omega;     // [2W]
+  int64_t slots;      // entries the arrays hold (0 = not recorded)
 };
 
 struct DevGraph {

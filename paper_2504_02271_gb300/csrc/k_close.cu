@@ -98,21 +98,27 @@ constexpr int kWarpQueue = 32 * kWarpUnroll + 32;
 constexpr int kCuckooTries = 16;
 constexpr int kStash = 8;
 
-template <int D_LOG2, bool PACKED>
+// OFF32: the oriented rows hold fewer than 2^32 entries, so row starts fit 32 bits.  In
+// the packed layout every |e| < 256, so sizes fit 8 bits.  The smaller per-warp state
+// lets more warps share an SM.
+template <int D_LOG2, bool PACKED, bool OFF32>
 struct alignas(16) WarpTables {
   static constexpr int D = 1 << D_LOG2;      // max out-degree of u
   static constexpr int T_LOG2 = D_LOG2 + 1;  // slots per cuckoo table
   static constexpr int T = 1 << T_LOG2;
+  static constexpr bool kPacked = PACKED;
   static_assert(D <= 256, "neighbour indices are packed in 8 bits");
   // (x << 8) | k; all ones = empty.  Packed rows have x < 2^24.
   using Item = typename std::conditional<PACKED, uint32_t, unsigned long long>::type;
+  using Off = typename std::conditional<OFF32, uint32_t, int64_t>::type;
+  using Sz = typename std::conditional<PACKED, uint8_t, uint16_t>::type;
   Item c1[T];
   Item c2[T];
   Item stash[kStash];
-  int64_t kbeg[D];
+  Off kbeg[D];
   int32_t kcnt[D];
   uint32_t kmask[D];                         // Omega_ux of the k-th out-neighbour x
-  uint16_t ksz[D];                           // |e_x|, then |e_x| - omega_ux once masks are built
+  Sz ksz[D];                                 // |e_x|, then |e_x| - omega_ux once masks are built
   uint32_t queue[kWarpQueue];                // hits: (k_v << 24) | (k_w << 8) | omega_vw
   int32_t qom[PACKED ? 1 : kWarpQueue];      // omega_vw when it may not fit 8 bits
   int32_t nstash;
@@ -217,12 +223,12 @@ __device__ __forceinline__ void warp_flush(RunHist& rh, uint32_t* hist,
 }
 
 // Classify queued hit number `at`: v and w are out-neighbours number kv and kw of u.
-template <int D_LOG2, bool PACKED>
-__device__ __forceinline__ void classify_queued(const WarpTables<D_LOG2, PACKED>& t, int at,
-                                                uint32_t fu, uint32_t* hist, RunHist& rh) {
+template <class TT>
+__device__ __forceinline__ void classify_queued(const TT& t, int at, uint32_t fu, uint32_t* hist,
+                                                RunHist& rh) {
   const uint32_t e = t.queue[at];
   const uint32_t kv = e >> 24, kw = (e >> 8) & 0xffu;
-  const int om = PACKED ? (int)(e & 0xffu) : t.qom[at];
+  const int om = TT::kPacked ? (int)(e & 0xffu) : t.qom[at];
   rh.add(region_bits(fu, t.kmask[kv], t.kmask[kw], t.ksz[kv], t.ksz[kw], om), hist);
 }
 
@@ -231,10 +237,11 @@ __device__ __forceinline__ void classify_queued(const WarpTables<D_LOG2, PACKED>
 // entry cj of out(v_ck)); kWarpUnroll loads in flight, then their probes; hits are
 // queued and classified 32 at a time.  STASH = false when the team's stash is empty
 // (the usual case): the probes then skip the stash scan altogether.
-template <int D_LOG2, bool PACKED, bool STASH>
-__device__ __forceinline__ void warp_walk(WarpTables<D_LOG2, PACKED>& t, const Oriented& o,
-                                          int32_t u, int32_t du, int32_t F, int nst,
-                                          uint32_t fu, uint32_t* hist, RunHist& rh, int lane) {
+template <class TT, bool STASH>
+__device__ __forceinline__ void warp_walk(TT& t, const Oriented& o, int32_t u, int32_t du,
+                                          int32_t F, int nst, uint32_t fu, uint32_t* hist,
+                                          RunHist& rh, int lane) {
+  constexpr bool PACKED = TT::kPacked;
   int qn = 0;   // queued hits (the same on every lane)
   int ck = 0, cj = lane;
   int ccnt = t.kcnt[0];   // du >= 2; past the last row ccnt stays INT32_MAX
@@ -274,7 +281,7 @@ __device__ __forceinline__ void warp_walk(WarpTables<D_LOG2, PACKED>& t, const O
 #pragma unroll
     for (int q = 0; q < kWarpUnroll; ++q) {
       const int32_t x = PACKED ? (int32_t)((uint32_t)ent_w[q] >> 8) : ent_w[q];
-      const int kw = warp_find<WarpTables<D_LOG2, PACKED>, STASH>(t, x, nst);
+      const int kw = warp_find<TT, STASH>(t, x, nst);
       const bool hit = kw >= 0;
       const unsigned bal = __ballot_sync(kFull, hit);
       if (hit) {
@@ -289,21 +296,21 @@ __device__ __forceinline__ void warp_walk(WarpTables<D_LOG2, PACKED>& t, const O
     // classify full rounds of 32 hits with every lane busy
     while (qn >= 32) {
       qn -= 32;
-      classify_queued<D_LOG2, PACKED>(t, qn + lane, fu, hist, rh);
+      classify_queued(t, qn + lane, fu, hist, rh);
       __syncwarp();
     }
   }
-  if (lane < qn) classify_queued<D_LOG2, PACKED>(t, lane, fu, hist, rh);
+  if (lane < qn) classify_queued(t, lane, fu, hist, rh);
   __syncwarp();
 }
 
-template <int D_LOG2, int WARPS, bool PACKED>
+template <int D_LOG2, int WARPS, bool PACKED, bool OFF32>
 __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
     k_close_warp(DevGraph g, Oriented o, const int32_t* __restrict__ list,
                  const int32_t* __restrict__ n_p, unsigned long long* __restrict__ hist_out,
                  unsigned long long* __restrict__ work, int32_t* __restrict__ counter,
                  int32_t* __restrict__ overflow, int32_t* __restrict__ n_overflow, int handover) {
-  using TT = WarpTables<D_LOG2, PACKED>;
+  using TT = WarpTables<D_LOG2, PACKED, OFF32>;
   using Item = typename TT::Item;
   constexpr int T = TT::T, T_LOG2 = TT::T_LOG2;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
@@ -371,8 +378,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
         if (at < kStash) t.stash[at] = it;
       }
       t.kmask[k] = 0;
-      t.ksz[k] = (uint16_t)xs;
-      t.kbeg[k] = xb;
+      t.ksz[k] = (typename TT::Sz)xs;
+      t.kbeg[k] = (typename TT::Off)xb;
       t.kcnt[k] = xc;
       my_cnt += xc;
     }
@@ -420,13 +427,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
     outs += (unsigned long long)du;
     __syncwarp();
     // |e_x| -> |e_x| - omega_ux, the part of e_x outside e_u
-    for (int k = lane; k < du; k += 32) t.ksz[k] = (uint16_t)(t.ksz[k] - __popc(t.kmask[k]));
+    for (int k = lane; k < du; k += 32)
+      t.ksz[k] = (typename TT::Sz)(t.ksz[k] - __popc(t.kmask[k]));
     const uint32_t fu = full_mask(szu);
     __syncwarp();
 
     // 3. closure over the flat range of all out(v), v in out(u)
-    if (nst == 0) warp_walk<D_LOG2, PACKED, false>(t, o, u, du, F, nst, fu, hist[w], rh, lane);
-    else warp_walk<D_LOG2, PACKED, true>(t, o, u, du, F, nst, fu, hist[w], rh, lane);
+    if (nst == 0) warp_walk<TT, false>(t, o, u, du, F, nst, fu, hist[w], rh, lane);
+    else warp_walk<TT, true>(t, o, u, du, F, nst, fu, hist[w], rh, lane);
   }
   warp_flush(rh, hist[w], hist_out + (size_t)cur * kBins, lane);
   if (lane == 0) {
@@ -1030,13 +1038,17 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank(), csize = (int)cluster.num_blocks();
-  constexpr int kCQ = 32 * kWideUnroll + 32;   // hit queue per warp
+  constexpr int kCU = 8;                       // entries of out(v) in flight per lane
+  constexpr int kCC = 32 * kCU + 32;           // candidate queue per warp
+  constexpr int kCH = 64;                      // hit queue per warp
   __shared__ uint32_t hist[kHistCopies][kBins];
   __shared__ int32_t s_r;
   __shared__ unsigned long long s_since;
   __shared__ uint32_t filt[(1 << kWideFilterLog2) / 32];
-  __shared__ int32_t qk[kClusterThreads / 32][kCQ];   // index of w in out(u)
-  __shared__ int32_t qo[kClusterThreads / 32][kCQ];   // omega_vw
+  __shared__ int32_t cx[kClusterThreads / 32][kCC];   // candidates: w (passed the filter)
+  __shared__ int32_t co[kClusterThreads / 32][kCC];   //             omega_vw
+  __shared__ int32_t qk[kClusterThreads / 32][kCH];   // hits: index of w in out(u)
+  __shared__ int32_t qo[kClusterThreads / 32][kCH];   //       omega_vw
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const int gt = rank * kClusterThreads + (int)threadIdx.x, GT = csize * kClusterThreads;
   const int gw = gt >> 5, GW = GT >> 5;
@@ -1158,8 +1170,10 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
       t.ksz[k] = __ldcg(t.ksz + k) - om;
     }
     cluster.sync();
-    // 4. closure: out-neighbour k (= v) per warp of the cluster; hits (w's index and
-    //    omega_vw) are queued and classified 32 at a time with every lane busy
+    // 4. closure: out-neighbour k (= v) per warp of the cluster.  Entries of out(v) that
+    //    pass this block's filter are queued as candidates; 32 candidates at a time are
+    //    looked up in the global tables with every lane busy; hits (w's index and
+    //    omega_vw) are queued and classified 32 at a time.
     for (int k = gw; k < du; k += GW) {
       const uint32_t* muv = t.mask + (size_t)k * words;
       const int rv = __ldcg(t.ksz + k);
@@ -1189,39 +1203,69 @@ __global__ void __launch_bounds__(kClusterThreads, 1)
                    ((uint32_t)(any_f != 0u) << 5) | ((uint32_t)(any_g != 0u) << 6),
                my_hist);
       };
-      int qn = 0;   // queued hits (the same on every lane)
-      for (int32_t j0 = 0; j0 < cnt; j0 += 32 * kWideUnroll) {
-        int32_t wv[kWideUnroll], om[kWideUnroll];
-#pragma unroll
-        for (int q = 0; q < kWideUnroll; ++q) {
-          const int32_t j = j0 + q * 32 + lane;
-          wv[q] = -1;
-          om[q] = 0;
-          if (j < cnt) get_entry<PACKED>(o, vb + j, wv[q], om[q]);
+      int cq = 0, qn = 0;   // queued candidates and hits (the same on every lane)
+      // look up candidates [cq - m, cq) (m <= 32, lane < m active); queue the hits and
+      // classify full rounds of 32
+      auto resolve = [&](int m) {
+        cq -= m;
+        int kw = -1, ow = 0;
+        if (lane < m) {
+          kw = wide_find_l2(t, cx[wl][cq + lane], dl, nst);
+          ow = co[wl][cq + lane];
         }
-#pragma unroll
-        for (int q = 0; q < kWideUnroll; ++q) {
-          const int32_t x = wv[q];
-          int kw = -1;
-          if (x >= 0) {
-            const uint32_t fb = filt_bit((uint32_t)x, fl);
-            if ((filt[fb >> 5] >> (fb & 31)) & 1u) kw = wide_find_l2(t, x, dl, nst);
-          }
-          const bool hit = kw >= 0;
-          const unsigned bal = __ballot_sync(kFull, hit);
-          if (hit) {
-            const int at = qn + __popc(bal & ((1u << lane) - 1u));
-            qk[wl][at] = kw;
-            qo[wl][at] = om[q];
-          }
-          qn += __popc(bal);
+        const bool hit = kw >= 0;
+        const unsigned bal = __ballot_sync(kFull, hit);
+        if (hit) {
+          const int at = qn + __popc(bal & ((1u << lane) - 1u));
+          qk[wl][at] = kw;
+          qo[wl][at] = ow;
         }
+        qn += __popc(bal);
         __syncwarp();
-        while (qn >= 32) {
+        if (qn >= 32) {
           qn -= 32;
           classify(qn + lane);
           __syncwarp();
         }
+      };
+      for (int32_t j0 = 0; j0 < cnt; j0 += 32 * kCU) {
+        int32_t wv[kCU], om[PACKED ? 1 : kCU];
+#pragma unroll
+        for (int q = 0; q < kCU; ++q) {
+          const int32_t j = j0 + q * 32 + lane;
+          if (PACKED) {
+            wv[q] = -1;   // raw entry (w << 8) | omega_vw; -1 = none
+            if (j < cnt) wv[q] = (int32_t)__ldg(o.packed + vb + j);
+          } else {
+            wv[q] = -1;
+            om[q] = 0;
+            if (j < cnt) get_entry<PACKED>(o, vb + j, wv[q], om[q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kCU; ++q) {
+          const int32_t x = PACKED ? (wv[q] == -1 ? -1 : (int32_t)((uint32_t)wv[q] >> 8)) : wv[q];
+          bool pass = false;
+          if (x >= 0) {
+            const uint32_t fb = filt_bit((uint32_t)x, fl);
+            pass = (filt[fb >> 5] >> (fb & 31)) & 1u;
+          }
+          const unsigned bal = __ballot_sync(kFull, pass);
+          if (pass) {
+            const int at = cq + __popc(bal & ((1u << lane) - 1u));
+            cx[wl][at] = x;
+            co[wl][at] = PACKED ? (int32_t)((uint32_t)wv[q] & 0xffu) : om[PACKED ? 0 : q];
+          }
+          cq += __popc(bal);
+        }
+        __syncwarp();
+        while (cq >= 32) resolve(32);
+      }
+      if (cq > 0) resolve(cq);
+      while (qn >= 32) {
+        qn -= 32;
+        classify(qn + lane);
+        __syncwarp();
       }
       if (lane < qn) classify(lane);
       __syncwarp();
@@ -1324,13 +1368,13 @@ __global__ void __launch_bounds__(kBucketThreads)
   }
 }
 
-template <int D_LOG2, int WARPS, bool PACKED>
+template <int D_LOG2, int WARPS, bool PACKED, bool OFF32>
 void launch_warp_t(const DevGraph& g, const Oriented& o, const int32_t* list, int32_t n,
                    const int32_t* n_p, unsigned long long* hist, unsigned long long* work,
                    int32_t* counter, int32_t* overflow, int32_t* n_overflow, int handover,
                    cudaStream_t s, int nsm) {
-  auto kern = k_close_warp<D_LOG2, WARPS, PACKED>;
-  const int smem = (int)(WARPS * sizeof(WarpTables<D_LOG2, PACKED>));
+  auto kern = k_close_warp<D_LOG2, WARPS, PACKED, OFF32>;
+  const int smem = (int)(WARPS * sizeof(WarpTables<D_LOG2, PACKED, OFF32>));
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
@@ -1347,12 +1391,19 @@ void launch_warp(const DevGraph& g, const Oriented& o, int packed, const int32_t
                  const int32_t* n_p, unsigned long long* hist, unsigned long long* work,
                  int32_t* counter, int32_t* overflow, int32_t* n_overflow, int handover,
                  cudaStream_t s, int nsm) {
-  if (packed)
-    launch_warp_t<D_LOG2, WARPS, true>(g, o, list, n, n_p, hist, work, counter, overflow,
-                                       n_overflow, handover, s, nsm);
+  const bool off32 = o.slots > 0 && o.slots < (int64_t(1) << 32);
+  if (packed && off32)
+    launch_warp_t<D_LOG2, WARPS, true, true>(g, o, list, n, n_p, hist, work, counter, overflow,
+                                             n_overflow, handover, s, nsm);
+  else if (packed)
+    launch_warp_t<D_LOG2, WARPS, true, false>(g, o, list, n, n_p, hist, work, counter, overflow,
+                                              n_overflow, handover, s, nsm);
+  else if (off32)
+    launch_warp_t<D_LOG2, WARPS, false, true>(g, o, list, n, n_p, hist, work, counter, overflow,
+                                              n_overflow, handover, s, nsm);
   else
-    launch_warp_t<D_LOG2, WARPS, false>(g, o, list, n, n_p, hist, work, counter, overflow,
-                                        n_overflow, handover, s, nsm);
+    launch_warp_t<D_LOG2, WARPS, false, false>(g, o, list, n, n_p, hist, work, counter,
+                                               overflow, n_overflow, handover, s, nsm);
 }
 
 template <int D_LOG2, int WARPS, bool PACKED>
