@@ -92,6 +92,16 @@ __device__ __forceinline__ uint32_t full_mask(int sz) { return sz >= 32 ? ~0u : 
 #define HG_CLOSE_WARP_UNROLL 8
 #endif
 constexpr int kWarpUnroll = HG_CLOSE_WARP_UNROLL;
+// warps of a block team (one block per SM: shared memory holds one team's tables).  On
+// the tag-shaped prefix of 500,000 hyperedges 16, 24 and 32 warps took 7.22, 5.73 and
+// 5.16 s per step (the teams were latency-bound at 16 warps per SM).  The unpacked
+// layout's hit queue is 4x wider, so it keeps to 24 warps (its out-degree-4096 tables
+// with 32 warps would leave under 2 KB of the 227 KB a block may use).
+#ifndef HG_BLOCK_WARPS
+#define HG_BLOCK_WARPS 32
+#endif
+constexpr int kBlockWarps = HG_BLOCK_WARPS;
+constexpr int kBlockWarpsUnpacked = HG_BLOCK_WARPS < 24 ? HG_BLOCK_WARPS : 24;
 constexpr int kBlockUnroll = 8;
 constexpr int kQueue = 32 * kBlockUnroll + 32;
 constexpr int kWarpQueue = 32 * kWarpUnroll + 32;
@@ -1423,17 +1433,17 @@ void launch_block_t(const DevGraph& g, const Oriented& o, const int32_t* list, i
                                          n_overflow, handover);
 }
 
-template <int D_LOG2, int WARPS>
+template <int D_LOG2>
 void launch_block(const DevGraph& g, const Oriented& o, int packed, const int32_t* list, int32_t n,
                   const int32_t* n_p, unsigned long long* hist, unsigned long long* work,
                   int32_t* counter, int32_t* overflow, int32_t* n_overflow, int handover,
                   cudaStream_t s, int nsm) {
   if (packed)
-    launch_block_t<D_LOG2, WARPS, true>(g, o, list, n, n_p, hist, work, counter, overflow,
-                                        n_overflow, handover, s, nsm);
+    launch_block_t<D_LOG2, kBlockWarps, true>(g, o, list, n, n_p, hist, work, counter, overflow,
+                                              n_overflow, handover, s, nsm);
   else
-    launch_block_t<D_LOG2, WARPS, false>(g, o, list, n, n_p, hist, work, counter, overflow,
-                                         n_overflow, handover, s, nsm);
+    launch_block_t<D_LOG2, kBlockWarpsUnpacked, false>(g, o, list, n, n_p, hist, work, counter,
+                                                       overflow, n_overflow, handover, s, nsm);
 }
 
 }  // namespace
@@ -1474,15 +1484,15 @@ void launch_close(int bucket, const DevGraph& g, const Oriented& o, int packed,
                         handover, s, nsm);
       break;
     case 3:
-      launch_block<10, 16>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow,
+      launch_block<10>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow,
                             handover, s, nsm);
       break;
     case 4:
-      launch_block<11, 16>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow,
+      launch_block<11>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow,
                             handover, s, nsm);
       break;
     case 5:
-      launch_block<12, 16>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow,
+      launch_block<12>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow,
                             handover, s, nsm);
       break;
     case kClusterBucket: {
