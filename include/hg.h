@@ -96,7 +96,9 @@ typedef struct hg_tuning {
                               counting pass); 0 = room for deg(i) per row (2W entries)
                               while that fits 8 GB.  Counts do not depend on it */
   int32_t gather_light_max; /* step one: rows gathering at most this many incidences take
-                               one warp, larger ones a block (0 = 256; 32..256) */
+                               one warp, larger ones a block (0 = the largest a warp's table
+                               holds: 512 in the packed layout, 256 otherwise; 32..512,
+                               capped at that largest) */
   int32_t warp_team_max;   /* step two: largest out-degree closed by a one-warp team; larger
                               ones take 16-warp block teams (0 = 256; 64, 128 or 256) */
   int32_t reserved[2];
@@ -129,7 +131,7 @@ hg_status hg_build_wedges(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out
  * Autotuner (no counterpart in the paper: the paper's parameters are its algorithms'
  * class split, not kernel shapes).  Picks, for this hypergraph, the hg_tuning fields
  * whose best value depends on the input - warp_team_max (64/128/256), gather_light_max
- * (64/128/256), orient_exact (0/1) and, for hyperedges of 32+ vertices, dense_min_size
+ * (128/256/default), orient_exact (0/1) and, for hyperedges of 32+ vertices, dense_min_size
  * (automatic / off / 64) - by coordinate descent: from the defaults, each field in turn
  * tries its other values with the rest at the best so far and keeps one that lowers the
  * device time of hg_build_wedges + hg_count_patterns (CUDA events on the handle's

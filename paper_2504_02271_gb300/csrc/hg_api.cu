@@ -556,7 +556,7 @@ bool tuning_ok(const hg_tuning* opt) {
   if (!opt) return true;
   const int32_t lm = opt->gather_light_max, wm = opt->warp_team_max;
   return opt->close_mode >= 0 && opt->close_mode <= 2 && opt->orient_exact >= 0 &&
-         opt->orient_exact <= 1 && (lm == 0 || (lm >= 32 && lm <= wedge_light_max_cand())) &&
+         opt->orient_exact <= 1 && (lm == 0 || (lm >= 32 && lm <= wedge_light_max_cand(1))) &&
          (wm == 0 || wm == 64 || wm == 128 || wm == 256);
 }
 
@@ -564,8 +564,11 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   if (!opt && g->has_tuned) opt = &g->tuned;
   g->close_mode = opt ? opt->close_mode : 0;
   g->warp_team_max = (opt && opt->warp_team_max) ? opt->warp_team_max : 256;
-  const int light_max = (opt && opt->gather_light_max) ? opt->gather_light_max
-                                                         : wedge_light_max_cand();
+  // (the packed flag is set below from the sizes; the same rule decides it here)
+  const int packed_layout = (g->ne < (int64_t(1) << 24) && g->max_size < 256) ? 1 : 0;
+  const int light_max = std::min((opt && opt->gather_light_max) ? opt->gather_light_max
+                                                                 : wedge_light_max_cand(1),
+                                 wedge_light_max_cand(packed_layout));
   cudaStream_t s = g->stream;
   release(g, g->count_blocks);
   release_sampling(g);
@@ -1151,7 +1154,7 @@ hg_status autotune_impl(hg_graph* g, hg_autotune_result* out) {
   };
   std::vector<Knob> knobs = {
       {&hg_tuning::warp_team_max, {128, 64}},
-      {&hg_tuning::gather_light_max, {128, 64}},
+      {&hg_tuning::gather_light_max, {256, 128}},
       {&hg_tuning::orient_exact, {1}},
   };
   if (g->max_size >= 32) knobs.push_back({&hg_tuning::dense_min_size, {-1, 64}});

@@ -121,7 +121,8 @@ struct WedgeBuckets {
 // rows gathering at most light_max incidences take one warp (light_max <= wedge_light_max_cand)
 void launch_bucket_rows(const int64_t* cand, int32_t ne, WedgeBuckets b, int light_max,
                         cudaStream_t s);
-int wedge_light_max_cand();
+// the largest gather count of a one-warp row in the packed (1) or unpacked (0) layout
+int wedge_light_max_cand(int packed);
 int wedge_medium_max_cand();
 // Per-row outputs of the count pass (each may be null): upc[i] = |{j > i}|,
 // wcr[i] = |{j > i : omega_ij = min(|e_i|, |e_j|)}| (inclusion-type hyperwedges).

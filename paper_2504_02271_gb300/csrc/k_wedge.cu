@@ -40,7 +40,17 @@ struct GatherSlot {
   }
 };
 
-constexpr int kLightCapLog2 = 9;     // 512 slots, rows with cand <= 256
+// One-warp rows: a shared table of up to 2^light_cap_log2 slots (32 KB per 8-warp
+// block in both layouts), for rows gathering at most half of that: 1,024 slots in the
+// packed layout (rows of up to 512 incidences), 512 64-bit slots otherwise.  On the
+// co-authorship workload 1,024 slots and 8 resident blocks per SM took the gather pass
+// from 1.44 to 1.24 ms (512 slots: 1.44 ms; 1,024 slots alone 1.33 ms; 8 blocks alone
+// 1.29 ms).
+#ifndef HG_LIGHT_CAP_LOG2
+#define HG_LIGHT_CAP_LOG2 10
+#endif
+template <bool PACKED>
+__host__ __device__ constexpr int light_cap_log2() { return PACKED ? HG_LIGHT_CAP_LOG2 : 9; }
 constexpr int kLightWarps = 8;
 constexpr int kMediumCapLog2 = 13;   // 8192 slots (32 KiB packed, 64 KiB wide), rows with cand <= 4096
 constexpr int kBlockThreads = 256;
@@ -101,14 +111,18 @@ __device__ __forceinline__ void put_entry(const Oriented& o, int64_t at, uint32_
 }
 
 // One warp per row; the table lives in shared memory.
+#ifndef HG_LIGHT_MIN_BLOCKS
+#define HG_LIGHT_MIN_BLOCKS 8
+#endif
 template <bool PACKED>
-__global__ void __launch_bounds__(kLightWarps * 32)
+__global__ void __launch_bounds__(kLightWarps * 32, HG_LIGHT_MIN_BLOCKS)
     k_wedge_light(DevGraph g, const int32_t* __restrict__ rows, const int32_t* __restrict__ nrows_p,
                   const int64_t* __restrict__ cand, int32_t* __restrict__ deg,
                   unsigned long long* __restrict__ wc, Oriented o, int* __restrict__ err,
                   int32_t* __restrict__ counter, DenseInfo dn, RowCounts rc) {
   using S = GatherSlot<PACKED>;
   using W = typename S::T;
+  constexpr int kLightCapLog2 = light_cap_log2<PACKED>();
   constexpr int CAP = 1 << kLightCapLog2;
   __shared__ W tab[kLightWarps][CAP];
   __shared__ unsigned long long blk_wc;
@@ -478,7 +492,9 @@ void launch_filter_t(bool count_only, const int64_t* src_ptr, const int32_t* len
 
 }  // namespace
 
-int wedge_light_max_cand() { return (1 << kLightCapLog2) / 2; }
+int wedge_light_max_cand(int packed) {
+  return (1 << (packed ? light_cap_log2<true>() : light_cap_log2<false>())) / 2;
+}
 int wedge_medium_max_cand() { return (1 << kMediumCapLog2) / 2; }
 
 size_t wedge_heavy_scratch_bytes(int64_t heavy_max_cand, int nsm) {

@@ -252,7 +252,7 @@ def test_rejected_tuning_leaves_the_handle_usable(hglib):
         hglib.hg_build_wedges(g)
         before = hglib.hg_count_patterns(g)
         for bad in ({"close_mode": 3}, {"close_mode": -1}, {"orient_exact": 2},
-                    {"gather_light_max": 16}, {"gather_light_max": 300}, {"warp_team_max": 100}):
+                    {"gather_light_max": 16}, {"gather_light_max": 600}, {"warp_team_max": 100}):
             with pytest.raises(hglib.HgError) as ei:
                 hglib.hg_build_wedges(g, **bad)
             assert ei.value.name == "HG_ERR_INVALID_ARG"
