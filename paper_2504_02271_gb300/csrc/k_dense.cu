@@ -10,17 +10,20 @@
 // hyperedges of at most 65,535 vertices, so every omega fits the uint16 output and
 // is far below 2^24, where FP32 stops representing integers exactly: omega is exact.
 //
-// Kernel shape: one CTA per 128 x 256 output tile; K runs over the vertices in
-// steps of 128 bytes.  CTAs take tiles in a grouped raster: consecutive CTA ids walk
-// down a group of kGroupM tile rows before moving one tile column right, so the CTAs
-// resident at one time share a few A panels (128 rows) and B panels (256 rows) in L2
-// instead of each tile row streaming every B panel again.  Warp 0 issues TMA loads (128-byte swizzle) of the A tile
-// (128 rows) and the B tile (256 rows, two boxes) into a 4-stage ring; warp 1
-// allocates 256 TMEM columns and one thread issues tcgen05.mma (M=128, N=256,
-// K=32 per instruction, 4 per stage) and commits each stage back to its ring
-// slot; warps 2-5 read the accumulator rows they own with tcgen05.ld and write
-// omega as uint16.  Every mbarrier wait is bounded: on time-out the kernel raises
+// Kernel shape: persistent, one CTA per SM, each taking 128 x 256 output tiles in a
+// grouped raster (consecutive tiles walk down a group of kGroupM tile rows before
+// moving one tile column right, so the CTAs working at one time share a few A panels
+// (128 rows) and B panels (256 rows) in L2); K runs over the vertices in steps of 128
+// bytes.  Warp 0 issues TMA loads (128-byte swizzle) of the A tile (128 rows) and the B
+// tile (256 rows, two boxes) into a 4-stage ring that runs on from tile to tile; warp
+// 1 allocates 512 TMEM columns (two 256-column accumulators) and one thread issues
+// tcgen05.mma (M=128, N=256, K=32 per instruction, 4 per stage), committing each stage
+// back to its ring slot and each finished accumulator to the epilogue; warps 2-5 read
+// the accumulator rows they own with tcgen05.ld and write omega as uint16 while the next
+// tile's MMAs fill the other accumulator.  Every mbarrier wait is bounded: on time-out the kernel raises
 // an error word, stops issuing, waits for its own copies and frees its TMEM.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -34,7 +37,7 @@ constexpr int kBM = 128, kBN = 256, kBK = 128;   // tile rows (A), rows (B), byt
 constexpr int kStages = 4;
 constexpr int kThreads = 192;
 constexpr uint32_t kStageBytes = (kBM + kBN) * kBK;
-constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kTmemCols = 512;   // two 256-column accumulators
 constexpr uint32_t kSpinLimit = 1u << 22;          // bounded waits (~ 1 s with backoff)
 constexpr int kGroupM = 16;                        // tile rows per raster group
 
@@ -93,6 +96,32 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
 // Instruction descriptor, kind::f8f6f4: A = B = e4m3, D = f32, both K-major, M=128, N=256.
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// tile t of the grouped raster -> (tile_m, tile_n), kGroupM tile rows per group
+__device__ __forceinline__ void tile_of(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
+  const int per_group = kGroupM * tiles_n;
+  const int first_m = (t / per_group) * kGroupM;
+  const int gm = min(tiles_m - first_m, kGroupM);
+  const int in_group = t % per_group;
+  tm = first_m + in_group % gm;
+  tn = in_group / gm;
+}
+
+// Persistent: each CTA takes tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... in the
+// grouped raster.  The TMA ring runs on across tiles (k-block g of the CTA uses stage
+// g % kStages); the accumulator alternates between two 256-column halves of TMEM, so
+// the epilogue of one tile overlaps the MMAs of the next (tfull[b]: MMAs of buffer b
+// done; tempty[b]: its 128 epilogue threads have read it).
 __global__ void __launch_bounds__(kThreads, 1)
     k_dense_omega(const __grid_constant__ CUtensorMap amap, int32_t rows, int32_t kblocks,
                   int32_t tiles_m, int32_t tiles_n, uint16_t* __restrict__ omega, int64_t ld,
@@ -102,23 +131,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char* base = (unsigned char*)(((uintptr_t)dyn_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = base;                                  // kStages x 16 KiB
   unsigned char* sB = base + kStages * kBM * kBK;            // kStages x 32 KiB
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accum;
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull[2], tempty[2], tdone;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // grouped raster: CTA id -> (tile_m, tile_n), kGroupM tile rows per group
-  const int per_group = kGroupM * tiles_n;
-  const int first_m = (int)(blockIdx.x / per_group) * kGroupM;
-  const int gm = min(tiles_m - first_m, kGroupM);
-  const int in_group = (int)(blockIdx.x % per_group);
-  const int tile_m = first_m + in_group % gm, tile_n = in_group / gm;
+  const int ntiles = tiles_m * tiles_n;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 128);
+    }
+    mbar_init(&tdone, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -136,69 +164,96 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {   // producer
-      int issued = 0;
-      for (int kb = 0; kb < kblocks; ++kb) {
-        const int s = kb % kStages;
-        const uint32_t round = (uint32_t)(kb / kStages);
-        if (kb >= kStages && !mbar_wait(&empty[s], (round & 1u) ^ 1u)) {
-          atomicExch(&abort_flag, 1);
-          break;
+      uint32_t g = 0;
+      for (int t = blockIdx.x; t < ntiles && !*(volatile int*)&abort_flag; t += gridDim.x) {
+        int tm, tn;
+        tile_of(t, tiles_m, tiles_n, tm, tn);
+        for (int kb = 0; kb < kblocks; ++kb, ++g) {
+          const int s = (int)(g % kStages);
+          const uint32_t round = g / kStages;
+          if (g >= (uint32_t)kStages && !mbar_wait(&empty[s], (round & 1u) ^ 1u)) {
+            atomicExch(&abort_flag, 1);
+            break;
+          }
+          if (*(volatile int*)&abort_flag) break;
+          mbar_expect_tx(&full[s], kStageBytes);
+          tma_load_2d(sA + s * kBM * kBK, &amap, kb * kBK, tm * kBM, &full[s]);
+          tma_load_2d(sB + s * kBN * kBK, &amap, kb * kBK, tn * kBN, &full[s]);
+          tma_load_2d(sB + s * kBN * kBK + 128 * kBK, &amap, kb * kBK, tn * kBN + 128, &full[s]);
         }
-        if (*(volatile int*)&abort_flag) break;
-        mbar_expect_tx(&full[s], kStageBytes);
-        tma_load_2d(sA + s * kBM * kBK, &amap, kb * kBK, tile_m * kBM, &full[s]);
-        tma_load_2d(sB + s * kBN * kBK, &amap, kb * kBK, tile_n * kBN, &full[s]);
-        tma_load_2d(sB + s * kBN * kBK + 128 * kBK, &amap, kb * kBK, tile_n * kBN + 128, &full[s]);
-        issued = kb + 1;
       }
       if (*(volatile int*)&abort_flag) {
-        // wait (bounded) for the copies this thread started and nobody consumed
-        for (int kb = issued - kStages < 0 ? 0 : issued - kStages; kb < issued; ++kb)
-          (void)mbar_wait(&full[kb % kStages], (uint32_t)(kb / kStages) & 1u);
+        // wait (bounded) for the copies this thread started that may still be landing
+        const uint32_t first = g > (uint32_t)kStages ? g - kStages : 0u;
+        for (uint32_t k = first; k < g; ++k)
+          (void)mbar_wait(&full[k % kStages], (k / kStages) & 1u);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {   // MMA issuer
-      for (int kb = 0; kb < kblocks; ++kb) {
-        const int s = kb % kStages;
-        if (!mbar_wait(&full[s], (uint32_t)(kb / kStages) & 1u)) {
+      uint32_t g = 0;
+      int li = 0;   // tiles of this CTA so far
+      bool issued_any = false;
+      for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++li) {
+        if (*(volatile int*)&abort_flag) break;
+        const int b = li & 1, n = li >> 1;   // accumulator half, its earlier uses
+        if (n >= 1 && !mbar_wait(&tempty[b], (uint32_t)(n - 1) & 1u)) {
           atomicExch(&abort_flag, 1);
           break;
         }
-        if (*(volatile int*)&abort_flag) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(sA + s * kBM * kBK), b0 = smem_u32(sB + s * kBN * kBK);
+        const uint32_t acc_d = tmem_d + (uint32_t)(b * kBN);
+        bool ok = true;
+        for (int kb = 0; kb < kblocks; ++kb, ++g) {
+          const int s = (int)(g % kStages);
+          if (!mbar_wait(&full[s], (g / kStages) & 1u)) {
+            atomicExch(&abort_flag, 1);
+            ok = false;
+            break;
+          }
+          if (*(volatile int*)&abort_flag) {
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_u32(sA + s * kBM * kBK), b0 = smem_u32(sB + s * kBN * kBK);
 #pragma unroll
-        for (int kk = 0; kk < kBK / 32; ++kk) {
-          const uint64_t ad = umma_desc(a0 + kk * 32), bd = umma_desc(b0 + kk * 32);
-          const uint32_t acc = (kb | kk) ? 1u : 0u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-              "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
-              : "memory");
+          for (int kk = 0; kk < kBK / 32; ++kk) {
+            const uint64_t ad = umma_desc(a0 + kk * 32), bd = umma_desc(b0 + kk * 32);
+            const uint32_t acc = (kb | kk) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_d),
+                "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+                : "memory");
+          }
+          issued_any = true;
+          umma_commit(&empty[s]);
         }
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&empty[s]))
-            : "memory");
+        if (!ok) break;
+        umma_commit(&tfull[b]);
       }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(&accum))
-          : "memory");
+      if (issued_any) {   // every MMA of this CTA has completed before TMEM is released
+        umma_commit(&tdone);
+        (void)mbar_wait(&tdone, 0);
+      }
     }
   } else {   // warps 2-5: epilogue, warp w reads TMEM lanes 32 * (w % 4) ..
     const int q = warp & 3;
-    const bool ok = mbar_wait(&accum, 0);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!ok) atomicExch(&abort_flag, 1);
-    const int row = tile_m * kBM + q * 32 + lane;
-    if (ok && !*(volatile int*)&abort_flag) {
+    int li = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++li) {
+      const int b = li & 1, n = li >> 1;
+      const bool ok = mbar_wait(&tfull[b], (uint32_t)n & 1u);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (!ok) atomicExch(&abort_flag, 1);
+      if (!ok || *(volatile int*)&abort_flag) break;
+      int tm, tn;
+      tile_of(t, tiles_m, tiles_n, tm, tn);
+      const int row = tm * kBM + q * 32 + lane;
 #pragma unroll 1
       for (int c0 = 0; c0 < kBN; c0 += 32) {
         uint32_t r[32];
-        const uint32_t taddr = tmem_d + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+        const uint32_t taddr = tmem_d + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kBN + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
             "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -219,12 +274,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t hi = (uint32_t)__float2uint_rn(__uint_as_float(r[2 * j + 1]));
             packed[j] = lo | (hi << 16);
           }
-          uint4* dst = reinterpret_cast<uint4*>(omega + (int64_t)row * ld + tile_n * kBN + c0);
+          uint4* dst = reinterpret_cast<uint4*>(omega + (int64_t)row * ld + tn * kBN + c0);
 #pragma unroll
           for (int j = 0; j < 4; ++j)
             dst[j] = make_uint4(packed[4 * j], packed[4 * j + 1], packed[4 * j + 2], packed[4 * j + 3]);
         }
       }
+      // this half of TMEM is read: the MMAs of the tile after next may overwrite it
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&tempty[b]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -334,8 +392,13 @@ cudaError_t launch_dense_omega(const uint8_t* a, int64_t rows, int64_t rows_pad,
                                        smem);
   if (e != cudaSuccess) return e;
   const int64_t tiles_m = rows_pad / kBM, tiles_n = rows_pad / kBN;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+    return cudaErrorInvalidValue;
+  const int64_t ctas = std::min<int64_t>(tiles_m * tiles_n, nsm);   // one per SM, persistent
   note_launch();
-  k_dense_omega<<<(unsigned)(tiles_m * tiles_n), kThreads, smem, s>>>(
+  k_dense_omega<<<(unsigned)ctas, kThreads, smem, s>>>(
       map, (int32_t)rows, (int32_t)(k_pad / kBK), (int32_t)tiles_m, (int32_t)tiles_n, omega,
       rows_pad, err);
   return cudaGetLastError();
