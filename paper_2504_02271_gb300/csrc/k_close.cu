@@ -147,6 +147,8 @@ __device__ __forceinline__ uint32_t cuckoo_h2(uint32_t key, int t_log2) {
 // at least 256 otherwise.  The empty item (all ones) would answer 255 to a key whose
 // low 24 bits are all ones; no hyperedge id of a packed layout (< 2^24 - 1) has
 // them, and lanes without an entry look up u itself, which is never in out(u).
+// A key sits in at most one place, so the smaller of the xor-ed items is k on a hit and
+// at least 256 otherwise: one min and one compare decide it.
 template <class TT, bool STASH = true>
 __device__ __forceinline__ int warp_find(const TT& t, int32_t x, int nst) {
   using Item = typename TT::Item;
@@ -154,15 +156,14 @@ __device__ __forceinline__ int warp_find(const TT& t, int32_t x, int nst) {
   const Item k8 = (Item)key << 8;
   const Item a = t.c1[cuckoo_h1(key, TT::T_LOG2)] ^ k8;
   const Item b = t.c2[cuckoo_h2(key, TT::T_LOG2)] ^ k8;
-  int k = a < 256 ? (int)a : -1;
-  k = b < 256 ? (int)b : k;
+  Item m = a < b ? a : b;
   if (STASH) {
     for (int i = 0; i < nst; ++i) {
       const Item c = t.stash[i] ^ k8;
-      k = c < 256 ? (int)c : k;
+      m = c < m ? c : m;
     }
   }
-  return k;
+  return m < 256 ? (int)m : -1;
 }
 
 // Start of out(x)'s entries in the oriented rows: a pointer per layout, so that a probe
@@ -314,8 +315,14 @@ __device__ __forceinline__ void warp_walk(TT& t, const Oriented& o, int32_t u, i
   __syncwarp();
 }
 
+// Threads of warp teams resident per SM that the register allocation aims at: 1,280 for
+// the out-degree-128 teams (six 6-warp blocks at 56 registers: 7.58 -> 7.33 ms on the
+// co-authorship workload), 1,024 for the others (at 1,280 the out-degree-256 teams
+// spill and slow down, 1.46 -> 1.55 ms).
+__host__ __device__ constexpr int warp_threads_per_sm(int d_log2) { return d_log2 == 7 ? 1280 : 1024; }
+
 template <int D_LOG2, int WARPS, bool PACKED, bool OFF32>
-__global__ void __launch_bounds__(WARPS * 32, 1024 / (WARPS * 32))
+__global__ void __launch_bounds__(WARPS * 32, warp_threads_per_sm(D_LOG2) / (WARPS * 32))
     k_close_warp(DevGraph g, Oriented o, const int32_t* __restrict__ list,
                  const int32_t* __restrict__ n_p, unsigned long long* __restrict__ hist_out,
                  unsigned long long* __restrict__ work, int32_t* __restrict__ counter,
@@ -500,11 +507,15 @@ template <int D_LOG2, int WARPS, bool PACKED, bool STASH = true>
 __device__ __forceinline__ int block_find(const BlockTables<D_LOG2, WARPS, PACKED>& t, int32_t x,
                                           int nst) {
   constexpr int SH = 32 - (D_LOG2 + 1);   // remainder bits
-  constexpr uint32_t RM = (1u << SH) - 1u, KM = (1u << D_LOG2) - 1u;
+  constexpr uint32_t RM = (1u << SH) - 1u;
   const uint32_t p1 = (uint32_t)x * kCuckooA1, p2 = (uint32_t)x * kCuckooA2;
-  const uint32_t a = t.c1[p1 >> SH], b = t.c2[p2 >> SH];
-  int k = (a >> D_LOG2) == (p1 & RM) ? (int)(a & KM) : -1;
-  k = (b >> D_LOG2) == (p2 & RM) ? (int)(b & KM) : k;
+  // an item (remainder << D_LOG2) | k xor-ed with the key's remainder so shifted is k
+  // (< D) when the remainders agree, and at least D otherwise (empty slots have the top
+  // bit, which no remainder has); a key sits in at most one table
+  const uint32_t a = t.c1[p1 >> SH] ^ ((p1 & RM) << D_LOG2);
+  const uint32_t b = t.c2[p2 >> SH] ^ ((p2 & RM) << D_LOG2);
+  const uint32_t m = a < b ? a : b;
+  int k = m < (uint32_t)(1u << D_LOG2) ? (int)m : -1;
   if (STASH)
     for (int i = 0; i < nst; ++i) k = t.skey[i] == x ? t.sidx[i] : k;
   return k;
