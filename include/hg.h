@@ -100,7 +100,7 @@ typedef struct hg_tuning {
                                holds: 512 in the packed layout, 256 otherwise; 32..512,
                                capped at that largest) */
   int32_t warp_team_max;   /* step two: largest out-degree closed by a one-warp team; larger
-                              ones take 16-warp block teams (0 = 256; 64, 128 or 256) */
+                              ones take block teams (0 = 256; 64, 128 or 256) */
   int32_t reserved[2];
 } hg_tuning;
 
@@ -175,6 +175,31 @@ hg_status hg_count_patterns(hg_graph* g, uint64_t counts[21]);
  * Requires hg_count_patterns (HG_ERR_STATE before).  No device work.
  */
 hg_status hg_mask_histogram(hg_graph* g, uint64_t masks[128]);
+
+/*
+ * Step two restricted to owners.  The closure orders the hyperedges by (|N(e)|, id),
+ * |N(e)| the number of other hyperedges sharing a vertex with e (Sec. 2), and finds each
+ * hyper-triangle (Def. 2.4) from its lowest-ranked member, its owner.  This call runs
+ * only the teams of the listed owners, with the same kernels and team shapes as
+ * hg_count_patterns, so any part of a large hypergraph can be checked against a
+ * reference that counts the same owners one by one.
+ *   owners[num_owners]  in, host: hyperedge ids in [0, |E|); repeats count once.
+ *   counts[21]          out: as hg_count_patterns, over the owned hyper-triangles.
+ *   masks[128]          out (may be NULL): as hg_mask_histogram, over the same.
+ * HG_ERR_INVALID_ARG for an id out of range; HG_ERR_UNSUPPORTED for a wave handle of a
+ * batch.  Requires hg_build_wedges; afterwards the handle is built but not counted
+ * (hg_mask_histogram and hg_clustering_coeff want a new hg_count_patterns).  Synchronises.
+ */
+hg_status hg_count_owned(hg_graph* g, const int32_t* owners, int32_t num_owners,
+                         uint64_t counts[21], uint64_t masks[128]);
+
+/*
+ * Out-degree of every hyperedge in the orientation step two uses: the number of its
+ * neighbours ranked above it in (|N(e)|, id) (see hg_count_owned).
+ *   out_degree[|E|]  out, host.
+ * Requires hg_build_wedges.  Synchronises.
+ */
+hg_status hg_out_degrees(hg_graph* g, int32_t* out_degree);
 
 /*
  * Hyperwedge-sampling estimate of the per-pattern counts (Sec. 4.1, Algorithm 6,
@@ -262,7 +287,8 @@ hg_status hg_clustering_coeff(hg_graph* g, const double eps[20], double* cc,
                               uint64_t* open_triples, uint64_t* connected_triples);
 
 /*
- * Work done by the last hg_count_patterns of a handle (counted by the kernels):
+ * Work done by the last hg_count_patterns or hg_count_owned of a handle (counted by the
+ * kernels):
  *   probes       sum over oriented wedges u->v of |out(v)|: out-list entries
  *                streamed and looked up in u's table (every hyper-triangle is
  *                one successful probe);

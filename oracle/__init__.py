@@ -79,6 +79,10 @@ def _load():
         lib.oracle_degrees.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p]
         lib.oracle_degrees.restype = ctypes.c_int
+        lib.oracle_count_owned.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                           ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_count_owned.restype = ctypes.c_int
         lib.oracle_canonical_mask.argtypes = [ctypes.c_int]
         lib.oracle_canonical_mask.restype = ctypes.c_int
         for f in (lib.oracle_classify, lib.oracle_region_mask):
@@ -173,6 +177,26 @@ def degrees(e_ptr, e_idx, num_vertices: int) -> np.ndarray:
     if rc != 0:
         raise ValueError(f"oracle: {_ERR.get(rc, rc)}")
     return out[:len(e_ptr) - 1]
+
+
+def count_owned(e_ptr, e_idx, num_vertices: int, owners, threads: int = 0):
+    """Hyper-triangles by owner, the member ranked lowest in the order (|N(e)|, id).
+
+    Returns (masks, above): masks uint64[n][128], masks[k][m] = hyper-triangles owned by
+    owners[k] whose canonical region mask is m; above int32[n], the neighbours of
+    owners[k] ranked above it."""
+    e_ptr = np.ascontiguousarray(e_ptr, dtype=np.int64)
+    e_idx = np.ascontiguousarray(e_idx, dtype=np.int32)
+    own = np.ascontiguousarray(np.asarray(owners, dtype=np.int32))
+    n = len(own)
+    masks = np.zeros((max(n, 1), 128), dtype=np.uint64)
+    above = np.zeros(max(n, 1), dtype=np.int32)
+    rc = _load().oracle_count_owned(int(num_vertices), len(e_ptr) - 1, e_ptr.ctypes.data,
+                                    e_idx.ctypes.data, own.ctypes.data, n, int(threads),
+                                    above.ctypes.data, masks.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle: {_ERR.get(rc, rc)}")
+    return masks[:n], above[:n]
 
 
 def _arr(x):

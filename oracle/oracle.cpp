@@ -10,7 +10,9 @@
 //   * per-pattern hyper-triangle counts H[1..20] and the total T (Def. 2.4);
 //   * hyperwedge statistics: W = |wedges|, W_t (intersection type), W_c
 //     (inclusion type) (Def. 2.2, Def. 2.3);
-//   * connected triples sum_i C(|N(e_i)|, 2) and open hyper-triangles (Def. 5.1).
+//   * connected triples sum_i C(|N(e_i)|, 2) and open hyper-triangles (Def. 5.1);
+//   * the same histogram split by owner, the member of each hyper-triangle ranked
+//     lowest in the order (|N(e)|, id) (oracle_count_owned).
 //
 // Two enumerations:
 //   * mode 0 follows Exact-bs (Algorithm 1): build the projection graph
@@ -400,6 +402,94 @@ int oracle_count(int32_t nv, int32_t ne, const int64_t* e_ptr, const int32_t* e_
   // every closed triple is counted three times in sum C(deg, 2), every open one once
   stats[ST_OPEN] = whole ? connected - 3 * counts[0] : 0;
   if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return bad ? -8 : 0;
+}
+
+// Hyper-triangles by owner.  Order the hyperedges by (|N(e)|, id), |N(e)| the number of
+// other hyperedges sharing a vertex with e (Sec. 2).  Every hyper-triangle {e_u, e_v, e_w}
+// (Def. 2.4) has exactly one member ranked lowest in that order: its owner.  For each
+// requested owner u = owners[k]:
+//   above[k]            the neighbours of e_u ranked above it;
+//   masks[128 k + m]    the hyper-triangles owned by u whose region mask, in canonical
+//                       form (oracle_canonical_mask), is m.
+// The degrees of e_u's neighbours are counted with a mark array: for each of them, every
+// id met in the E_y lists of its vertices is counted the first time it is met.
+// Returns 0, a negative input error as oracle_count, -6 for an owner out of range, or
+// -8 (unclassifiable triple).
+int oracle_count_owned(int32_t nv, int32_t ne, const int64_t* e_ptr, const int32_t* e_idx,
+                       const int32_t* owners, int32_t n, int nthreads, int32_t* above,
+                       uint64_t* masks) {
+  if (nv < 0 || ne < 0 || n < 0 || (n > 0 && (!owners || !above || !masks))) return -6;
+  if (!oracle_pattern_table_ok()) return -7;
+  for (int32_t k = 0; k < n; ++k)
+    if (owners[k] < 0 || owners[k] >= ne) return -6;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+  Graph g;
+  int rc = load(g, nv, ne, e_ptr, e_idx);
+  if (rc) return rc;
+  const auto& pm = pattern_map();
+  const auto& cm = canon_map();
+  int nth = 1;
+#ifdef _OPENMP
+  nth = omp_get_max_threads();
+#endif
+  int bad = 0;
+  for (int32_t k = 0; k < n; ++k) {
+    const int32_t u = owners[k];
+    const std::vector<int32_t> Nu = neighbours(g, u);
+    const int64_t du = (int64_t)Nu.size();
+    // |N(e_x)| of every neighbour x
+    std::vector<int64_t> dx(Nu.size(), 0);
+#pragma omp parallel
+    {
+      std::vector<int32_t> mark((size_t)ne, -1);
+#pragma omp for schedule(dynamic, 16)
+      for (size_t a = 0; a < Nu.size(); ++a) {
+        const int32_t x = Nu[a];
+        int64_t d = 0;
+        for (int32_t v : g.e[x])
+          for (int32_t j : g.Ev[v])
+            if (j != x && mark[j] != x) {
+              mark[j] = x;
+              ++d;
+            }
+        dx[a] = d;
+      }
+    }
+    // the neighbours ranked above u, ascending id
+    std::vector<int32_t> R;
+    for (size_t a = 0; a < Nu.size(); ++a)
+      if (dx[a] > du || (dx[a] == du && Nu[a] > u)) R.push_back(Nu[a]);
+    above[k] = (int32_t)R.size();
+    // every pair {v, w} of them whose hyperedges intersect closes a hyper-triangle
+    std::vector<uint64_t> Ms((size_t)nth * 128, 0);
+#pragma omp parallel
+    {
+      int tid = 0;
+#ifdef _OPENMP
+      tid = omp_get_thread_num();
+#endif
+      uint64_t* M = &Ms[(size_t)tid * 128];
+#pragma omp for schedule(dynamic, 8) reduction(| : bad)
+      for (size_t a = 0; a < R.size(); ++a)
+        for (size_t b = a + 1; b < R.size(); ++b) {
+          if (!intersects(g.e[R[a]], g.e[R[b]])) continue;
+          const int m = region_mask(g.e[u], g.e[R[a]], g.e[R[b]]);
+          if (pm.of_mask[m] == 0) {
+            bad = 1;
+            continue;
+          }
+          ++M[cm.of_mask[m]];
+        }
+    }
+    uint64_t* out = masks + 128 * (size_t)k;
+    for (int m = 0; m < 128; ++m) {
+      out[m] = 0;
+      for (int t = 0; t < nth; ++t) out[m] += Ms[(size_t)t * 128 + m];
+    }
+  }
   return bad ? -8 : 0;
 }
 

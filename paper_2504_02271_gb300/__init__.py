@@ -8,7 +8,7 @@ from . import hg  # noqa: F401  (fails loudly when libhg.so is missing)
 from .hg import (  # noqa: F401
     Graph, HgError, hg_build_wedges, hg_enumerate_pattern, hg_close_stats_get, hg_clustering_coeff, hg_count_patterns, hg_free,
     hg_kernel_launches, hg_kernel_times, hg_load_csr, hg_pattern_table, hg_canonical_masks,
-    hg_mask_histogram, hg_batch_mask_histogram, hg_autotune, hg_batch_autotune, hg_sample_estimate, hg_sample_estimate_adv, hg_sample_work_get, hg_set_allocator,
+    hg_mask_histogram, hg_count_owned, hg_out_degrees, hg_batch_mask_histogram, hg_autotune, hg_batch_autotune, hg_sample_estimate, hg_sample_estimate_adv, hg_sample_work_get, hg_set_allocator,
     hg_set_timing, hg_status_str, hg_wait_flag,
     use_default_allocator, use_torch_allocator,
     Batch, concat_members, hg_batch_build_wedges, hg_batch_clustering_coeff, hg_batch_count_patterns,

@@ -120,6 +120,7 @@ struct hg_graph {
   uint64_t counts[21] = {0};
   uint64_t masks[128] = {0};   // canonical region-mask histogram of the last count
   hg_close_stats cstats{};
+  bool have_cstats = false;    // cstats describe the last hg_count_patterns or hg_count_owned
   // a wave of a batch: nm members, member m owning hyperedges [m_eoff[m], m_eoff[m+1])
   // and union vertices [m_voff[m], m_voff[m+1])
   int32_t nm = 0;
@@ -574,7 +575,7 @@ hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
   release_sampling(g);
   release(g, g->build_blocks);
   g->built = false;
-  g->counted = false;
+  g->counted = g->have_cstats = false;
   const int64_t ne = g->ne;
   const size_t ne1 = (size_t)std::max<int64_t>(ne, 1);
   g->packed = (ne < (int64_t(1) << 24) && g->max_size < 256) ? 1 : 0;
@@ -988,14 +989,22 @@ hg_status sample_impl(hg_graph* g, uint64_t seed, uint64_t first, uint64_t num, 
   return HG_OK;
 }
 
-hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
+// h_sel: NULL (every hyper-triangle), or one host byte per hyperedge: then only the
+// hyper-triangles owned by the hyperedges u with h_sel[u] != 0 (their teams alone run).
+hg_status count_impl(hg_graph* g, uint64_t counts[21], const uint8_t* h_sel = nullptr) {
   cudaStream_t s = g->stream;
   release(g, g->count_blocks);
-  g->counted = false;
+  g->counted = g->have_cstats = false;
   const int64_t ne = g->ne;
   Small h;
   int32_t* lists = alloc_t<int32_t>(g, g->count_blocks, (kCloseBuckets + 1) * ne);  // + overflow
   if (!lists) return HG_ERR_OOM;
+  uint8_t* sel = nullptr;
+  if (h_sel) {
+    sel = alloc_t<uint8_t>(g, g->count_blocks, std::max<int64_t>(ne, 1));
+    if (!sel) return HG_ERR_OOM;
+    HG_CUDA(cudaMemcpyAsync(sel, h_sel, (size_t)ne, cudaMemcpyHostToDevice, s));
+  }
   HG_CUDA(cudaMemsetAsync(g->small->bucket_count + 3, 0, sizeof(int32_t) * (1 + kCloseBuckets), s));
   HG_CUDA(cudaMemsetAsync(g->small->wide_max, 0, sizeof(g->small->wide_max), s));
   HG_CUDA(cudaMemsetAsync(g->small->hist, 0, sizeof(g->small->hist), s));
@@ -1018,7 +1027,7 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   t_begin(g, "close_bucket");
   // warp tables keep |e_x| in 16 bits: larger hyperedges send everything to block teams
   launch_bucket_close(d, g->ori, cb, g->small->wide_max,
-                      g->close_mode == 1 || g->max_size >= 65536, g->warp_team_max, s);
+                      g->close_mode == 1 || g->max_size >= 65536, g->warp_team_max, sel, s);
   t_end(g);
   HG_TRY(sync_small(g, &h));
   int32_t n[kCloseBuckets];
@@ -1088,6 +1097,7 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21]) {
   }
   g->cstats.bucket_teams[kWideBucket] += (uint64_t)n_over;   // handed from the warp kernels
   g->counted = true;
+  g->have_cstats = true;
   if (counts) std::memcpy(counts, g->counts, sizeof(g->counts));
   return HG_OK;
 }
@@ -1405,7 +1415,7 @@ hg_status hg_autotune(hg_graph* g, hg_autotune_result* out) {
     cudaStreamSynchronize(g->stream);
     cudaGetLastError();
     g->pending.clear();
-    g->built = g->counted = false;
+    g->built = g->counted = g->have_cstats = false;
   }
   return st;
 }
@@ -1627,7 +1637,7 @@ hg_status hg_batch_autotune(hg_batch* b, int32_t wave, hg_autotune_result* out) 
     cudaStreamSynchronize(g->stream);
     cudaGetLastError();
     g->pending.clear();
-    g->built = g->counted = false;
+    g->built = g->counted = g->have_cstats = false;
     return st;
   }
   for (hg_graph* w : b->waves) {
@@ -1740,7 +1750,7 @@ hg_status hg_batch_free(hg_batch* b) {
 
 hg_status hg_close_stats_get(hg_graph* g, hg_close_stats* out) {
   if (!g || !out) return HG_ERR_INVALID_ARG;
-  if (!g->counted) return HG_ERR_STATE;
+  if (!g->have_cstats) return HG_ERR_STATE;
   *out = g->cstats;
   return HG_OK;
 }
@@ -1774,6 +1784,38 @@ hg_status hg_mask_histogram(hg_graph* g, uint64_t masks[128]) {
   if (!g || !masks) return HG_ERR_INVALID_ARG;
   if (!g->counted) return HG_ERR_STATE;
   std::memcpy(masks, g->masks, sizeof(g->masks));
+  return HG_OK;
+}
+
+hg_status hg_count_owned(hg_graph* g, const int32_t* owners, int32_t num_owners,
+                         uint64_t counts[21], uint64_t masks[128]) {
+  if (!g || !counts || num_owners < 0 || (num_owners > 0 && !owners)) return HG_ERR_INVALID_ARG;
+  if (!g->built) return HG_ERR_STATE;
+  if (g->nm > 0) return HG_ERR_UNSUPPORTED;
+  std::vector<uint8_t> sel((size_t)std::max<int64_t>(g->ne, 1), 0);
+  for (int32_t k = 0; k < num_owners; ++k) {
+    if (owners[k] < 0 || (int64_t)owners[k] >= g->ne) return HG_ERR_INVALID_ARG;
+    sel[(size_t)owners[k]] = 1;
+  }
+  hg_status st = count_impl(g, counts, sel.data());
+  if (st != HG_OK) {
+    cudaStreamSynchronize(g->stream);
+    cudaGetLastError();
+    g->pending.clear();
+  } else if (masks) {
+    std::memcpy(masks, g->masks, sizeof(g->masks));
+  }
+  g->counted = false;   // the handle's bins hold a part of the hyper-triangles only
+  return st;
+}
+
+hg_status hg_out_degrees(hg_graph* g, int32_t* out_degree) {
+  if (!g || !out_degree) return HG_ERR_INVALID_ARG;
+  if (!g->built) return HG_ERR_STATE;
+  if (g->ne == 0) return HG_OK;
+  HG_CUDA(cudaMemcpyAsync(out_degree, g->ori.dplus, sizeof(int32_t) * (size_t)g->ne,
+                          cudaMemcpyDeviceToHost, g->stream));
+  HG_CUDA(cudaStreamSynchronize(g->stream));
   return HG_OK;
 }
 

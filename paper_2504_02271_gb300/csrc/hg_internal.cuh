@@ -223,9 +223,11 @@ struct CloseBuckets {
 // all_block: send every hyperedge to the global-table kernel (bucket 6)
 // warp_max: the largest out-degree a warp team takes (64, 128 or 256); larger out-degrees
 // (and |e_u| > 32) go to block teams
+// sel: NULL, or one byte per hyperedge; then only the hyperedges u with sel[u] != 0
+// get a team (the hyper-triangles they own).
 void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,
                          unsigned long long* wide_max, bool all_block, int warp_max,
-                         cudaStream_t s);
+                         const uint8_t* sel, cudaStream_t s);
 // n: list length (host copy); n_p: the same on the device; counter: zeroed fetch counter;
 // work[0] += probes (entries of out(v) streamed), work[1] += E_y entries scanned for masks;
 // warp kernels append hyperedges their tables cannot hold (every hyperedge when

@@ -1327,7 +1327,8 @@ constexpr int kBucketRowsPerBlock = kBucketThreads * kBucketRowsPerThread;
 
 __global__ void __launch_bounds__(kBucketThreads)
     k_bucket_close(DevGraph g, Oriented o, CloseBuckets b,
-                   unsigned long long* __restrict__ wide_max, bool all_block, int warp_max) {
+                   unsigned long long* __restrict__ wide_max, bool all_block, int warp_max,
+                   const uint8_t* __restrict__ sel) {
   __shared__ int32_t s_cnt[kCloseBuckets], s_base[kCloseBuckets];
   const int lane = threadIdx.x & 31;
   unsigned long long my_d = 0, my_s = 0;
@@ -1340,7 +1341,7 @@ __global__ void __launch_bounds__(kBucketThreads)
     for (int q = 0; q < kBucketRowsPerThread; ++q) {   // rows r0 + q * 256 + thread
       const int64_t u = r0 + (int64_t)q * kBucketThreads + threadIdx.x;
       bk[q] = -1;
-      if (u < g.ne) {
+      if (u < g.ne && (!sel || sel[u])) {
         const int32_t d = o.dplus[u], sz = g.esize[u];
         bk[q] = close_bucket_of(d, sz, all_block, warp_max);
         if (bk[q] >= kWideBucket) {
@@ -1461,13 +1462,13 @@ void launch_block(const DevGraph& g, const Oriented& o, int packed, const int32_
 
 void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,
                          unsigned long long* wide_max, bool all_block, int warp_max,
-                         cudaStream_t s) {
+                         const uint8_t* sel, cudaStream_t s) {
   if (g.ne == 0) return;
   int64_t blocks = (g.ne + kBucketRowsPerBlock - 1) / kBucketRowsPerBlock;
   if (blocks > 4096) blocks = 4096;
   note_launch();
   k_bucket_close<<<(unsigned)blocks, kBucketThreads, 0, s>>>(g, o, b, wide_max, all_block,
-                                                             warp_max);
+                                                             warp_max, sel);
 }
 
 size_t close_wide_scratch_bytes(int64_t cap, int64_t words, int64_t dmax, int nsm) {

@@ -38,7 +38,7 @@ EXPORTED = ("hg_set_allocator", "hg_load_csr", "hg_build_wedges", "hg_count_patt
             "hg_server_drain", "hg_server_cancel", "hg_server_stats_get", "hg_server_destroy",
             "hg_sample_estimate_adv", "hg_enumerate_pattern", "hg_sample_work_get",
             "hg_canonical_masks", "hg_mask_histogram", "hg_batch_mask_histogram",
-            "hg_autotune", "hg_batch_autotune")
+            "hg_autotune", "hg_batch_autotune", "hg_count_owned", "hg_out_degrees")
 
 
 class HgError(RuntimeError):
@@ -164,6 +164,8 @@ def _open():
     lib.hg_pattern_table.argtypes = [vp]
     lib.hg_canonical_masks.argtypes = [vp]
     lib.hg_mask_histogram.argtypes = [vp, vp]
+    lib.hg_count_owned.argtypes = [vp, vp, i32, vp, vp]
+    lib.hg_out_degrees.argtypes = [vp, vp]
     lib.hg_batch_mask_histogram.argtypes = [vp, vp]
     lib.hg_autotune.argtypes = [vp, vp]
     lib.hg_batch_autotune.argtypes = [vp, i32, vp]
@@ -366,6 +368,25 @@ def hg_mask_histogram(g: Graph) -> np.ndarray:
     return out
 
 
+def hg_count_owned(g: Graph, owners) -> tuple[np.ndarray, np.ndarray]:
+    """Step two over the hyper-triangles owned by `owners` (their lowest-ranked member):
+    (counts uint64[21], canonical masks uint64[128])."""
+    own = np.ascontiguousarray(np.asarray(owners, dtype=np.int32))
+    counts = np.zeros(21, dtype=np.uint64)
+    masks = np.zeros(128, dtype=np.uint64)
+    _check("hg_count_owned", _lib.hg_count_owned(ctypes.c_void_p(g.ptr), own.ctypes.data,
+                                                 len(own), counts.ctypes.data,
+                                                 masks.ctypes.data))
+    return counts, masks
+
+
+def hg_out_degrees(g: Graph) -> np.ndarray:
+    """int32[|E|]: each hyperedge's neighbours ranked above it in (|N(e)|, id)."""
+    out = np.zeros(max(g.num_edges, 1), dtype=np.int32)
+    _check("hg_out_degrees", _lib.hg_out_degrees(ctypes.c_void_p(g.ptr), out.ctypes.data))
+    return out[:g.num_edges]
+
+
 def hg_sample_estimate(g: Graph, seed: int, first_sample: int, num_samples: int,
                        sigma: float = 1.0) -> tuple[np.ndarray, np.ndarray]:
     """Hyperwedge-sampling estimate (Algorithm 6): (raw uint64[21], est float64[21])."""
@@ -434,7 +455,8 @@ def hg_clustering_coeff(g: Graph, eps) -> tuple[float, int, int]:
 
 
 def hg_close_stats_get(g: Graph) -> dict:
-    """Work of the last hg_count_patterns: probes, gathers, out_entries, teams, bucket_teams."""
+    """Work of the last hg_count_patterns or hg_count_owned: probes, gathers, out_entries,
+    teams, bucket_teams."""
     st = _CloseStats()
     _check("hg_close_stats_get", _lib.hg_close_stats_get(ctypes.c_void_p(g.ptr), ctypes.byref(st)))
     return {"probes": int(st.probes), "gathers": int(st.gathers),

@@ -525,3 +525,63 @@ def test_degrees_are_line_graph_row_sums(orc):
     e_ptr, e_idx = hgen.prefix(*hgen.generate(hgen.TINY_PLAIN), 400)
     A = line_graph_adjacency(e_ptr, e_idx, 1000)
     assert orc.degrees(e_ptr, e_idx, 1000).tolist() == A.sum(1).tolist()
+
+
+# ---------------------------------------------------------------- hyper-triangles by owner
+
+def owned_brute_py(edges, A):
+    """Per hyperedge u: the canonical-mask histogram of the hyper-triangles whose other two
+    members both rank above u in (|N(e)|, id), and the number of neighbours ranking above
+    u; |N(e)| from the line-graph adjacency A, triangles from all triples."""
+    E = [set(e) for e in edges]
+    deg = A.sum(1).tolist()
+    rank = lambda x: (deg[x], x)  # noqa: E731
+    hist = [[0] * 128 for _ in E]
+    for t in itertools.combinations(range(len(E)), 3):
+        if pairwise_connected(*(E[x] for x in t)):
+            hist[min(t, key=rank)][canonical_py(tuple(E[x] for x in t))] += 1
+    above = [sum(1 for x in range(len(E)) if A[u, x] and rank(x) > rank(u)) for u in range(len(E))]
+    return hist, above
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_owned_histograms_match_python_brute_force(orc, seed):
+    import hgen
+
+    for attempt in range(20):
+        rnd = random.Random(80 + seed + 1000 * attempt)
+        spec = hgen.HypergraphSpec(rnd.randint(6, 30), rnd.randint(10, 60), 7 + seed + 1000 * attempt,
+                                   hgen.SIZE_UNIFORM, 1, rnd.randint(2, 6),
+                                   zipf_s=rnd.uniform(0.3, 1.5), name="t")
+        try:
+            e_ptr, e_idx = hgen.generate(spec)
+            break
+        except RuntimeError:
+            continue
+    else:
+        raise AssertionError("no drawable case among 20 derived seeds")
+    ne = len(e_ptr) - 1
+    edges = [e_idx[e_ptr[i]:e_ptr[i + 1]].tolist() for i in range(ne)]
+    hist, above = owned_brute_py(edges, line_graph_adjacency(e_ptr, e_idx, spec.num_vertices))
+    owners = list(range(ne))[::-1]   # any order; each row answers its own owner
+    masks, ab = orc.count_owned(e_ptr, e_idx, spec.num_vertices, owners)
+    assert masks.tolist() == [hist[u] for u in owners]
+    assert ab.tolist() == [above[u] for u in owners]
+
+
+def test_owners_partition_the_histogram(orc):
+    # every hyper-triangle has exactly one owner, every hyperwedge one lower end
+    import hgen
+
+    e_ptr, e_idx = hgen.prefix(*hgen.generate(hgen.TINY_PLAIN), 500)
+    r = orc.count(e_ptr, e_idx, 1000)
+    masks, above = orc.count_owned(e_ptr, e_idx, 1000, range(500))
+    assert masks.sum(0).tolist() == r.masks.tolist()
+    assert int(above.sum()) == r.W
+    # an owner listed twice answers twice; none listed answers nothing
+    m2, a2 = orc.count_owned(e_ptr, e_idx, 1000, [7, 7])
+    assert m2[0].tolist() == m2[1].tolist() == masks[7].tolist() and a2.tolist() == [above[7]] * 2
+    m0, a0 = orc.count_owned(e_ptr, e_idx, 1000, [])
+    assert m0.shape == (0, 128) and len(a0) == 0
+    with pytest.raises(ValueError):
+        orc.count_owned(e_ptr, e_idx, 1000, [500])
