@@ -122,7 +122,8 @@ typedef struct hg_wedge_stats {
  * HG_ERR_DUPLICATE_HYPEREDGE.  May be called again; it rebuilds.  Synchronises.
  * A tuning field out of its range (close_mode not 0-2, orient_exact not 0-1) is
  * rejected with HG_ERR_INVALID_ARG before anything changes: a built handle stays
- * built.  Any other error leaves the handle unbuilt (counting then answers
+ * built.  HG_ERR_UNSUPPORTED for a hyperedge whose vertices lie in 2^30 or more
+ * hyperedges in all (sum over its vertices v of |E_v| - 1).  Any other error leaves the handle unbuilt (counting then answers
  * HG_ERR_STATE until a build succeeds).
  */
 hg_status hg_build_wedges(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out);

@@ -562,6 +562,10 @@ bool tuning_ok(const hg_tuning* opt) {
 }
 
 hg_status build_impl(hg_graph* g, const hg_tuning* opt, hg_wedge_stats* out) {
+  // the gather and closure kernels keep a hyperedge's incidence prefix sums (the E_y
+  // lists of its vertices, laid end to end) in 32 bits, and the heavy rows' tables use
+  // 32-bit slot indices for twice a row's incidences
+  if (g->max_cand >= (int64_t(1) << 30)) return HG_ERR_UNSUPPORTED;
   if (!opt && g->has_tuned) opt = &g->tuned;
   g->close_mode = opt ? opt->close_mode : 0;
   g->warp_team_max = (opt && opt->warp_team_max) ? opt->warp_team_max : 256;

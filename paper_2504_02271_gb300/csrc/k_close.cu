@@ -407,29 +407,30 @@ __global__ void __launch_bounds__(WARPS * 32, warp_threads_per_sm(D_LOG2) / (WAR
       __syncwarp();
       continue;
     }
-    // 2. Omega_ux masks: flat walk over the E_y lists of the vertices of e_u
+    // 2. Omega_ux masks: flat walk over the E_y lists of the vertices of e_u (fewer
+    // than 2^30 entries in all: the build refuses larger rows, so the prefix sums are
+    // 32-bit; each lane keeps the 64-bit start of its list minus its exclusive prefix)
     {
-      const int64_t len = ye - yb;   // lanes >= szu hold 0
-      int64_t incl = len;
+      const int32_t len = (int32_t)(ye - yb);   // lanes >= szu hold 0
+      int32_t incl = len;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
-        const int64_t o2 = __shfl_up_sync(kFull, incl, d);
+        const int32_t o2 = __shfl_up_sync(kFull, incl, d);
         if (lane >= d) incl += o2;
       }
-      const int64_t total = __shfl_sync(kFull, incl, 31);
+      const int64_t ybase = yb - (incl - len);   // flat position f of this list: v_idx[ybase + f]
+      const int32_t total = __shfl_sync(kFull, incl, 31);
       gathers += (unsigned long long)total;
-      for (int64_t f0 = 0; f0 < total; f0 += 32) {   // warp-uniform: all lanes shuffle
-        const int64_t f = f0 + lane;
+      for (int32_t f0 = 0; f0 < total; f0 += 32) {   // warp-uniform: all lanes shuffle
+        const int32_t f = f0 + lane;
         int lo = 0, hi = 31;   // owner p: first lane whose inclusive prefix exceeds f
 #pragma unroll
         for (int it = 0; it < 5; ++it) {
           const int mid = (lo + hi) >> 1;
-          const int64_t v = __shfl_sync(kFull, incl, mid);
-          if (v > f) hi = mid; else lo = mid + 1;
+          if (__shfl_sync(kFull, incl, mid) > f) hi = mid; else lo = mid + 1;
         }
         const int p = lo;
-        const int64_t start = __shfl_sync(kFull, yb, p) - (__shfl_sync(kFull, incl, p) -
-                                                          __shfl_sync(kFull, len, p));
+        const int64_t start = __shfl_sync(kFull, ybase, p);
         if (f >= total) continue;
         const int32_t x = __ldg(g.v_idx + start + f);
         const int kx = warp_find(t, x, nst);

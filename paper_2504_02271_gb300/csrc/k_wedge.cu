@@ -145,31 +145,34 @@ __global__ void __launch_bounds__(kLightWarps * 32, HG_LIGHT_MIN_BLOCKS)
     const int32_t hi = dn.heavy_idx ? dn.heavy_idx[i] : -1;
     const int64_t b = g.e_ptr[i], e = g.e_ptr[i + 1];
     // 32 vertices of e_i at a time: their E_v ranges in one round trip (lane l holds
-    // vertex p0 + l), then the concatenated lists as one flat range, 32 entries per step
+    // vertex p0 + l), then the concatenated lists as one flat range, 32 entries per step.
+    // A light row gathers at most 2^kLightCapLog2 incidences, so the prefix sums are
+    // 32-bit; each lane keeps the 64-bit start of its list minus its exclusive prefix.
     for (int64_t p0 = b; p0 < e; p0 += 32) {
-      int64_t yb = 0, len = 0;
+      int64_t yb = 0;
+      int32_t len = 0;
       if (p0 + lane < e) {
         const int32_t v = g.e_idx[p0 + lane];
         yb = g.v_ptr[v];
-        len = g.v_ptr[v + 1] - yb;
+        len = (int32_t)(g.v_ptr[v + 1] - yb);
       }
-      int64_t incl = len;
+      int32_t incl = len;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
-        const int64_t o2 = __shfl_up_sync(kFull, incl, d);
+        const int32_t o2 = __shfl_up_sync(kFull, incl, d);
         if (lane >= d) incl += o2;
       }
-      const int64_t total = __shfl_sync(kFull, incl, 31);
-      for (int64_t f0 = 0; f0 < total; f0 += 32) {   // warp-uniform: all lanes shuffle
-        const int64_t f = f0 + lane;
+      const int64_t base = yb - (incl - len);   // flat position f of this list: v_idx[base + f]
+      const int32_t total = __shfl_sync(kFull, incl, 31);
+      for (int32_t f0 = 0; f0 < total; f0 += 32) {   // warp-uniform: all lanes shuffle
+        const int32_t f = f0 + lane;
         int lo = 0, hi2 = 31;   // owner: first lane whose inclusive prefix exceeds f
 #pragma unroll
         for (int it = 0; it < 5; ++it) {
           const int mid = (lo + hi2) >> 1;
           if (__shfl_sync(kFull, incl, mid) > f) hi2 = mid; else lo = mid + 1;
         }
-        const int64_t start = __shfl_sync(kFull, yb, lo) - (__shfl_sync(kFull, incl, lo) -
-                                                           __shfl_sync(kFull, len, lo));
+        const int64_t start = __shfl_sync(kFull, base, lo);
         if (f >= total) continue;
         const int32_t j = g.v_idx[start + f];
         if (j != i && gather_pair(dn, hi, j)) ht_add<PACKED>(T, cl, (uint32_t)j);
@@ -240,7 +243,8 @@ __global__ void __launch_bounds__(kBlockThreads)
   __shared__ int32_t s_row;
   __shared__ int32_t s_cnt, s_up, s_incl;
   __shared__ unsigned long long s_wc;
-  __shared__ int64_t s_ybeg[32], s_yincl[32];
+  __shared__ int64_t s_ybeg[32];
+  __shared__ int32_t s_yincl[32];   // a row gathers fewer than 2^30 incidences (host check)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int32_t nrows = *nrows_p;
   if (threadIdx.x == 0) s_wc = 0;
@@ -267,24 +271,25 @@ __global__ void __launch_bounds__(kBlockThreads)
     // shared memory, then every thread takes flat positions of the concatenated lists
     for (int64_t p0 = b; p0 < e; p0 += 32) {   // block-uniform
       if (w == 0) {
-        int64_t yb = 0, len = 0;
+        int64_t yb = 0;
+        int32_t len = 0;
         if (p0 + lane < e) {
           const int32_t v = g.e_idx[p0 + lane];
           yb = g.v_ptr[v];
-          len = g.v_ptr[v + 1] - yb;
+          len = (int32_t)(g.v_ptr[v + 1] - yb);
         }
-        int64_t incl = len;
+        int32_t incl = len;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-          const int64_t o2 = __shfl_up_sync(kFull, incl, d);
+          const int32_t o2 = __shfl_up_sync(kFull, incl, d);
           if (lane >= d) incl += o2;
         }
         s_ybeg[lane] = yb - (incl - len);   // flat position f of this list maps to s_ybeg + f
         s_yincl[lane] = incl;
       }
       __syncthreads();
-      const int64_t total = s_yincl[31];
-      for (int64_t f = threadIdx.x; f < total; f += kBlockThreads) {
+      const int32_t total = s_yincl[31];
+      for (int32_t f = threadIdx.x; f < total; f += kBlockThreads) {
         int lo = 0, hi2 = 31;   // owner: first vertex whose inclusive prefix exceeds f
 #pragma unroll
         for (int it = 0; it < 5; ++it) {
