@@ -299,10 +299,11 @@ hg_status hg_clustering_coeff(hg_graph* g, const double eps[20], double* cc,
  *   teams        hyperedges u that owned a closing team (out-degree >= 2);
  *   bucket_*     the same per team shape: warp teams for out-degree <= 64, <= 128,
  *                <= 256 (indices 0-2); block teams with shared-memory tables for <= 1024,
- *                <= 2048 and <= 4096 (3-5); block teams with global-memory tables for
- *                hyperedges of more than 32 vertices with out-degree <= 4096 and for
- *                what the other teams hand over (6); thread-block clusters sharing
- *                global-memory tables for out-degree above 4096 (7).
+ *                <= 2048 and <= 6144 (<= 4096 when omega or ids need the 8-byte row
+ *                layout) (3-5); block teams with global-memory tables for hyperedges of
+ *                more than 32 vertices with out-degree <= 4096 and for what the other
+ *                teams hand over (6); thread-block clusters sharing global-memory tables
+ *                for larger out-degrees (7).
  */
 typedef struct hg_close_stats {
   uint64_t probes;

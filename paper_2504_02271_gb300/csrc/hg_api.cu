@@ -1031,7 +1031,8 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21], const uint8_t* h_sel = nu
   t_begin(g, "close_bucket");
   // warp tables keep |e_x| in 16 bits: larger hyperedges send everything to block teams
   launch_bucket_close(d, g->ori, cb, g->small->wide_max,
-                      g->close_mode == 1 || g->max_size >= 65536, g->warp_team_max, sel, s);
+                      g->close_mode == 1 || g->max_size >= 65536, g->warp_team_max,
+                      g->packed ? kBlockMaxPacked : kBlockMaxUnpacked, sel, s);
   t_end(g);
   HG_TRY(sync_small(g, &h));
   int32_t n[kCloseBuckets];
@@ -1041,7 +1042,8 @@ hg_status count_impl(hg_graph* g, uint64_t counts[21], const uint8_t* h_sel = nu
   // hyperedges they hand over
   int64_t team_dmax = 256;
   for (int k = 3; k < kWideBucket; ++k)
-    if (n[k] > 0) team_dmax = int64_t(1024) << (k - 3);
+    if (n[k] > 0)
+      team_dmax = k < 5 ? int64_t(1024) << (k - 3) : (g->packed ? kBlockMaxPacked : kBlockMaxUnpacked);
   const int64_t dmax = std::max<int64_t>((int64_t)h.wide_max[0], team_dmax);
   const int64_t words = std::max<int64_t>(((int64_t)h.wide_max[1] + 31) / 32, 1);
   int64_t cap = 16;

@@ -209,13 +209,15 @@ size_t wedge_heavy_scratch_bytes(int64_t heavy_max_cand, int nsm);
 
 // k_close.cu
 // close team shapes: warp teams (out-degree <= 64, 128, 256), block teams with shared
-// tables (<= 1024, <= 2048, <= 4096), block teams with global scratch (|e_u| > 32 with
-// out-degree <= 4096, and teams handed over), cluster teams with global scratch
-// (out-degree above kWideLargeMin)
+// tables (<= 1024, <= 2048, and <= kBlockMaxPacked or kBlockMaxUnpacked by the row
+// layout), block teams with global scratch (|e_u| > 32 with out-degree <= kWideLargeMin,
+// and teams handed over), cluster teams with global scratch (the rest)
 constexpr int kCloseBuckets = 8;
 constexpr int kWideBucket = 6;
 constexpr int kClusterBucket = 7;
 constexpr int kWideLargeMin = 4096;
+constexpr int kBlockMaxPacked = 6144;     // 4-byte queue entries leave room for 6,144 indices
+constexpr int kBlockMaxUnpacked = 4096;
 struct CloseBuckets {
   int32_t* lists[kCloseBuckets];
   int32_t* count;     // [kCloseBuckets]
@@ -225,9 +227,11 @@ struct CloseBuckets {
 // (and |e_u| > 32) go to block teams
 // sel: NULL, or one byte per hyperedge; then only the hyperedges u with sel[u] != 0
 // get a team (the hyper-triangles they own).
+// block_max: largest out-degree of the shared-table block teams (kBlockMaxPacked or
+// kBlockMaxUnpacked, by the row layout).
 void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,
                          unsigned long long* wide_max, bool all_block, int warp_max,
-                         const uint8_t* sel, cudaStream_t s);
+                         int block_max, const uint8_t* sel, cudaStream_t s);
 // n: list length (host copy); n_p: the same on the device; counter: zeroed fetch counter;
 // work[0] += probes (entries of out(v) streamed), work[1] += E_y entries scanned for masks;
 // warp kernels append hyperedges their tables cannot hold (every hyperedge when

@@ -483,11 +483,17 @@ constexpr uint32_t kCuckooA2 = 0x85EBCA6Bu, kCuckooA2Inv = 0xA5CB9243u;
 static_assert(kCuckooA1 * kCuckooA1Inv == 1u && kCuckooA2 * kCuckooA2Inv == 1u,
               "multiplicative inverses mod 2^32");
 
-template <int D_LOG2, int WARPS, bool PACKED>
+// DMAX below 2^D_LOG2 (the 6,144 shape): indices keep D_LOG2 bits, each table has
+// 2^D_LOG2 slots (at most 3/8 of both tables in use), and a slot's remainder and index
+// fill all 32 bits; the empty word (all ones) still matches no key, because its index
+// field (all ones) is at least DMAX.
+template <int D_LOG2, int WARPS, bool PACKED, int DMAX = (1 << D_LOG2)>
 struct alignas(16) BlockTables {
-  static constexpr int D = 1 << D_LOG2;
-  static constexpr int T_LOG2 = D_LOG2 + 1;
+  static constexpr int D = DMAX;
+  static constexpr int T_LOG2 = DMAX == (1 << D_LOG2) ? D_LOG2 + 1 : D_LOG2;
   static constexpr int T = 1 << T_LOG2;
+  static_assert(DMAX == (1 << D_LOG2) || (DMAX < (1 << D_LOG2) && 4 * DMAX <= 3 * (1 << D_LOG2)),
+                "a smaller DMAX keeps the tables at most 3/8 full");
   uint32_t c1[T];
   uint32_t c2[T];
   int32_t skey[kStash];
@@ -504,19 +510,20 @@ struct alignas(16) BlockTables {
 };
 
 // Index k in out(u) of hyperedge x, or -1 (x = -1 matches nothing: keys are < 2^31).
-template <int D_LOG2, int WARPS, bool PACKED, bool STASH = true>
-__device__ __forceinline__ int block_find(const BlockTables<D_LOG2, WARPS, PACKED>& t, int32_t x,
-                                          int nst) {
-  constexpr int SH = 32 - (D_LOG2 + 1);   // remainder bits
+template <int D_LOG2, int WARPS, bool PACKED, int DMAX, bool STASH = true>
+__device__ __forceinline__ int block_find(const BlockTables<D_LOG2, WARPS, PACKED, DMAX>& t,
+                                          int32_t x, int nst) {
+  constexpr int SH = 32 - BlockTables<D_LOG2, WARPS, PACKED, DMAX>::T_LOG2;   // remainder bits
   constexpr uint32_t RM = (1u << SH) - 1u;
   const uint32_t p1 = (uint32_t)x * kCuckooA1, p2 = (uint32_t)x * kCuckooA2;
   // an item (remainder << D_LOG2) | k xor-ed with the key's remainder so shifted is k
-  // (< D) when the remainders agree, and at least D otherwise (empty slots have the top
-  // bit, which no remainder has); a key sits in at most one table
+  // (< DMAX) when the remainders agree, and at least 2^D_LOG2 otherwise; an empty slot
+  // gives at least DMAX (the top bit, or an index field of all ones); a key sits in at
+  // most one table
   const uint32_t a = t.c1[p1 >> SH] ^ ((p1 & RM) << D_LOG2);
   const uint32_t b = t.c2[p2 >> SH] ^ ((p2 & RM) << D_LOG2);
   const uint32_t m = a < b ? a : b;
-  int k = m < (uint32_t)(1u << D_LOG2) ? (int)m : -1;
+  int k = m < (uint32_t)DMAX ? (int)m : -1;
   if (STASH)
     for (int i = 0; i < nst; ++i) k = t.skey[i] == x ? t.sidx[i] : k;
   return k;
@@ -526,8 +533,8 @@ __device__ __forceinline__ int block_find(const BlockTables<D_LOG2, WARPS, PACKE
 // out(v), v in out(u), walked like the warp teams' (kBlockUnroll loads in flight, a
 // cursor per lane, queued 32-wide classification); the slice start is found by a
 // binary search over the prefix sums kpre of the out-degrees.
-template <int D_LOG2, int WARPS, bool PACKED, bool STASH>
-__device__ __forceinline__ void block_walk(BlockTables<D_LOG2, WARPS, PACKED>& t,
+template <int D_LOG2, int WARPS, bool PACKED, int DMAX, bool STASH>
+__device__ __forceinline__ void block_walk(BlockTables<D_LOG2, WARPS, PACKED, DMAX>& t,
                                            const Oriented& o, int32_t u, int32_t du,
                                            int32_t f_lo, int32_t f_hi, int nst, uint32_t fu,
                                            uint32_t* hist, RunHist& rh, int lane, int w) {
@@ -578,7 +585,7 @@ __device__ __forceinline__ void block_walk(BlockTables<D_LOG2, WARPS, PACKED>& t
 #pragma unroll
     for (int q = 0; q < kBlockUnroll; ++q) {
       const int32_t x = PACKED ? (int32_t)((uint32_t)ent_w[q] >> 8) : ent_w[q];
-      const int kw = block_find<D_LOG2, WARPS, PACKED, STASH>(t, x, nst);
+      const int kw = block_find<D_LOG2, WARPS, PACKED, DMAX, STASH>(t, x, nst);
       const bool hit = kw >= 0;
       const unsigned bal = __ballot_sync(kFull, hit);
       if (hit) {
@@ -609,32 +616,35 @@ __device__ __forceinline__ void block_walk(BlockTables<D_LOG2, WARPS, PACKED>& t
   __syncwarp();
 }
 
-template <int D_LOG2, int WARPS, bool PACKED>
+template <int D_LOG2, int WARPS, bool PACKED, int DMAX>
 __global__ void __launch_bounds__(WARPS * 32, 1)
     k_close_block(DevGraph g, Oriented o, const int32_t* __restrict__ list,
                   const int32_t* __restrict__ n_p, unsigned long long* __restrict__ hist_out,
                   unsigned long long* __restrict__ work, int32_t* __restrict__ counter,
                   int32_t* __restrict__ overflow, int32_t* __restrict__ n_overflow, int handover) {
-  using TT = BlockTables<D_LOG2, WARPS, PACKED>;
+  using TT = BlockTables<D_LOG2, WARPS, PACKED, DMAX>;
+  // shared pattern bins: one set per warp, or 8 sets shared by the warps when the tables
+  // leave no room for more (the 6,144 shape)
+  constexpr int HC = DMAX == (1 << D_LOG2) ? WARPS : 8;
   constexpr int T = TT::T, SH = 32 - TT::T_LOG2;
   constexpr uint32_t RM = (1u << SH) - 1u, KM = (1u << D_LOG2) - 1u;
   constexpr int NT = WARPS * 32;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   TT& t = *reinterpret_cast<TT*>(dyn_smem);
-  __shared__ uint32_t hist[WARPS][kBins];
+  __shared__ uint32_t hist[HC][kBins];
   __shared__ int32_t s_r;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int k = threadIdx.x; k < WARPS * kBins; k += NT) (&hist[0][0])[k] = 0;
+  for (int k = threadIdx.x; k < HC * kBins; k += NT) (&hist[0][0])[k] = 0;
   const int32_t n = *n_p;
   RunHist rh;
   unsigned long long probes = 0, gathers = 0, outs = 0, since_flush = 0;
   int32_t cur = 0;   // member whose bins the shared histograms hold
   auto block_flush = [&]() {
-    rh.flush(hist[w]);
+    rh.flush(hist[w % HC]);
     __syncthreads();
     for (int k = threadIdx.x; k < kBins; k += NT) {
       unsigned long long x = 0;
-      for (int ww = 0; ww < WARPS; ++ww) {
+      for (int ww = 0; ww < HC; ++ww) {
         x += hist[ww][k];
         hist[ww][k] = 0;
       }
@@ -767,9 +777,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1)
     // 3. closure: warp w walks the flat slice [F*w/WARPS, F*(w+1)/WARPS)
     const int32_t f_lo = (int32_t)((int64_t)F * w / WARPS), f_hi = (int32_t)((int64_t)F * (w + 1) / WARPS);
     if (nst == 0)
-      block_walk<D_LOG2, WARPS, PACKED, false>(t, o, u, du, f_lo, f_hi, nst, fu, hist[w], rh, lane, w);
+      block_walk<D_LOG2, WARPS, PACKED, DMAX, false>(t, o, u, du, f_lo, f_hi, nst, fu, hist[w % HC],
+                                                     rh, lane, w);
     else
-      block_walk<D_LOG2, WARPS, PACKED, true>(t, o, u, du, f_lo, f_hi, nst, fu, hist[w], rh, lane, w);
+      block_walk<D_LOG2, WARPS, PACKED, DMAX, true>(t, o, u, du, f_lo, f_hi, nst, fu, hist[w % HC],
+                                                    rh, lane, w);
   }
   block_flush();
   if (threadIdx.x == 0) {
@@ -1308,13 +1320,13 @@ constexpr int kWarpMaskBits = 32;   // warp tables keep Omega_ux in one 32-bit w
 
 // Team shape of u (bucket index, -1 when u closes nothing).
 __device__ __forceinline__ int close_bucket_of(int32_t d, int32_t sz, bool all_block,
-                                               int warp_max) {
+                                               int warp_max, int block_max) {
   if (d < 2) return -1;
   if (all_block) return kWideBucket;
   if (sz <= kWarpMaskBits && d <= warp_max) return d <= 64 ? 0 : (d <= 128 ? 1 : 2);
   if (sz <= kWarpMaskBits && d <= 1024) return 3;
   if (sz <= kWarpMaskBits && d <= 2048) return 4;
-  if (sz <= kWarpMaskBits && d <= 4096) return 5;
+  if (sz <= kWarpMaskBits && d <= block_max) return 5;
   return d > kWideLargeMin ? kClusterBucket : kWideBucket;
 }
 
@@ -1329,7 +1341,7 @@ constexpr int kBucketRowsPerBlock = kBucketThreads * kBucketRowsPerThread;
 __global__ void __launch_bounds__(kBucketThreads)
     k_bucket_close(DevGraph g, Oriented o, CloseBuckets b,
                    unsigned long long* __restrict__ wide_max, bool all_block, int warp_max,
-                   const uint8_t* __restrict__ sel) {
+                   int block_max, const uint8_t* __restrict__ sel) {
   __shared__ int32_t s_cnt[kCloseBuckets], s_base[kCloseBuckets];
   const int lane = threadIdx.x & 31;
   unsigned long long my_d = 0, my_s = 0;
@@ -1344,7 +1356,7 @@ __global__ void __launch_bounds__(kBucketThreads)
       bk[q] = -1;
       if (u < g.ne && (!sel || sel[u])) {
         const int32_t d = o.dplus[u], sz = g.esize[u];
-        bk[q] = close_bucket_of(d, sz, all_block, warp_max);
+        bk[q] = close_bucket_of(d, sz, all_block, warp_max, block_max);
         if (bk[q] >= kWideBucket) {
           my_d = (unsigned long long)d > my_d ? (unsigned long long)d : my_d;
           my_s = (unsigned long long)sz > my_s ? (unsigned long long)sz : my_s;
@@ -1429,13 +1441,19 @@ void launch_warp(const DevGraph& g, const Oriented& o, int packed, const int32_t
                                                overflow, n_overflow, handover, s, nsm);
 }
 
-template <int D_LOG2, int WARPS, bool PACKED>
+template <int D_LOG2, int WARPS, bool PACKED, int DMAX = (1 << D_LOG2)>
 void launch_block_t(const DevGraph& g, const Oriented& o, const int32_t* list, int32_t n,
                     const int32_t* n_p, unsigned long long* hist, unsigned long long* work,
                     int32_t* counter, int32_t* overflow, int32_t* n_overflow, int handover,
                     cudaStream_t s, int nsm) {
-  auto kern = k_close_block<D_LOG2, WARPS, PACKED>;
-  const int smem = (int)sizeof(BlockTables<D_LOG2, WARPS, PACKED>);
+  auto kern = k_close_block<D_LOG2, WARPS, PACKED, DMAX>;
+  const int smem = (int)sizeof(BlockTables<D_LOG2, WARPS, PACKED, DMAX>);
+  // the tables plus the kernel's static bins (one set per warp, or 8) and fetch slot fit
+  // the 232,448 bytes of shared memory a block may use
+  static_assert(sizeof(BlockTables<D_LOG2, WARPS, PACKED, DMAX>) +
+                        sizeof(uint32_t) * kBins * (DMAX == (1 << D_LOG2) ? WARPS : 8) + 16 <=
+                    232448,
+                "block-team shared memory");
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
@@ -1463,13 +1481,13 @@ void launch_block(const DevGraph& g, const Oriented& o, int packed, const int32_
 
 void launch_bucket_close(const DevGraph& g, const Oriented& o, CloseBuckets b,
                          unsigned long long* wide_max, bool all_block, int warp_max,
-                         const uint8_t* sel, cudaStream_t s) {
+                         int block_max, const uint8_t* sel, cudaStream_t s) {
   if (g.ne == 0) return;
   int64_t blocks = (g.ne + kBucketRowsPerBlock - 1) / kBucketRowsPerBlock;
   if (blocks > 4096) blocks = 4096;
   note_launch();
   k_bucket_close<<<(unsigned)blocks, kBucketThreads, 0, s>>>(g, o, b, wide_max, all_block,
-                                                             warp_max, sel);
+                                                             warp_max, block_max, sel);
 }
 
 size_t close_wide_scratch_bytes(int64_t cap, int64_t words, int64_t dmax, int nsm) {
@@ -1504,9 +1522,14 @@ void launch_close(int bucket, const DevGraph& g, const Oriented& o, int packed,
       launch_block<11>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow,
                             handover, s, nsm);
       break;
-    case 5:
-      launch_block<12>(g, o, packed, list, n, n_p, hist, work, counter, overflow, n_overflow,
-                            handover, s, nsm);
+    case 5:   // the packed layout's shape reaches out-degree 6,144 (13-bit indices)
+      if (packed)
+        launch_block_t<13, kBlockWarps, true, kBlockMaxPacked>(g, o, list, n, n_p, hist, work,
+                                                               counter, overflow, n_overflow,
+                                                               handover, s, nsm);
+      else
+        launch_block_t<12, kBlockWarpsUnpacked, false>(g, o, list, n, n_p, hist, work, counter,
+                                                       overflow, n_overflow, handover, s, nsm);
       break;
     case kClusterBucket: {
       // clusters of kWideCluster blocks, as many as can be resident at once

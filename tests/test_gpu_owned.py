@@ -14,18 +14,20 @@ from conftest import load_json
 pytestmark = pytest.mark.gpu
 
 WARP_MASK_BITS = 32     # |e_u| a warp or block team holds in one mask word
-WIDE_LARGE_MIN = 4096   # out-degrees above it go to the cluster-capable teams
+WIDE_LARGE_MIN = 4096   # |e_u| > 32: out-degrees above it go to the cluster-capable teams
+BLOCK_MAX = 6144        # largest shared-table block team (packed rows)
 BUCKET_NAMES = ("warp<=64", "warp<=128", "warp<=256", "block<=1024", "block<=2048",
-                "block<=4096", "wide", "cluster")
+                "block<=6144", "wide", "cluster")
 
 
 def bucket_of(d, sz, warp_max=256):
-    """The team shape of an owner with out-degree d and |e_u| = sz under the default tuning."""
+    """The team shape of an owner with out-degree d and |e_u| = sz under the default tuning
+    (packed rows)."""
     if d < 2:
         return -1
     if sz <= WARP_MASK_BITS and d <= warp_max:
         return 0 if d <= 64 else (1 if d <= 128 else 2)
-    for k, lim in ((3, 1024), (4, 2048), (5, 4096)):
+    for k, lim in ((3, 1024), (4, 2048), (5, BLOCK_MAX)):
         if sz <= WARP_MASK_BITS and d <= lim:
             return k
     return 7 if d > WIDE_LARGE_MIN else 6
@@ -112,9 +114,9 @@ def test_tag_heavy_full_size_sampled_owners(hglib):
         bk[(od > 128) & (size <= WARP_MASK_BITS) & (od <= 256)] = 2
         bk[(od > 256) & (size <= WARP_MASK_BITS) & (od <= 1024)] = 3
         bk[(od > 1024) & (size <= WARP_MASK_BITS) & (od <= 2048)] = 4
-        bk[(od > 2048) & (size <= WARP_MASK_BITS) & (od <= 4096)] = 5
+        bk[(od > 2048) & (size <= WARP_MASK_BITS) & (od <= BLOCK_MAX)] = 5
         bk[(od >= 2) & (size > WARP_MASK_BITS) & (od <= WIDE_LARGE_MIN)] = 6
-        bk[od > WIDE_LARGE_MIN] = 7
+        bk[(od > WIDE_LARGE_MIN) & ((size > WARP_MASK_BITS) | (od > BLOCK_MAX))] = 7
         rng = np.random.default_rng(11)
         owners, want_bucket = [], []
         for k in range(8):
@@ -142,3 +144,45 @@ def test_tag_heavy_full_size_sampled_owners(hglib):
     for k, u in enumerate(owners):
         assert got[k].tolist() == want[k].tolist(), (u, BUCKET_NAMES[want_bucket[k]])
     assert all(int(w.sum()) > 0 for w in want)   # every sampled owner closes triangles
+
+
+def test_hub_large_teams_sampled_owners_repeated(hglib):
+    """A hub vertex in 9,000 hyperedges: every pair of them intersects, so the out-degrees
+    run from 0 to 8,999 and both the largest shared-table block teams (out-degree 4,097 to
+    6,144) and the cluster-capable teams beyond run.  Sampled owners of each, three times
+    over, against the oracle's per-owner histograms (a schedule-dependent miscount would
+    show as a run that differs)."""
+    import hgen
+    import oracle
+
+    nv, e_ptr, e_idx = hgen.hub(9000, 300, 4)
+    ne = len(e_ptr) - 1
+    size = np.diff(e_ptr)
+    g, _ = loaded(hglib, nv, e_ptr, e_idx)
+    try:
+        hglib.hg_build_wedges(g)
+        od = hglib.hg_out_degrees(g)
+        rng = np.random.default_rng(21)
+        owners, shape = [], []
+        for k, lo, hi in ((5, 4097, BLOCK_MAX), (7, BLOCK_MAX + 1, 1 << 30)):
+            pool = np.flatnonzero((od >= lo) & (od <= hi))
+            assert len(pool) >= 3, BUCKET_NAMES[k]
+            for u in rng.choice(pool, 3, replace=False).tolist():
+                assert bucket_of(int(od[u]), int(size[u])) == k
+                owners.append(u)
+                shape.append(k)
+        runs = []
+        for _ in range(3):
+            got = []
+            for u, k in zip(owners, shape):
+                c, m = hglib.hg_count_owned(g, [u])
+                teams = hglib.hg_close_stats_get(g)["bucket_teams"]
+                assert [i for i, t in enumerate(teams) if t] in ([k], [k, 6]), (u, teams)
+                got.append(m.tolist())
+            runs.append(got)
+    finally:
+        hglib.hg_free(g)
+    want, above = oracle.count_owned(e_ptr, e_idx, nv, owners)
+    assert od[owners].tolist() == above.tolist()
+    for got in runs:
+        assert got == want.tolist()
