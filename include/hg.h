@@ -357,9 +357,8 @@ hg_status hg_wait_flag(const int32_t* flag, int32_t limit_us, void* cuda_stream)
  * degrees are then incomplete).  Equal hyperedges give HG_ERR_DUPLICATE_HYPEREDGE.
  * The array is placed on a device when the library's device code is loaded there
  * (under lazy module loading: at the first call on that device).  The first call on
- * a device also looks up the array's device address (with that device current);
- * make that first call before any stream capture.  Calls share
- * the array and its previous contents: the call clears what must start at zero,
+ * a device also looks up the array's device address (with that device current).  Calls
+ * share the array and its previous contents: the call clears what must start at zero,
  * and two calls whose work overlaps on the same GPU (for example on two streams)
  * race on the array and corrupt each other.  No cudaMalloc, cudaFree or
  * allocating library call is made.
