@@ -186,3 +186,27 @@ def test_hub_large_teams_sampled_owners_repeated(hglib):
     assert od[owners].tolist() == above.tolist()
     for got in runs:
         assert got == want.tolist()
+
+
+@pytest.mark.parametrize("close_mode", [1, 2])
+def test_hub_large_teams_other_team_modes(hglib, close_mode):
+    """The same owners under the other team modes: every team on the global-table blocks
+    (1), or the shared-table teams building their tables and then handing every owner over
+    to them (2); each owner's histogram equal to the oracle's."""
+    import hgen
+    import oracle
+
+    nv, e_ptr, e_idx = hgen.hub(9000, 300, 4)
+    g, _ = loaded(hglib, nv, e_ptr, e_idx)
+    try:
+        hglib.hg_build_wedges(g, close_mode=close_mode)
+        od = hglib.hg_out_degrees(g)
+        rng = np.random.default_rng(22)
+        owners = []
+        for lo, hi in ((4097, BLOCK_MAX), (BLOCK_MAX + 1, 1 << 30)):
+            owners += rng.choice(np.flatnonzero((od >= lo) & (od <= hi)), 2, replace=False).tolist()
+        got = [hglib.hg_count_owned(g, [u])[1].tolist() for u in owners]
+    finally:
+        hglib.hg_free(g)
+    want, _ = oracle.count_owned(e_ptr, e_idx, nv, owners)
+    assert got == want.tolist()
