@@ -125,8 +125,11 @@ struct alignas(16) WarpTables {
   Item c1[T];
   Item c2[T];
   Item stash[kStash];
-  Off kbeg[D];
-  int32_t kcnt[D];
+  // entry f of the flat range of all out(x), x in out(u), lies at packed/nbr index
+  // adj[k] + f for the out-neighbour k whose list holds f (the list's start in the rows
+  // minus kpre[k]; modulo 2^32 when Off is 32-bit, which every true index fits)
+  Off adj[D];
+  int32_t kpre[D + 1];                       // exclusive prefix of the out-degrees of out(u)
   uint32_t kmask[D];                         // Omega_ux of the k-th out-neighbour x
   Sz ksz[D];                                 // |e_x|, then |e_x| - omega_ux once masks are built
   uint32_t queue[kWarpQueue];                // hits: (k_v << 24) | (k_w << 8) | omega_vw
@@ -243,49 +246,56 @@ __device__ __forceinline__ void classify_queued(const TT& t, int at, uint32_t fu
   rh.add(region_bits(fu, t.kmask[kv], t.kmask[kw], t.ksz[kv], t.ksz[kw], om), hist);
 }
 
-// Step 3 of a warp team: the flat range of all out(v), v in out(u) (F entries), each
-// lane walking entries lane, lane + 32, ... with its own cursor (row ck of out(u),
-// entry cj of out(v_ck)); kWarpUnroll loads in flight, then their probes; hits are
-// queued and classified 32 at a time.  STASH = false when the team's stash is empty
-// (the usual case): the probes then skip the stash scan altogether.
+// Step 3 of a warp team: the flat range of all out(v), v in out(u) (F entries), 32
+// consecutive entries per window, lane l taking entry f0 + l.  The window's lists are
+// found by a warp-uniform cursor over the prefix sums kpre: the lanes start in the list
+// that holds f0, and every list that starts inside the window moves the lanes at or past
+// its start over to it (predicated, no divergent branch).  kWarpUnroll windows are
+// loaded before their probes; hits are queued and classified 32 at a time.  STASH =
+// false when the team's stash is empty (the usual case): the probes then skip the stash
+// scan altogether.
 template <class TT, bool STASH>
 __device__ __forceinline__ void warp_walk(TT& t, const Oriented& o, int32_t u, int32_t du,
                                           int32_t F, int nst, uint32_t fu, uint32_t* hist,
                                           RunHist& rh, int lane) {
   constexpr bool PACKED = TT::kPacked;
+  using Off = typename TT::Off;
   int qn = 0;   // queued hits (the same on every lane)
-  int ck = 0, cj = lane;
-  int ccnt = t.kcnt[0];   // du >= 2; past the last row ccnt stays INT32_MAX
-  while (cj >= ccnt) {
-    cj -= ccnt;
-    ++ck;
-    ccnt = ck < du ? t.kcnt[ck] : INT32_MAX;
-  }
-  RowPtr<PACKED> rp;
-  rp.at(o, ck < du ? t.kbeg[ck] : 0);
-  for (int base = 0; base < F; base += 32 * kWarpUnroll) {
+  // uniform cursor: list wk starts at or before the next window; wnext = kpre[wk + 1]
+  int wk = 0;
+  int32_t wnext = t.kpre[1];
+  Off wadj = t.adj[0];
+  for (int32_t base = 0; base < F; base += 32 * kWarpUnroll) {
     // packed: the raw entry (w << 8) | omega_vw in one register; no entry: u << 8
     // (u is never in out(u)).  Unpacked: w and omega_vw apart.
     int32_t ent_w[kWarpUnroll], ent_om[PACKED ? 1 : kWarpUnroll], ent_k[kWarpUnroll];
 #pragma unroll
     for (int q = 0; q < kWarpUnroll; ++q) {
-      ent_k[q] = ck;
+      const int32_t f0 = base + 32 * q, f = f0 + lane;
+      const int32_t wend = f0 + 32 < F ? f0 + 32 : F;
+      Off my_adj = wadj;
+      int my_k = wk;
+      while (wnext < wend) {   // uniform: list wk + 1 starts inside this window
+        ++wk;                  // (wk + 1 < du: wnext < F = kpre[du])
+        wadj = t.adj[wk];
+        if (f >= wnext) {
+          my_adj = wadj;
+          my_k = wk;
+        }
+        wnext = t.kpre[wk + 1];
+      }
+      ent_k[q] = my_k;
+      const Off at = my_adj + (Off)f;
       if (PACKED) {
         ent_w[q] = (int32_t)((uint32_t)u << 8);
-        if (ck < du) ent_w[q] = (int32_t)rp.raw(cj);
+        if (f < F) ent_w[q] = (int32_t)__ldg(o.packed + at);
       } else {
         ent_w[q] = u;
         ent_om[q] = 0;
-        if (ck < du) rp.load(cj, ent_w[q], ent_om[q]);
-      }
-      cj += 32;
-      if (cj >= ccnt) {   // next row(s): the row pointer is set once, at the row reached
-        do {
-          cj -= ccnt;
-          ++ck;
-          ccnt = ck < du ? t.kcnt[ck] : INT32_MAX;
-        } while (cj >= ccnt);
-        if (ck < du) rp.at(o, t.kbeg[ck]);
+        if (f < F) {
+          ent_w[q] = __ldg(o.nbr + at);
+          ent_om[q] = __ldg(o.omega + at);
+        }
       }
     }
     // probe; hits go to the warp's queue as (index of v, index of w, omega_vw)
@@ -374,7 +384,6 @@ __global__ void __launch_bounds__(WARPS * 32, warp_threads_per_sm(D_LOG2) / (WAR
     }
     __syncwarp();
     // 1. out(u) into the cuckoo set
-    int32_t my_cnt = 0;
     for (int k = lane; k < du; k += 32) {
       int32_t x, om;
       get_entry<PACKED>(o, bu + k, x, om);
@@ -396,9 +405,8 @@ __global__ void __launch_bounds__(WARPS * 32, warp_threads_per_sm(D_LOG2) / (WAR
       }
       t.kmask[k] = 0;
       t.ksz[k] = (typename TT::Sz)xs;
-      t.kbeg[k] = (typename TT::Off)xb;
-      t.kcnt[k] = xc;
-      my_cnt += xc;
+      t.adj[k] = (typename TT::Off)xb;   // the list start until the prefix sums exist
+      t.kpre[k + 1] = xc;                 // the out-degree until the prefix sums exist
     }
     __syncwarp();
     const int nst = *((volatile int32_t*)&t.nstash);
@@ -437,9 +445,25 @@ __global__ void __launch_bounds__(WARPS * 32, warp_threads_per_sm(D_LOG2) / (WAR
         if (kx >= 0) atomicOr(&t.kmask[kx], 1u << p);   // lanes may be at different p
       }
     }
-    int32_t F = my_cnt;
+    // out-degrees -> their exclusive prefix kpre, list starts -> adj = start - kpre (each
+    // lane reads and rewrites only its own k)
+    int32_t F = 0;
+    for (int k0 = 0; k0 < du; k0 += 32) {   // warp-uniform
+      const int k = k0 + lane;
+      const int32_t c = k < du ? t.kpre[k + 1] : 0;
+      int32_t incl = c;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) F += __shfl_xor_sync(kFull, F, d);
+      for (int d = 1; d < 32; d <<= 1) {
+        const int32_t o2 = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += o2;
+      }
+      if (k < du) {
+        t.kpre[k + 1] = F + incl;
+        t.adj[k] -= (typename TT::Off)(F + incl - c);
+      }
+      F += __shfl_sync(kFull, incl, 31);
+    }
+    if (lane == 0) t.kpre[0] = 0;
     probes += (unsigned long long)F;
     since_flush += (unsigned long long)F;
     outs += (unsigned long long)du;
