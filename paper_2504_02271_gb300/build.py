@@ -7,8 +7,9 @@ clustering coefficient's double arithmetic is not fused into FMAs.
 
 The environment variable ``HG_DEFINES`` (comma-separated ``NAME=VALUE`` items) adds
 preprocessor definitions, for the compile-time kernel shapes the sources leave open
-(``HG_CLOSE_WARP_UNROLL``, ``HG_WIDE_THREADS``, ``HG_WIDE_CLUSTER``); a change of them
-rebuilds everything.
+(``HG_CLOSE_WARP_UNROLL``, ``HG_WARP128_THREADS_PER_SM``, ``HG_BLOCK_WARPS``,
+``HG_WIDE_THREADS``, ``HG_WIDE_CLUSTER``, ``HG_LIGHT_CAP_LOG2``, ``HG_LIGHT_MIN_BLOCKS``);
+a change of them rebuilds everything.
 """
 from __future__ import annotations
 

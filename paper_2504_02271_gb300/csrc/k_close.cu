@@ -87,11 +87,15 @@ __device__ __forceinline__ uint32_t full_mask(int sz) { return sz >= 32 ? ~0u : 
 // 32 at a time, so the classification runs with every lane active.
 
 // Entries of out(v) loaded per lane before their probes (loads in flight per warp):
-// kWarpUnroll in the warp teams, kBlockUnroll in the block teams.
-#ifndef HG_CLOSE_WARP_UNROLL
-#define HG_CLOSE_WARP_UNROLL 8
+// warp_unroll(D_LOG2) in the warp teams, kBlockUnroll in the block teams.  On the
+// co-authorship workload the out-degree-128 teams were fastest with 6 (6.01 ms; 8: 6.13,
+// 10: 6.09), the out-degree-64 and -256 ones with 10 (0.875 and 1.184 ms; 8: 0.885 and
+// 1.198).  HG_CLOSE_WARP_UNROLL sets one value for all three.
+#ifdef HG_CLOSE_WARP_UNROLL
+__host__ __device__ constexpr int warp_unroll(int) { return HG_CLOSE_WARP_UNROLL; }
+#else
+__host__ __device__ constexpr int warp_unroll(int d_log2) { return d_log2 == 7 ? 6 : 10; }
 #endif
-constexpr int kWarpUnroll = HG_CLOSE_WARP_UNROLL;
 // warps of a block team (one block per SM: shared memory holds one team's tables).  On
 // the tag-shaped prefix of 500,000 hyperedges 16, 24 and 32 warps took 7.22, 5.73 and
 // 5.16 s per step (the teams were latency-bound at 16 warps per SM).  The unpacked
@@ -104,7 +108,6 @@ constexpr int kBlockWarps = HG_BLOCK_WARPS;
 constexpr int kBlockWarpsUnpacked = HG_BLOCK_WARPS < 24 ? HG_BLOCK_WARPS : 24;
 constexpr int kBlockUnroll = 8;
 constexpr int kQueue = 32 * kBlockUnroll + 32;
-constexpr int kWarpQueue = 32 * kWarpUnroll + 32;
 constexpr int kCuckooTries = 16;
 constexpr int kStash = 8;
 
@@ -118,6 +121,8 @@ struct alignas(16) WarpTables {
   static constexpr int T = 1 << T_LOG2;
   static constexpr bool kPacked = PACKED;
   static_assert(D <= 256, "neighbour indices are packed in 8 bits");
+  static constexpr int kUnroll = warp_unroll(D_LOG2);   // loads in flight per lane
+  static constexpr int kQueue = 32 * kUnroll + 32;       // a round of hits plus a partial one
   // (x << 8) | k; all ones = empty.  Packed rows have x < 2^24.
   using Item = typename std::conditional<PACKED, uint32_t, unsigned long long>::type;
   using Off = typename std::conditional<OFF32, uint32_t, int64_t>::type;
@@ -132,8 +137,8 @@ struct alignas(16) WarpTables {
   int32_t kpre[D + 1];                       // exclusive prefix of the out-degrees of out(u)
   uint32_t kmask[D];                         // Omega_ux of the k-th out-neighbour x
   Sz ksz[D];                                 // |e_x|, then |e_x| - omega_ux once masks are built
-  uint32_t queue[kWarpQueue];                // hits: (k_v << 24) | (k_w << 8) | omega_vw
-  int32_t qom[PACKED ? 1 : kWarpQueue];      // omega_vw when it may not fit 8 bits
+  uint32_t queue[kQueue];                    // hits: (k_v << 24) | (k_w << 8) | omega_vw
+  int32_t qom[PACKED ? 1 : kQueue];          // omega_vw when it may not fit 8 bits
   int32_t nstash;
 };
 
@@ -250,7 +255,7 @@ __device__ __forceinline__ void classify_queued(const TT& t, int at, uint32_t fu
 // consecutive entries per window, lane l taking entry f0 + l.  The window's lists are
 // found by a warp-uniform cursor over the prefix sums kpre: the lanes start in the list
 // that holds f0, and every list that starts inside the window moves the lanes at or past
-// its start over to it (predicated, no divergent branch).  kWarpUnroll windows are
+// its start over to it (predicated, no divergent branch).  TT::kUnroll windows are
 // loaded before their probes; hits are queued and classified 32 at a time.  STASH =
 // false when the team's stash is empty (the usual case): the probes then skip the stash
 // scan altogether.
@@ -259,6 +264,7 @@ __device__ __forceinline__ void warp_walk(TT& t, const Oriented& o, int32_t u, i
                                           int32_t F, int nst, uint32_t fu, uint32_t* hist,
                                           RunHist& rh, int lane) {
   constexpr bool PACKED = TT::kPacked;
+  constexpr int kWarpUnroll = TT::kUnroll;
   using Off = typename TT::Off;
   int qn = 0;   // queued hits (the same on every lane)
   // uniform cursor: list wk starts at or before the next window; wnext = kpre[wk + 1]
@@ -329,7 +335,12 @@ __device__ __forceinline__ void warp_walk(TT& t, const Oriented& o, int32_t u, i
 // the out-degree-128 teams (six 6-warp blocks at 56 registers: 7.58 -> 7.33 ms on the
 // co-authorship workload), 1,024 for the others (at 1,280 the out-degree-256 teams
 // spill and slow down, 1.46 -> 1.55 ms).
-__host__ __device__ constexpr int warp_threads_per_sm(int d_log2) { return d_log2 == 7 ? 1280 : 1024; }
+#ifndef HG_WARP128_THREADS_PER_SM
+#define HG_WARP128_THREADS_PER_SM 1280
+#endif
+__host__ __device__ constexpr int warp_threads_per_sm(int d_log2) {
+  return d_log2 == 7 ? HG_WARP128_THREADS_PER_SM : 1024;
+}
 
 template <int D_LOG2, int WARPS, bool PACKED, bool OFF32>
 __global__ void __launch_bounds__(WARPS * 32, warp_threads_per_sm(D_LOG2) / (WARPS * 32))
