@@ -76,15 +76,16 @@ __device__ __forceinline__ uint32_t full_mask(int sz) { return sz >= 32 ? ~0u : 
 // memory per warp holds out(u) as a two-table cuckoo set: key x sits at slot
 // h1(x) of table 1 or at slot h2(x) of table 2 (2D slots each, so at most a
 // quarter of the slots are used), each slot packing x with its index k in out(u).
-// A lookup is two shared loads and two compares, the same on every lane: no
+// A lookup is two shared loads, two xors and a min, the same on every lane: no
 // probing loop, no divergence.  Keys that insertion could not place within
 // kCuckooTries evictions go to a small stash that every lookup of the team also
 // scans; a team whose stash overflows is handed to the global-table teams.
-// Per-neighbour arrays hold the row start, out-degree, Omega_ux mask and |e_x|.
-// The closure walks the concatenation of the out(v) lists as one flat range:
-// lane l takes flat entries base + l + 32 q, so each load instruction reads 32
-// consecutive entries and every slot is full.  Hits are queued and classified
-// 32 at a time, so the classification runs with every lane active.
+// Per-neighbour arrays hold the list base (row start minus the prefix of the list
+// lengths), the prefix sums themselves, the Omega_ux mask and |e_x|.  The closure
+// walks the concatenation of the out(v) lists as one flat range: lane l takes flat
+// entries base + l + 32 q, so each load instruction reads 32 consecutive entries and
+// every slot is full.  Hits are queued and classified 32 at a time, so the
+// classification runs with every lane active.
 
 // Entries of out(v) loaded per lane before their probes (loads in flight per warp):
 // warp_unroll(D_LOG2) in the warp teams, kBlockUnroll in the block teams.  On the
