@@ -112,3 +112,18 @@ def test_server_and_batch_structs_match_the_header(lib):
     got = [ctypes.sizeof(t) for t in (hg._Result, hg._Query, hg._ServerOptions, hg._ServerStats,
                                       hg._CloseStats, hg._Tuning, hg._AutotuneResult)]
     assert got == want
+
+
+def test_owner_entry_points_reject_bad_arguments(lib):
+    # argument checks come before any device work, so they run without a GPU
+    import numpy as np
+
+    so = ctypes.CDLL(lib.hg.LIB_PATH)
+    counts = np.zeros(21, dtype=np.uint64)
+    owners = np.zeros(4, dtype=np.int32)
+    vp = ctypes.c_void_p
+    so.hg_count_owned.argtypes = [vp, vp, ctypes.c_int32, vp, vp]
+    so.hg_out_degrees.argtypes = [vp, vp]
+    invalid = {name: code for code, name in lib.hg.STATUS.items()}["HG_ERR_INVALID_ARG"]
+    assert so.hg_count_owned(None, owners.ctypes.data, 4, counts.ctypes.data, None) == invalid
+    assert so.hg_out_degrees(None, owners.ctypes.data) == invalid
