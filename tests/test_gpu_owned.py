@@ -210,3 +210,42 @@ def test_hub_large_teams_other_team_modes(hglib, close_mode):
         hglib.hg_free(g)
     want, _ = oracle.count_owned(e_ptr, e_idx, nv, owners)
     assert got == want.tolist()
+
+
+def test_unpacked_layout_large_teams_sampled_owners(hglib):
+    """A hyperedge of 300 vertices forces the unpacked row layout (8-byte entries), whose
+    shared-table block teams stop at out-degree 4,096 (24 warps); here it is an isolated
+    hyperedge beside a 6,000-spoke hub, so the hub's teams keep their out-degrees.  Sampled
+    owners of the unpacked block shapes and of the cluster-capable teams beyond 4,096,
+    against the oracle's per-owner histograms."""
+    import hgen
+    import oracle
+
+    nv0, p0, i0 = hgen.hub(6000, 200, 5)
+    e_ptr = np.concatenate([p0, [p0[-1] + 300]]).astype(np.int64)
+    e_idx = np.concatenate([i0, np.arange(nv0, nv0 + 300)]).astype(np.int32)
+    nv = nv0 + 300
+    size = np.diff(e_ptr)
+    g, _ = loaded(hglib, nv, e_ptr, e_idx)
+    try:
+        hglib.hg_build_wedges(g)
+        od = hglib.hg_out_degrees(g)
+        rng = np.random.default_rng(23)
+        owners, shape = [], []
+        for k, lo, hi in ((3, 257, 1024), (4, 1025, 2048), (5, 2049, 4096), (7, 4097, 1 << 30)):
+            pool = np.flatnonzero((od >= lo) & (od <= hi) & (size <= WARP_MASK_BITS))
+            assert len(pool) >= 2, BUCKET_NAMES[k]
+            for u in rng.choice(pool, 2, replace=False).tolist():
+                owners.append(u)
+                shape.append(k)
+        got = []
+        for u, k in zip(owners, shape):
+            c, m = hglib.hg_count_owned(g, [u])
+            teams = hglib.hg_close_stats_get(g)["bucket_teams"]
+            assert [i for i, t in enumerate(teams) if t] in ([k], [k, 6]), (u, k, teams)
+            got.append(m.tolist())
+    finally:
+        hglib.hg_free(g)
+    want, above = oracle.count_owned(e_ptr, e_idx, nv, owners)
+    assert od[owners].tolist() == above.tolist()
+    assert got == want.tolist()
